@@ -15,7 +15,8 @@ updates; the steps below follow that order.
          B = L L^T; on failure or cond(B) > 1e14 drop P and retry; if that
          fails too, Cholesky-QR W and retry.
          eig(L^-1 A L^-T) -> lowest m pairs (Theta, Z); Y = L^-T Z.
-         X = S Y, HX = (HS) Y, P = [W P] Y_WP, HP = [HW HP] Y_WP.
+         X = S Y, HX = (HS) Y, P = [W P] Y_WP, HP = [HW HP] Y_WP, then the
+         columns of P (and HP with them) scaled to unit norm.
 Blocks are (k, N_g) arrays whose rows are the vectors.  The residual is the
 absolute Euclidean norm |H x - theta x| / |x| in Ha, max over the kept J, no
 locking.
@@ -123,5 +124,11 @@ def lobpcg(el, x0: np.ndarray, tol: float | None = None, maxit: int = 500,
         y_wp = y[m:]
         x, hx = y.T @ s, y.T @ hs
         p, hp = y_wp.T @ s_wp, y_wp.T @ hs_wp
+        # unit columns for P: a rescaling of the basis, which leaves the
+        # Rayleigh-Ritz result unchanged but keeps cond(S^T S) a measure of
+        # linear dependence rather than of the shrinking step length
+        pn = np.linalg.norm(p, axis=1)
+        pn[pn == 0.0] = 1.0
+        p, hp = p / pn[:, None], hp / pn[:, None]
     return {"X": x, "HX": hx, "theta": theta, "res": res, "iterations": it,
             "converged": converged, "history": hist}
