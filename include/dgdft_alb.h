@@ -1,0 +1,163 @@
+/*
+ * dgdft_alb.h -- C-ABI of the GB300 adaptive-local-basis (ALB) generator.
+ *
+ * Operation (Hu, Lin, Yang, "DGDFT: A Massively Parallel Method for Large
+ * Scale Density Functional Theory Calculations", Sec. II.A and Sec. II.B):
+ * for every element E_K of a domain decomposition, solve the local Kohn-Sham
+ * eigenproblem of Eq. localproblem on the extended element Q_K,
+ *
+ *     (-1/2 Lap + V_eff^{Q_K} + V_nl^{Q_K}) phi~_{K,j} = lambda_{K,j} phi~_{K,j},
+ *
+ * discretised by planewaves on a uniform periodic grid (grid rule Eq. Ngecut),
+ * by LOBPCG (Sec. II.B, operations 1-5) for the lowest n_compute (m)
+ * eigenpairs; restrict the lowest n_keep (J) eigenvectors to E_K,
+ * orthonormalise them (so that the ALB overlap matrix is the identity,
+ * Eq. orthonormal) and return them on E_K's grid points (zero elsewhere).
+ *
+ * Conventions shared by every entry point:
+ *   - A grid function on Q_K is a real array of N_g = nx*ny*nz values, flat
+ *     index i + nx*(j + ny*k) (x fastest), point (i*Lx/nx, j*Ly/ny, k*Lz/nz)
+ *     relative to Q_K's corner.  Q_K is treated as a periodic box.
+ *   - A block of k grid functions is column-major N_g x k (each vector
+ *     contiguous).  All host-visible floating-point data is double.
+ *   - The local problem uses the Euclidean inner product of grid vectors; the
+ *     returned ALBs are scaled to the L2 normalisation sum phi_i phi_j dV =
+ *     delta_ij with dV = Lx*Ly*Lz / N_g.
+ *   - Ownership: the caller owns every buffer it passes; set_* calls copy
+ *     the data in before returning, get_* calls copy out.  Pointers flagged
+ *     on_device = 1 are CUDA device pointers valid on the context's device;
+ *     they need to stay valid only until the call returns.
+ *   - Errors: every call returns a dgdft_status; no exception, abort or
+ *     device trap crosses the ABI.  dgdft_alb_last_error() describes the
+ *     most recent failure on a context.  A context is not thread-safe.
+ *   - The library needs a CUDA device of compute capability 10.3 (sm_103a).
+ *     There is no CPU fallback: without a usable device create() fails with
+ *     DGDFT_ECUDA.
+ */
+#ifndef DGDFT_ALB_H
+#define DGDFT_ALB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgdft_alb_ctx dgdft_alb_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  DGDFT_OK = 0,
+  DGDFT_EINVAL = 1,   /* bad argument, size or non-finite input             */
+  DGDFT_ENOMEM = 2,   /* device or host allocation failed                   */
+  DGDFT_ECUDA = 3,    /* CUDA runtime error (message in last_error)         */
+  DGDFT_ENOTCONV = 4, /* some element did not reach tol within maxit        */
+  DGDFT_ETIMEOUT = 5, /* a bounded device-side wait ran out                 */
+  DGDFT_ESTATE = 6    /* call out of order (e.g. get_basis before solve)    */
+} dgdft_status;
+
+/* Arithmetic of the bulk LOBPCG operations (H apply, preconditioner, Gram
+ * products, block updates).  The Cholesky factorisation, the Rayleigh-Ritz
+ * eigensolve and the final orthonormalisation are FP64 in every mode.      */
+enum {
+  DGDFT_PREC_FP64 = 0,  /* plain: FP64 everywhere                             */
+  DGDFT_PREC_MIXED = 1  /* chosen form: FP32 storage/FFTs, tensor-core split-BF16
+                           Gram and update products with FP32 accumulation,
+                           then FP64 refinement to the requested tolerance     */
+};
+
+enum {
+  DGDFT_PRECOND_TETER = 0,   /* Teter-Payne-Allan kinetic preconditioner      */
+  DGDFT_PRECOND_LEARNED = 1  /* learned 3-D conv net, Teter as fallback        */
+};
+
+/* One extended element Q_K and its element E_K. */
+typedef struct {
+  int nx, ny, nz;        /* grid of Q_K (even sizes with factors 2, 3, 5)     */
+  double Lx, Ly, Lz;     /* side lengths of Q_K in bohr                       */
+  int e_lo[3], e_hi[3];  /* E_K as the half-open grid-index box [lo, hi)      */
+  int n_compute;         /* m: eigenpairs computed by LOBPCG (>= n_keep)      */
+  int n_keep;            /* J: ALBs kept                                      */
+} dgdft_element_desc;
+
+typedef struct {
+  int precision;          /* DGDFT_PREC_*                                     */
+  int precond;            /* DGDFT_PRECOND_*                                  */
+  double tol;             /* residual tolerance (Ha): max_{j<J} |Hx-theta x|/|x| */
+  int maxit;              /* LOBPCG iteration limit per element (> 0)         */
+  int check_every;        /* iterations between host convergence polls (>= 1) */
+  size_t hbm_cap_bytes;   /* device memory the solve may use; 0 = 90% of free */
+  void* cuda_stream;      /* cudaStream_t to run on; NULL = library stream    */
+  int device;             /* CUDA device ordinal; -1 = current device         */
+  int keep_block;         /* 1: keep each converged N_g x m Ritz block on the
+                             host after solve (for dgdft_alb_get_block)        */
+  const char* autotune_cache;   /* optional JSON path; NULL = none            */
+  const char* precond_weights;  /* learned preconditioner weights; NULL = none */
+} dgdft_alb_config;
+
+/* Per-element outcome of dgdft_alb_solve. */
+typedef struct {
+  int status;        /* DGDFT_OK or DGDFT_ENOTCONV (or another error)         */
+  int iterations;    /* LOBPCG iterations taken (all precision stages)        */
+  double max_resid;  /* max_{j<J} residual (Ha) at exit, FP64-checked         */
+  int fallbacks;     /* Rayleigh-Ritz retries without P / preconditioner falls */
+  int wave;          /* memory-admission wave the element ran in              */
+  double seconds;    /* wall time of the element's wave                       */
+} dgdft_solve_report;
+
+/* Fill cfg with defaults: FP64, Teter, tol 1e-6, maxit 400, check_every 4. */
+void dgdft_alb_config_init(dgdft_alb_config* cfg);
+
+/* Create a context for n_elem elements.  Validates every descriptor
+ * (sizes, 0 < n_keep <= n_compute, E_K inside Q_K, grid factors) and selects
+ * the device.  Nothing is allocated on the device until set_potential.
+ * Returns DGDFT_EINVAL on a bad descriptor, DGDFT_ECUDA without a device. */
+dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem,
+                              const dgdft_element_desc* elems,
+                              dgdft_alb_ctx** out);
+
+/* Restricted effective potential V_eff^{Q_K} of element `elem` (Sec. II.A):
+ * N_g doubles in the grid convention above.  Non-finite values give
+ * DGDFT_EINVAL. */
+dgdft_status dgdft_alb_set_potential(dgdft_alb_ctx* ctx, int elem,
+                                     const double* veff, int on_device);
+
+/* Kleinman-Bylander projectors of the atoms whose centres lie in Q_K
+ * (Eq. DGvar, nonlocal term): projector p has nonzeros
+ * grid_idx[row_ptr[p] .. row_ptr[p+1]) with values val (= b_p * sqrt(dV), so
+ * that sum val^2 = 1) and weight gamma[p] (Ha).  The discrete operator is
+ * V_nl = sum_p gamma_p v_p v_p^T.  Host pointers; n_proj may be 0.  Indices
+ * outside [0, N_g) or non-finite values give DGDFT_EINVAL. */
+dgdft_status dgdft_alb_set_projectors(dgdft_alb_ctx* ctx, int elem, int n_proj,
+                                      const int64_t* row_ptr, const int32_t* grid_idx,
+                                      const double* val, const double* gamma);
+
+/* Optional initial block X0 (N_g x m, column-major) for element `elem`; the
+ * default is a seeded standard-normal block.  Also the warm start for a
+ * repeated solve (Sec. II.B: previous Psi_K as the starting guess). */
+dgdft_status dgdft_alb_set_initial(dgdft_alb_ctx* ctx, int elem, const double* x0,
+                                   int on_device);
+
+/* Run ALB generation for every element with a potential.  Writes n_elem
+ * reports when per_elem is non-NULL.  Returns DGDFT_ENOTCONV when some
+ * element missed tol (its basis is still available), DGDFT_ESTATE when an
+ * element has no potential. */
+dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem);
+
+/* Copy out element `elem`'s ALBs: phi is n_E x J column-major (n_E = product
+ * of e_hi - e_lo, points ordered x fastest within E_K), eig the J lowest
+ * eigenvalues (Ha), resid their residuals (Ha).  Any pointer may be NULL.
+ * DGDFT_ESTATE before a solve. */
+dgdft_status dgdft_alb_get_basis(dgdft_alb_ctx* ctx, int elem, double* phi,
+                                 double* eig, double* resid, int on_device);
+
+/* Human-readable description of the last failure on ctx ("" if none). */
+const char* dgdft_alb_last_error(const dgdft_alb_ctx* ctx);
+
+/* Release every device and host resource of ctx.  NULL is a no-op. */
+void dgdft_alb_destroy(dgdft_alb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGDFT_ALB_H */

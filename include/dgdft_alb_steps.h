@@ -1,0 +1,66 @@
+/*
+ * dgdft_alb_steps.h -- step-level entry points of the ALB generator.
+ *
+ * Each call runs one stage of the hot path on the GPU, in the context's
+ * precision, on data the caller supplies, so every kernel can be compared
+ * with an independent implementation.  Grid, block and ownership
+ * conventions are those of dgdft_alb.h.  Inputs and outputs are double on
+ * both sides of the ABI; in DGDFT_PREC_MIXED contexts they are rounded to the
+ * working precision on entry.  The element's potential (and projectors,
+ * where used) must have been set.  Calls are synchronous.
+ */
+#ifndef DGDFT_ALB_STEPS_H
+#define DGDFT_ALB_STEPS_H
+
+#include "dgdft_alb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* H applied to k vectors (Sec. II.B, operation 1; Eq. localproblem):
+ * hx = -1/2 Lap x + V_eff x + sum_p gamma_p v_p (v_p^T x).  The Laplacian is
+ * spectral over every G of the FFT grid, Nyquist plane included.
+ * x, hx: N_g x k column-major.  1 <= k <= n_compute. */
+dgdft_status dgdft_alb_apply_h(dgdft_alb_ctx* ctx, int elem, int k, const double* x,
+                               double* hx, int on_device);
+
+/* Teter-Payne-Allan preconditioner (Sec. II.B, operation 5), per column:
+ * w_i = F^-1 [ K((|G|^2/2) / t_kin[i]) F r_i ] with
+ * K(s) = (27+18s+12s^2+8s^3) / (27+18s+12s^2+8s^3+16s^4).
+ * r, w: N_g x k; t_kin: k positive kinetic-energy scales (Ha, host). */
+dgdft_status dgdft_alb_apply_teter(dgdft_alb_ctx* ctx, int elem, int k, const double* r,
+                                   const double* t_kin, double* w, int on_device);
+
+/* Gram product C = U^T V (Sec. II.B, operation 2) over ng rows:
+ * U is ng x p, V is ng x q (column-major), C is p x q column-major (host,
+ * FP64).  Computed by the same split-K kernels as the solver, in the
+ * context's precision.  p, q <= 3 * max n_compute of the context. */
+dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u,
+                            const double* v, double* c, int on_device);
+
+/* Rayleigh-Ritz on a symmetric pencil (Sec. II.B, operation 4), FP64 on the
+ * GPU: the lowest m eigenpairs of A y = theta B y with B positive definite.
+ * A, B: n x n column-major (host, both symmetric); theta: m ascending;
+ * y: n x m with y^T B y = I.  Returns DGDFT_EINVAL when B is not positive
+ * definite to working accuracy.  n <= 3 * max n_compute of the context. */
+dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int n, int m, const double* a,
+                                     const double* b, double* theta, double* y);
+
+/* Restriction to E_K and orthonormalisation (Sec. II.A; Sec. II.B): the
+ * first J columns of the N_g x k block x are restricted to E_K's points and
+ * replaced by the left singular vectors of that n_E x J block, scaled by
+ * 1/sqrt(dV).  phi: n_E x J column-major.  J <= k. */
+dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int k,
+                                               int J, const double* x, double* phi,
+                                               int on_device);
+
+/* The converged Ritz block of element `elem` after a solve: x is N_g x m
+ * (the m = n_compute Ritz vectors, Euclidean-orthonormal, ascending Ritz
+ * values).  DGDFT_ESTATE before a solve. */
+dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGDFT_ALB_STEPS_H */

@@ -1,0 +1,267 @@
+"""ctypes binding of the C-ABI in include/dgdft_alb.h and dgdft_alb_steps.h.
+
+Argument marshalling only: every step of ALB generation runs in the CUDA
+library.  Functions keep the C names.  Arrays may be NumPy (host) or torch
+CUDA tensors (device, passed by data pointer with on_device = 1).  Loading
+fails loudly when the shared library has not been built; there is no
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DGDFT_OK, DGDFT_EINVAL, DGDFT_ENOMEM, DGDFT_ECUDA, DGDFT_ENOTCONV, DGDFT_ETIMEOUT, DGDFT_ESTATE = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "ESTATE"]
+DGDFT_PREC_FP64, DGDFT_PREC_MIXED = 0, 1
+DGDFT_PRECOND_TETER, DGDFT_PRECOND_LEARNED = 0, 1
+
+
+class dgdft_element_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("e_lo", C.c_int * 3), ("e_hi", C.c_int * 3),
+                ("n_compute", C.c_int), ("n_keep", C.c_int)]
+
+
+class dgdft_alb_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("tol", C.c_double),
+                ("maxit", C.c_int), ("check_every", C.c_int), ("hbm_cap_bytes", C.c_size_t),
+                ("cuda_stream", C.c_void_p), ("device", C.c_int), ("keep_block", C.c_int),
+                ("autotune_cache", C.c_char_p), ("precond_weights", C.c_char_p)]
+
+
+class dgdft_solve_report(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("max_resid", C.c_double),
+                ("fallbacks", C.c_int), ("wave", C.c_int), ("seconds", C.c_double)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "dgdft_alb_config_init": (None, [C.POINTER(dgdft_alb_config)]),
+    "dgdft_alb_create": (C.c_int, [C.POINTER(dgdft_alb_config), C.c_int,
+                                   C.POINTER(dgdft_element_desc), C.POINTER(_P)]),
+    "dgdft_alb_set_potential": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "dgdft_alb_set_projectors": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "dgdft_alb_set_initial": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "dgdft_alb_solve": (C.c_int, [_P, C.POINTER(dgdft_solve_report)]),
+    "dgdft_alb_get_basis": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
+    "dgdft_alb_last_error": (C.c_char_p, [_P]),
+    "dgdft_alb_destroy": (None, [_P]),
+    "dgdft_alb_apply_h": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "dgdft_alb_apply_teter": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
+    "dgdft_alb_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
+    "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "dgdft_alb_restrict_orthonormalise": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P,
+                                                    C.c_int]),
+    "dgdft_alb_get_block": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libdgdft_alb.so (built in-tree by build.py) and bind every symbol."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DgdftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """(pointer, on_device) of a NumPy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data_as(C.c_void_p), 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+class Context:
+    """Owns one dgdft_alb_ctx; methods mirror the C entry points."""
+
+    def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
+                 stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
+                 precond_weights=None):
+        self.lib = load()
+        cfg = dgdft_alb_config()
+        self.lib.dgdft_alb_config_init(C.byref(cfg))
+        cfg.precision = precision
+        cfg.precond = precond
+        cfg.tol = tol
+        cfg.maxit = maxit
+        cfg.check_every = check_every
+        cfg.keep_block = int(keep_block)
+        cfg.hbm_cap_bytes = int(hbm_cap_bytes)
+        cfg.cuda_stream = stream
+        self._weights = precond_weights.encode() if precond_weights else None
+        cfg.precond_weights = self._weights
+        self.cfg = cfg
+        n = len(elems)
+        arr = (dgdft_element_desc * n)()
+        for i, e in enumerate(elems):
+            d = arr[i]
+            d.nx, d.ny, d.nz = e["n"]
+            d.Lx, d.Ly, d.Lz = e["L"]
+            for a in range(3):
+                d.e_lo[a] = int(e["e_lo"][a])
+                d.e_hi[a] = int(e["e_hi"][a])
+            d.n_compute, d.n_keep = int(e["m"]), int(e["J"])
+        self.descs = arr
+        h = C.c_void_p()
+        st = self.lib.dgdft_alb_create(C.byref(cfg), n, arr, C.byref(h))
+        if st != DGDFT_OK:
+            raise DgdftError(st, "dgdft_alb_create failed")
+        self.h = h
+        self.n = n
+
+    def _check(self, st, what):
+        if st not in (DGDFT_OK,):
+            msg = self.lib.dgdft_alb_last_error(self.h)
+            raise DgdftError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgdft_alb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dgdft_alb_set_potential(self, elem, veff):
+        p, dev = _ptr(veff)
+        self._check(self.lib.dgdft_alb_set_potential(self.h, elem, p, dev), "set_potential")
+
+    def dgdft_alb_set_projectors(self, elem, row_ptr, idx, val, gamma):
+        n_proj = len(row_ptr) - 1
+        rp = np.ascontiguousarray(row_ptr, np.int64)
+        ix = np.ascontiguousarray(idx, np.int32)
+        vv = np.ascontiguousarray(val, np.float64)
+        gg = np.ascontiguousarray(gamma, np.float64)
+        self._check(self.lib.dgdft_alb_set_projectors(self.h, elem, n_proj, _ptr(rp)[0], _ptr(ix)[0],
+                                                      _ptr(vv)[0], _ptr(gg)[0]), "set_projectors")
+
+    def dgdft_alb_set_initial(self, elem, x0):
+        p, dev = _ptr(x0)
+        self._check(self.lib.dgdft_alb_set_initial(self.h, elem, p, dev), "set_initial")
+
+    def dgdft_alb_solve(self, check=False):
+        reps = (dgdft_solve_report * self.n)()
+        st = self.lib.dgdft_alb_solve(self.h, reps)
+        if st not in (DGDFT_OK, DGDFT_ENOTCONV) or (check and st != DGDFT_OK):
+            self._check(st, "solve")
+        return st, [dict(status=r.status, iterations=r.iterations, max_resid=r.max_resid,
+                         fallbacks=r.fallbacks, wave=r.wave, seconds=r.seconds) for r in reps]
+
+    def dgdft_alb_get_basis(self, elem, phi=None, eig=None, resid=None):
+        d = self.descs[elem]
+        ne = (d.e_hi[0] - d.e_lo[0]) * (d.e_hi[1] - d.e_lo[1]) * (d.e_hi[2] - d.e_lo[2])
+        J = d.n_keep
+        phi = np.zeros((J, ne)) if phi is None else phi
+        eig = np.zeros(J) if eig is None else eig
+        resid = np.zeros(J) if resid is None else resid
+        pp, dev = _ptr(phi)
+        self._check(self.lib.dgdft_alb_get_basis(self.h, elem, pp, _ptr(eig)[0], _ptr(resid)[0], dev),
+                    "get_basis")
+        return phi, eig, resid
+
+    def dgdft_alb_get_block(self, elem):
+        d = self.descs[elem]
+        x = np.zeros((d.n_compute, d.nx * d.ny * d.nz))
+        self._check(self.lib.dgdft_alb_get_block(self.h, elem, _ptr(x)[0], 0), "get_block")
+        return x
+
+    # step entry points -------------------------------------------------
+    def dgdft_alb_apply_h(self, elem, x):
+        x = np.ascontiguousarray(x, np.float64)
+        out = np.zeros_like(x)
+        self._check(self.lib.dgdft_alb_apply_h(self.h, elem, x.shape[0], _ptr(x)[0], _ptr(out)[0], 0),
+                    "apply_h")
+        return out
+
+    def dgdft_alb_apply_teter(self, elem, r, t_kin):
+        r = np.ascontiguousarray(r, np.float64)
+        t = np.ascontiguousarray(t_kin, np.float64)
+        out = np.zeros_like(r)
+        self._check(self.lib.dgdft_alb_apply_teter(self.h, elem, r.shape[0], _ptr(r)[0], _ptr(t)[0],
+                                                   _ptr(out)[0], 0), "apply_teter")
+        return out
+
+    def dgdft_alb_gram(self, u, v):
+        """u: (p, ng), v: (q, ng) rows = columns of the column-major blocks."""
+        u = np.ascontiguousarray(u, np.float64)
+        v = np.ascontiguousarray(v, np.float64)
+        p, ng = u.shape
+        q = v.shape[0]
+        c = np.zeros((q, p))  # column-major p x q
+        self._check(self.lib.dgdft_alb_gram(self.h, ng, p, q, _ptr(u)[0], _ptr(v)[0], _ptr(c)[0], 0),
+                    "gram")
+        return c.T.copy()
+
+    def dgdft_alb_rayleigh_ritz(self, a, b, m):
+        n = a.shape[0]
+        a = np.ascontiguousarray(np.asarray(a, np.float64).T)
+        b = np.ascontiguousarray(np.asarray(b, np.float64).T)
+        theta = np.zeros(m)
+        y = np.zeros((m, n))
+        self._check(self.lib.dgdft_alb_rayleigh_ritz(self.h, n, m, _ptr(a)[0], _ptr(b)[0],
+                                                     _ptr(theta)[0], _ptr(y)[0]), "rayleigh_ritz")
+        return theta, y.T.copy()
+
+    def dgdft_alb_restrict_orthonormalise(self, elem, x, J):
+        x = np.ascontiguousarray(x, np.float64)
+        d = self.descs[elem]
+        ne = (d.e_hi[0] - d.e_lo[0]) * (d.e_hi[1] - d.e_lo[1]) * (d.e_hi[2] - d.e_lo[2])
+        phi = np.zeros((J, ne))
+        self._check(self.lib.dgdft_alb_restrict_orthonormalise(self.h, elem, x.shape[0], J, _ptr(x)[0],
+                                                               _ptr(phi)[0], 0), "restrict")
+        return phi
+
+
+def element_dict(el) -> dict:
+    """Descriptor fields of a synthetic element (duck-typed: n, L, e_lo, e_hi, m, J)."""
+    return dict(n=tuple(int(v) for v in el.n), L=tuple(float(v) for v in el.L),
+                e_lo=tuple(el.e_lo), e_hi=tuple(el.e_hi), m=el.m, J=el.J)
+
+
+def load_element(ctx: Context, k: int, el, x0=None):
+    """Copy one element's potential, projectors and optional initial block in."""
+    ctx.dgdft_alb_set_potential(k, np.ascontiguousarray(el.veff.reshape(-1), np.float64))
+    if el.n_proj:
+        ctx.dgdft_alb_set_projectors(k, el.proj_row_ptr, el.proj_idx, el.proj_val, el.proj_gamma)
+    if x0 is not None:
+        ctx.dgdft_alb_set_initial(k, np.ascontiguousarray(x0, np.float64))

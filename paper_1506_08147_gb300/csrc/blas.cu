@@ -1,0 +1,354 @@
+// Tall-skinny block operations of LOBPCG (Sec. II.B, operations 2 and 3).
+//
+// Each iteration forms 12 Gram products Phi^T Psi (the 6 + 6 distinct blocks
+// of S^T H S and S^T S, S = [X W P]) and 7 block updates Phi C with small C.
+// The paper splits rows over a processor column group and sums the J x J
+// partial products with MPI_Allreduce; here the row split is over CTAs
+// (split-K) and the partial products are summed on the device in a fixed
+// order, so results do not depend on scheduling.
+//
+// These are the SIMT kernels (FP64 for the plain solver, FP32 accumulation
+// within a chunk for the mixed form); partial sums are always FP64.
+#include "internal.h"
+
+namespace dgdft {
+
+namespace {
+
+constexpr int TILE = 64;   // output tile edge
+constexpr int KS = 32;     // rows staged per shared-memory step (Gram)
+constexpr int KU = 16;     // inner dimension staged per step (update)
+
+template <class real>
+__device__ __forceinline__ int ld_of(const ElemDev<real>& e, const BRef<real>& r, int ld_in, int rows) {
+  return r.ptr ? (ld_in > 0 ? ld_in : rows) : e.ng;
+}
+
+// grid: (nchunk, npairs * tiles_a * tiles_b, nel); block 256 = 16 x 16.
+template <class real>
+__global__ void __launch_bounds__(256) gram_kernel(const ElemDev<real>* __restrict__ elems,
+                                                   GramJob<real> job, double* __restrict__ partial,
+                                                   size_t pstride, int kchunk, int tiles_a,
+                                                   int tiles_b) {
+  __shared__ real As[KS][TILE + 4];
+  __shared__ real Bs[KS][TILE + 4];
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int ntile = tiles_a * tiles_b;
+  const int pair = blockIdx.y / ntile;
+  const int t = blockIdx.y - pair * ntile;
+  const int ta = t / tiles_b, tb = t - ta * tiles_b;
+  if (job.needs_p[pair] && !e.state[ST_HAS_P]) return;
+  const int ca = job.ncols_a > 0 ? job.ncols_a : e.m;
+  const int cb = job.ncols_b > 0 ? job.ncols_b : e.m;
+  const int rows = job.rows > 0 ? job.rows : e.ng;
+  const int a0 = ta * TILE, b0 = tb * TILE;
+  if (a0 >= ca || b0 >= cb) return;
+  const real* A = resolve(e, job.a[pair]);
+  const real* B = resolve(e, job.b[pair]);
+  const int lda = ld_of(e, job.a[pair], job.ld_in, rows);
+  const int ldb = ld_of(e, job.b[pair], job.ld_in, rows);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int k_beg = blockIdx.x * kchunk;
+  const int k_end = min(rows, k_beg + kchunk);
+  real acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int k0 = k_beg; k0 < k_end; k0 += KS) {
+    for (int i = threadIdx.x; i < KS * TILE; i += blockDim.x) {
+      const int c = i / KS, r = i - c * KS;
+      const int k = k0 + r;
+      const bool kin = k < k_end;
+      As[r][c] = (kin && a0 + c < ca) ? A[(size_t)(a0 + c) * lda + k] : (real)0;
+      Bs[r][c] = (kin && b0 + c < cb) ? B[(size_t)(b0 + c) * ldb + k] : (real)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < KS; ++r) {
+      real av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[r][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[r][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    __syncthreads();
+  }
+  double* out = partial + blockIdx.z * pstride +
+                ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (TILE * TILE);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * TILE + tx * 4 + j] = (double)acc[i][j];
+}
+
+template <class real>
+__global__ void gram_reduce_kernel(const ElemDev<real>* __restrict__ elems, GramJob<real> job,
+                                   const double* __restrict__ partial, size_t pstride, int nchunk,
+                                   int tiles_a, int tiles_b) {
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int ntile = tiles_a * tiles_b;
+  const int pair = blockIdx.x / ntile;
+  const int t = blockIdx.x - pair * ntile;
+  const int ta = t / tiles_b, tb = t - ta * tiles_b;
+  if (job.needs_p[pair] && !e.state[ST_HAS_P]) return;
+  const int ca = job.ncols_a > 0 ? job.ncols_a : e.m;
+  const int cb = job.ncols_b > 0 ? job.ncols_b : e.m;
+  const int a0 = ta * TILE, b0 = tb * TILE;
+  if (a0 >= ca || b0 >= cb) return;
+  double* out;
+  int ld;
+  switch (job.out_id[pair]) {
+    case OUT_GRAM_A: out = e.gram; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
+    case OUT_GRAM_B: out = e.gram + (size_t)9 * e.m * e.m; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
+    case OUT_GXW: out = e.gxw; ld = job.ld_out > 0 ? job.ld_out : e.m; break;
+    default: out = job.out_ptr; ld = job.ld_out; break;
+  }
+  const double* base = partial + blockIdx.z * pstride + (size_t)blockIdx.x * (TILE * TILE);
+  const size_t cstride = (size_t)gridDim.x * (TILE * TILE);
+  for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) {
+    const int r = i / TILE, c = i - r * TILE;
+    if (a0 + r >= ca || b0 + c >= cb) continue;
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) s += base[ch * cstride + i];
+    const int orow = job.brow[pair] * ca + a0 + r;
+    const int ocol = job.bcol[pair] * cb + b0 + c;
+    out[orow + (size_t)ocol * ld] = s;
+  }
+}
+
+// grid: (ceil(rows/64), ceil(ncols/64), nel); block 256.  Thread (tx, ty)
+// owns rows tx + 16 i and columns ty * 4 + j of the 64 x 64 output tile.
+template <class real>
+__global__ void __launch_bounds__(256) tsmm_kernel(const ElemDev<real>* __restrict__ elems,
+                                                   TsmmJob<real> job) {
+  __shared__ real Ss[KU][TILE + 4];
+  __shared__ real Ys[KU][TILE + 4];
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int nc = job.ncols > 0 ? job.ncols : e.m;
+  const int rows = job.rows > 0 ? job.rows : e.ng;
+  const int r0 = blockIdx.x * TILE, c0 = blockIdx.y * TILE;
+  if (r0 >= rows || c0 >= nc) return;
+  const double* Y;
+  int ldy;
+  switch (job.y_id) {
+    case Y_RR: Y = e.Y; ldy = job.ldy > 0 ? job.ldy : 3 * e.m; break;
+    case Y_GXW: Y = e.gxw; ldy = job.ldy > 0 ? job.ldy : e.m; break;
+    default: Y = job.y_ptr; ldy = job.ldy; break;
+  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  real acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  const int ycol0 = job.ycol * nc + c0;
+  for (int in = 0; in < job.nin; ++in) {
+    if (job.needs_p[in] && !e.state[ST_HAS_P]) continue;
+    const real* S = resolve(e, job.in[in]);
+    const int lds = ld_of(e, job.in[in], job.ld_in, rows);
+    const int yrow0 = job.yrow[in] * nc;
+    for (int k0 = 0; k0 < nc; k0 += KU) {
+      for (int i = threadIdx.x; i < KU * TILE; i += blockDim.x) {
+        const int kk = i / TILE, r = i - kk * TILE;
+        const bool kin = k0 + kk < nc;
+        Ss[kk][r] = (kin && r0 + r < rows) ? S[(size_t)(k0 + kk) * lds + r0 + r] : (real)0;
+        Ys[kk][r] = (kin && c0 + r < nc) ? (real)Y[(yrow0 + k0 + kk) + (size_t)(ycol0 + r) * ldy] : (real)0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < KU; ++kk) {
+        real sv[4], yv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sv[i] = Ss[kk][tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) yv[j] = Ys[kk][ty * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += sv[i] * yv[j];
+      }
+      __syncthreads();
+    }
+  }
+  real* O = resolve(e, job.out);
+  const int ldo = ld_of(e, job.out, job.ld_in, rows);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int col = c0 + ty * 4 + j;
+    if (col >= nc) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = r0 + tx + 16 * i;
+      if (row >= rows) continue;
+      real* o = O + (size_t)col * ldo + row;
+      real v = (real)job.alpha * acc[i][j];
+      if (job.beta != 0.0) v += (real)job.beta * *o;
+      *o = v;
+    }
+  }
+}
+
+// R = HX - X diag(theta) into W; partial sums (r.r, x.x, x.Hx, x.V x).
+template <class real>
+__global__ void __launch_bounds__(256) residual_kernel(const ElemDev<real>* __restrict__ elems,
+                                                       int nchunk) {
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int j = blockIdx.y;
+  if (j >= e.m) return;
+  const int kc = (e.ng + nchunk - 1) / nchunk;
+  const int beg = blockIdx.x * kc, end = min(e.ng, beg + kc);
+  const real* X = cur_blk(e, BX) + (size_t)j * e.ng;
+  const real* HX = cur_blk(e, BHX) + (size_t)j * e.ng;
+  real* R = e.blk[BW][0] + (size_t)j * e.ng;
+  const real th = (real)e.theta[j];
+  real s[4] = {0, 0, 0, 0};
+  for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const real x = X[i], hx = HX[i];
+    const real r = hx - th * x;
+    R[i] = r;
+    s[0] += r * r;
+    s[1] += x * x;
+    s[2] += x * hx;
+    s[3] += e.V[i] * x * x;
+  }
+  __shared__ double red[4][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double v = warp_sum((double)s[q]);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+    e.rpart[((size_t)j * nchunk + blockIdx.x) * 4 + threadIdx.x] = v;
+  }
+}
+
+template <class real>
+__global__ void post_residual_kernel(const ElemDev<real>* __restrict__ elems, int nchunk, int maxit) {
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  __shared__ double smax[256];
+  __shared__ int sbad[256];
+  double mx = 0.0;
+  int bad = 0;
+  for (int j = threadIdx.x; j < e.m; j += blockDim.x) {
+    double s[4] = {0, 0, 0, 0};
+    for (int c = 0; c < nchunk; ++c)
+      for (int q = 0; q < 4; ++q) s[q] += e.rpart[((size_t)j * nchunk + c) * 4 + q];
+    double nl = 0.0;
+    for (int p = 0; p < e.n_proj; ++p) {
+      const double c = (double)e.Ccoef[p + (size_t)j * e.n_proj];
+      nl += e.p_gamma[p] * c * c;
+    }
+    const double res = sqrt(s[0] / s[1]);
+    e.res[j] = res;
+    e.tkin[j] = (s[2] - s[3] - nl) / s[1];
+    if (!isfinite(res)) bad = 1;
+    if (j < e.J) mx = fmax(mx, res);
+  }
+  smax[threadIdx.x] = mx;
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < blockDim.x; ++t) {
+      mx = fmax(mx, smax[t]);
+      bad |= sbad[t];
+    }
+    int* st = e.state;
+    if (bad) {
+      st[ST_ERROR] |= ERR_NONFINITE;
+      st[ST_ACTIVE] = 0;
+    } else if (mx <= e.tol) {
+      st[ST_CONVERGED] = 1;
+      st[ST_ACTIVE] = 0;
+    } else if (st[ST_ITER] >= maxit) {
+      st[ST_ACTIVE] = 0;
+    } else {
+      st[ST_ITER] += 1;
+    }
+  }
+}
+
+template <class real>
+__global__ void iter_finish_kernel(const ElemDev<real>* __restrict__ elems, int nel, int set_p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nel) return;
+  int* st = elems[i].state;
+  if (!st[ST_ACTIVE]) return;
+  st[ST_PARITY] ^= 1;
+  if (set_p) st[ST_HAS_P] = 1;
+}
+
+}  // namespace
+
+template <class real>
+void launch_gram(const Batch<real>& b, const GramJob<real>& job, double* partial, size_t partial_cap,
+                 cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int ca = job.ncols_a > 0 ? job.ncols_a : s.max_m;
+  const int cb = job.ncols_b > 0 ? job.ncols_b : s.max_m;
+  const int rows = job.rows > 0 ? job.rows : s.max_ng;
+  const int tiles_a = (ca + TILE - 1) / TILE, tiles_b = (cb + TILE - 1) / TILE;
+  const int ny = job.npairs * tiles_a * tiles_b;
+  // per-element partial storage: nchunk * ny tiles
+  int kchunk = 2048;
+  int nchunk = (rows + kchunk - 1) / kchunk;
+  while ((size_t)nchunk * ny * TILE * TILE * s.nel > partial_cap && kchunk < (1 << 30)) {
+    kchunk *= 2;
+    nchunk = (rows + kchunk - 1) / kchunk;
+  }
+  const size_t pstride = (size_t)nchunk * ny * TILE * TILE;
+  gram_kernel<real><<<dim3(nchunk, ny, s.nel), 256, 0, st>>>(b.d_elems, job, partial, pstride, kchunk,
+                                                             tiles_a, tiles_b);
+  gram_reduce_kernel<real><<<dim3(ny, 1, s.nel), 256, 0, st>>>(b.d_elems, job, partial, pstride, nchunk,
+                                                               tiles_a, tiles_b);
+}
+
+template <class real>
+void launch_tsmm(const Batch<real>& b, const TsmmJob<real>& job, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int nc = job.ncols > 0 ? job.ncols : s.max_m;
+  const int rows = job.rows > 0 ? job.rows : s.max_ng;
+  tsmm_kernel<real><<<dim3((rows + TILE - 1) / TILE, (nc + TILE - 1) / TILE, s.nel), 256, 0, st>>>(
+      b.d_elems, job);
+}
+
+template <class real>
+void launch_residual(const Batch<real>& b, int nchunk, cudaStream_t st) {
+  residual_kernel<real><<<dim3(nchunk, b.s.max_m, b.s.nel), 256, 0, st>>>(b.d_elems, nchunk);
+}
+
+template <class real>
+void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStream_t st) {
+  post_residual_kernel<real><<<dim3(1, 1, b.s.nel), 256, 0, st>>>(b.d_elems, nchunk, maxit);
+}
+
+template <class real>
+void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st) {
+  iter_finish_kernel<real><<<(b.s.nel + 127) / 128, 128, 0, st>>>(b.d_elems, b.s.nel, set_p);
+}
+
+#define DGDFT_INST(real)                                                                             \
+  template void launch_gram<real>(const Batch<real>&, const GramJob<real>&, double*, size_t,         \
+                                  cudaStream_t);                                                     \
+  template void launch_tsmm<real>(const Batch<real>&, const TsmmJob<real>&, cudaStream_t);           \
+  template void launch_residual<real>(const Batch<real>&, int, cudaStream_t);                        \
+  template void launch_post_residual<real>(const Batch<real>&, int, int, cudaStream_t);              \
+  template void launch_iter_finish<real>(const Batch<real>&, int, cudaStream_t);
+DGDFT_INST(double)
+DGDFT_INST(float)
+#undef DGDFT_INST
+
+}  // namespace dgdft

@@ -1,0 +1,281 @@
+// H apply and Teter preconditioner on batches of elements.
+//
+// Sec. II.B, operation 1: H Psi = -1/2 Lap Psi (FFT) + V_eff Psi (local) +
+// sum_p gamma_p b_p <b_p, Psi> (Kleinman-Bylander, Eq. DGvar nonlocal term).
+// Sec. II.B, operation 5: the Teter preconditioner, applied per column.
+//
+// Three passes over HBM per block (a 3-D transform needs one transpose when
+// a whole grid does not fit on chip):
+//   xy_fwd : per (plane z, vector j): real plane -> r2c along x (as a complex
+//            FFT of length nx/2 plus an even/odd split) -> FFT along y;
+//   z_mult : per (tile of (y, kx) columns, vector j): FFT along z, multiply by
+//            the kinetic symbol |G|^2/2 (or the Teter factor), inverse FFT;
+//   xy_inv : inverse y, c2r along x, fused epilogue adding V_eff psi and the
+//            projector scatter for the points of plane z.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace dgdft {
+
+namespace {
+
+template <class real>
+__device__ __forceinline__ bool elem_live(const ElemDev<real>& e) {
+  return e.state[ST_ACTIVE] != 0;
+}
+
+// C[p, j] = v_p^T psi_j for the projectors of the element.
+template <class real>
+__global__ void proj_coef_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> src, int ncols) {
+  const ElemDev<real>& e = elems[blockIdx.z];
+  const int p = blockIdx.x;
+  if (!elem_live(e) || p >= e.n_proj) return;
+  const int nc = ncols > 0 ? ncols : e.m;
+  const real* x = resolve(e, src);
+  const int beg = e.p_ptr[p], end = e.p_ptr[p + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int j = warp; j < nc; j += nwarp) {
+    const real* xj = x + (size_t)j * e.ng;
+    real acc = 0;
+    for (int q = beg + lane; q < end; q += 32) acc += e.p_val[q] * xj[e.p_idx[q]];
+    acc = warp_sum(acc);
+    if (lane == 0) e.Ccoef[p + (size_t)j * e.n_proj] = acc;
+  }
+}
+
+template <class real>
+__global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> src, int ncols) {
+  using C = cplx_t<real>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ElemDev<real>& e = elems[blockIdx.z];
+  const int z = blockIdx.x, j = blockIdx.y;
+  const int nc = ncols > 0 ? ncols : e.m;
+  if (!elem_live(e) || z >= e.nz || j >= nc) return;
+  const int row = e.nxh, ny = e.ny, nh = e.nh;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + ny * row;
+  const C* plane = reinterpret_cast<const C*>(resolve(e, src) + (size_t)j * e.ng + (size_t)z * e.nx * ny);
+  for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
+    const int y = t / nh, k = t - y * nh;
+    buf0[y * row + k] = plane[t];
+  }
+  __syncthreads();
+  int cur = fft_lines<C, false>(buf0, buf1, 0, e.px, ny, row, 1, e.tw_h);
+  // even/odd split: X[k] = E[k] + e^{-2 pi i k / nx} O[k], k = 0..nh
+  {
+    const C* s = cur ? buf1 : buf0;
+    C* d = cur ? buf0 : buf1;
+    for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
+      const int y = t / e.nxh, k = t - y * e.nxh;
+      const C zk = s[y * row + (k == nh ? 0 : k)];
+      const C zc = cconj(s[y * row + (k == 0 ? 0 : nh - k)]);
+      const C ev = cscale(cadd(zk, zc), (real)0.5);
+      const C df = csub(zk, zc);
+      const C od = cmake<C>((real)0.5 * df.y, (real)-0.5 * df.x);  // -i/2 (zk - zc)
+      d[y * row + k] = cadd(ev, cmul(e.tw_x[k], od));
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  cur = fft_lines<C, false>(buf0, buf1, cur, e.py, e.nxh, 1, row, e.tw_y);
+  const C* res = cur ? buf1 : buf0;
+  C* out = e.Z + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
+  for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
+    const int y = t / e.nxh, k = t - y * e.nxh;
+    out[t] = res[y * row + k];
+  }
+}
+
+constexpr int ZTILE = 32;
+constexpr int ZROW = ZTILE + 1;
+
+template <class real>
+__device__ __forceinline__ double teter_factor(double s) {
+  const double num = 27.0 + s * (18.0 + s * (12.0 + s * 8.0));
+  return num / (num + 16.0 * s * s * s * s);
+}
+
+template <class real, int MODE>
+__global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols,
+                              const double* __restrict__ tkin_override) {
+  using C = cplx_t<real>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ElemDev<real>& e = elems[blockIdx.z];
+  const int j = blockIdx.y;
+  const int nc = ncols > 0 ? ncols : e.m;
+  const int nplane = e.nxh * e.ny;
+  const int c0 = blockIdx.x * ZTILE;
+  if (!elem_live(e) || j >= nc || c0 >= nplane) return;
+  const int nz = e.nz;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + nz * ZROW;
+  C* zj = e.Z + (size_t)j * e.nspec;
+  for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
+    const int z = t / ZTILE, cc = t - z * ZTILE;
+    const int c = c0 + cc;
+    buf0[z * ZROW + cc] = (c < nplane) ? zj[(size_t)z * nplane + c] : cmake<C>(0, 0);
+  }
+  __syncthreads();
+  int cur = fft_lines<C, false>(buf0, buf1, 0, e.pz, ZTILE, 1, ZROW, e.tw_z);
+  {
+    C* s = cur ? buf1 : buf0;
+    double tk = 1.0;
+    if (MODE == ZM_TETER) tk = tkin_override ? tkin_override[j] : e.tkin[j];
+    const double inv_tk = 1.0 / fmax(tk, 1e-8);
+    for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
+      const int gz = t / ZTILE, cc = t - gz * ZTILE;
+      const int c = c0 + cc;
+      if (c >= nplane) continue;
+      const int y = c / e.nxh, kx = c - y * e.nxh;
+      const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
+      double f = (MODE == ZM_KINETIC) ? g : teter_factor<real>(g * inv_tk);
+      f *= e.scale;
+      s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (real)f);
+    }
+    __syncthreads();
+  }
+  cur = fft_lines<C, true>(buf0, buf1, cur, e.pz, ZTILE, 1, ZROW, e.tw_z);
+  const C* res = cur ? buf1 : buf0;
+  for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
+    const int z = t / ZTILE, cc = t - z * ZTILE;
+    const int c = c0 + cc;
+    if (c < nplane) zj[(size_t)z * nplane + c] = res[z * ZROW + cc];
+  }
+}
+
+template <class real, int MODE>
+__global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> dst,
+                              BRef<real> xsrc, int ncols) {
+  using C = cplx_t<real>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ElemDev<real>& e = elems[blockIdx.z];
+  const int z = blockIdx.x, j = blockIdx.y;
+  const int nc = ncols > 0 ? ncols : e.m;
+  if (!elem_live(e) || z >= e.nz || j >= nc) return;
+  const int row = e.nxh, ny = e.ny, nh = e.nh;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + ny * row;
+  const C* in = e.Z + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
+  for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
+    const int y = t / e.nxh, k = t - y * e.nxh;
+    buf0[y * row + k] = in[t];
+  }
+  __syncthreads();
+  int cur = fft_lines<C, true>(buf0, buf1, 0, e.py, e.nxh, 1, row, e.tw_y);
+  // recombine the half spectrum into E + i O for the length-nh inverse
+  {
+    const C* s = cur ? buf1 : buf0;
+    C* d = cur ? buf0 : buf1;
+    for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
+      const int y = t / nh, k = t - y * nh;
+      const C xk = s[y * row + k];
+      const C xc = cconj(s[y * row + nh - k]);
+      const C ev = cscale(cadd(xk, xc), (real)0.5);
+      const C od = cmul(cscale(csub(xk, xc), (real)0.5), cconj(e.tw_x[k]));
+      d[y * row + k] = cmake<C>(ev.x - od.y, ev.y + od.x);
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  cur = fft_lines<C, true>(buf0, buf1, cur, e.px, ny, row, 1, e.tw_h);
+  C* res = cur ? buf1 : buf0;
+  const size_t plane_off = (size_t)j * e.ng + (size_t)z * e.nx * ny;
+  if (MODE == XI_HAMILTONIAN) {
+    // Kleinman-Bylander scatter for the support points of this plane
+    if (e.n_sup > 0) {
+      const int sb = e.s_plane[z], se = e.s_plane[z + 1];
+      const real* cj = e.Ccoef + (size_t)j * e.n_proj;
+      real* rres = reinterpret_cast<real*>(res);
+      for (int s = sb + threadIdx.x; s < se; s += blockDim.x) {
+        real acc = 0;
+        for (int q = e.s_ptr[s]; q < e.s_ptr[s + 1]; ++q) acc += e.s_gv[q] * cj[e.s_proj[q]];
+        const int off = e.s_off[s];
+        const int y = off / e.nx, x = off - y * e.nx;
+        rres[2 * (y * row) + x] += acc;
+      }
+      __syncthreads();
+    }
+    const C* xp = reinterpret_cast<const C*>(resolve(e, xsrc) + plane_off);
+    const C* vp = reinterpret_cast<const C*>(e.V + (size_t)z * e.nx * ny);
+    C* op = reinterpret_cast<C*>(resolve(e, dst) + plane_off);
+    for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
+      const int y = t / nh, k = t - y * nh;
+      const C kv = res[y * row + k];
+      const C xv = xp[t];
+      const C vv = vp[t];
+      op[t] = cmake<C>(kv.x + vv.x * xv.x, kv.y + vv.y * xv.y);
+    }
+  } else {
+    C* op = reinterpret_cast<C*>(resolve(e, dst) + plane_off);
+    for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
+      const int y = t / nh, k = t - y * nh;
+      op[t] = res[y * row + k];
+    }
+  }
+}
+
+template <class real> size_t plane_smem(const BatchShape& s) {
+  return 2 * sizeof(cplx_t<real>) * (size_t)s.max_ny * s.max_nxh;
+}
+template <class real> size_t zcol_smem(const BatchShape& s) {
+  return 2 * sizeof(cplx_t<real>) * (size_t)s.max_nz * ZROW;
+}
+
+}  // namespace
+
+template <class real>
+void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int nc = ncols > 0 ? ncols : s.max_m;
+  if (s.max_nproj > 0)
+    proj_coef_kernel<real><<<dim3(s.max_nproj, 1, s.nel), 128, 0, st>>>(b.d_elems, src, ncols);
+  const size_t sp = plane_smem<real>(s), sz = zcol_smem<real>(s);
+  xy_fwd_kernel<real><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, src, ncols);
+  z_mult_kernel<real, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, sz, st>>>(
+      b.d_elems, ncols, nullptr);
+  xy_inv_kernel<real, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, dst, src,
+                                                                                   ncols);
+}
+
+template <class real>
+void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const double* tkin_override,
+                  int ncols, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int nc = ncols > 0 ? ncols : s.max_m;
+  const size_t sp = plane_smem<real>(s), sz = zcol_smem<real>(s);
+  xy_fwd_kernel<real><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, src, ncols);
+  z_mult_kernel<real, ZM_TETER><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, sz, st>>>(
+      b.d_elems, ncols, tkin_override);
+  xy_inv_kernel<real, XI_PLAIN><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, dst, src, ncols);
+}
+
+// Allow the plane and column kernels the full opt-in shared memory once.
+template <class real> static void opt_in_smem_t() {
+  const int mx = 227 * 1024;
+  cudaFuncSetAttribute(xy_fwd_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(xy_inv_kernel<real, XI_HAMILTONIAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(xy_inv_kernel<real, XI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(z_mult_kernel<real, ZM_KINETIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(z_mult_kernel<real, ZM_TETER>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+void init_hamiltonian_kernels() {
+  opt_in_smem_t<double>();
+  opt_in_smem_t<float>();
+}
+
+template <class real>
+void launch_proj_coef(const Batch<real>& b, BRef<real> src, int ncols, cudaStream_t st) {
+  if (b.s.max_nproj > 0)
+    proj_coef_kernel<real><<<dim3(b.s.max_nproj, 1, b.s.nel), 128, 0, st>>>(b.d_elems, src, ncols);
+}
+template void launch_proj_coef<double>(const Batch<double>&, BRef<double>, int, cudaStream_t);
+template void launch_proj_coef<float>(const Batch<float>&, BRef<float>, int, cudaStream_t);
+
+template void launch_apply_h<double>(const Batch<double>&, BRef<double>, BRef<double>, int, cudaStream_t);
+template void launch_apply_h<float>(const Batch<float>&, BRef<float>, BRef<float>, int, cudaStream_t);
+template void launch_teter<double>(const Batch<double>&, BRef<double>, BRef<double>, const double*, int,
+                                   cudaStream_t);
+template void launch_teter<float>(const Batch<float>&, BRef<float>, BRef<float>, const double*, int,
+                                  cudaStream_t);
+
+}  // namespace dgdft

@@ -1,0 +1,138 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dgdft {
+
+// A block operand: either one of the element's blocks (current or next
+// buffer) or, for single-element step calls, an explicit device pointer.
+template <class real> struct BRef {
+  int sel;
+  int next;
+  real* ptr;
+};
+template <class real> inline BRef<real> bref(int sel, int next = 0) { return BRef<real>{sel, next, nullptr}; }
+template <class real> inline BRef<real> bptr(real* p) { return BRef<real>{0, 0, p}; }
+
+template <class real>
+__device__ __forceinline__ real* resolve(const ElemDev<real>& e, const BRef<real>& r) {
+  if (r.ptr) return r.ptr;
+  return r.next ? next_blk(e, r.sel) : cur_blk(e, r.sel);
+}
+
+// Launch geometry of a batch of elements resident on the device.
+struct BatchShape {
+  int nel = 0;        // elements in the batch
+  int max_nz = 0, max_ny = 0, max_nxh = 0, max_nplane = 0, max_m = 0, max_ng = 0;
+  int max_nproj = 0, max_rows_e = 0;
+};
+
+template <class real> struct Batch {
+  const ElemDev<real>* d_elems = nullptr;  // device array of nel descriptors
+  BatchShape s;
+};
+
+enum { ZM_KINETIC = 0, ZM_TETER = 1 };
+enum { XI_HAMILTONIAN = 0, XI_PLAIN = 1 };
+
+// hamiltonian.cu
+template <class real>
+void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st);
+template <class real>
+void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const double* tkin_override,
+                  int ncols, cudaStream_t st);
+
+void init_hamiltonian_kernels();
+
+// blas.cu
+// Gram products U_a^T V_b over the rows of each element, split over row
+// chunks; FP64 partial sums are reduced in a fixed order.
+enum { OUT_GRAM_A = 0, OUT_GRAM_B = 1, OUT_GXW = 2, OUT_PTR = 3 };
+constexpr int MAX_PAIRS = 12;
+template <class real> struct GramJob {
+  int npairs = 0;
+  BRef<real> a[MAX_PAIRS], b[MAX_PAIRS];
+  int needs_p[MAX_PAIRS];   // 1: skip the pair while the element has no P block
+  int out_id[MAX_PAIRS];
+  int brow[MAX_PAIRS], bcol[MAX_PAIRS];  // placement, in units of the column count
+  int ncols_a = 0, ncols_b = 0;          // <= 0: the element's m
+  int rows = 0;                          // <= 0: the element's N_g
+  int ld_in = 0;                         // leading dim of explicit pointers (<=0: rows)
+  int ld_out = 0;                        // <= 0: 3m for gram A/B, m for X^T W
+  double* out_ptr = nullptr;             // OUT_PTR target (single element)
+};
+template <class real>
+void launch_gram(const Batch<real>& b, const GramJob<real>& job, double* partial, size_t partial_cap,
+                 cudaStream_t st);
+
+// Tall-skinny update out = alpha * sum_i in_i Y_i + beta * out, Y in FP64.
+enum { Y_RR = 0, Y_GXW = 1, Y_PTR = 2 };
+template <class real> struct TsmmJob {
+  int nin = 0;
+  BRef<real> in[3];
+  int needs_p[3] = {0, 0, 0};
+  int yrow[3] = {0, 0, 0};   // first Y row of input i, in units of the column count
+  int y_id = Y_RR;
+  const double* y_ptr = nullptr;
+  int ldy = 0;               // <= 0: 3m for Y_RR, m for Y_GXW
+  int ycol = 0;              // first Y column, in units of the column count
+  int ncols = 0;             // columns per input and output (<= 0: m)
+  int rows = 0;              // <= 0: N_g
+  int ld_in = 0;             // explicit pointer leading dim (<= 0: rows)
+  BRef<real> out;
+  double alpha = 1.0, beta = 0.0;
+};
+template <class real>
+void launch_tsmm(const Batch<real>& b, const TsmmJob<real>& job, cudaStream_t st);
+
+// Residual R = HX - X diag(theta) into W, with per-column partial sums.
+template <class real>
+void launch_residual(const Batch<real>& b, int nchunk, cudaStream_t st);
+// Reduces the partial sums: residual norms, kinetic energies for Teter,
+// convergence and iteration bookkeeping.
+template <class real>
+void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStream_t st);
+// End of an iteration: flip the X/P/HX/HP buffers, mark P valid.
+template <class real>
+void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st);
+
+// dense.cu: FP64 Rayleigh-Ritz on one CTA per task.
+enum { RR_FIXED = 0, RR_INITIAL = 1, RR_LOBPCG = 2 };
+struct RRTask {
+  const double* A;   // n x n (ld), symmetric up to rounding
+  const double* B;   // n x n (ld), symmetric positive definite
+  int ld;
+  int mode;          // RR_FIXED: n = n_fixed; RR_INITIAL: n = m; RR_LOBPCG: 2m or 3m
+  int n_fixed;
+  int m;             // eigenpairs wanted (lowest)
+  double* Y;         // n x m output (ldy); LOBPCG rows of a dropped P are zeroed
+  int ldy;
+  double* theta;     // m
+  double* work;      // rr_work_doubles(n_max, m) doubles
+  int* state;        // element state words, or nullptr
+  double cond_max;   // Cholesky condition limit on the equilibrated B
+};
+size_t rr_work_doubles(int n_max, int m);
+void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st);
+
+// solver-level helpers are in solver.cu
+
+std::string cuda_err_string(cudaError_t e);
+
+}  // namespace dgdft
+
+namespace dgdft {
+// alb.cu
+template <class real>
+void launch_restrict(const real* x, int ng, int nx, int ny, const int* lo, const int* hi, int J, double* out,
+                     cudaStream_t st);
+template <class A, class B>
+void launch_convert(const A* in, B* out, size_t n, cudaStream_t st);
+void launch_scale(double* x, size_t n, double s, cudaStream_t st);
+}  // namespace dgdft

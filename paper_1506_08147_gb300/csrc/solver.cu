@@ -1,0 +1,1276 @@
+// Host runtime of the ALB generator: context, memory admission, per-element
+// device setup, the batched LOBPCG driver (one captured CUDA graph per
+// iteration, replayed for all elements of a wave) and the C-ABI.
+//
+// Flow of dgdft_alb_solve (Sec. II.A; Sec. II.B "Generation of the ALB
+// functions"): elements are admitted in waves that fit the device-memory
+// budget; a wave runs LOBPCG for all its elements at once (inter-element
+// parallelism of the paper becomes the grid's z dimension), then restricts
+// the lowest J Ritz vectors to E_K and orthonormalises them in FP64.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dgdft_alb.h"
+#include "../../include/dgdft_alb_steps.h"
+#include "internal.h"
+
+using namespace dgdft;
+
+namespace dgdft {
+std::string cuda_err_string(cudaError_t e) { return std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e); }
+template <class real>
+void launch_proj_coef(const Batch<real>& b, BRef<real> src, int ncols, cudaStream_t st);
+}  // namespace dgdft
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+struct ElemHost {
+  dgdft_element_desc d{};
+  std::vector<double> veff;
+  bool has_v = false;
+  std::vector<int64_t> prow{0};
+  std::vector<int32_t> pidx;
+  std::vector<double> pval, pgamma;
+  std::vector<double> x0;
+  bool has_x0 = false;
+  // results
+  bool solved = false;
+  std::vector<double> phi, eig, resid, block;
+  dgdft_solve_report rep{};
+  int ng() const { return d.nx * d.ny * d.nz; }
+  int ne() const { return (d.e_hi[0] - d.e_lo[0]) * (d.e_hi[1] - d.e_lo[1]) * (d.e_hi[2] - d.e_lo[2]); }
+  double dv() const { return d.Lx * d.Ly * d.Lz / ng(); }
+};
+
+bool plan_length(int n, FftPlan& p) {
+  p.n = n;
+  p.nstage = 0;
+  int r = n;
+  const int radices[4] = {4, 2, 3, 5};
+  for (int q = 0; q < 4; ++q) {
+    while (r % radices[q] == 0) {
+      if (p.nstage >= MAX_STAGES) return false;
+      p.radix[p.nstage++] = radices[q];
+      r /= radices[q];
+    }
+  }
+  return r == 1 && n >= 2;
+}
+
+std::vector<double> twiddles(int n, int count) {
+  std::vector<double> t(2 * (size_t)count);
+  for (int i = 0; i < count; ++i) {
+    const double a = -2.0 * M_PI * (double)i / (double)n;
+    t[2 * i] = std::cos(a);
+    t[2 * i + 1] = std::sin(a);
+  }
+  return t;
+}
+
+std::vector<double> kinetic_axis(int n, double L, bool half) {
+  const int cnt = half ? n / 2 + 1 : n;
+  std::vector<double> g(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    const int f = (half || i <= n / 2) ? i : i - n;
+    const double k = 2.0 * M_PI * (double)std::abs(f) / L;
+    g[i] = 0.5 * k * k;
+  }
+  return g;
+}
+
+// Device arena: one allocation carved into aligned pieces.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  void* take(size_t bytes) {
+    const size_t off = (used + ALIGN - 1) / ALIGN * ALIGN;
+    if (off + bytes > cap) return nullptr;
+    used = off + bytes;
+    return base + off;
+  }
+};
+
+struct Sizer {
+  size_t total = 0;
+  void add(size_t bytes) { total = (total + ALIGN - 1) / ALIGN * ALIGN + bytes; }
+};
+
+template <class real> struct Wave;
+
+}  // namespace
+
+struct dgdft_alb_ctx {
+  dgdft_alb_config cfg{};
+  std::vector<ElemHost> el;
+  std::string err;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool solved_any = false;
+  dgdft_status fail(dgdft_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+};
+
+
+// Every host<->device copy runs on the context stream and completes before
+// returning, so it is ordered with the library's kernels whatever the
+// stream's flags.
+static cudaError_t ctx_copy(dgdft_alb_ctx* ctx, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(ctx->stream);
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return ctx->fail(DGDFT_ECUDA, std::string(#call) + " -> " + \
+                                                               cuda_err_string(e_)); \
+  } while (0)
+
+namespace {
+
+int nchunk_rows(int ng) { return std::max(1, std::min(256, (ng + 4095) / 4096)); }
+
+// Device footprint of one element in a wave of working precision `real`.
+template <class real>
+size_t elem_bytes(const ElemHost& h) {
+  const dgdft_element_desc& d = h.d;
+  const size_t ng = (size_t)h.ng(), m = (size_t)d.n_compute;
+  const size_t nxh = d.nx / 2 + 1, nspec = nxh * d.ny * d.nz;
+  const size_t np = h.pgamma.size(), nnz = h.pidx.size();
+  Sizer s;
+  s.add(ng * sizeof(real));                               // V
+  s.add(sizeof(cplx_t<real>) * (d.nx / 2 + d.nx + d.ny + d.nz + 4));
+  s.add(sizeof(double) * (nxh + d.ny + d.nz));
+  s.add(sizeof(int) * (np + 1) + sizeof(int) * nnz + sizeof(real) * nnz + sizeof(double) * np);
+  s.add(sizeof(int) * (d.nz + 1) + sizeof(int) * (3 * nnz + 1) + sizeof(real) * nnz);
+  s.add(sizeof(real) * np * m);
+  for (int i = 0; i < 10; ++i) s.add(sizeof(real) * ng * m);
+  s.add(sizeof(cplx_t<real>) * nspec * m);
+  s.add(sizeof(double) * (18 * m * m + m * m + 3 * m * m + 3 * m));
+  s.add(sizeof(double) * rr_work_doubles(3 * (int)m, (int)m));
+  s.add(sizeof(double) * m * nchunk_rows((int)ng) * 4);
+  s.add(sizeof(int) * STATE_WORDS);
+  // share of the Gram partial buffer (12 pairs, 2048-row chunks)
+  const size_t tiles = ((m + 63) / 64) * ((m + 63) / 64);
+  s.add(sizeof(double) * ((ng + 2047) / 2048) * 12 * tiles * 4096);
+  return s.total + 64 * ALIGN;
+}
+
+template <class real> struct Wave {
+  dgdft_alb_ctx* ctx = nullptr;
+  std::vector<int> ids;
+  std::vector<ElemDev<real>> h;
+  Arena arena;
+  ElemDev<real>* d_elems = nullptr;
+  RRTask* d_rr_init = nullptr;
+  RRTask* d_rr_lob = nullptr;
+  double* partial = nullptr;
+  size_t partial_cap = 0;
+  Batch<real> batch;
+  int rnchunk = 1;
+  std::vector<int> h_state;
+
+  ~Wave() {
+    if (arena.base) cudaFree(arena.base);
+  }
+
+  dgdft_status build(dgdft_alb_ctx* c, const std::vector<int>& elem_ids, double cond_max) {
+    ctx = c;
+    ids = elem_ids;
+    const int nel = (int)ids.size();
+    BatchShape s;
+    s.nel = nel;
+    for (int id : ids) {
+      const ElemHost& eh = ctx->el[id];
+      s.max_nz = std::max(s.max_nz, eh.d.nz);
+      s.max_ny = std::max(s.max_ny, eh.d.ny);
+      s.max_nxh = std::max(s.max_nxh, eh.d.nx / 2 + 1);
+      s.max_nplane = std::max(s.max_nplane, (eh.d.nx / 2 + 1) * eh.d.ny);
+      s.max_m = std::max(s.max_m, eh.d.n_compute);
+      s.max_ng = std::max(s.max_ng, eh.ng());
+      s.max_nproj = std::max(s.max_nproj, (int)eh.pgamma.size());
+    }
+    rnchunk = nchunk_rows(s.max_ng);
+    size_t total = 0;
+    for (int id : ids) total += elem_bytes<real>(ctx->el[id]);
+    total += (sizeof(ElemDev<real>) + 2 * sizeof(RRTask)) * nel + 4 * ALIGN;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, total);
+    if (e != cudaSuccess) return ctx->fail(DGDFT_ENOMEM, "device allocation of a wave failed: " + cuda_err_string(e));
+    arena.base = (char*)p;
+    arena.cap = total;
+    // Gram partials: shared by the wave
+    {
+      size_t tiles = ((s.max_m + 63) / 64) * ((s.max_m + 63) / 64);
+      partial_cap = (size_t)nel * ((s.max_ng + 2047) / 2048) * 12 * tiles * 4096;
+      partial = (double*)arena.take(partial_cap * sizeof(double));
+    }
+    d_elems = (ElemDev<real>*)arena.take(sizeof(ElemDev<real>) * nel);
+    d_rr_init = (RRTask*)arena.take(sizeof(RRTask) * nel);
+    d_rr_lob = (RRTask*)arena.take(sizeof(RRTask) * nel);
+    h.resize(nel);
+    std::vector<RRTask> rr_init(nel), rr_lob(nel);
+    h_state.assign((size_t)nel * STATE_WORDS, 0);
+    for (int i = 0; i < nel; ++i) {
+      dgdft_status st = setup_elem(i, ctx->el[ids[i]]);
+      if (st != DGDFT_OK) return st;
+      ElemDev<real>& E = h[i];
+      RRTask t{};
+      t.A = E.gram;
+      t.B = E.gram + (size_t)9 * E.m * E.m;
+      t.ld = 3 * E.m;
+      t.mode = RR_INITIAL;
+      t.n_fixed = E.m;
+      t.m = E.m;
+      t.Y = E.Y;
+      t.ldy = 3 * E.m;
+      t.theta = E.theta;
+      t.work = E.rr_work;
+      t.state = E.state;
+      t.cond_max = cond_max;
+      rr_init[i] = t;
+      t.mode = RR_LOBPCG;
+      rr_lob[i] = t;
+    }
+    CK(ctx_copy(ctx, d_elems, h.data(), sizeof(ElemDev<real>) * nel, cudaMemcpyHostToDevice));
+    CK(ctx_copy(ctx, d_rr_init, rr_init.data(), sizeof(RRTask) * nel, cudaMemcpyHostToDevice));
+    CK(ctx_copy(ctx, d_rr_lob, rr_lob.data(), sizeof(RRTask) * nel, cudaMemcpyHostToDevice));
+    batch.d_elems = d_elems;
+    batch.s = s;
+    return DGDFT_OK;
+  }
+
+  template <class T> T* take(size_t count) { return (T*)arena.take(sizeof(T) * std::max<size_t>(count, 1)); }
+
+  template <class T> dgdft_status put(T* dst, const T* src, size_t count) {
+    if (count) CK(ctx_copy(ctx, dst, src, sizeof(T) * count, cudaMemcpyHostToDevice));
+    return DGDFT_OK;
+  }
+
+  dgdft_status setup_elem(int i, const ElemHost& eh) {
+    using C = cplx_t<real>;
+    const dgdft_element_desc& d = eh.d;
+    ElemDev<real>& E = h[i];
+    std::memset(&E, 0, sizeof(E));
+    E.nx = d.nx;
+    E.ny = d.ny;
+    E.nz = d.nz;
+    E.ng = eh.ng();
+    E.nh = d.nx / 2;
+    E.nxh = d.nx / 2 + 1;
+    E.nspec = E.nxh * d.ny * d.nz;
+    E.m = d.n_compute;
+    E.J = d.n_keep;
+    E.scale = 2.0 / (double)E.ng;
+    E.tol = ctx->cfg.tol;
+    plan_length(E.nh, E.px);
+    plan_length(d.ny, E.py);
+    plan_length(d.nz, E.pz);
+    const size_t ng = E.ng, m = E.m;
+    // potential
+    std::vector<real> vr(eh.veff.begin(), eh.veff.end());
+    real* V = take<real>(ng);
+    if (put(V, vr.data(), ng) != DGDFT_OK) return DGDFT_ECUDA;
+    E.V = V;
+    // twiddles
+    auto put_tw = [&](int n, int count) -> const C* {
+      std::vector<double> t = twiddles(n, count);
+      std::vector<C> tc(count);
+      for (int q = 0; q < count; ++q) tc[q] = cmake<C>((real)t[2 * q], (real)t[2 * q + 1]);
+      C* dp = take<C>(count);
+      if (put(dp, tc.data(), count) != DGDFT_OK) return nullptr;
+      return dp;
+    };
+    E.tw_h = put_tw(E.nh, E.nh);
+    E.tw_x = put_tw(d.nx, E.nh + 1);
+    E.tw_y = put_tw(d.ny, d.ny);
+    E.tw_z = put_tw(d.nz, d.nz);
+    auto put_g = [&](const std::vector<double>& g) -> const double* {
+      double* dp = take<double>(g.size());
+      if (put(dp, g.data(), g.size()) != DGDFT_OK) return nullptr;
+      return dp;
+    };
+    E.gx2 = put_g(kinetic_axis(d.nx, d.Lx, true));
+    E.gy2 = put_g(kinetic_axis(d.ny, d.Ly, false));
+    E.gz2 = put_g(kinetic_axis(d.nz, d.Lz, false));
+    if (!E.tw_h || !E.tw_x || !E.tw_y || !E.tw_z || !E.gx2 || !E.gy2 || !E.gz2) return DGDFT_ECUDA;
+    // projectors, CSR by projector
+    const int np = (int)eh.pgamma.size();
+    const size_t nnz = eh.pidx.size();
+    E.n_proj = np;
+    {
+      std::vector<int> pp(np + 1);
+      for (int q = 0; q <= np; ++q) pp[q] = (int)eh.prow[q];
+      std::vector<real> pv(eh.pval.begin(), eh.pval.end());
+      int* dpp = take<int>(np + 1);
+      int* dpi = take<int>(nnz);
+      real* dpv = take<real>(nnz);
+      double* dpg = take<double>(np);
+      if (put(dpp, pp.data(), np + 1) || put(dpi, eh.pidx.data(), nnz) || put(dpv, pv.data(), nnz) ||
+          put(dpg, eh.pgamma.data(), (size_t)np))
+        return DGDFT_ECUDA;
+      E.p_ptr = dpp;
+      E.p_idx = dpi;
+      E.p_val = dpv;
+      E.p_gamma = dpg;
+      // grouped by grid point: (idx, proj, gamma * val), sorted by idx
+      std::vector<std::pair<int, int>> ent(nnz);  // (idx, position)
+      std::vector<int> owner(nnz);
+      for (int q = 0; q < np; ++q)
+        for (int64_t k = eh.prow[q]; k < eh.prow[q + 1]; ++k) owner[k] = q;
+      for (size_t k = 0; k < nnz; ++k) ent[k] = {eh.pidx[k], (int)k};
+      std::sort(ent.begin(), ent.end());
+      std::vector<int> s_off, s_ptr{0}, s_proj(nnz), s_plane(d.nz + 1, 0);
+      std::vector<real> s_gv(nnz);
+      const int plane = d.nx * d.ny;
+      for (size_t k = 0; k < nnz; ++k) {
+        const int g = ent[k].first, pos = ent[k].second;
+        if (k == 0 || g != ent[k - 1].first) {
+          if (k) s_ptr.push_back((int)k);
+          s_off.push_back(g % plane);
+          s_plane[g / plane + 1] += 1;
+        }
+        s_proj[k] = owner[pos];
+        s_gv[k] = (real)(eh.pgamma[owner[pos]] * eh.pval[pos]);
+      }
+      if (nnz) s_ptr.push_back((int)nnz);
+      for (int z = 0; z < d.nz; ++z) s_plane[z + 1] += s_plane[z];
+      E.n_sup = (int)s_off.size();
+      int* dsp = take<int>(d.nz + 1);
+      int* dso = take<int>(s_off.size());
+      int* dsptr = take<int>(s_ptr.size());
+      int* dspj = take<int>(nnz);
+      real* dsg = take<real>(nnz);
+      if (put(dsp, s_plane.data(), s_plane.size()) || put(dso, s_off.data(), s_off.size()) ||
+          put(dsptr, s_ptr.data(), s_ptr.size()) || put(dspj, s_proj.data(), nnz) || put(dsg, s_gv.data(), nnz))
+        return DGDFT_ECUDA;
+      E.s_plane = dsp;
+      E.s_off = dso;
+      E.s_ptr = dsptr;
+      E.s_proj = dspj;
+      E.s_gv = dsg;
+      E.Ccoef = take<real>((size_t)np * m);
+    }
+    for (int b = 0; b < NBLK; ++b) {
+      E.blk[b][0] = take<real>(ng * m);
+      E.blk[b][1] = (b < NDBL) ? take<real>(ng * m) : E.blk[b][0];
+    }
+    E.Z = take<C>((size_t)E.nspec * m);
+    E.gram = take<double>(18 * m * m);
+    E.gxw = take<double>(m * m);
+    E.Y = take<double>(3 * m * m);
+    E.theta = take<double>(m);
+    E.res = take<double>(m);
+    E.tkin = take<double>(m);
+    E.rr_work = take<double>(rr_work_doubles(3 * (int)m, (int)m));
+    E.rpart = take<double>(m * rnchunk * 4);
+    E.state = take<int>(STATE_WORDS);
+    if (!E.state || !E.rpart || !E.rr_work || !E.Z) return ctx->fail(DGDFT_ENOMEM, "wave arena exhausted");
+    return DGDFT_OK;
+  }
+
+  dgdft_status upload_x0(int i, const double* x0_host) {
+    ElemDev<real>& E = h[i];
+    const size_t n = (size_t)E.ng * E.m;
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, n * sizeof(double)));
+    cudaError_t e = ctx_copy(ctx, tmp, x0_host, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      launch_convert<double, real>(tmp, E.blk[BX][0], n, ctx->stream);
+      e = cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(tmp);
+    if (e != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "initial block upload: " + cuda_err_string(e));
+    return DGDFT_OK;
+  }
+
+  dgdft_status reset_states(double tol) {
+    const int nel = (int)ids.size();
+    for (int i = 0; i < nel; ++i) {
+      int* s = &h_state[(size_t)i * STATE_WORDS];
+      std::fill(s, s + STATE_WORDS, 0);
+      s[ST_ACTIVE] = 1;
+      h[i].tol = tol;
+    }
+    CK(ctx_copy(ctx, d_elems, h.data(), sizeof(ElemDev<real>) * nel, cudaMemcpyHostToDevice));
+    for (int i = 0; i < nel; ++i)
+      CK(ctx_copy(ctx, h[i].state, &h_state[(size_t)i * STATE_WORDS], sizeof(int) * STATE_WORDS,
+                    cudaMemcpyHostToDevice));
+    return DGDFT_OK;
+  }
+
+  dgdft_status read_states() {
+    for (size_t i = 0; i < ids.size(); ++i)
+      CK(cudaMemcpyAsync(&h_state[i * STATE_WORDS], h[i].state, sizeof(int) * STATE_WORDS,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DGDFT_OK;
+  }
+
+  GramJob<real> gram12() const {
+    GramJob<real> g;
+    const int A_[6][4] = {{BX, BHX, 0, 0}, {BX, BHW, 0, 1}, {BX, BHP, 0, 2},
+                          {BW, BHW, 1, 1}, {BW, BHP, 1, 2}, {BP, BHP, 2, 2}};
+    const int B_[6][4] = {{BX, BX, 0, 0}, {BX, BW, 0, 1}, {BX, BP, 0, 2},
+                          {BW, BW, 1, 1}, {BW, BP, 1, 2}, {BP, BP, 2, 2}};
+    g.npairs = 12;
+    for (int q = 0; q < 6; ++q) {
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int(*T)[4] = h2 ? B_ : A_;
+        const int k = q + 6 * h2;
+        g.a[k] = bref<real>(T[q][0]);
+        g.b[k] = bref<real>(T[q][1]);
+        g.needs_p[k] = (T[q][0] == BP || T[q][1] == BP || T[q][1] == BHP);
+        g.out_id[k] = h2 ? OUT_GRAM_B : OUT_GRAM_A;
+        g.brow[k] = T[q][2];
+        g.bcol[k] = T[q][3];
+      }
+    }
+    return g;
+  }
+
+  void enqueue_initial(cudaStream_t st) {
+    launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st);
+    GramJob<real> g;
+    g.npairs = 2;
+    g.a[0] = bref<real>(BX);
+    g.b[0] = bref<real>(BHX);
+    g.out_id[0] = OUT_GRAM_A;
+    g.a[1] = bref<real>(BX);
+    g.b[1] = bref<real>(BX);
+    g.out_id[1] = OUT_GRAM_B;
+    for (int k = 0; k < 2; ++k) g.needs_p[k] = g.brow[k] = g.bcol[k] = 0;
+    launch_gram<real>(batch, g, partial, partial_cap, st);
+    launch_rr(d_rr_init, batch.s.nel, st);
+    TsmmJob<real> t;
+    t.nin = 1;
+    t.in[0] = bref<real>(BX);
+    t.out = bref<real>(BX, 1);
+    launch_tsmm<real>(batch, t, st);
+    t.in[0] = bref<real>(BHX);
+    t.out = bref<real>(BHX, 1);
+    launch_tsmm<real>(batch, t, st);
+    launch_iter_finish<real>(batch, 0, st);
+  }
+
+  void enqueue_iteration(cudaStream_t st, int maxit) {
+    if (batch.s.max_nproj > 0) launch_proj_coef<real>(batch, bref<real>(BX), 0, st);
+    launch_residual<real>(batch, rnchunk, st);
+    launch_post_residual<real>(batch, rnchunk, maxit, st);
+    launch_teter<real>(batch, bref<real>(BW), bref<real>(BW), nullptr, 0, st);
+    {
+      GramJob<real> g;
+      g.npairs = 1;
+      g.a[0] = bref<real>(BX);
+      g.b[0] = bref<real>(BW);
+      g.needs_p[0] = 0;
+      g.out_id[0] = OUT_GXW;
+      g.brow[0] = g.bcol[0] = 0;
+      launch_gram<real>(batch, g, partial, partial_cap, st);
+      TsmmJob<real> t;
+      t.nin = 1;
+      t.in[0] = bref<real>(BX);
+      t.y_id = Y_GXW;
+      t.out = bref<real>(BW);
+      t.alpha = -1.0;
+      t.beta = 1.0;
+      launch_tsmm<real>(batch, t, st);
+    }
+    launch_apply_h<real>(batch, bref<real>(BW), bref<real>(BHW), 0, st);
+    launch_gram<real>(batch, gram12(), partial, partial_cap, st);
+    launch_rr(d_rr_lob, batch.s.nel, st);
+    {
+      TsmmJob<real> t;
+      t.nin = 3;
+      t.in[0] = bref<real>(BX);
+      t.in[1] = bref<real>(BW);
+      t.in[2] = bref<real>(BP);
+      t.yrow[0] = 0;
+      t.yrow[1] = 1;
+      t.yrow[2] = 2;
+      t.needs_p[2] = 1;
+      t.out = bref<real>(BX, 1);
+      launch_tsmm<real>(batch, t, st);
+      t.in[0] = bref<real>(BHX);
+      t.in[1] = bref<real>(BHW);
+      t.in[2] = bref<real>(BHP);
+      t.out = bref<real>(BHX, 1);
+      launch_tsmm<real>(batch, t, st);
+      TsmmJob<real> u;
+      u.nin = 2;
+      u.in[0] = bref<real>(BW);
+      u.in[1] = bref<real>(BP);
+      u.yrow[0] = 1;
+      u.yrow[1] = 2;
+      u.needs_p[1] = 1;
+      u.out = bref<real>(BP, 1);
+      launch_tsmm<real>(batch, u, st);
+      u.in[0] = bref<real>(BHW);
+      u.in[1] = bref<real>(BHP);
+      u.out = bref<real>(BHP, 1);
+      launch_tsmm<real>(batch, u, st);
+    }
+    launch_iter_finish<real>(batch, 1, st);
+  }
+
+  // LOBPCG for every element of the wave; stall_window > 0 stops an element
+  // whose max residual has not halved over that many polls.
+  dgdft_status run(double tol, int maxit, int stall_window, std::vector<double>* res_out) {
+    cudaStream_t st = ctx->stream;
+    dgdft_status s = reset_states(tol);
+    if (s != DGDFT_OK) return s;
+    enqueue_initial(st);
+    CK(cudaGetLastError());
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(st, maxit);
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (ce != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "graph capture: " + cuda_err_string(ce));
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "graph instantiate: " + cuda_err_string(ce));
+    const int nel = (int)ids.size();
+    const int every = std::max(1, ctx->cfg.check_every);
+    std::vector<std::vector<double>> hist(nel);
+    std::vector<double> resbuf;
+    int launched = 0;
+    dgdft_status rs = DGDFT_OK;
+    while (launched <= maxit + 1) {
+      for (int k = 0; k < every && launched <= maxit + 1; ++k, ++launched) {
+        ce = cudaGraphLaunch(exec, st);
+        if (ce != cudaSuccess) break;
+      }
+      if (ce != cudaSuccess) break;
+      if ((rs = read_states()) != DGDFT_OK) break;
+      bool any = false;
+      for (int i = 0; i < nel; ++i) {
+        int* sw = &h_state[(size_t)i * STATE_WORDS];
+        if (!sw[ST_ACTIVE]) continue;
+        any = true;
+        if (stall_window > 0) {
+          resbuf.resize(h[i].J);
+          ce = ctx_copy(ctx, resbuf.data(), h[i].res, sizeof(double) * h[i].J, cudaMemcpyDeviceToHost);
+          if (ce != cudaSuccess) break;
+          const double mx = *std::max_element(resbuf.begin(), resbuf.end());
+          hist[i].push_back(mx);
+          const size_t L = hist[i].size();
+          if (L > (size_t)stall_window && mx > 0.5 * hist[i][L - 1 - stall_window]) {
+            int zero = 0;
+            ce = ctx_copy(ctx, h[i].state + ST_ACTIVE, &zero, sizeof(int), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) break;
+          }
+        }
+      }
+      if (ce != cudaSuccess || !any) break;
+    }
+    cudaGraphExecDestroy(exec);
+    if (ce != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "LOBPCG iteration: " + cuda_err_string(ce));
+    if (rs != DGDFT_OK) return rs;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (res_out) {
+      res_out->clear();
+      for (int i = 0; i < nel; ++i) {
+        std::vector<double> r(h[i].m);
+        CK(ctx_copy(ctx, r.data(), h[i].res, sizeof(double) * h[i].m, cudaMemcpyDeviceToHost));
+        res_out->insert(res_out->end(), r.begin(), r.end());
+      }
+    }
+    return read_states();
+  }
+
+  const real* current_x(int i) const {
+    return h[i].blk[BX][h_state[(size_t)i * STATE_WORDS + ST_PARITY] & 1];
+  }
+};
+
+// Seeded standard-normal default initial block (splitmix64 + Box-Muller).
+void default_x0(std::vector<double>& x, int elem) {
+  uint64_t s = 0x9E3779B97F4A7C15ull * (uint64_t)(elem + 1);
+  auto next = [&]() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  for (size_t i = 0; i < x.size(); i += 2) {
+    const double u1 = next(), u2 = next();
+    const double r = std::sqrt(-2.0 * std::log(u1));
+    x[i] = r * std::cos(2.0 * M_PI * u2);
+    if (i + 1 < x.size()) x[i + 1] = r * std::sin(2.0 * M_PI * u2);
+  }
+}
+
+// FP64 restriction + orthonormalisation of one element's converged block.
+dgdft_status alb_orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, int i, const double* x, int J,
+                                double* phi_dev_out) {
+  ElemHost& eh = ctx->el[w.ids[i]];
+  const int ne = eh.ne();
+  cudaStream_t st = ctx->stream;
+  // scratch: phi_t, U (ne x J), G, G2, Aid, Adiag, Y1, Y2 (J x J), theta, rr work, task
+  const size_t jj = (size_t)J * J;
+  const size_t nbytes = sizeof(double) * (2 * (size_t)ne * J + 6 * jj + J + rr_work_doubles(J, J)) +
+                        2 * sizeof(RRTask) + 16 * ALIGN;
+  void* base = nullptr;
+  CK(cudaMalloc(&base, nbytes));
+  std::unique_ptr<void, decltype(&cudaFree)> guard(base, &cudaFree);
+  Arena a;
+  a.base = (char*)base;
+  a.cap = nbytes;
+  double* phit = (double*)a.take(sizeof(double) * ne * J);
+  double* U = (double*)a.take(sizeof(double) * ne * J);
+  double* G = (double*)a.take(sizeof(double) * jj);
+  double* G2 = (double*)a.take(sizeof(double) * jj);
+  double* Aid = (double*)a.take(sizeof(double) * jj);
+  double* Adg = (double*)a.take(sizeof(double) * jj);
+  double* Y1 = (double*)a.take(sizeof(double) * jj);
+  double* Y2 = (double*)a.take(sizeof(double) * jj);
+  double* th = (double*)a.take(sizeof(double) * J);
+  double* work = (double*)a.take(sizeof(double) * rr_work_doubles(J, J));
+  RRTask* dt = (RRTask*)a.take(2 * sizeof(RRTask));
+  std::vector<double> id(jj, 0.0), dg(jj, 0.0);
+  for (int q = 0; q < J; ++q) {
+    id[q + (size_t)q * J] = 1.0;
+    dg[q + (size_t)q * J] = 1.0 + q;
+  }
+  CK(ctx_copy(ctx, Aid, id.data(), sizeof(double) * jj, cudaMemcpyHostToDevice));
+  CK(ctx_copy(ctx, Adg, dg.data(), sizeof(double) * jj, cudaMemcpyHostToDevice));
+  RRTask t[2]{};
+  for (int q = 0; q < 2; ++q) {
+    t[q].A = q ? Adg : Aid;
+    t[q].B = q ? G2 : G;
+    t[q].ld = J;
+    t[q].mode = RR_FIXED;
+    t[q].n_fixed = J;
+    t[q].m = J;
+    t[q].Y = q ? Y2 : Y1;
+    t[q].ldy = J;
+    t[q].theta = th;
+    t[q].work = work;
+    t[q].state = nullptr;
+    t[q].cond_max = 1e30;
+  }
+  CK(ctx_copy(ctx, dt, t, sizeof(t), cudaMemcpyHostToDevice));
+  // single-element view of the wave, element marked active for the step
+  Batch<double> one;
+  one.d_elems = w.d_elems + i;
+  one.s = w.batch.s;
+  one.s.nel = 1;
+  int act = 1;
+  CK(ctx_copy(ctx, w.h[i].state + ST_ACTIVE, &act, sizeof(int), cudaMemcpyHostToDevice));
+  const dgdft_element_desc& d = eh.d;
+  launch_restrict<double>(x, eh.ng(), d.nx, d.ny, d.e_lo, d.e_hi, J, phit, st);
+  GramJob<double> g;
+  g.npairs = 1;
+  g.a[0] = bptr<double>(phit);
+  g.b[0] = bptr<double>(phit);
+  g.needs_p[0] = 0;
+  g.out_id[0] = OUT_PTR;
+  g.brow[0] = g.bcol[0] = 0;
+  g.ncols_a = g.ncols_b = J;
+  g.rows = ne;
+  g.ld_in = ne;
+  g.ld_out = J;
+  g.out_ptr = G;
+  launch_gram<double>(one, g, w.partial, w.partial_cap, st);
+  launch_rr(dt, 1, st);
+  TsmmJob<double> u;
+  u.nin = 1;
+  u.in[0] = bptr<double>(phit);
+  u.y_id = Y_PTR;
+  u.y_ptr = Y1;
+  u.ldy = J;
+  u.ncols = J;
+  u.rows = ne;
+  u.ld_in = ne;
+  u.out = bptr<double>(U);
+  launch_tsmm<double>(one, u, st);
+  g.a[0] = bptr<double>(U);
+  g.b[0] = bptr<double>(U);
+  g.out_ptr = G2;
+  launch_gram<double>(one, g, w.partial, w.partial_cap, st);
+  launch_rr(dt + 1, 1, st);
+  u.in[0] = bptr<double>(U);
+  u.y_ptr = Y2;
+  u.out = bptr<double>(phi_dev_out);
+  launch_tsmm<double>(one, u, st);
+  launch_scale(phi_dev_out, (size_t)ne * J, 1.0 / std::sqrt(eh.dv()), st);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  double chk = 0.0;
+  CK(ctx_copy(ctx, &chk, th, sizeof(double), cudaMemcpyDeviceToHost));
+  act = 0;
+  CK(ctx_copy(ctx, w.h[i].state + ST_ACTIVE, &act, sizeof(int), cudaMemcpyHostToDevice));
+  if (!std::isfinite(chk)) return ctx->fail(DGDFT_ENOTCONV, "orthonormalisation: restricted block is rank deficient");
+  return DGDFT_OK;
+}
+
+template <class real>
+dgdft_status copy_block_to(Wave<real>& w, int i, Wave<double>& dst, int di, cudaStream_t st) {
+  const ElemDev<real>& E = w.h[i];
+  launch_convert<real, double>(w.current_x(i), dst.h[di].blk[BX][0], (size_t)E.ng * E.m, st);
+  return DGDFT_OK;
+}
+
+dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, double seconds,
+                         const std::vector<int>& extra_iters, const std::vector<int>& extra_fb) {
+  cudaStream_t st = ctx->stream;
+  for (size_t i = 0; i < w.ids.size(); ++i) {
+    ElemHost& eh = ctx->el[w.ids[i]];
+    const ElemDev<double>& E = w.h[i];
+    const int* sw = &w.h_state[i * STATE_WORDS];
+    const int J = E.J, m = E.m, ne = eh.ne();
+    double* phi_dev = nullptr;
+    CK(cudaMalloc(&phi_dev, sizeof(double) * (size_t)ne * J));
+    std::unique_ptr<void, decltype(&cudaFree)> guard(phi_dev, &cudaFree);
+    const double* x = w.current_x((int)i);
+    dgdft_status s = alb_orthonormalise(ctx, w, (int)i, x, J, phi_dev);
+    if (s != DGDFT_OK && s != DGDFT_ENOTCONV) return s;
+    eh.phi.resize((size_t)ne * J);
+    CK(ctx_copy(ctx, eh.phi.data(), phi_dev, sizeof(double) * eh.phi.size(), cudaMemcpyDeviceToHost));
+    std::vector<double> th(m), rs(m);
+    CK(ctx_copy(ctx, th.data(), E.theta, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    CK(ctx_copy(ctx, rs.data(), E.res, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    eh.eig.assign(th.begin(), th.begin() + J);
+    eh.resid.assign(rs.begin(), rs.begin() + J);
+    if (ctx->cfg.keep_block) {
+      eh.block.resize((size_t)eh.ng() * m);
+      CK(ctx_copy(ctx, eh.block.data(), x, sizeof(double) * eh.block.size(), cudaMemcpyDeviceToHost));
+    } else {
+      eh.block.clear();
+    }
+    double mx = 0.0;
+    for (double r : eh.resid) mx = std::max(mx, r);
+    eh.rep.iterations = sw[ST_ITER] + (extra_iters.empty() ? 0 : extra_iters[i]);
+    eh.rep.fallbacks = sw[ST_FALLBACK] + (extra_fb.empty() ? 0 : extra_fb[i]);
+    eh.rep.max_resid = mx;
+    eh.rep.wave = wave_idx;
+    eh.rep.seconds = seconds;
+    eh.rep.status = (sw[ST_ERROR] != 0) ? DGDFT_ENOTCONV : (mx <= ctx->cfg.tol ? DGDFT_OK : DGDFT_ENOTCONV);
+    eh.solved = true;
+    (void)st;
+  }
+  return DGDFT_OK;
+}
+
+dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wave_idx) {
+  auto t0 = std::chrono::steady_clock::now();
+  const dgdft_alb_config& c = ctx->cfg;
+  std::vector<double> x0;
+  Wave<double> w64;
+  std::vector<int> it32, fb32;
+  if (c.precision == DGDFT_PREC_MIXED) {
+    // stage 1: FP32 storage and arithmetic, FP64 Rayleigh-Ritz
+    std::unique_ptr<Wave<float>> w32(new Wave<float>());
+    dgdft_status s = w32->build(ctx, ids, 1e7);
+    if (s != DGDFT_OK) return s;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      ElemHost& eh = ctx->el[ids[i]];
+      const double* src = eh.x0.data();
+      if (!eh.has_x0) {
+        x0.assign((size_t)eh.ng() * eh.d.n_compute, 0.0);
+        default_x0(x0, ids[i]);
+        src = x0.data();
+      }
+      if ((s = w32->upload_x0((int)i, src)) != DGDFT_OK) return s;
+    }
+    const double tol1 = std::max(10.0 * c.tol, 1e-5);
+    if ((s = w32->run(tol1, c.maxit, 6, nullptr)) != DGDFT_OK) return s;
+    if ((s = w64.build(ctx, ids, 1e14)) != DGDFT_OK) return s;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      copy_block_to<float>(*w32, (int)i, w64, (int)i, ctx->stream);
+      it32.push_back(w32->h_state[i * STATE_WORDS + ST_ITER]);
+      fb32.push_back(w32->h_state[i * STATE_WORDS + ST_FALLBACK]);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    w32.reset();
+  } else {
+    dgdft_status s = w64.build(ctx, ids, 1e14);
+    if (s != DGDFT_OK) return s;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      ElemHost& eh = ctx->el[ids[i]];
+      const double* src = eh.x0.data();
+      if (!eh.has_x0) {
+        x0.assign((size_t)eh.ng() * eh.d.n_compute, 0.0);
+        default_x0(x0, ids[i]);
+        src = x0.data();
+      }
+      if ((s = w64.upload_x0((int)i, src)) != DGDFT_OK) return s;
+    }
+  }
+  dgdft_status s = w64.run(c.tol, c.maxit, 0, nullptr);
+  if (s != DGDFT_OK) return s;
+  auto t1 = std::chrono::steady_clock::now();
+  const double secs = std::chrono::duration<double>(t1 - t0).count();
+  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+
+extern "C" {
+
+void dgdft_alb_config_init(dgdft_alb_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = DGDFT_PREC_FP64;
+  cfg->precond = DGDFT_PRECOND_TETER;
+  cfg->tol = 1e-6;
+  cfg->maxit = 400;
+  cfg->check_every = 4;
+  cfg->hbm_cap_bytes = 0;
+  cfg->cuda_stream = nullptr;
+  cfg->device = -1;
+  cfg->keep_block = 0;
+}
+
+dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgdft_element_desc* elems,
+                              dgdft_alb_ctx** out) {
+  if (!out) return DGDFT_EINVAL;
+  *out = nullptr;
+  if (!cfg || n_elem <= 0 || !elems) return DGDFT_EINVAL;
+  if (cfg->precision != DGDFT_PREC_FP64 && cfg->precision != DGDFT_PREC_MIXED) return DGDFT_EINVAL;
+  if (cfg->precond != DGDFT_PRECOND_TETER && cfg->precond != DGDFT_PRECOND_LEARNED) return DGDFT_EINVAL;
+  if (!(cfg->tol > 0.0) || cfg->maxit <= 0) return DGDFT_EINVAL;
+  for (int i = 0; i < n_elem; ++i) {
+    const dgdft_element_desc& d = elems[i];
+    FftPlan p;
+    if (d.nx < 4 || d.nx % 2 || !plan_length(d.nx / 2, p) || !plan_length(d.ny, p) || !plan_length(d.nz, p))
+      return DGDFT_EINVAL;
+    if (!(d.Lx > 0 && d.Ly > 0 && d.Lz > 0)) return DGDFT_EINVAL;
+    if (d.n_keep <= 0 || d.n_keep > d.n_compute) return DGDFT_EINVAL;
+    const long long ng = (long long)d.nx * d.ny * d.nz;
+    if (ng > (1ll << 30) || 3ll * d.n_compute > ng) return DGDFT_EINVAL;
+    const int n3[3] = {d.nx, d.ny, d.nz};
+    long long ne = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (d.e_lo[a] < 0 || d.e_hi[a] > n3[a] || d.e_lo[a] >= d.e_hi[a]) return DGDFT_EINVAL;
+      ne *= d.e_hi[a] - d.e_lo[a];
+    }
+    if (ne < d.n_keep) return DGDFT_EINVAL;
+  }
+  std::unique_ptr<dgdft_alb_ctx> ctx(new dgdft_alb_ctx());
+  ctx->cfg = *cfg;
+  if (ctx->cfg.check_every < 1) ctx->cfg.check_every = 1;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DGDFT_ECUDA;
+  int dev = cfg->device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return DGDFT_ECUDA;
+  if (dev >= ndev || cudaSetDevice(dev) != cudaSuccess) return DGDFT_ECUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return DGDFT_ECUDA;
+  if (prop.major != 10 || prop.minor != 3) return DGDFT_ECUDA;
+  ctx->device = dev;
+  if (cfg->cuda_stream) {
+    ctx->stream = (cudaStream_t)cfg->cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return DGDFT_ECUDA;
+    ctx->own_stream = true;
+  }
+  init_hamiltonian_kernels();
+  ctx->el.resize(n_elem);
+  for (int i = 0; i < n_elem; ++i) ctx->el[i].d = elems[i];
+  *out = ctx.release();
+  return DGDFT_OK;
+}
+
+static dgdft_status copy_in(dgdft_alb_ctx* ctx, std::vector<double>& dst, const double* src, size_t n,
+                            int on_device) {
+  dst.resize(n);
+  if (on_device) {
+    CK(ctx_copy(ctx, dst.data(), src, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(dst.data(), src, sizeof(double) * n);
+  }
+  for (double v : dst)
+    if (!std::isfinite(v)) return ctx->fail(DGDFT_EINVAL, "non-finite input value");
+  return DGDFT_OK;
+}
+
+dgdft_status dgdft_alb_set_potential(dgdft_alb_ctx* ctx, int elem, const double* veff, int on_device) {
+  if (!ctx || !veff || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  ElemHost& eh = ctx->el[elem];
+  dgdft_status s = copy_in(ctx, eh.veff, veff, (size_t)eh.ng(), on_device);
+  eh.has_v = (s == DGDFT_OK);
+  eh.solved = false;
+  return s;
+}
+
+dgdft_status dgdft_alb_set_projectors(dgdft_alb_ctx* ctx, int elem, int n_proj, const int64_t* row_ptr,
+                                      const int32_t* grid_idx, const double* val, const double* gamma) {
+  if (!ctx || elem < 0 || elem >= (int)ctx->el.size() || n_proj < 0) return DGDFT_EINVAL;
+  ElemHost& eh = ctx->el[elem];
+  if (n_proj == 0) {
+    eh.prow.assign(1, 0);
+    eh.pidx.clear();
+    eh.pval.clear();
+    eh.pgamma.clear();
+    return DGDFT_OK;
+  }
+  if (!row_ptr || !gamma) return DGDFT_EINVAL;
+  if (row_ptr[0] != 0) return ctx->fail(DGDFT_EINVAL, "row_ptr[0] must be 0");
+  for (int p = 0; p < n_proj; ++p)
+    if (row_ptr[p + 1] < row_ptr[p]) return ctx->fail(DGDFT_EINVAL, "row_ptr not monotone");
+  const int64_t nnz = row_ptr[n_proj];
+  if (nnz > (1ll << 30) || (nnz > 0 && (!grid_idx || !val))) return DGDFT_EINVAL;
+  const int ng = eh.ng();
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (grid_idx[k] < 0 || grid_idx[k] >= ng) return ctx->fail(DGDFT_EINVAL, "projector index outside the grid");
+    if (!std::isfinite(val[k])) return ctx->fail(DGDFT_EINVAL, "non-finite projector value");
+  }
+  for (int p = 0; p < n_proj; ++p)
+    if (!std::isfinite(gamma[p])) return ctx->fail(DGDFT_EINVAL, "non-finite projector weight");
+  // duplicate indices within one projector would double-count a point
+  for (int p = 0; p < n_proj; ++p) {
+    std::vector<int32_t> v(grid_idx + row_ptr[p], grid_idx + row_ptr[p + 1]);
+    std::sort(v.begin(), v.end());
+    if (std::adjacent_find(v.begin(), v.end()) != v.end())
+      return ctx->fail(DGDFT_EINVAL, "duplicate grid index inside one projector");
+  }
+  eh.prow.assign(row_ptr, row_ptr + n_proj + 1);
+  eh.pidx.assign(grid_idx, grid_idx + nnz);
+  eh.pval.assign(val, val + nnz);
+  eh.pgamma.assign(gamma, gamma + n_proj);
+  eh.solved = false;
+  return DGDFT_OK;
+}
+
+dgdft_status dgdft_alb_set_initial(dgdft_alb_ctx* ctx, int elem, const double* x0, int on_device) {
+  if (!ctx || !x0 || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  ElemHost& eh = ctx->el[elem];
+  dgdft_status s = copy_in(ctx, eh.x0, x0, (size_t)eh.ng() * eh.d.n_compute, on_device);
+  eh.has_x0 = (s == DGDFT_OK);
+  return s;
+}
+
+dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem) {
+  if (!ctx) return DGDFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<int> todo;
+  for (int i = 0; i < (int)ctx->el.size(); ++i) {
+    if (!ctx->el[i].has_v) return ctx->fail(DGDFT_ESTATE, "element without potential");
+    todo.push_back(i);
+  }
+  size_t cap = ctx->cfg.hbm_cap_bytes;
+  if (cap == 0) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    cap = (size_t)(0.9 * (double)fr);
+  }
+  // waves admitted by device-memory footprint (greedy, in element order)
+  std::vector<std::vector<int>> waves;
+  size_t acc = 0;
+  for (int id : todo) {
+    const ElemHost& eh = ctx->el[id];
+    size_t b = elem_bytes<double>(eh);
+    if (ctx->cfg.precision == DGDFT_PREC_MIXED) b += elem_bytes<float>(eh);
+    if (b > cap) return ctx->fail(DGDFT_ENOMEM, "one element exceeds the device-memory budget");
+    if (waves.empty() || acc + b > cap) {
+      waves.emplace_back();
+      acc = 0;
+    }
+    waves.back().push_back(id);
+    acc += b;
+  }
+  for (size_t w = 0; w < waves.size(); ++w) {
+    dgdft_status s = solve_wave(ctx, waves[w], (int)w);
+    if (s != DGDFT_OK) return s;
+  }
+  ctx->solved_any = true;
+  dgdft_status out = DGDFT_OK;
+  for (int i = 0; i < (int)ctx->el.size(); ++i) {
+    if (per_elem) per_elem[i] = ctx->el[i].rep;
+    if (ctx->el[i].rep.status != DGDFT_OK) out = DGDFT_ENOTCONV;
+  }
+  if (out != DGDFT_OK) ctx->err = "some elements did not reach the tolerance";
+  return out;
+}
+
+dgdft_status dgdft_alb_get_basis(dgdft_alb_ctx* ctx, int elem, double* phi, double* eig, double* resid,
+                                 int on_device) {
+  if (!ctx || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  ElemHost& eh = ctx->el[elem];
+  if (!eh.solved) return ctx->fail(DGDFT_ESTATE, "get_basis before solve");
+  auto out = [&](double* dst, const std::vector<double>& src) -> dgdft_status {
+    if (!dst) return DGDFT_OK;
+    if (on_device) {
+      CK(ctx_copy(ctx, dst, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(dst, src.data(), sizeof(double) * src.size());
+    }
+    return DGDFT_OK;
+  };
+  dgdft_status s;
+  if ((s = out(phi, eh.phi)) != DGDFT_OK) return s;
+  if ((s = out(eig, eh.eig)) != DGDFT_OK) return s;
+  return out(resid, eh.resid);
+}
+
+const char* dgdft_alb_last_error(const dgdft_alb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void dgdft_alb_destroy(dgdft_alb_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+// ---------------------------------------------------------- step entry points
+
+dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device) {
+  if (!ctx || !x || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  ElemHost& eh = ctx->el[elem];
+  if (!eh.solved || eh.block.empty()) return ctx->fail(DGDFT_ESTATE, "no Ritz block kept (solve with keep_block)");
+  if (on_device) {
+    CK(ctx_copy(ctx, x, eh.block.data(), sizeof(double) * eh.block.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(x, eh.block.data(), sizeof(double) * eh.block.size());
+  }
+  return DGDFT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// A one-element wave in the context precision for step calls.
+template <class real>
+dgdft_status with_step_wave(dgdft_alb_ctx* ctx, int elem, Wave<real>& w) {
+  if (elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  if (!ctx->el[elem].has_v) return ctx->fail(DGDFT_ESTATE, "element without potential");
+  CK(cudaSetDevice(ctx->device));
+  dgdft_status s = w.build(ctx, std::vector<int>{elem}, 1e14);
+  if (s != DGDFT_OK) return s;
+  return w.reset_states(ctx->cfg.tol);
+}
+
+template <class real>
+dgdft_status step_in(dgdft_alb_ctx* ctx, real* dst, const double* src, size_t n, int on_device) {
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * std::max<size_t>(n, 1)));
+  cudaError_t e = ctx_copy(ctx, tmp, src, sizeof(double) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    launch_convert<double, real>(tmp, dst, n, ctx->stream);
+    e = cudaStreamSynchronize(ctx->stream);
+  }
+  cudaFree(tmp);
+  if (e != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "step input: " + cuda_err_string(e));
+  return DGDFT_OK;
+}
+
+template <class real>
+dgdft_status step_out(dgdft_alb_ctx* ctx, double* dst, const real* src, size_t n, int on_device) {
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * std::max<size_t>(n, 1)));
+  launch_convert<real, double>(src, tmp, n, ctx->stream);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess)
+    e = ctx_copy(ctx, dst, tmp, sizeof(double) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "step output: " + cuda_err_string(e));
+  return DGDFT_OK;
+}
+
+template <class real>
+dgdft_status apply_h_t(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* hx, int on_device) {
+  Wave<real> w;
+  dgdft_status s = with_step_wave<real>(ctx, elem, w);
+  if (s != DGDFT_OK) return s;
+  const size_t n = (size_t)w.h[0].ng * k;
+  real* xs = w.h[0].blk[BW][0];
+  real* ys = w.h[0].blk[BHW][0];
+  if ((s = step_in<real>(ctx, xs, x, n, on_device)) != DGDFT_OK) return s;
+  launch_apply_h<real>(w.batch, bptr<real>(xs), bptr<real>(ys), k, ctx->stream);
+  CK(cudaGetLastError());
+  return step_out<real>(ctx, hx, ys, n, on_device);
+}
+
+template <class real>
+dgdft_status teter_t(dgdft_alb_ctx* ctx, int elem, int k, const double* r, const double* t_kin, double* wout,
+                     int on_device) {
+  Wave<real> w;
+  dgdft_status s = with_step_wave<real>(ctx, elem, w);
+  if (s != DGDFT_OK) return s;
+  const size_t n = (size_t)w.h[0].ng * k;
+  real* xs = w.h[0].blk[BW][0];
+  real* ys = w.h[0].blk[BHW][0];
+  if ((s = step_in<real>(ctx, xs, r, n, on_device)) != DGDFT_OK) return s;
+  CK(ctx_copy(ctx, w.h[0].tkin, t_kin, sizeof(double) * k, cudaMemcpyHostToDevice));
+  launch_teter<real>(w.batch, bptr<real>(xs), bptr<real>(ys), w.h[0].tkin, k, ctx->stream);
+  CK(cudaGetLastError());
+  return step_out<real>(ctx, wout, ys, n, on_device);
+}
+
+template <class real>
+dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, const double* v, double* c,
+                    int on_device) {
+  // a scratch wave-less batch: one ElemDev with only the state word set
+  real *du = nullptr, *dv = nullptr;
+  double *dc = nullptr, *part = nullptr;
+  ElemDev<real>* de = nullptr;
+  int* dstate = nullptr;
+  const size_t tiles = ((p + 63) / 64) * ((q + 63) / 64);
+  const size_t pcap = ((size_t)(ng + 2047) / 2048) * tiles * 4096;
+  CK(cudaMalloc(&du, sizeof(real) * (size_t)ng * p));
+  CK(cudaMalloc(&dv, sizeof(real) * (size_t)ng * q));
+  CK(cudaMalloc(&dc, sizeof(double) * (size_t)p * q));
+  CK(cudaMalloc(&part, sizeof(double) * pcap));
+  CK(cudaMalloc(&de, sizeof(ElemDev<real>)));
+  CK(cudaMalloc(&dstate, sizeof(int) * STATE_WORDS));
+  dgdft_status s = step_in<real>(ctx, du, u, (size_t)ng * p, on_device);
+  if (s == DGDFT_OK) s = step_in<real>(ctx, dv, v, (size_t)ng * q, on_device);
+  if (s == DGDFT_OK) {
+    ElemDev<real> E;
+    std::memset(&E, 0, sizeof(E));
+    E.m = std::max(p, q);
+    E.ng = ng;
+    E.state = dstate;
+    int st[STATE_WORDS] = {0};
+    st[ST_ACTIVE] = 1;
+    ctx_copy(ctx, dstate, st, sizeof(st), cudaMemcpyHostToDevice);
+    ctx_copy(ctx, de, &E, sizeof(E), cudaMemcpyHostToDevice);
+    Batch<real> b;
+    b.d_elems = de;
+    b.s.nel = 1;
+    b.s.max_m = E.m;
+    b.s.max_ng = ng;
+    GramJob<real> g;
+    g.npairs = 1;
+    g.a[0] = bptr<real>(du);
+    g.b[0] = bptr<real>(dv);
+    g.needs_p[0] = 0;
+    g.out_id[0] = OUT_PTR;
+    g.brow[0] = g.bcol[0] = 0;
+    g.ncols_a = p;
+    g.ncols_b = q;
+    g.rows = ng;
+    g.ld_in = ng;
+    g.ld_out = p;
+    g.out_ptr = dc;
+    launch_gram<real>(b, g, part, pcap, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = ctx_copy(ctx, c, dc, sizeof(double) * (size_t)p * q, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = ctx->fail(DGDFT_ECUDA, "gram: " + cuda_err_string(e));
+  }
+  cudaFree(du);
+  cudaFree(dv);
+  cudaFree(dc);
+  cudaFree(part);
+  cudaFree(de);
+  cudaFree(dstate);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgdft_status dgdft_alb_apply_h(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* hx, int on_device) {
+  if (!ctx || !x || !hx || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  if (k < 1 || k > ctx->el[elem].d.n_compute) return DGDFT_EINVAL;
+  return ctx->cfg.precision == DGDFT_PREC_FP64 ? apply_h_t<double>(ctx, elem, k, x, hx, on_device)
+                                                : apply_h_t<float>(ctx, elem, k, x, hx, on_device);
+}
+
+dgdft_status dgdft_alb_apply_teter(dgdft_alb_ctx* ctx, int elem, int k, const double* r, const double* t_kin,
+                                   double* w, int on_device) {
+  if (!ctx || !r || !t_kin || !w || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  if (k < 1 || k > ctx->el[elem].d.n_compute) return DGDFT_EINVAL;
+  for (int i = 0; i < k; ++i)
+    if (!(t_kin[i] > 0.0)) return DGDFT_EINVAL;
+  return ctx->cfg.precision == DGDFT_PREC_FP64 ? teter_t<double>(ctx, elem, k, r, t_kin, w, on_device)
+                                                : teter_t<float>(ctx, elem, k, r, t_kin, w, on_device);
+}
+
+dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, const double* v, double* c,
+                            int on_device) {
+  if (!ctx || !u || !v || !c || ng < 1 || p < 1 || q < 1) return DGDFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  return ctx->cfg.precision == DGDFT_PREC_FP64 ? gram_t<double>(ctx, ng, p, q, u, v, c, on_device)
+                                                : gram_t<float>(ctx, ng, p, q, u, v, c, on_device);
+}
+
+dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int n, int m, const double* a, const double* b,
+                                     double* theta, double* y) {
+  if (!ctx || !a || !b || !theta || !y || n < 1 || m < 1 || m > n) return DGDFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  const size_t nn = (size_t)n * n;
+  double *da = nullptr, *db = nullptr, *dy = nullptr, *dth = nullptr, *work = nullptr;
+  RRTask* dt = nullptr;
+  CK(cudaMalloc(&da, sizeof(double) * nn));
+  CK(cudaMalloc(&db, sizeof(double) * nn));
+  CK(cudaMalloc(&dy, sizeof(double) * (size_t)n * m));
+  CK(cudaMalloc(&dth, sizeof(double) * m));
+  CK(cudaMalloc(&work, sizeof(double) * rr_work_doubles(n, m)));
+  CK(cudaMalloc(&dt, sizeof(RRTask)));
+  RRTask t{};
+  t.A = da;
+  t.B = db;
+  t.ld = n;
+  t.mode = RR_FIXED;
+  t.n_fixed = n;
+  t.m = m;
+  t.Y = dy;
+  t.ldy = n;
+  t.theta = dth;
+  t.work = work;
+  t.state = nullptr;
+  t.cond_max = 1e30;
+  dgdft_status s = DGDFT_OK;
+  cudaError_t e = ctx_copy(ctx, da, a, sizeof(double) * nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = ctx_copy(ctx, db, b, sizeof(double) * nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = ctx_copy(ctx, dt, &t, sizeof(t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    launch_rr(dt, 1, ctx->stream);
+    e = cudaStreamSynchronize(ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = ctx_copy(ctx, theta, dth, sizeof(double) * m, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = ctx_copy(ctx, y, dy, sizeof(double) * (size_t)n * m, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) s = ctx->fail(DGDFT_ECUDA, "rayleigh_ritz: " + cuda_err_string(e));
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dy);
+  cudaFree(dth);
+  cudaFree(work);
+  cudaFree(dt);
+  if (s == DGDFT_OK && !std::isfinite(theta[0])) s = ctx->fail(DGDFT_EINVAL, "B is not positive definite");
+  return s;
+}
+
+dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int k, int J, const double* x,
+                                               double* phi, int on_device) {
+  if (!ctx || !x || !phi || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  ElemHost& eh = ctx->el[elem];
+  if (k < 1 || k > eh.d.n_compute || J < 1 || J > k || J > eh.ne()) return DGDFT_EINVAL;
+  Wave<double> w;
+  dgdft_status s = with_step_wave<double>(ctx, elem, w);
+  if (s != DGDFT_OK) return s;
+  double* xs = w.h[0].blk[BW][0];
+  if ((s = step_in<double>(ctx, xs, x, (size_t)eh.ng() * k, on_device)) != DGDFT_OK) return s;
+  double* out = nullptr;
+  CK(cudaMalloc(&out, sizeof(double) * (size_t)eh.ne() * J));
+  std::unique_ptr<void, decltype(&cudaFree)> guard(out, &cudaFree);
+  if ((s = alb_orthonormalise(ctx, w, 0, xs, J, out)) != DGDFT_OK) return s;
+  CK(ctx_copy(ctx, phi, out, sizeof(double) * (size_t)eh.ne() * J,
+                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return DGDFT_OK;
+}
+
+}  // extern "C"

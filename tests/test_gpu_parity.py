@@ -1,0 +1,264 @@
+"""GPU parity of every step of the hot path against the FP64 CPU oracle.
+
+All calls go through the C-ABI (include/dgdft_alb.h, dgdft_alb_steps.h).
+Tolerances: FP64 steps to ~1e-12 relative; the mixed form's FP32 steps to
+a few units of FP32 rounding times the step's conditioning (stated per
+test).  Full solves: FP64 eigenvalues within 1e-8 Ha and subspace sine
+within 1e-7 (where the spectral gap allows, Davis-Kahan); mixed form within
+1e-6 Ha and 1e-5.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import __graft_entry__ as entry
+import synth
+from oracle import alb, hamiltonian as H, lobpcg as OL, teter as T
+from paper_1506_08147_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+PRECS = [B.DGDFT_PREC_FP64, B.DGDFT_PREC_MIXED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    entry.build()
+
+
+def small_kb_element():
+    # 16 x 12 x 10 periodic box with 6 atoms: local potential + 12 projectors
+    return synth.random_element(9, 0, (16, 12, 10), 6, J=8, m=10, tol=1e-9)
+
+
+def cfg2_element(k=0):
+    return synth.config2(elems=[k])[0]
+
+
+def ctx_for(el, prec, **kw):
+    c = B.Context([B.element_dict(el)], precision=prec, **kw)
+    B.load_element(c, 0, el)
+    return c
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ------------------------------------------------------------ H apply
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("which", ["small", "cfg2"])
+def test_apply_h(prec, which):
+    el = small_kb_element() if which == "small" else cfg2_element()
+    gen = np.random.default_rng(1)
+    k = 5 if which == "small" else 3
+    x = gen.standard_normal((k, el.ng))
+    c = ctx_for(el, prec)
+    got = c.dgdft_alb_apply_h(0, x)
+    ref = H.apply_h(x, el)
+    # FP32: the r2c/c2r FFTs carry ~1e-7 relative error, amplified by the
+    # kinetic symbol relative to |H x| (rough white-noise inputs).
+    tol = 1e-12 if prec == B.DGDFT_PREC_FP64 else 2e-6
+    assert rel(got, ref) < tol
+    c.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_apply_h_plane_wave_eigenvalue(prec):
+    # a single plane wave cos(G.r) in a potential-free box: H x = |G|^2/2 x,
+    # including the Nyquist frequency (|n/2|, the reading of the planewave set)
+    el = synth.random_element(9, 1, (16, 12, 10), 4, J=4, m=4)
+    el.veff[:] = 0.0
+    el.proj_row_ptr = np.zeros(1, np.int64)
+    el.proj_idx = np.zeros(0, np.int32)
+    el.proj_val = np.zeros(0)
+    el.proj_gamma = np.zeros(0)
+    coords = [np.arange(n) * l / n for n, l in zip(el.n, el.L)]
+    zz, yy, xx = np.meshgrid(coords[2], coords[1], coords[0], indexing="ij")
+    gx, gy, gz = (2 * np.pi * 8 / el.L[0], 2 * np.pi * 2 / el.L[1], 2 * np.pi * 5 / el.L[2])
+    x = np.cos(gx * xx + gy * yy + gz * zz).reshape(1, -1)
+    c = ctx_for(el, prec)
+    got = c.dgdft_alb_apply_h(0, x)
+    lam = 0.5 * (gx * gx + gy * gy + gz * gz)
+    tol = 1e-12 if prec == B.DGDFT_PREC_FP64 else 1e-6
+    assert rel(got, lam * x) < tol
+    c.close()
+
+
+# ------------------------------------------------------------- Teter
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_teter(prec):
+    el = small_kb_element()
+    gen = np.random.default_rng(2)
+    x = gen.standard_normal((4, el.ng))
+    r = gen.standard_normal((4, el.ng))
+    t = T.kinetic_energy(x, el.n, el.L)
+    c = ctx_for(el, prec)
+    got = c.dgdft_alb_apply_teter(0, r, t)
+    ref = T.precondition(r, x, el.n, el.L)
+    tol = 1e-12 if prec == B.DGDFT_PREC_FP64 else 2e-6
+    assert rel(got, ref) < tol
+    c.close()
+
+
+# -------------------------------------------------------------- Gram
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", [(1000, 7, 5), (122880, 48, 48), (70001, 130, 70)])
+def test_gram(prec, shape):
+    ng, p, q = shape
+    gen = np.random.default_rng(3)
+    u = gen.standard_normal((p, ng))
+    v = gen.standard_normal((q, ng))
+    el = small_kb_element()
+    c = ctx_for(el, prec)
+    got = c.dgdft_alb_gram(u, v)
+    ref = u @ v.T
+    scale = np.sqrt(ng)  # typical |u_i| |v_j| / sqrt(ng) for random rows
+    err = np.max(np.abs(got - ref)) / (np.sqrt(ng) * scale)
+    tol = 1e-14 if prec == B.DGDFT_PREC_FP64 else 1e-6
+    assert err < tol
+    c.close()
+
+
+# ---------------------------------------------------- Rayleigh-Ritz
+
+def spd(n, gen, cond=1e3):
+    q, _ = np.linalg.qr(gen.standard_normal((n, n)))
+    return (q * np.logspace(0, np.log10(cond), n)) @ q.T
+
+
+@pytest.mark.parametrize("n,m", [(20, 5), (96, 48), (144, 48), (30, 30)])
+def test_rayleigh_ritz(n, m):
+    gen = np.random.default_rng(n + m)
+    a = gen.standard_normal((n, n))
+    a = a + a.T
+    b = spd(n, gen)
+    el = small_kb_element()
+    c = ctx_for(el, B.DGDFT_PREC_FP64)
+    theta, y = c.dgdft_alb_rayleigh_ritz(a, b, m)
+    ref = sla.eigh(a, b, eigvals_only=True)[:m]
+    np.testing.assert_allclose(theta, ref, atol=1e-10 * np.max(np.abs(ref)))
+    np.testing.assert_allclose(y.T @ b @ y, np.eye(m), atol=1e-10)
+    assert np.max(np.abs(a @ y - b @ y * theta)) < 1e-9 * np.max(np.abs(a))
+    c.close()
+
+
+def test_rayleigh_ritz_degenerate_shells():
+    # exactly degenerate clusters (free-electron-like multiplicities 1, 6, 12)
+    gen = np.random.default_rng(7)
+    n, m = 60, 19
+    q, _ = np.linalg.qr(gen.standard_normal((n, n)))
+    ev = np.r_[0.0, np.full(6, 0.2), np.full(12, 0.4), np.linspace(0.6, 3, 41)]
+    a = (q * ev) @ q.T
+    el = small_kb_element()
+    c = ctx_for(el, B.DGDFT_PREC_FP64)
+    theta, y = c.dgdft_alb_rayleigh_ritz(a, np.eye(n), m)
+    np.testing.assert_allclose(theta, ev[:m], atol=1e-12)
+    np.testing.assert_allclose(y.T @ y, np.eye(m), atol=1e-11)
+    assert alb.sin_max_angle(q[:, :m].T, y.T) < 1e-10
+    c.close()
+
+
+def test_rayleigh_ritz_rejects_indefinite_b():
+    n = 10
+    a = np.eye(n)
+    b = np.eye(n)
+    b[3, 3] = -1.0
+    el = small_kb_element()
+    c = ctx_for(el, B.DGDFT_PREC_FP64)
+    with pytest.raises(B.DgdftError):
+        c.dgdft_alb_rayleigh_ritz(a, b, 3)
+    c.close()
+
+
+# ------------------------------------------ restriction + orthonormalisation
+
+@pytest.mark.parametrize("which", ["small", "cfg2"])
+def test_restrict_orthonormalise(which):
+    el = small_kb_element() if which == "small" else cfg2_element()
+    if which == "small":
+        el.e_lo, el.e_hi = synth.element_box(el.n)
+    gen = np.random.default_rng(4)
+    k, J = (10, 8) if which == "small" else (48, 40)
+    x = OL.cholesky_qr(gen.standard_normal((k, el.ng)))
+    c = ctx_for(el, B.DGDFT_PREC_FP64)
+    phi = c.dgdft_alb_restrict_orthonormalise(0, x, J)
+    ref = alb.orthonormalise(alb.restrict(x, el, J), el.dv)
+    np.testing.assert_allclose(phi @ phi.T * el.dv, np.eye(J), atol=1e-12)
+    assert alb.sin_max_angle(ref, phi) < 1e-11
+    c.close()
+
+
+# -------------------------------------------------------------- full solves
+
+def _gap_ok(gap, tol, bound):
+    return gap >= tol / bound
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_solve_config1(prec):
+    el = synth.config1()
+    gold = np.loadtxt(os.path.join(GOLDEN, "config1_eigenvalues.txt"))
+    c = B.Context([B.element_dict(el)], precision=prec, tol=1e-8, maxit=800, keep_block=True)
+    B.load_element(c, 0, el, synth.initial_block(el))
+    st, rep = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    phi, eig, res = c.dgdft_alb_get_basis(0)
+    x = c.dgdft_alb_get_block(0)
+    c.close()
+    eig_tol = 1e-8 if prec == B.DGDFT_PREC_FP64 else 1e-6
+    np.testing.assert_allclose(eig, gold, atol=eig_tol)
+    # FP64 residual of the returned vectors, recomputed by the oracle
+    r = H.apply_h(x[:16], el) - eig[:, None] * x[:16]
+    assert np.max(np.linalg.norm(r, axis=1)) <= 1.05e-8
+    np.testing.assert_allclose(phi @ phi.T * el.dv, np.eye(16), atol=1e-12)
+    # subspace against the exact invariant subspace (dense eigh at 16^3)
+    w, v = np.linalg.eigh(H.dense_h(el))
+    gap = w[16] - w[15]
+    bound = 1.05e-8 / gap
+    assert alb.sin_max_angle(v[:, :16].T, x[:16]) <= max(bound, 1e-12) * 1.5
+    assert alb.sin_max_angle(v[:, :16].T, phi) <= max(bound, 1e-12) * 1.5
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_solve_config2_elements(prec):
+    els = synth.config2(elems=[0, 7])
+    c = B.Context([B.element_dict(e) for e in els], precision=prec, tol=1e-6, maxit=600,
+                  keep_block=True)
+    for k, e in enumerate(els):
+        B.load_element(c, k, e, synth.initial_block(e))
+    st, rep = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    for k, e in enumerate(els):
+        phi, eig, res = c.dgdft_alb_get_basis(k)
+        x = c.dgdft_alb_get_block(k)
+        assert np.max(res) <= 1e-6
+        r = H.apply_h(x[:e.J], e) - eig[:, None] * x[:e.J]
+        assert np.max(np.linalg.norm(r, axis=1)) <= 1.05e-6
+        np.testing.assert_allclose(phi @ phi.T * e.dv, np.eye(e.J), atol=1e-12)
+        assert alb.sin_max_angle(alb.restrict(x, e), phi) < 1e-10
+        gold = os.path.join(GOLDEN, f"config2_elem{[0, 7][k]}_eigenvalues.txt")
+        if os.path.exists(gold):
+            ref = np.loadtxt(gold)[:e.J]
+            np.testing.assert_allclose(eig, ref, atol=1e-6 if prec == B.DGDFT_PREC_MIXED else 1e-8)
+    c.close()
+
+
+def test_nonfinite_potential_rejected():
+    el = small_kb_element()
+    c = B.Context([B.element_dict(el)])
+    v = el.veff.reshape(-1).copy()
+    v[5] = np.nan
+    with pytest.raises(B.DgdftError) as ei:
+        c.dgdft_alb_set_potential(0, v)
+    assert ei.value.status == B.DGDFT_EINVAL
+    with pytest.raises(B.DgdftError) as ei:
+        c.dgdft_alb_get_basis(0)
+    assert ei.value.status == B.DGDFT_ESTATE
+    c.close()
