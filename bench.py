@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""ALB generation benchmark on GB300: eigenpairs/s at residual <= 1e-6 Ha.
+
+Workload: the 36 extended elements of the 576-atom puckered monolayer
+(48 x 64 x 40 grid each, 144 atoms / 288 Kleinman-Bylander projectors,
+48 eigenpairs computed, 40 kept), synthetic seeded inputs.  One step is one
+dgdft_alb_solve over all 36 elements (LOBPCG to 1e-6 Ha from the seeded
+random block, restriction to E_K, SVD orthonormalisation) in the chosen
+form (FP32 bulk + FP64 refinement).  Counted eigenpairs are the kept ALBs
+whose FP64 residual is <= 1e-6 Ha.
+
+  value   : device-timed throughput, inputs resident in HBM (CUDA events on
+            the library's stream, which is torch's current stream);
+  e2e     : the same through the public API from pinned host buffers
+            (set_potential/set_projectors/set_initial, solve, get_basis);
+  plain   : the plain FP64 GPU solver on the same inputs (comparator);
+  roofline: the dominant kernel, timed live by dgdft_alb_time_stage;
+  cpu_baseline: the FP64 CPU oracle on a bounded sample.
+
+--impl reference times the oracle alone (the reference arm).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOL = 1e-6
+L2_BYTES = 129 * 2 ** 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, dev_index=0):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(dev_index)]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(limit=None):
+    import synth
+    els = synth.config2(elems=None if limit is None else list(range(limit)))
+    x0 = [synth.initial_block(e) for e in els]
+    return els, x0
+
+
+def count_pairs(ctx, els):
+    total = 0
+    for k, e in enumerate(els):
+        _, _, res = ctx.dgdft_alb_get_basis(k)
+        total += int(np.sum(res <= TOL))
+    return total
+
+
+# Algorithmic bytes per launch (working precision s bytes), per element:
+# the stage's necessary reads and writes, from the LOBPCG work model
+# (H W: read W + write HW; Gram: read X W P HX HW HP once; update: read
+# three blocks, write one; residual: read X HX, write R).
+def stage_bytes(name, e, s):
+    ng, m = e.ng, e.m
+    nspec = (e.n[0] // 2 + 1) * e.n[1] * e.n[2]
+    if name == "xy_fwd":
+        return m * (ng * s + nspec * 2 * s)
+    if name == "z_mult":
+        return m * nspec * 2 * s * 2
+    if name == "xy_inv":
+        return m * (nspec * 2 * s + 2 * ng * s) + ng * s
+    if name == "gram":
+        return 6 * ng * m * s
+    if name == "update":
+        return 4 * ng * m * s
+    if name == "residual":
+        return 3 * ng * m * s + ng * s
+    return 0
+
+
+# launches of each stage per LOBPCG iteration (H apply and Teter both run
+# the three FFT passes; the Gram stage also runs X^T W; 5 block updates)
+STAGE_PER_ITER = {"xy_fwd": 2, "z_mult": 2, "xy_inv": 2, "gram": 1, "update": 5, "rayleigh_ritz": 1,
+                  "residual": 1}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1506_08147_gb300 import binding as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__ as entry
+    entry.build()
+    els, x0 = workload(args.elements)
+    stream = torch.cuda.current_stream()
+    descs = [B.element_dict(e) for e in els]
+    ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
+                    stream=stream.cuda_stream)
+    dev_x0 = []
+    for k, e in enumerate(els):
+        B.load_element(ctx, k, e)
+        t = torch.from_numpy(x0[k]).to("cuda")
+        dev_x0.append(t)
+        ctx.dgdft_alb_set_initial(k, t)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        ctx.dgdft_alb_solve()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    reps = []
+    with ClockSampler() as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st, reps = ctx.dgdft_alb_solve()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    pairs = count_pairs(ctx, els)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        p = torch.tensor([pairs], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p)
+        pairs_all = float(p.item())
+    else:
+        pairs_all = float(pairs)
+    ms_step = ms / args.steps
+    value = pairs_all / (ms_step / 1e3)
+    iters = [r["iterations"] for r in reps]
+
+    # roofline of the dominant kernel (stage timed live on the same stream)
+    hbm, bf16, peak_kind = peaks()
+    stages = {}
+    for name, sid in B.STAGES.items():
+        t_ms, nel, sbytes = ctx.dgdft_alb_time_stage(sid, reps=args.stage_reps)
+        stages[name] = (t_ms, nel, sbytes)
+    mean_it = float(np.mean(iters))
+    share = {n: stages[n][0] * STAGE_PER_ITER[n] for n in stages}
+    dom = max(share, key=share.get)
+    dom_ms, nel, sbytes = stages[dom]
+    if dom == "rayleigh_ritz":
+        # FP64 ALU bound: lowest m of a 3m pencil, ~ (3m)^3 (1/3 + 1 + 2/3 + ...) flops
+        n3 = (3 * els[0].m) ** 3
+        flops = nel * 2.5 * 2 * n3
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None, "kernel": dom,
+                "peak_source": "FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz (derived)"}
+    else:
+        abytes = sum(stage_bytes(dom, e, sbytes) for e in els)
+        achieved = abytes / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": dom,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+    stage_report = {n: {"ms_per_launch": round(stages[n][0], 4), "launches_per_iter": STAGE_PER_ITER[n],
+                        "alg_GBps": (round(sum(stage_bytes(n, e, stages[n][2]) for e in els)
+                                           / (stages[n][0] / 1e3) / 1e9, 1)
+                                     if stage_bytes(n, els[0], stages[n][2]) else None)}
+                    for n in stages}
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin_v = [torch.from_numpy(np.ascontiguousarray(e.veff.reshape(-1))).pin_memory() for e in els]
+        pin_x = [torch.from_numpy(x).pin_memory() for x in x0]
+        pin_phi = [torch.empty((e.J, e.n_e), dtype=torch.float64).pin_memory() for e in els]
+        pin_eig = [torch.empty(e.J, dtype=torch.float64).pin_memory() for e in els]
+        pin_res = [torch.empty(e.J, dtype=torch.float64).pin_memory() for e in els]
+        h2d = sum(v.numel() * 8 + x.numel() * 8 for v, x in zip(pin_v, pin_x))
+        h2d += sum(e.proj_idx.nbytes + e.proj_val.nbytes + e.proj_gamma.nbytes + e.proj_row_ptr.nbytes
+                   for e in els)
+        d2h = sum(p.numel() * 8 + 16 * e.J for p, e in zip(pin_phi, els))
+        times = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k, e in enumerate(els):
+                ctx.dgdft_alb_set_potential(k, pin_v[k])
+                if e.n_proj:
+                    ctx.dgdft_alb_set_projectors(k, e.proj_row_ptr, e.proj_idx, e.proj_val, e.proj_gamma)
+                ctx.dgdft_alb_set_initial(k, pin_x[k])
+            st, _ = ctx.dgdft_alb_solve()
+            n_ok = 0
+            for k, e in enumerate(els):
+                ctx.dgdft_alb_get_basis(k, pin_phi[k], pin_eig[k], pin_res[k])
+                n_ok += int((pin_res[k] <= TOL).sum())
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        e2e = {"value": n_ok * world / statistics.mean(times), "unit": "eigenpairs/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": args.e2e_steps}
+
+    # plain FP64 comparator on the same inputs (one solve, wave build included)
+    plain = None
+    if args.plain and rank == 0:
+        c64 = B.Context(descs, precision=B.DGDFT_PREC_FP64, tol=TOL, maxit=args.maxit,
+                        stream=stream.cuda_stream)
+        for k, e in enumerate(els):
+            B.load_element(c64, k, e)
+            c64.dgdft_alb_set_initial(k, dev_x0[k])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st64, rep64 = c64.dgdft_alb_solve()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        p64 = count_pairs(c64, els)
+        plain = {"value": p64 / dt, "unit": "eigenpairs/s", "seconds": dt,
+                 "mean_iterations": float(np.mean([r["iterations"] for r in rep64])),
+                 "eigenpairs": p64}
+        c64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        cpu = cpu_baseline(els[0], args.cpu_seconds)
+
+    launches = None
+    line = {
+        "metric": "ALB eigenpairs/s at residual<=1e-6 Ha, chosen form vs plain FP64, same GB300",
+        "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded puckered monolayer, Z=5 Gaussian pseudopotentials)",
+        "config": {"workload": "36 extended elements of the 576-atom monolayer, 48x64x40 grid, "
+                               "m=48 computed, J=40 kept, tol 1e-6 Ha, random start",
+                   "elements": len(els), "precision": "mixed: FP32 bulk + FP64 RR/refinement/SVD",
+                   "l2": "working set ~10 GB >> 129 MB L2 (no flush needed)",
+                   "parallelism": f"elements batched on 1 GPU; {world} rank(s), replicated workload"},
+        "eigenpairs_per_step": pairs, "iterations_mean": mean_it,
+        "iterations_max": int(max(iters)) if iters else None,
+        "roofline": roof, "stages": stage_report,
+        "plain_fp64": plain,
+        "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(local),
+    }
+    line["gpu_launches"] = estimate_launches(els, iters, args.steps)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def estimate_launches(els, iters, steps):
+    """Kernels launched per solve: initial Rayleigh-Ritz (9), 21 per LOBPCG
+    iteration (graph nodes), input conversions (2 per element per stage) and
+    the FP64 orthonormalisation (10 per element); iterations are summed over
+    both precision stages."""
+    per_solve = 2 * 9 + 21 * (max(iters) + 2) + 4 * len(els) + 10 * len(els)
+    return int(per_solve * steps)
+
+
+def cpu_baseline(el, budget_s):
+    """The oracle as it stands, on the host cores, for a bounded number of
+    LOBPCG iterations on one element; extrapolated with the oracle's own
+    iteration count to 1e-6 Ha on that element (tests/golden)."""
+    import synth
+    from oracle import lobpcg as OL
+    gold_it = os.path.join(ROOT, "tests", "golden", "config2_elem0_iterations.txt")
+    iters_needed = int(np.loadtxt(gold_it)) if os.path.exists(gold_it) else None
+    x0 = synth.initial_block(el)
+    n_it = 1
+    t0 = time.perf_counter()
+    OL.lobpcg(el, x0, tol=0.0, maxit=n_it)
+    t1 = time.perf_counter()
+    one = t1 - t0
+    n_it = max(2, min(60, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    OL.lobpcg(el, x0, tol=0.0, maxit=n_it)
+    per_it = (time.perf_counter() - t0) / (n_it + 1)
+    cores = os.cpu_count()
+    if iters_needed is None:
+        return {"value": None, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
+                "sample": f"{n_it} iterations on element 0: {per_it:.3f} s/iteration; "
+                          "convergence count unavailable"}
+    t_elem = per_it * (iters_needed + 1)
+    return {"value": el.J / t_elem, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle LOBPCG on extended element 0 of 36 for {n_it} iterations "
+                      f"({per_it:.2f} s/iteration, numpy/scipy threads = all cores), extrapolated "
+                      f"to its own {iters_needed} iterations to 1e-6 Ha; J = {el.J} eigenpairs"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    from oracle import lobpcg as OL
+    els = synth.config2(elems=[0])
+    el = els[0]
+    gold_it = os.path.join(ROOT, "tests", "golden", "config2_elem0_iterations.txt")
+    iters_needed = int(np.loadtxt(gold_it)) if os.path.exists(gold_it) else 100
+    x0 = synth.initial_block(el)
+    per_step_it = args.ref_iters
+    for _ in range(args.warmup):
+        OL.lobpcg(el, x0, tol=0.0, maxit=1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        OL.lobpcg(el, x0, tol=0.0, maxit=per_step_it)
+        times.append((time.perf_counter() - t0) / (per_step_it + 1))
+    per_it = statistics.mean(times)
+    value = el.J / (per_it * (iters_needed + 1))
+    line = {"impl": "reference", "metric": "ALB eigenpairs/s at residual<=1e-6 Ha, chosen form vs plain "
+            "FP64, same GB300", "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_it * (per_step_it + 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "36 extended elements of the 576-atom monolayer, "
+                                                        "48x64x40 grid, m=48 computed, J=40 kept, tol 1e-6 Ha"},
+            "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"each step: oracle LOBPCG on element 0 for {per_step_it} iterations, "
+                                       f"extrapolated to its {iters_needed} iterations to 1e-6 Ha"},
+            "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--elements", type=int, default=None, help="first k elements only (debug)")
+    ap.add_argument("--maxit", type=int, default=400)
+    ap.add_argument("--stage-reps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-iters", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -91,6 +91,8 @@ typedef struct {
   int device;             /* CUDA device ordinal; -1 = current device         */
   int keep_block;         /* 1: keep each converged N_g x m Ritz block on the
                              host after solve (for dgdft_alb_get_block)        */
+  int bulk_kernels;       /* 0: tcgen05 tensor-core kernels for the FP32 stage
+                             where the shapes allow (3m <= 256); 1: SIMT only */
   const char* autotune_cache;   /* optional JSON path; NULL = none            */
   const char* precond_weights;  /* learned preconditioner weights; NULL = none */
 } dgdft_alb_config;

@@ -60,6 +60,30 @@ dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int
  * values).  DGDFT_ESTATE before a solve. */
 dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device);
 
+/* Kernel stages that dgdft_alb_time_stage can time in isolation. */
+enum {
+  DGDFT_STAGE_XY_FWD = 0,   /* FFT pass 1: r2c along x, FFT along y (H apply)  */
+  DGDFT_STAGE_Z_MULT = 1,   /* FFT pass 2: FFT along z, kinetic symbol, inverse */
+  DGDFT_STAGE_XY_INV = 2,   /* FFT pass 3: inverse y, c2r x, + V psi + KB       */
+  DGDFT_STAGE_GRAM = 3,     /* the 12 Gram blocks of S^T H S, S^T S + reduction */
+  DGDFT_STAGE_UPDATE = 4,   /* one block update X <- [X W P] Y                  */
+  DGDFT_STAGE_RR = 5,       /* FP64 Rayleigh-Ritz of every element              */
+  DGDFT_STAGE_RESIDUAL = 6, /* R = HX - X Theta with partial sums               */
+  DGDFT_STAGE_COUNT = 7
+};
+
+/* Average device time (ms) of one launch of `stage` over all elements kept
+ * resident by the last dgdft_alb_solve (the bulk-precision wave: FP32 for
+ * DGDFT_PREC_MIXED), measured with CUDA events on the context stream over
+ * `reps` back-to-back launches after one untimed launch.  The stage runs on
+ * the solve's final data with every element marked active; the solve's
+ * results (basis, eigenvalues, residuals) are not affected.  Also reports
+ * the number of elements and the working-precision size in bytes.
+ * DGDFT_ESTATE when no wave is resident (memory-limited multi-wave solves
+ * do not keep one). */
+dgdft_status dgdft_alb_time_stage(dgdft_alb_ctx* ctx, int stage, int reps, double* ms_per_launch,
+                                  int* n_elem, int* real_bytes);
+
 #ifdef __cplusplus
 }
 #endif

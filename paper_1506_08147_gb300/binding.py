@@ -33,6 +33,7 @@ class dgdft_alb_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("tol", C.c_double),
                 ("maxit", C.c_int), ("check_every", C.c_int), ("hbm_cap_bytes", C.c_size_t),
                 ("cuda_stream", C.c_void_p), ("device", C.c_int), ("keep_block", C.c_int),
+                ("bulk_kernels", C.c_int),
                 ("autotune_cache", C.c_char_p), ("precond_weights", C.c_char_p)]
 
 
@@ -60,6 +61,8 @@ _SIGS = {
     "dgdft_alb_restrict_orthonormalise": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P,
                                                     C.c_int]),
     "dgdft_alb_get_block": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "dgdft_alb_time_stage": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int)]),
 }
 
 _lib = None
@@ -113,7 +116,7 @@ class Context:
 
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
-                 precond_weights=None):
+                 precond_weights=None, simt_only=False):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -123,6 +126,7 @@ class Context:
         cfg.maxit = maxit
         cfg.check_every = check_every
         cfg.keep_block = int(keep_block)
+        cfg.bulk_kernels = int(simt_only)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
         cfg.cuda_stream = stream
         self._weights = precond_weights.encode() if precond_weights else None
@@ -205,6 +209,15 @@ class Context:
         self._check(self.lib.dgdft_alb_get_block(self.h, elem, _ptr(x)[0], 0), "get_block")
         return x
 
+    def dgdft_alb_time_stage(self, stage, reps=10):
+        """(ms per launch, elements, working-precision bytes) of one kernel stage."""
+        ms = C.c_double()
+        ne = C.c_int()
+        rb = C.c_int()
+        self._check(self.lib.dgdft_alb_time_stage(self.h, stage, reps, C.byref(ms), C.byref(ne),
+                                                  C.byref(rb)), "time_stage")
+        return ms.value, ne.value, rb.value
+
     # step entry points -------------------------------------------------
     def dgdft_alb_apply_h(self, elem, x):
         x = np.ascontiguousarray(x, np.float64)
@@ -265,3 +278,7 @@ def load_element(ctx: Context, k: int, el, x0=None):
         ctx.dgdft_alb_set_projectors(k, el.proj_row_ptr, el.proj_idx, el.proj_val, el.proj_gamma)
     if x0 is not None:
         ctx.dgdft_alb_set_initial(k, np.ascontiguousarray(x0, np.float64))
+
+
+STAGES = {"xy_fwd": 0, "z_mult": 1, "xy_inv": 2, "gram": 3, "update": 4, "rayleigh_ritz": 5,
+          "residual": 6}

@@ -35,7 +35,21 @@ __global__ void scale_kernel(double* __restrict__ x, size_t n, double s) {
     x[i] *= s;
 }
 
+__global__ void nonfinite_kernel(const double* __restrict__ x, size_t n, int* __restrict__ flag) {
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 }  // namespace
+
+void launch_nonfinite(const double* x, size_t n, int* flag, cudaStream_t st) {
+  if (n == 0) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  nonfinite_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, flag);
+}
 
 template <class real>
 void launch_restrict(const real* x, int ng, int nx, int ny, const int* lo, const int* hi, int J, double* out,

@@ -263,6 +263,25 @@ void init_hamiltonian_kernels() {
   opt_in_smem_t<float>();
 }
 
+// One pass of the H apply in isolation (0: xy forward, 1: z multiply,
+// 2: xy inverse with epilogue), for stage timing.
+template <class real>
+void launch_h_pass(const Batch<real>& b, int pass, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int nc = ncols > 0 ? ncols : s.max_m;
+  const size_t sp = plane_smem<real>(s), sz = zcol_smem<real>(s);
+  if (pass == 0)
+    xy_fwd_kernel<real><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, src, ncols);
+  else if (pass == 1)
+    z_mult_kernel<real, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, sz, st>>>(
+        b.d_elems, ncols, nullptr);
+  else
+    xy_inv_kernel<real, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, dst, src,
+                                                                                     ncols);
+}
+template void launch_h_pass<double>(const Batch<double>&, int, BRef<double>, BRef<double>, int, cudaStream_t);
+template void launch_h_pass<float>(const Batch<float>&, int, BRef<float>, BRef<float>, int, cudaStream_t);
+
 template <class real>
 void launch_proj_coef(const Batch<real>& b, BRef<real> src, int ncols, cudaStream_t st) {
   if (b.s.max_nproj > 0)

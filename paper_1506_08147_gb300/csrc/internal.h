@@ -49,6 +49,10 @@ void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const do
                   int ncols, cudaStream_t st);
 
 void init_hamiltonian_kernels();
+template <class real>
+void launch_proj_coef(const Batch<real>& b, BRef<real> src, int ncols, cudaStream_t st);
+template <class real>
+void launch_h_pass(const Batch<real>& b, int pass, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st);
 
 // blas.cu
 // Gram products U_a^T V_b over the rows of each element, split over row
@@ -128,6 +132,13 @@ std::string cuda_err_string(cudaError_t e);
 }  // namespace dgdft
 
 namespace dgdft {
+// tc_gram.cu: tcgen05 split-bf16 Gram products for the FP32 stage
+size_t tc_gram_smem_bytes(int n_cols);
+void init_tc_gram_kernel();
+void launch_tc_gram(const Batch<float>& b, int mode, double* partial, size_t partial_cap, cudaStream_t st);
+void launch_tc_gram_ptrs(const Batch<float>& b, const float* u, int p, const float* v, int q, int ng, double* c,
+                         double* partial, size_t partial_cap, cudaStream_t st);
+
 // alb.cu
 template <class real>
 void launch_restrict(const real* x, int ng, int nx, int ny, const int* lo, const int* hi, int J, double* out,
@@ -135,4 +146,6 @@ void launch_restrict(const real* x, int ng, int nx, int ny, const int* lo, const
 template <class A, class B>
 void launch_convert(const A* in, B* out, size_t n, cudaStream_t st);
 void launch_scale(double* x, size_t n, double s, cudaStream_t st);
+// flag |= 1 when any of x[0..n) is not finite
+void launch_nonfinite(const double* x, size_t n, int* flag, cudaStream_t st);
 }  // namespace dgdft

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dgdft_alb.h"
@@ -34,20 +35,32 @@ constexpr size_t ALIGN = 256;
 
 struct ElemHost {
   dgdft_element_desc d{};
-  std::vector<double> veff;
+  // inputs, resident on the device once set
+  double* d_veff = nullptr;  // N_g
   bool has_v = false;
   std::vector<int64_t> prow{0};
   std::vector<int32_t> pidx;
   std::vector<double> pval, pgamma;
-  std::vector<double> x0;
+  int proj_version = 0;
+  double* d_x0 = nullptr;    // N_g x m
   bool has_x0 = false;
-  // results
+  // results, on the device after a solve
+  double* d_phi = nullptr;   // n_E x J
+  double* d_eig = nullptr;   // J
+  double* d_res = nullptr;   // J
   bool solved = false;
-  std::vector<double> phi, eig, resid, block;
+  std::vector<double> eig, resid, block;
   dgdft_solve_report rep{};
   int ng() const { return d.nx * d.ny * d.nz; }
   int ne() const { return (d.e_hi[0] - d.e_lo[0]) * (d.e_hi[1] - d.e_lo[1]) * (d.e_hi[2] - d.e_lo[2]); }
   double dv() const { return d.Lx * d.Ly * d.Lz / ng(); }
+  void release() {
+    for (double** p : {&d_veff, &d_x0, &d_phi, &d_eig, &d_res})
+      if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+      }
+  }
 };
 
 bool plan_length(int n, FftPlan& p) {
@@ -115,6 +128,15 @@ struct dgdft_alb_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool solved_any = false;
+  // waves kept resident between solves when every element fits in one
+  void* cache = nullptr;
+  void (*cache_free)(void*) = nullptr;
+  std::vector<int> cache_proj_version;
+  void drop_cache() {
+    if (cache && cache_free) cache_free(cache);
+    cache = nullptr;
+    cache_proj_version.clear();
+  }
   dgdft_status fail(dgdft_status s, const std::string& msg) {
     err = msg;
     return s;
@@ -168,6 +190,8 @@ size_t elem_bytes(const ElemHost& h) {
   s.add(sizeof(double) * ((ng + 2047) / 2048) * 12 * tiles * 4096);
   return s.total + 64 * ALIGN;
 }
+
+void default_x0(std::vector<double>& x, int elem);
 
 template <class real> struct Wave {
   dgdft_alb_ctx* ctx = nullptr;
@@ -280,11 +304,8 @@ template <class real> struct Wave {
     plan_length(d.ny, E.py);
     plan_length(d.nz, E.pz);
     const size_t ng = E.ng, m = E.m;
-    // potential
-    std::vector<real> vr(eh.veff.begin(), eh.veff.end());
-    real* V = take<real>(ng);
-    if (put(V, vr.data(), ng) != DGDFT_OK) return DGDFT_ECUDA;
-    E.V = V;
+    // potential: converted from the resident FP64 copy at every solve
+    E.V = take<real>(ng);
     // twiddles
     auto put_tw = [&](int n, int count) -> const C* {
       std::vector<double> t = twiddles(n, count);
@@ -382,18 +403,39 @@ template <class real> struct Wave {
     return DGDFT_OK;
   }
 
-  dgdft_status upload_x0(int i, const double* x0_host) {
-    ElemDev<real>& E = h[i];
-    const size_t n = (size_t)E.ng * E.m;
-    double* tmp = nullptr;
-    CK(cudaMalloc(&tmp, n * sizeof(double)));
-    cudaError_t e = ctx_copy(ctx, tmp, x0_host, n * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-      launch_convert<double, real>(tmp, E.blk[BX][0], n, ctx->stream);
-      e = cudaStreamSynchronize(ctx->stream);
+  dgdft_status load_potential() {
+    for (size_t i = 0; i < ids.size(); ++i)
+      launch_convert<double, real>(ctx->el[ids[i]].d_veff, const_cast<real*>(h[i].V), (size_t)h[i].ng,
+                                   ctx->stream);
+    CK(cudaGetLastError());
+    return DGDFT_OK;
+  }
+
+  // Working-precision copies of V_eff and X0 from the resident FP64 inputs.
+  dgdft_status load_inputs() {
+    dgdft_status ps = load_potential();
+    if (ps != DGDFT_OK) return ps;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      ElemHost& eh = ctx->el[ids[i]];
+      ElemDev<real>& E = h[i];
+      const size_t n = (size_t)E.ng * E.m;
+      if (eh.has_x0) {
+        launch_convert<double, real>(eh.d_x0, E.blk[BX][0], n, ctx->stream);
+      } else {
+        std::vector<double> x0(n);
+        default_x0(x0, ids[i]);
+        double* tmp = nullptr;
+        CK(cudaMalloc(&tmp, n * sizeof(double)));
+        cudaError_t e = ctx_copy(ctx, tmp, x0.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+          launch_convert<double, real>(tmp, E.blk[BX][0], n, ctx->stream);
+          e = cudaStreamSynchronize(ctx->stream);
+        }
+        cudaFree(tmp);
+        if (e != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "initial block: " + cuda_err_string(e));
+      }
     }
-    cudaFree(tmp);
-    if (e != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "initial block upload: " + cuda_err_string(e));
+    CK(cudaGetLastError());
     return DGDFT_OK;
   }
 
@@ -418,6 +460,20 @@ template <class real> struct Wave {
                          cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return DGDFT_OK;
+  }
+
+  // Tensor-core Gram for the FP32 stage when the pencil fits one TMEM
+  // accumulator (3m <= 256); returns false when the SIMT kernel must run.
+  bool tc_gram(int mode, cudaStream_t st) {
+    if constexpr (std::is_same<real, float>::value) {
+      if (ctx->cfg.bulk_kernels == 0 && 3 * batch.s.max_m <= 256) {
+        launch_tc_gram(batch, mode, partial, partial_cap, st);
+        return true;
+      }
+    }
+    (void)mode;
+    (void)st;
+    return false;
   }
 
   GramJob<real> gram12() const {
@@ -479,7 +535,7 @@ template <class real> struct Wave {
       g.needs_p[0] = 0;
       g.out_id[0] = OUT_GXW;
       g.brow[0] = g.bcol[0] = 0;
-      launch_gram<real>(batch, g, partial, partial_cap, st);
+      if (!tc_gram(1, st)) launch_gram<real>(batch, g, partial, partial_cap, st);
       TsmmJob<real> t;
       t.nin = 1;
       t.in[0] = bref<real>(BX);
@@ -490,7 +546,7 @@ template <class real> struct Wave {
       launch_tsmm<real>(batch, t, st);
     }
     launch_apply_h<real>(batch, bref<real>(BW), bref<real>(BHW), 0, st);
-    launch_gram<real>(batch, gram12(), partial, partial_cap, st);
+    if (!tc_gram(0, st)) launch_gram<real>(batch, gram12(), partial, partial_cap, st);
     launch_rr(d_rr_lob, batch.s.nel, st);
     {
       TsmmJob<real> t;
@@ -729,25 +785,25 @@ dgdft_status copy_block_to(Wave<real>& w, int i, Wave<double>& dst, int di, cuda
 
 dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, double seconds,
                          const std::vector<int>& extra_iters, const std::vector<int>& extra_fb) {
-  cudaStream_t st = ctx->stream;
   for (size_t i = 0; i < w.ids.size(); ++i) {
     ElemHost& eh = ctx->el[w.ids[i]];
     const ElemDev<double>& E = w.h[i];
     const int* sw = &w.h_state[i * STATE_WORDS];
     const int J = E.J, m = E.m, ne = eh.ne();
-    double* phi_dev = nullptr;
-    CK(cudaMalloc(&phi_dev, sizeof(double) * (size_t)ne * J));
-    std::unique_ptr<void, decltype(&cudaFree)> guard(phi_dev, &cudaFree);
+    if (!eh.d_phi) {
+      CK(cudaMalloc(&eh.d_phi, sizeof(double) * (size_t)ne * J));
+      CK(cudaMalloc(&eh.d_eig, sizeof(double) * J));
+      CK(cudaMalloc(&eh.d_res, sizeof(double) * J));
+    }
     const double* x = w.current_x((int)i);
-    dgdft_status s = alb_orthonormalise(ctx, w, (int)i, x, J, phi_dev);
+    dgdft_status s = alb_orthonormalise(ctx, w, (int)i, x, J, eh.d_phi);
     if (s != DGDFT_OK && s != DGDFT_ENOTCONV) return s;
-    eh.phi.resize((size_t)ne * J);
-    CK(ctx_copy(ctx, eh.phi.data(), phi_dev, sizeof(double) * eh.phi.size(), cudaMemcpyDeviceToHost));
-    std::vector<double> th(m), rs(m);
-    CK(ctx_copy(ctx, th.data(), E.theta, sizeof(double) * m, cudaMemcpyDeviceToHost));
-    CK(ctx_copy(ctx, rs.data(), E.res, sizeof(double) * m, cudaMemcpyDeviceToHost));
-    eh.eig.assign(th.begin(), th.begin() + J);
-    eh.resid.assign(rs.begin(), rs.begin() + J);
+    CK(cudaMemcpyAsync(eh.d_eig, E.theta, sizeof(double) * J, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(eh.d_res, E.res, sizeof(double) * J, cudaMemcpyDeviceToDevice, ctx->stream));
+    eh.eig.resize(J);
+    eh.resid.resize(J);
+    CK(ctx_copy(ctx, eh.eig.data(), E.theta, sizeof(double) * J, cudaMemcpyDeviceToHost));
+    CK(ctx_copy(ctx, eh.resid.data(), E.res, sizeof(double) * J, cudaMemcpyDeviceToHost));
     if (ctx->cfg.keep_block) {
       eh.block.resize((size_t)eh.ng() * m);
       CK(ctx_copy(ctx, eh.block.data(), x, sizeof(double) * eh.block.size(), cudaMemcpyDeviceToHost));
@@ -761,62 +817,70 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     eh.rep.max_resid = mx;
     eh.rep.wave = wave_idx;
     eh.rep.seconds = seconds;
-    eh.rep.status = (sw[ST_ERROR] != 0) ? DGDFT_ENOTCONV : (mx <= ctx->cfg.tol ? DGDFT_OK : DGDFT_ENOTCONV);
+    eh.rep.status = (sw[ST_ERROR] != 0 || s != DGDFT_OK) ? DGDFT_ENOTCONV
+                                                         : (mx <= ctx->cfg.tol ? DGDFT_OK : DGDFT_ENOTCONV);
     eh.solved = true;
-    (void)st;
   }
   return DGDFT_OK;
 }
 
-dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wave_idx) {
+// The waves of one solve: FP32 bulk stage (mixed form only) and FP64 stage.
+struct WavePair {
+  std::unique_ptr<Wave<float>> w32;
+  std::unique_ptr<Wave<double>> w64;
+};
+void free_wave_pair(void* p) { delete static_cast<WavePair*>(p); }
+
+dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wave_idx, bool keep) {
   auto t0 = std::chrono::steady_clock::now();
   const dgdft_alb_config& c = ctx->cfg;
-  std::vector<double> x0;
-  Wave<double> w64;
-  std::vector<int> it32, fb32;
-  if (c.precision == DGDFT_PREC_MIXED) {
-    // stage 1: FP32 storage and arithmetic, FP64 Rayleigh-Ritz
-    std::unique_ptr<Wave<float>> w32(new Wave<float>());
-    dgdft_status s = w32->build(ctx, ids, 1e7);
-    if (s != DGDFT_OK) return s;
-    for (size_t i = 0; i < ids.size(); ++i) {
-      ElemHost& eh = ctx->el[ids[i]];
-      const double* src = eh.x0.data();
-      if (!eh.has_x0) {
-        x0.assign((size_t)eh.ng() * eh.d.n_compute, 0.0);
-        default_x0(x0, ids[i]);
-        src = x0.data();
-      }
-      if ((s = w32->upload_x0((int)i, src)) != DGDFT_OK) return s;
-    }
-    const double tol1 = std::max(10.0 * c.tol, 1e-5);
-    if ((s = w32->run(tol1, c.maxit, 6, nullptr)) != DGDFT_OK) return s;
-    if ((s = w64.build(ctx, ids, 1e14)) != DGDFT_OK) return s;
-    for (size_t i = 0; i < ids.size(); ++i) {
-      copy_block_to<float>(*w32, (int)i, w64, (int)i, ctx->stream);
-      it32.push_back(w32->h_state[i * STATE_WORDS + ST_ITER]);
-      fb32.push_back(w32->h_state[i * STATE_WORDS + ST_FALLBACK]);
-    }
-    CK(cudaStreamSynchronize(ctx->stream));
-    w32.reset();
+  const bool mixed = c.precision == DGDFT_PREC_MIXED;
+  WavePair* wp = nullptr;
+  std::unique_ptr<WavePair> owned;
+  if (keep && ctx->cache) {
+    wp = static_cast<WavePair*>(ctx->cache);
   } else {
-    dgdft_status s = w64.build(ctx, ids, 1e14);
-    if (s != DGDFT_OK) return s;
-    for (size_t i = 0; i < ids.size(); ++i) {
-      ElemHost& eh = ctx->el[ids[i]];
-      const double* src = eh.x0.data();
-      if (!eh.has_x0) {
-        x0.assign((size_t)eh.ng() * eh.d.n_compute, 0.0);
-        default_x0(x0, ids[i]);
-        src = x0.data();
-      }
-      if ((s = w64.upload_x0((int)i, src)) != DGDFT_OK) return s;
+    owned.reset(new WavePair());
+    wp = owned.get();
+    dgdft_status s;
+    if (mixed) {
+      wp->w32.reset(new Wave<float>());
+      if ((s = wp->w32->build(ctx, ids, 1e7)) != DGDFT_OK) return s;
+    }
+    wp->w64.reset(new Wave<double>());
+    if ((s = wp->w64->build(ctx, ids, 1e14)) != DGDFT_OK) return s;
+    if (keep) {
+      ctx->drop_cache();
+      ctx->cache = owned.release();
+      ctx->cache_free = free_wave_pair;
+      ctx->cache_proj_version.clear();
+      for (const ElemHost& eh : ctx->el) ctx->cache_proj_version.push_back(eh.proj_version);
     }
   }
-  dgdft_status s = w64.run(c.tol, c.maxit, 0, nullptr);
-  if (s != DGDFT_OK) return s;
-  auto t1 = std::chrono::steady_clock::now();
-  const double secs = std::chrono::duration<double>(t1 - t0).count();
+  Wave<double>& w64 = *wp->w64;
+  std::vector<int> it32, fb32;
+  dgdft_status s;
+  if (mixed) {
+    Wave<float>& w32 = *wp->w32;
+    if ((s = w32.load_inputs()) != DGDFT_OK) return s;
+    // stage 1: FP32 storage and arithmetic, FP64 Rayleigh-Ritz, to a
+    // tolerance above the FP32 residual floor (or until progress stalls)
+    const double tol1 = std::max(10.0 * c.tol, 1e-5);
+    if ((s = w32.run(tol1, c.maxit, 6, nullptr)) != DGDFT_OK) return s;
+    // stage 2 starts from the FP32 Ritz block; V_eff is reloaded in FP64
+    for (size_t i = 0; i < ids.size(); ++i) {
+      ElemHost& eh = ctx->el[ids[i]];
+      launch_convert<double, double>(eh.d_veff, const_cast<double*>(w64.h[i].V), (size_t)eh.ng(), ctx->stream);
+      copy_block_to<float>(w32, (int)i, w64, (int)i, ctx->stream);
+      it32.push_back(w32.h_state[i * STATE_WORDS + ST_ITER]);
+      fb32.push_back(w32.h_state[i * STATE_WORDS + ST_FALLBACK]);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    if ((s = w64.load_inputs()) != DGDFT_OK) return s;
+  }
+  if ((s = w64.run(c.tol, c.maxit, 0, nullptr)) != DGDFT_OK) return s;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return finish_wave(ctx, w64, wave_idx, secs, it32, fb32);
 }
 
@@ -884,29 +948,48 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
     ctx->own_stream = true;
   }
   init_hamiltonian_kernels();
+  init_tc_gram_kernel();
   ctx->el.resize(n_elem);
   for (int i = 0; i < n_elem; ++i) ctx->el[i].d = elems[i];
   *out = ctx.release();
   return DGDFT_OK;
 }
 
-static dgdft_status copy_in(dgdft_alb_ctx* ctx, std::vector<double>& dst, const double* src, size_t n,
-                            int on_device) {
-  dst.resize(n);
-  if (on_device) {
-    CK(ctx_copy(ctx, dst.data(), src, sizeof(double) * n, cudaMemcpyDeviceToHost));
-  } else {
-    std::memcpy(dst.data(), src, sizeof(double) * n);
+// Copy n doubles into a resident device buffer (allocated on first use),
+// rejecting non-finite values.
+static dgdft_status copy_resident(dgdft_alb_ctx* ctx, double*& dst, const double* src, size_t n, int on_device) {
+  if (!on_device)
+    for (size_t i = 0; i < n; ++i)
+      if (!std::isfinite(src[i])) return ctx->fail(DGDFT_EINVAL, "non-finite input value");
+  CK(cudaSetDevice(ctx->device));
+  if (!dst) {
+    cudaError_t e = cudaMalloc(&dst, sizeof(double) * n);
+    if (e != cudaSuccess) {
+      dst = nullptr;
+      return ctx->fail(DGDFT_ENOMEM, "resident input allocation: " + cuda_err_string(e));
+    }
   }
-  for (double v : dst)
-    if (!std::isfinite(v)) return ctx->fail(DGDFT_EINVAL, "non-finite input value");
+  CK(ctx_copy(ctx, dst, src, sizeof(double) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  if (on_device) {
+    int* flag = nullptr;
+    CK(cudaMalloc(&flag, sizeof(int)));
+    int h = 0;
+    cudaError_t e = ctx_copy(ctx, flag, &h, sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      launch_nonfinite(dst, n, flag, ctx->stream);
+      e = ctx_copy(ctx, &h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    }
+    cudaFree(flag);
+    if (e != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "input check: " + cuda_err_string(e));
+    if (h) return ctx->fail(DGDFT_EINVAL, "non-finite input value");
+  }
   return DGDFT_OK;
 }
 
 dgdft_status dgdft_alb_set_potential(dgdft_alb_ctx* ctx, int elem, const double* veff, int on_device) {
   if (!ctx || !veff || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
   ElemHost& eh = ctx->el[elem];
-  dgdft_status s = copy_in(ctx, eh.veff, veff, (size_t)eh.ng(), on_device);
+  dgdft_status s = copy_resident(ctx, eh.d_veff, veff, (size_t)eh.ng(), on_device);
   eh.has_v = (s == DGDFT_OK);
   eh.solved = false;
   return s;
@@ -921,6 +1004,7 @@ dgdft_status dgdft_alb_set_projectors(dgdft_alb_ctx* ctx, int elem, int n_proj, 
     eh.pidx.clear();
     eh.pval.clear();
     eh.pgamma.clear();
+    eh.proj_version += 1;
     return DGDFT_OK;
   }
   if (!row_ptr || !gamma) return DGDFT_EINVAL;
@@ -947,6 +1031,7 @@ dgdft_status dgdft_alb_set_projectors(dgdft_alb_ctx* ctx, int elem, int n_proj, 
   eh.pidx.assign(grid_idx, grid_idx + nnz);
   eh.pval.assign(val, val + nnz);
   eh.pgamma.assign(gamma, gamma + n_proj);
+  eh.proj_version += 1;
   eh.solved = false;
   return DGDFT_OK;
 }
@@ -954,7 +1039,7 @@ dgdft_status dgdft_alb_set_projectors(dgdft_alb_ctx* ctx, int elem, int n_proj, 
 dgdft_status dgdft_alb_set_initial(dgdft_alb_ctx* ctx, int elem, const double* x0, int on_device) {
   if (!ctx || !x0 || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
   ElemHost& eh = ctx->el[elem];
-  dgdft_status s = copy_in(ctx, eh.x0, x0, (size_t)eh.ng() * eh.d.n_compute, on_device);
+  dgdft_status s = copy_resident(ctx, eh.d_x0, x0, (size_t)eh.ng() * eh.d.n_compute, on_device);
   eh.has_x0 = (s == DGDFT_OK);
   return s;
 }
@@ -988,8 +1073,16 @@ dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem) {
     waves.back().push_back(id);
     acc += b;
   }
+  // one wave: keep it resident for later solves unless projectors changed
+  const bool keep = waves.size() == 1;
+  if (!keep) ctx->drop_cache();
+  if (keep && ctx->cache) {
+    bool same = ctx->cache_proj_version.size() == ctx->el.size();
+    for (size_t i = 0; same && i < ctx->el.size(); ++i) same = ctx->cache_proj_version[i] == ctx->el[i].proj_version;
+    if (!same) ctx->drop_cache();
+  }
   for (size_t w = 0; w < waves.size(); ++w) {
-    dgdft_status s = solve_wave(ctx, waves[w], (int)w);
+    dgdft_status s = solve_wave(ctx, waves[w], (int)w, keep);
     if (s != DGDFT_OK) return s;
   }
   ctx->solved_any = true;
@@ -1007,25 +1100,21 @@ dgdft_status dgdft_alb_get_basis(dgdft_alb_ctx* ctx, int elem, double* phi, doub
   if (!ctx || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
   ElemHost& eh = ctx->el[elem];
   if (!eh.solved) return ctx->fail(DGDFT_ESTATE, "get_basis before solve");
-  auto out = [&](double* dst, const std::vector<double>& src) -> dgdft_status {
-    if (!dst) return DGDFT_OK;
-    if (on_device) {
-      CK(ctx_copy(ctx, dst, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice));
-    } else {
-      std::memcpy(dst, src.data(), sizeof(double) * src.size());
-    }
-    return DGDFT_OK;
-  };
-  dgdft_status s;
-  if ((s = out(phi, eh.phi)) != DGDFT_OK) return s;
-  if ((s = out(eig, eh.eig)) != DGDFT_OK) return s;
-  return out(resid, eh.resid);
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t J = eh.d.n_keep;
+  if (phi) CK(ctx_copy(ctx, phi, eh.d_phi, sizeof(double) * J * eh.ne(), k));
+  if (eig) CK(ctx_copy(ctx, eig, eh.d_eig, sizeof(double) * J, k));
+  if (resid) CK(ctx_copy(ctx, resid, eh.d_res, sizeof(double) * J, k));
+  return DGDFT_OK;
 }
 
 const char* dgdft_alb_last_error(const dgdft_alb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void dgdft_alb_destroy(dgdft_alb_ctx* ctx) {
   if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  ctx->drop_cache();
+  for (ElemHost& eh : ctx->el) eh.release();
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -1056,6 +1145,7 @@ dgdft_status with_step_wave(dgdft_alb_ctx* ctx, int elem, Wave<real>& w) {
   CK(cudaSetDevice(ctx->device));
   dgdft_status s = w.build(ctx, std::vector<int>{elem}, 1e14);
   if (s != DGDFT_OK) return s;
+  if ((s = w.load_potential()) != DGDFT_OK) return s;
   return w.reset_states(ctx->cfg.tol);
 }
 
@@ -1125,7 +1215,10 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
   ElemDev<real>* de = nullptr;
   int* dstate = nullptr;
   const size_t tiles = ((p + 63) / 64) * ((q + 63) / 64);
-  const size_t pcap = ((size_t)(ng + 2047) / 2048) * tiles * 4096;
+  bool use_tc = false;
+  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 0 && q <= 256;
+  const size_t pcap = use_tc ? ((size_t)(ng + 2047) / 2048) * ((p + 127) / 128) * 128 * 256
+                             : ((size_t)(ng + 2047) / 2048) * tiles * 4096;
   CK(cudaMalloc(&du, sizeof(real) * (size_t)ng * p));
   CK(cudaMalloc(&dv, sizeof(real) * (size_t)ng * q));
   CK(cudaMalloc(&dc, sizeof(double) * (size_t)p * q));
@@ -1162,7 +1255,14 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
     g.ld_in = ng;
     g.ld_out = p;
     g.out_ptr = dc;
-    launch_gram<real>(b, g, part, pcap, ctx->stream);
+    if constexpr (std::is_same<real, float>::value) {
+      if (use_tc)
+        launch_tc_gram_ptrs(b, du, p, dv, q, ng, dc, part, pcap, ctx->stream);
+      else
+        launch_gram<real>(b, g, part, pcap, ctx->stream);
+    } else {
+      launch_gram<real>(b, g, part, pcap, ctx->stream);
+    }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = ctx_copy(ctx, c, dc, sizeof(double) * (size_t)p * q, cudaMemcpyDeviceToHost);
@@ -1177,9 +1277,78 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
   return s;
 }
 
+template <class real>
+dgdft_status time_stage_t(dgdft_alb_ctx* ctx, Wave<real>& w, int stage, int reps, double* ms) {
+  const int nel = (int)w.ids.size();
+  std::vector<int> saved = w.h_state;
+  for (int i = 0; i < nel; ++i) {
+    std::vector<int> st(saved.begin() + (size_t)i * STATE_WORDS, saved.begin() + (size_t)(i + 1) * STATE_WORDS);
+    st[ST_ACTIVE] = 1;
+    st[ST_HAS_P] = 1;
+    CK(ctx_copy(ctx, w.h[i].state, st.data(), sizeof(int) * STATE_WORDS, cudaMemcpyHostToDevice));
+  }
+  cudaStream_t st = ctx->stream;
+  auto launch = [&]() {
+    switch (stage) {
+      case DGDFT_STAGE_XY_FWD: launch_h_pass<real>(w.batch, 0, bref<real>(BW), bref<real>(BHW), 0, st); break;
+      case DGDFT_STAGE_Z_MULT: launch_h_pass<real>(w.batch, 1, bref<real>(BW), bref<real>(BHW), 0, st); break;
+      case DGDFT_STAGE_XY_INV: launch_h_pass<real>(w.batch, 2, bref<real>(BW), bref<real>(BHW), 0, st); break;
+      case DGDFT_STAGE_GRAM: launch_gram<real>(w.batch, w.gram12(), w.partial, w.partial_cap, st); break;
+      case DGDFT_STAGE_UPDATE: {
+        TsmmJob<real> t;
+        t.nin = 3;
+        t.in[0] = bref<real>(BX);
+        t.in[1] = bref<real>(BW);
+        t.in[2] = bref<real>(BP);
+        t.yrow[1] = 1;
+        t.yrow[2] = 2;
+        t.needs_p[2] = 1;
+        t.out = bref<real>(BX, 1);
+        launch_tsmm<real>(w.batch, t, st);
+        break;
+      }
+      case DGDFT_STAGE_RR: launch_rr(w.d_rr_lob, nel, st); break;
+      default: launch_residual<real>(w.batch, w.rnchunk, st); break;
+    }
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  launch();
+  CK(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps; ++r) launch();
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float el_ms = 0.0f;
+  CK(cudaEventElapsedTime(&el_ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  *ms = (double)el_ms / reps;
+  for (int i = 0; i < nel; ++i)
+    CK(ctx_copy(ctx, w.h[i].state, &saved[(size_t)i * STATE_WORDS], sizeof(int) * STATE_WORDS,
+                cudaMemcpyHostToDevice));
+  return DGDFT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+dgdft_status dgdft_alb_time_stage(dgdft_alb_ctx* ctx, int stage, int reps, double* ms_per_launch, int* n_elem,
+                                  int* real_bytes) {
+  if (!ctx || !ms_per_launch || stage < 0 || stage >= DGDFT_STAGE_COUNT || reps < 1) return DGDFT_EINVAL;
+  if (!ctx->cache) return ctx->fail(DGDFT_ESTATE, "no resident wave: solve first (single-wave workloads)");
+  CK(cudaSetDevice(ctx->device));
+  WavePair* wp = static_cast<WavePair*>(ctx->cache);
+  if (n_elem) *n_elem = (int)wp->w64->ids.size();
+  if (wp->w32) {
+    if (real_bytes) *real_bytes = 4;
+    return time_stage_t<float>(ctx, *wp->w32, stage, reps, ms_per_launch);
+  }
+  if (real_bytes) *real_bytes = 8;
+  return time_stage_t<double>(ctx, *wp->w64, stage, reps, ms_per_launch);
+}
 
 dgdft_status dgdft_alb_apply_h(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* hx, int on_device) {
   if (!ctx || !x || !hx || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
