@@ -155,7 +155,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, simt_only=args.simt, h_fp64_forward=args.fwd64)
     dev_x0 = []
     for k, e in enumerate(els):
         B.load_element(ctx, k, e)
@@ -195,6 +195,7 @@ def run_ours(args):
     ms_step = ms / args.steps
     value = pairs_all / (ms_step / 1e3)
     iters = [r["iterations"] for r in reps]
+    iters32 = [r["iterations_bulk"] for r in reps]
 
     # roofline of the dominant kernel (stage timed live on the same stream)
     hbm, bf16, peak_kind = peaks()
@@ -296,6 +297,8 @@ def run_ours(args):
                    "l2": "working set ~10 GB >> 129 MB L2 (no flush needed)",
                    "parallelism": f"elements batched on 1 GPU; {world} rank(s), replicated workload"},
         "eigenpairs_per_step": pairs, "iterations_mean": mean_it,
+        "iterations_fp32_mean": float(np.mean(iters32)),
+        "elements_needing_fp64_iterations": int(sum(1 for a, b in zip(iters, iters32) if a > b)),
         "iterations_max": int(max(iters)) if iters else None,
         "roofline": roof, "stages": stage_report,
         "plain_fp64": plain,
@@ -401,6 +404,8 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=3)
+    ap.add_argument("--simt", action="store_true", help="SIMT kernels only (no tcgen05)")
+    ap.add_argument("--fwd64", action="store_true", help="FP64 forward FFT in the FP32 stage's H apply")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

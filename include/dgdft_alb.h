@@ -93,6 +93,8 @@ typedef struct {
                              host after solve (for dgdft_alb_get_block)        */
   int bulk_kernels;       /* 0: tcgen05 tensor-core kernels for the FP32 stage
                              where the shapes allow (3m <= 256); 1: SIMT only */
+  int h_fp64_forward;     /* 1: the FP32 stage's H apply runs its forward FFT
+                             in FP64 (lower noise, ~10x slower passes)        */
   const char* autotune_cache;   /* optional JSON path; NULL = none            */
   const char* precond_weights;  /* learned preconditioner weights; NULL = none */
 } dgdft_alb_config;
@@ -105,6 +107,8 @@ typedef struct {
   int fallbacks;     /* Rayleigh-Ritz retries without P / preconditioner falls */
   int wave;          /* memory-admission wave the element ran in              */
   double seconds;    /* wall time of the element's wave                       */
+  int iterations_bulk; /* of `iterations`, those run in the FP32 stage (mixed) */
+  double resid_bulk;   /* max_{j<J} residual (Ha) when the FP32 stage ended   */
 } dgdft_solve_report;
 
 /* Fill cfg with defaults: FP64, Teter, tol 1e-6, maxit 400, check_every 4. */

@@ -60,6 +60,58 @@ dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int
  * values).  DGDFT_ESTATE before a solve. */
 dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device);
 
+/* ---- Learned preconditioner (the chosen form's replacement of the Teter
+ * preconditioner of Sec. II.B, operation 5).  A 3-D convolutional network:
+ * inputs (r / rms(r), V_eff), 4 layers of 3x3x3 circular convolutions,
+ * 2 -> 16 -> 16 -> 16 -> 1 channels, ReLU between layers; correction =
+ * rms(r) * output.  Weights are stored in BF16 (FP32 master copy for
+ * training), arithmetic accumulates in FP32.  Parameter vector layout: per
+ * layer, weights [c_out][c_in][3][3][3] (taps dz, dy, dx = offsets -1..1)
+ * then c_out biases; DGDFT_PRECOND_PARAMS floats in total.  Fields are
+ * [sample][channel][z][y][x] float32. */
+#define DGDFT_PRECOND_PARAMS 15169
+
+/* He-normal initial weights from `seed`, zero biases. */
+dgdft_status dgdft_alb_precond_init(dgdft_alb_ctx* ctx, uint64_t seed);
+dgdft_status dgdft_alb_precond_set_params(dgdft_alb_ctx* ctx, const float* params);
+dgdft_status dgdft_alb_precond_get_params(dgdft_alb_ctx* ctx, float* params);
+/* Weights file: "DGALBNN1", int32 layer count, per layer int32 c_in, c_out,
+ * then the float32 parameter vector.  The same file can be named in
+ * dgdft_alb_config.precond_weights. */
+dgdft_status dgdft_alb_precond_save(dgdft_alb_ctx* ctx, const char* path);
+dgdft_status dgdft_alb_precond_load(dgdft_alb_ctx* ctx, const char* path);
+
+/* Network output for B samples of nz x ny x nx: in is B x 2 fields, out is
+ * B x 1 fields (float32, host or device per on_device). */
+dgdft_status dgdft_alb_precond_forward(dgdft_alb_ctx* ctx, int B, int nz, int ny, int nx, const float* in,
+                                       float* out, int on_device);
+
+/* Mean squared error of the output against tgt over the window [lo, hi) of
+ * every axis (mean over B samples and window points) and its gradient with
+ * respect to every parameter (host array, parameter layout). */
+dgdft_status dgdft_alb_precond_loss_grad(dgdft_alb_ctx* ctx, int B, int nz, int ny, int nx, int lo, int hi,
+                                         const float* in, const float* tgt, double* loss, float* grads,
+                                         int on_device);
+
+/* Train with Adam (lr, betas 0.9/0.999) on `steps` batches of `batch` random
+ * crops of edge `crop` (periodic wrap) from nfields fields r, v, t (device
+ * arrays, nfields x nz x ny x nx each): input (r / rms(r), v), target
+ * t / rms(r), loss on the crop interior [4, crop - 4).  Reports the mean loss
+ * of the first and last min(10, steps) batches. */
+dgdft_status dgdft_alb_precond_train(dgdft_alb_ctx* ctx, int nfields, int nz, int ny, int nx, const float* r,
+                                     const float* v, const float* t, int crop, int batch, int steps, double lr,
+                                     uint64_t seed, double* loss_first, double* loss_last);
+
+/* Training pairs from the plain solver: for each snapshot q the FP64 LOBPCG
+ * of element `elem` is run from its initial block for snap_iters[q]
+ * iterations; its residual block R (m fields) goes to r_out, and
+ * t = (H - sigma I)^-1 R, sigma = (lowest Ritz value) - 1 Ha, solved by FP64
+ * conjugate gradients to relative residual 1e-10, goes to t_out (device
+ * float32, nsnap x m x N_g each).  sigma and CG iteration counts per snapshot
+ * are returned when the pointers are non-NULL. */
+dgdft_status dgdft_alb_precond_make_data(dgdft_alb_ctx* ctx, int elem, int nsnap, const int* snap_iters,
+                                         float* r_out, float* t_out, double* sigma, int* cg_iters);
+
 /* Kernel stages that dgdft_alb_time_stage can time in isolation. */
 enum {
   DGDFT_STAGE_XY_FWD = 0,   /* FFT pass 1: r2c along x, FFT along y (H apply)  */

@@ -33,13 +33,14 @@ class dgdft_alb_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("tol", C.c_double),
                 ("maxit", C.c_int), ("check_every", C.c_int), ("hbm_cap_bytes", C.c_size_t),
                 ("cuda_stream", C.c_void_p), ("device", C.c_int), ("keep_block", C.c_int),
-                ("bulk_kernels", C.c_int),
+                ("bulk_kernels", C.c_int), ("h_fp64_forward", C.c_int),
                 ("autotune_cache", C.c_char_p), ("precond_weights", C.c_char_p)]
 
 
 class dgdft_solve_report(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("max_resid", C.c_double),
-                ("fallbacks", C.c_int), ("wave", C.c_int), ("seconds", C.c_double)]
+                ("fallbacks", C.c_int), ("wave", C.c_int), ("seconds", C.c_double),
+                ("iterations_bulk", C.c_int), ("resid_bulk", C.c_double)]
 
 
 _P = C.c_void_p
@@ -63,7 +64,21 @@ _SIGS = {
     "dgdft_alb_get_block": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "dgdft_alb_time_stage": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int)]),
+    "dgdft_alb_precond_init": (C.c_int, [_P, C.c_uint64]),
+    "dgdft_alb_precond_set_params": (C.c_int, [_P, _P]),
+    "dgdft_alb_precond_get_params": (C.c_int, [_P, _P]),
+    "dgdft_alb_precond_save": (C.c_int, [_P, C.c_char_p]),
+    "dgdft_alb_precond_load": (C.c_int, [_P, C.c_char_p]),
+    "dgdft_alb_precond_forward": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "dgdft_alb_precond_loss_grad": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P,
+                                              C.POINTER(C.c_double), _P, C.c_int]),
+    "dgdft_alb_precond_train": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int,
+                                          C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]),
+    "dgdft_alb_precond_make_data": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
 }
+
+PRECOND_PARAMS = 15169
 
 _lib = None
 
@@ -116,7 +131,7 @@ class Context:
 
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
-                 precond_weights=None, simt_only=False):
+                 precond_weights=None, simt_only=False, h_fp64_forward=False):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -127,6 +142,7 @@ class Context:
         cfg.check_every = check_every
         cfg.keep_block = int(keep_block)
         cfg.bulk_kernels = int(simt_only)
+        cfg.h_fp64_forward = int(h_fp64_forward)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
         cfg.cuda_stream = stream
         self._weights = precond_weights.encode() if precond_weights else None
@@ -189,7 +205,8 @@ class Context:
         if st not in (DGDFT_OK, DGDFT_ENOTCONV) or (check and st != DGDFT_OK):
             self._check(st, "solve")
         return st, [dict(status=r.status, iterations=r.iterations, max_resid=r.max_resid,
-                         fallbacks=r.fallbacks, wave=r.wave, seconds=r.seconds) for r in reps]
+                         fallbacks=r.fallbacks, wave=r.wave, seconds=r.seconds,
+                         iterations_bulk=r.iterations_bulk, resid_bulk=r.resid_bulk) for r in reps]
 
     def dgdft_alb_get_basis(self, elem, phi=None, eig=None, resid=None):
         d = self.descs[elem]
@@ -217,6 +234,76 @@ class Context:
         self._check(self.lib.dgdft_alb_time_stage(self.h, stage, reps, C.byref(ms), C.byref(ne),
                                                   C.byref(rb)), "time_stage")
         return ms.value, ne.value, rb.value
+
+    # learned preconditioner ---------------------------------------------
+    def dgdft_alb_precond_init(self, seed=0):
+        self._check(self.lib.dgdft_alb_precond_init(self.h, seed), "precond_init")
+
+    def dgdft_alb_precond_set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == PRECOND_PARAMS
+        self._check(self.lib.dgdft_alb_precond_set_params(self.h, _ptr(p)[0]), "precond_set_params")
+
+    def dgdft_alb_precond_get_params(self):
+        p = np.zeros(PRECOND_PARAMS, np.float32)
+        self._check(self.lib.dgdft_alb_precond_get_params(self.h, _ptr(p)[0]), "precond_get_params")
+        return p
+
+    def dgdft_alb_precond_save(self, path):
+        self._check(self.lib.dgdft_alb_precond_save(self.h, path.encode()), "precond_save")
+
+    def dgdft_alb_precond_load(self, path):
+        self._check(self.lib.dgdft_alb_precond_load(self.h, path.encode()), "precond_load")
+
+    def dgdft_alb_precond_forward(self, inp):
+        """inp: (B, 2, nz, ny, nx) float32 (NumPy or CUDA tensor)."""
+        B, _, nz, ny, nx = inp.shape
+        if isinstance(inp, np.ndarray):
+            inp = np.ascontiguousarray(inp, np.float32)
+            out = np.zeros((B, 1, nz, ny, nx), np.float32)
+        else:
+            import torch
+            out = torch.zeros((B, 1, nz, ny, nx), dtype=torch.float32, device=inp.device)
+        pi, dev = _ptr(inp)
+        self._check(self.lib.dgdft_alb_precond_forward(self.h, B, nz, ny, nx, pi, _ptr(out)[0], dev),
+                    "precond_forward")
+        return out
+
+    def dgdft_alb_precond_loss_grad(self, inp, tgt, lo, hi):
+        inp = np.ascontiguousarray(inp, np.float32)
+        tgt = np.ascontiguousarray(tgt, np.float32)
+        B, _, nz, ny, nx = inp.shape
+        loss = C.c_double()
+        g = np.zeros(PRECOND_PARAMS, np.float32)
+        self._check(self.lib.dgdft_alb_precond_loss_grad(self.h, B, nz, ny, nx, lo, hi, _ptr(inp)[0],
+                                                         _ptr(tgt)[0], C.byref(loss), _ptr(g)[0], 0),
+                    "precond_loss_grad")
+        return loss.value, g
+
+    def dgdft_alb_precond_train(self, r, v, t, crop=32, batch=8, steps=100, lr=1e-3, seed=0):
+        """r, v, t: CUDA float32 tensors (nfields, nz, ny, nx)."""
+        nf, nz, ny, nx = r.shape
+        l0 = C.c_double()
+        l1 = C.c_double()
+        self._check(self.lib.dgdft_alb_precond_train(self.h, nf, nz, ny, nx, _ptr(r)[0], _ptr(v)[0], _ptr(t)[0],
+                                                     crop, batch, steps, lr, seed, C.byref(l0), C.byref(l1)),
+                    "precond_train")
+        return l0.value, l1.value
+
+    def dgdft_alb_precond_make_data(self, elem, snap_iters):
+        """(r, t, sigma, cg_iters): CUDA float32 tensors (nsnap * m, nz, ny, nx)."""
+        import torch
+        d = self.descs[elem]
+        ns = len(snap_iters)
+        shape = (ns * d.n_compute, d.nz, d.ny, d.nx)
+        r = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        t = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        it = np.ascontiguousarray(snap_iters, np.int32)
+        sig = np.zeros(ns)
+        cg = np.zeros(ns, np.int32)
+        self._check(self.lib.dgdft_alb_precond_make_data(self.h, elem, ns, _ptr(it)[0], _ptr(r)[0], _ptr(t)[0],
+                                                         _ptr(sig)[0], _ptr(cg)[0]), "precond_make_data")
+        return r, t, sig, cg
 
     # step entry points -------------------------------------------------
     def dgdft_alb_apply_h(self, elem, x):

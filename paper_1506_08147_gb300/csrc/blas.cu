@@ -108,6 +108,7 @@ __global__ void gram_reduce_kernel(const ElemDev<real>* __restrict__ elems, Gram
     case OUT_GRAM_A: out = e.gram; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
     case OUT_GRAM_B: out = e.gram + (size_t)9 * e.m * e.m; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
     case OUT_GXW: out = e.gxw; ld = job.ld_out > 0 ? job.ld_out : e.m; break;
+    case OUT_Y: out = e.Y; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
     default: out = job.out_ptr; ld = job.ld_out; break;
   }
   const double* base = partial + blockIdx.z * pstride + (size_t)blockIdx.x * (TILE * TILE);
@@ -281,6 +282,26 @@ __global__ void post_residual_kernel(const ElemDev<real>* __restrict__ elems, in
   }
 }
 
+// theta_j = 0 (mode 0) or the Rayleigh quotient x.Hx / x.x from the residual
+// partial sums (mode 1), for every column of every active element.
+template <class real>
+__global__ void theta_kernel(const ElemDev<real>* __restrict__ elems, int nchunk, int mode) {
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  for (int j = threadIdx.x; j < e.m; j += blockDim.x) {
+    if (mode == 0) {
+      e.theta[j] = 0.0;
+      continue;
+    }
+    double xx = 0.0, xhx = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      xx += e.rpart[((size_t)j * nchunk + c) * 4 + 1];
+      xhx += e.rpart[((size_t)j * nchunk + c) * 4 + 2];
+    }
+    e.theta[j] = xhx / xx;
+  }
+}
+
 template <class real>
 __global__ void iter_finish_kernel(const ElemDev<real>* __restrict__ elems, int nel, int set_p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -336,6 +357,11 @@ void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStrea
 }
 
 template <class real>
+void launch_theta(const Batch<real>& b, int nchunk, int mode, cudaStream_t st) {
+  theta_kernel<real><<<dim3(1, 1, b.s.nel), 128, 0, st>>>(b.d_elems, nchunk, mode);
+}
+
+template <class real>
 void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st) {
   iter_finish_kernel<real><<<(b.s.nel + 127) / 128, 128, 0, st>>>(b.d_elems, b.s.nel, set_p);
 }
@@ -346,7 +372,8 @@ void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st) {
   template void launch_tsmm<real>(const Batch<real>&, const TsmmJob<real>&, cudaStream_t);           \
   template void launch_residual<real>(const Batch<real>&, int, cudaStream_t);                        \
   template void launch_post_residual<real>(const Batch<real>&, int, int, cudaStream_t);              \
-  template void launch_iter_finish<real>(const Batch<real>&, int, cudaStream_t);
+  template void launch_iter_finish<real>(const Batch<real>&, int, cudaStream_t);                    \
+  template void launch_theta<real>(const Batch<real>&, int, int, cudaStream_t);
 DGDFT_INST(double)
 DGDFT_INST(float)
 #undef DGDFT_INST

@@ -45,11 +45,13 @@ enum {
   ST_ERROR = 4,     // bit flags, see ERR_*
   ST_CONVERGED = 5, // 1 once max residual <= tol
   ST_FALLBACK = 6,  // Rayleigh-Ritz retries without P
+  ST_TETER = 7,     // 1: precondition with Teter (the learned network's fallback)
   STATE_WORDS = 8
 };
 enum { ERR_CHOL = 1, ERR_NONFINITE = 2, ERR_EIG = 4 };
 
 constexpr int MAX_STAGES = 8;
+enum { TW_H = 0, TW_X = 1, TW_Y = 2, TW_Z = 3 };
 
 struct FftPlan {
   int n;                    // transform length
@@ -66,10 +68,11 @@ template <class real> struct ElemDev {
   double scale;             // 2 / N_g: normalisation of r2c forward + c2r inverse
   double tol;
   FftPlan px, py, pz;       // x plan is for the half length nh
-  const C* tw_h;            // e^{-2 pi i t / nh}, t < nh
-  const C* tw_x;            // e^{-2 pi i t / nx}, t <= nh (r2c post-processing)
-  const C* tw_y;            // e^{-2 pi i t / ny}
-  const C* tw_z;            // e^{-2 pi i t / nz}
+  // twiddle tables e^{-2 pi i t / n} per axis: [TW_H] n = nx/2 (t < nh),
+  // [TW_X] n = nx (t <= nh, r2c post-processing), [TW_Y] n = ny, [TW_Z] n = nz;
+  // in working precision and in FP64 (the same table for FP64 waves)
+  const C* tw[4];
+  const double2* tw64[4];
   const double* gx2;        // (2 pi kx / Lx)^2 / 2, kx = 0..nh
   const double* gy2;        // (2 pi f_y / Ly)^2 / 2 over y index (|f| <= ny/2)
   const double* gz2;
@@ -90,7 +93,7 @@ template <class real> struct ElemDev {
   real* Ccoef;              // n_proj x m projector coefficients (column j contiguous)
   // blocks
   real* blk[NBLK][2];       // [sel][buffer]; single-buffered blocks use [0]
-  C* Z;                     // FFT scratch, m * nspec
+  void* Z;                  // FFT scratch, m * nspec complex of up to FP64 size
   // small FP64 workspace
   double* gram;             // 2 x (3m)^2: A then B (ld 3m)
   double* gxw;              // m x m: X^T W
@@ -110,6 +113,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Twiddle table of axis `a` in the transform's compute precision TC.
+template <class TC, class real>
+__device__ __forceinline__ const cplx_t<TC>* twp(const ElemDev<real>& e, int a) {
+  if constexpr (sizeof(TC) == sizeof(double)) {
+    return e.tw64[a];
+  } else {
+    return reinterpret_cast<const cplx_t<TC>*>(e.tw[a]);
+  }
 }
 
 template <class real>

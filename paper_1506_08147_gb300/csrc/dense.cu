@@ -71,6 +71,19 @@ __device__ double block_min(double v, double* red) {
 
 __device__ double block_max(double v, double* red) { return -block_min(-v, red); }
 
+// Number of eigenvalues of the tridiagonal (d, e) below x, in FP32 (used to
+// locate shifts; FP64 is ~60x slower per operation on this part).
+__device__ int sturm_count_f(const float* d, const float* e2, int n, float x, float tiny) {
+  int c = 0;
+  float q = 1.0f;
+  for (int i = 0; i < n; ++i) {
+    q = d[i] - x - ((i > 0) ? __fdividef(e2[i - 1], q) : 0.0f);
+    if (fabsf(q) < tiny) q = -tiny;
+    if (q < 0.0f) ++c;
+  }
+  return c;
+}
+
 // Number of eigenvalues of the tridiagonal (d, e) below x.
 __device__ int sturm_count(const double* d, const double* e, int n, double x, double tiny) {
   int c = 0;
@@ -362,8 +375,12 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
       W.lam[i] = 0.5 * (lo + hi);
     }
     __syncthreads();
-    // 6. inverse iteration, clusters re-orthogonalised
-    const double ortol = 1e-3 * gnorm;
+    // 6. inverse iteration, one thread per eigenvalue.  Eigenvalues closer
+    // than 1e-7 |T| form a cluster whose vectors one thread computes in
+    // turn, orthogonalising against the cluster (inverse iteration alone
+    // cannot separate them); all other vectors are accurate to ~eps |T| / gap
+    // on their own.  A modified Gram-Schmidt pass over all m vectors follows.
+    const double ortol = 1e-7 * gnorm;
     if (tid == 0) {
       for (int i = 0; i < m; ++i)
         W.cstart[i] = (i == 0 || W.lam[i] - W.lam[i - 1] > ortol) ? i : W.cstart[i - 1];
@@ -383,7 +400,7 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
         double* u2 = u1 + n;
         double* mul = u2 + n;
         for (int i = 0; i < n; ++i) b[i] = hash_unit(i, q + 7919u * blockIdx.x);
-        for (int it = 0; it < 4; ++it) {
+        for (int it = 0; it < 3; ++it) {
           double nb = 0.0;
           for (int i = 0; i < n; ++i) nb += b[i] * b[i];
           nb = 1.0 / sqrt(nb);
@@ -403,6 +420,32 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
       }
     }
     __syncthreads();
+    {
+      // modified Gram-Schmidt over the m vectors (columns of Z, length n)
+      const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+      for (int j = 0; j < m; ++j) {
+        double* zj = W.Z + (size_t)j * n;
+        double part = 0.0;
+        for (int i = tid; i < n; i += nt) part += zj[i] * zj[i];
+        const double inv = 1.0 / sqrt(block_sum(part, red));
+        for (int i = tid; i < n; i += nt) zj[i] *= inv;
+        __syncthreads();
+        for (int k = j + 1 + warp; k < m; k += nw) {
+          const double* zk = W.Z + (size_t)k * n;
+          double s2 = 0.0;
+          for (int i = lane; i < n; i += 32) s2 += zj[i] * zk[i];
+          s2 = warp_sum(s2);
+          if (lane == 0) W.ptmp[k] = s2;
+        }
+        __syncthreads();
+        const int rest = m - j - 1;
+        for (int t = tid; t < rest * n; t += nt) {
+          const int k = j + 1 + t / n, i = t - (k - j - 1) * n;
+          W.Z[i + (size_t)k * n] -= W.ptmp[k] * zj[i];
+        }
+        __syncthreads();
+      }
+    }
     // 7. back-transformation by the reflectors, then Y = D L^-T Z
     for (int k = n - 3; k >= 0; --k) {
       const double* v = W.H + (size_t)k * n;
@@ -441,6 +484,387 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
   }
 }
 
+
+// Shared-memory variant for pencils whose n x n working matrix and n x m
+// eigenvector block fit in one CTA's shared memory (n = 3m <= ~150 at m = 48).
+// Same algorithm; every O(n^3) phase runs on shared memory with all threads
+// (right-looking triangular solves, in-place Householder reflectors) and the
+// eigenvalues are found by parallel multisection of the Sturm count.
+constexpr int RRS_THREADS = 512;
+
+__global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __restrict__ tasks) {
+  const RRTask T = tasks[blockIdx.x];
+  if (T.state && !T.state[ST_ACTIVE]) return;
+  extern __shared__ __align__(16) double smd[];
+  __shared__ double red[32];
+  __shared__ int sflag;
+  __shared__ double sval[4];
+  const int m = T.m;
+  int n = (T.mode == RR_FIXED) ? T.n_fixed
+          : (T.mode == RR_INITIAL) ? m
+          : (T.state[ST_HAS_P] ? 3 * m : 2 * m);
+  const int bm = (T.mode == RR_FIXED) ? n : m;
+  const int n_out = (T.mode == RR_LOBPCG) ? 3 * m : n;
+  const int nmax = n;  // shared layout is sized for the first attempt
+  double* S = smd;                          // n x n working matrix
+  double* Z = S + (size_t)nmax * nmax;      // n x m eigenvectors
+  double* d = Z + (size_t)nmax * m;         // tridiagonal diagonal
+  double* e = d + nmax;                     // off-diagonal
+  double* scal = e + nmax;                  // equilibration
+  double* ptmp = scal + nmax;               // n scratch
+  double* lam = ptmp + nmax;                // m eigenvalues
+  double* lo_s = lam + m;                   // m interval bounds
+  double* hi_s = lo_s + m;
+  int* cnt = reinterpret_cast<int*>(hi_s + m);  // multisection counts (nt)
+  bool dropped = false;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+
+  for (;;) {
+    RRWork W = carve(T.work, n, m);  // global: L (n x n), tri-solve scratch, cluster starts
+    // 1. B: symmetrise, equilibrate, Cholesky in shared memory
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx % n, c = idx / n;
+      const int br = r / bm, bc = c / bm;
+      double b;
+      if (br < bc) b = T.B[r + (size_t)c * T.ld];
+      else if (br > bc) b = T.B[c + (size_t)r * T.ld];
+      else b = 0.5 * (T.B[r + (size_t)c * T.ld] + T.B[c + (size_t)r * T.ld]);
+      S[idx] = b;
+    }
+    if (tid == 0) sflag = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+      const double bii = S[i + (size_t)i * n];
+      if (!(bii > 0.0) || !isfinite(bii)) {
+        sflag = 1;
+        scal[i] = 0.0;
+      } else {
+        scal[i] = 1.0 / sqrt(bii);
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nt) S[idx] *= scal[idx % n] * scal[idx / n];
+    __syncthreads();
+    double pmin = DBL_MAX, pmax = 0.0;
+    for (int k = 0; k < n && !sflag; ++k) {
+      if (tid == 0) {
+        const double p = S[k + (size_t)k * n];
+        if (!(p > 0.0) || !isfinite(p)) {
+          sflag = 1;
+        } else {
+          sval[0] = sqrt(p);
+          S[k + (size_t)k * n] = sval[0];
+        }
+      }
+      __syncthreads();
+      if (sflag) break;
+      const double dk = sval[0];
+      pmin = fmin(pmin, dk);
+      pmax = fmax(pmax, dk);
+      const double inv = 1.0 / dk;
+      for (int i = k + 1 + tid; i < n; i += nt) S[i + (size_t)k * n] *= inv;
+      __syncthreads();
+      const int nk = n - k - 1;
+      for (int t = tid; t < nk * nk; t += nt) {
+        const int jj = t / nk, ii = t - jj * nk;
+        if (ii < jj) continue;
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        S[i + (size_t)j * n] -= S[i + (size_t)k * n] * S[j + (size_t)k * n];
+      }
+      __syncthreads();
+    }
+    bool fail = sflag != 0;
+    if (!fail && (pmax / pmin) * (pmax / pmin) > T.cond_max) fail = true;
+    __syncthreads();
+    if (fail) {
+      if (T.mode == RR_LOBPCG && n == 3 * m) {
+        n = 2 * m;
+        dropped = true;
+        __syncthreads();
+        continue;
+      }
+      if (tid == 0 && T.state) {
+        T.state[ST_ERROR] |= ERR_CHOL;
+        T.state[ST_ACTIVE] = 0;
+      }
+      if (tid == 0 && !T.state) T.theta[0] = __longlong_as_double(0x7ff8000000000000LL);
+      return;
+    }
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx % n, c = idx / n;
+      const double l = (r >= c) ? S[idx] : 0.0;
+      W.L[idx] = l;                    // L, column-major
+      W.H[c + (size_t)r * n] = l;      // L^T, for the final back-substitution
+    }
+    __syncthreads();
+    // 2. C = L^-1 A L^-T: A into shared memory, two right-looking solves
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx % n, c = idx / n;
+      const int br = r / bm, bc = c / bm;
+      double a;
+      if (br < bc) a = T.A[r + (size_t)c * T.ld];
+      else if (br > bc) a = T.A[c + (size_t)r * T.ld];
+      else a = 0.5 * (T.A[r + (size_t)c * T.ld] + T.A[c + (size_t)r * T.ld]);
+      S[idx] = a * scal[r] * scal[c];
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int k = 0; k < n; ++k) {
+        const double inv = 1.0 / W.L[k + (size_t)k * n];
+        for (int c = tid; c < n; c += nt) S[k + (size_t)c * n] *= inv;
+        __syncthreads();
+        const int nk = n - k - 1;
+        for (int t = tid; t < nk * n; t += nt) {
+          const int c = t / nk, i = k + 1 + (t - c * nk);
+          S[i + (size_t)c * n] -= W.L[i + (size_t)k * n] * S[k + (size_t)c * n];
+        }
+        __syncthreads();
+      }
+      if (pass == 0) {  // S <- S^T
+        for (int idx = tid; idx < n * n; idx += nt) {
+          const int r = idx % n, c = idx / n;
+          if (r < c) {
+            const double t = S[idx];
+            S[idx] = S[c + (size_t)r * n];
+            S[c + (size_t)r * n] = t;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx % n, c = idx / n;
+      if (r < c) {
+        const double v = 0.5 * (S[idx] + S[c + (size_t)r * n]);
+        S[idx] = v;
+        S[c + (size_t)r * n] = v;
+      }
+    }
+    __syncthreads();
+    // 3. Householder tridiagonalisation; reflector k kept in S[k+1.., k]
+    for (int k = 0; k + 2 < n; ++k) {
+      double part = 0.0;
+      for (int i = k + 1 + tid; i < n; i += nt) {
+        const double x = S[i + (size_t)k * n];
+        part += x * x;
+      }
+      const double xx = block_sum(part, red);
+      const double x0 = S[k + 1 + (size_t)k * n];
+      const double alpha = (x0 >= 0.0) ? -sqrt(xx) : sqrt(xx);
+      const double vn2 = xx - 2.0 * alpha * x0 + alpha * alpha;
+      if (tid == 0) {
+        d[k] = S[k + (size_t)k * n];
+        e[k] = (vn2 > 0.0) ? alpha : x0;
+      }
+      __syncthreads();
+      double* v = S + (size_t)k * n;  // column k, rows > k
+      if (!(vn2 > 0.0)) {
+        for (int i = k + 1 + tid; i < n; i += nt) v[i] = 0.0;
+        __syncthreads();
+        continue;
+      }
+      const double inv = 1.0 / sqrt(vn2);
+      for (int i = k + 1 + tid; i < n; i += nt) v[i] = (i == k + 1 ? x0 - alpha : v[i]) * inv;
+      __syncthreads();
+      for (int i = k + 1 + warp; i < n; i += nw) {
+        double s2 = 0.0;
+        for (int j = k + 1 + lane; j < n; j += 32) s2 += S[j + (size_t)i * n] * v[j];
+        s2 = warp_sum(s2);
+        if (lane == 0) ptmp[i] = s2;
+      }
+      __syncthreads();
+      double kp = 0.0;
+      for (int i = k + 1 + tid; i < n; i += nt) kp += v[i] * ptmp[i];
+      const double K = block_sum(kp, red);
+      for (int i = k + 1 + tid; i < n; i += nt) ptmp[i] = 2.0 * ptmp[i] - 2.0 * K * v[i];
+      __syncthreads();
+      const int nk = n - k - 1;
+      for (int t = tid; t < nk * nk; t += nt) {
+        const int jj = t / nk, ii = t - jj * nk;
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        S[i + (size_t)j * n] -= v[i] * ptmp[j] + ptmp[i] * v[j];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (n >= 2) {
+        d[n - 2] = S[n - 2 + (size_t)(n - 2) * n];
+        e[n - 2] = S[n - 1 + (size_t)(n - 2) * n];
+      }
+      d[n - 1] = S[n - 1 + (size_t)(n - 1) * n];
+      e[n - 1] = 0.0;
+      if (n >= 2) S[n - 1 + (size_t)(n - 2) * n] = 0.0;  // no reflector for the last columns
+    }
+    __syncthreads();
+    // 4. eigenvalue shifts: FP32 Sturm bisection, one thread per eigenvalue
+    // (final eigenvalues are FP64 Rayleigh quotients after inverse iteration)
+    double glo = DBL_MAX, ghi = -DBL_MAX, gnorm = 0.0;
+    for (int i = tid; i < n; i += nt) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+      glo = fmin(glo, d[i] - r);
+      ghi = fmax(ghi, d[i] + r);
+      gnorm = fmax(gnorm, fabs(d[i]) + r);
+    }
+    glo = block_min(glo, red);
+    ghi = block_max(ghi, red);
+    gnorm = block_max(gnorm, red);
+    const double eps = DBL_EPSILON;
+    float* df = reinterpret_cast<float*>(cnt);    // n <= RRS_THREADS floats
+    float* ef2 = reinterpret_cast<float*>(ptmp);  // n floats in n doubles
+    for (int i = tid; i < n; i += nt) {
+      df[i] = (float)d[i];
+      ef2[i] = (float)(e[i] * e[i]);
+    }
+    __syncthreads();
+    {
+      const float tinyf = 1e-30f;
+      const float padf = 1e-6f * (float)fmax(gnorm, 1e-30);
+      for (int j = tid; j < m; j += nt) {
+        float lo = (float)glo - padf, hi = (float)ghi + padf;
+        for (int it = 0; it < 40; ++it) {
+          const float mid = 0.5f * (lo + hi);
+          if (!(mid > lo && mid < hi)) break;
+          if (sturm_count_f(df, ef2, n, mid, tinyf) > j)
+            hi = mid;
+          else
+            lo = mid;
+        }
+        lam[j] = 0.5 * ((double)lo + (double)hi);
+      }
+    }
+    __syncthreads();
+    // 5. inverse iteration (one thread per eigenvalue); shifts closer than the
+    // FP32 location accuracy form clusters orthogonalised in turn
+    const double ortol = 1e-5 * gnorm;
+    if (tid == 0) {
+      for (int i = 0; i < m; ++i)
+        W.cstart[i] = (i == 0 || lam[i] - lam[i - 1] > ortol) ? i : W.cstart[i - 1];
+    }
+    __syncthreads();
+    const double sep = 10.0 * eps * gnorm;
+    for (int s0 = tid; s0 < m; s0 += nt) {
+      if (W.cstart[s0] != s0) continue;
+      const bool single = (s0 + 1 >= m) || (W.cstart[s0 + 1] != s0);
+      double lam_prev = -DBL_MAX;
+      for (int q = s0; q < m && W.cstart[q] == s0; ++q) {
+        double lq = lam[q];
+        if (q > s0 && lq - lam_prev < sep) lq = lam_prev + sep;
+        lam_prev = lq;
+        double* b = Z + (size_t)q * n;
+        double* u0 = W.tri + (size_t)5 * n * q;
+        double* u1 = u0 + n;
+        double* u2 = u1 + n;
+        double* mul = u2 + n;
+        for (int i = 0; i < n; ++i) b[i] = hash_unit(i, q + 7919u * blockIdx.x);
+        for (int it = 0; it < 4; ++it) {
+          double nb = 0.0;
+          for (int i = 0; i < n; ++i) nb += b[i] * b[i];
+          nb = 1.0 / sqrt(nb);
+          for (int i = 0; i < n; ++i) b[i] *= nb;
+          if (single && it > 0) {
+            // Rayleigh-quotient shift from the current unit vector (cubic
+            // convergence from the FP32-located start)
+            double rq = 0.0;
+            for (int i = 0; i < n; ++i) {
+              double t = d[i] * b[i];
+              if (i > 0) t += e[i - 1] * b[i - 1];
+              if (i + 1 < n) t += e[i] * b[i + 1];
+              rq += b[i] * t;
+            }
+            lq = rq;
+          }
+          tri_solve(d, e, n, lq, b, u0, u1, u2, mul, eps * fmax(gnorm, 1e-300));
+          for (int p = s0; p < q; ++p) {
+            const double* zp = Z + (size_t)p * n;
+            double dp = 0.0;
+            for (int i = 0; i < n; ++i) dp += zp[i] * b[i];
+            for (int i = 0; i < n; ++i) b[i] -= dp * zp[i];
+          }
+        }
+        double nb = 0.0;
+        for (int i = 0; i < n; ++i) nb += b[i] * b[i];
+        nb = 1.0 / sqrt(nb);
+        for (int i = 0; i < n; ++i) b[i] *= nb;
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {  // modified Gram-Schmidt over the m vectors
+      double* zj = Z + (size_t)j * n;
+      double part = 0.0;
+      for (int i = tid; i < n; i += nt) part += zj[i] * zj[i];
+      const double inv = 1.0 / sqrt(block_sum(part, red));
+      for (int i = tid; i < n; i += nt) zj[i] *= inv;
+      __syncthreads();
+      for (int k = j + 1 + warp; k < m; k += nw) {
+        const double* zk = Z + (size_t)k * n;
+        double s3 = 0.0;
+        for (int i = lane; i < n; i += 32) s3 += zj[i] * zk[i];
+        s3 = warp_sum(s3);
+        if (lane == 0) ptmp[k] = s3;
+      }
+      __syncthreads();
+      const int rest = m - j - 1;
+      for (int t = tid; t < rest * n; t += nt) {
+        const int k = j + 1 + t / n, i = t - (k - j - 1) * n;
+        Z[i + (size_t)k * n] -= ptmp[k] * zj[i];
+      }
+      __syncthreads();
+    }
+    // eigenvalues as FP64 Rayleigh quotients z^T T z of the unit vectors
+    for (int j = warp; j < m; j += nw) {
+      const double* zj = Z + (size_t)j * n;
+      double s5 = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        double t = d[i] * zj[i];
+        if (i > 0) t += e[i - 1] * zj[i - 1];
+        if (i + 1 < n) t += e[i] * zj[i + 1];
+        s5 += zj[i] * t;
+      }
+      s5 = warp_sum(s5);
+      if (lane == 0) lam[j] = s5;
+    }
+    __syncthreads();
+    // 6. back-transformation, then Y = D L^-T Z (right-looking)
+    for (int k = n - 3; k >= 0; --k) {
+      const double* v = S + (size_t)k * n;
+      for (int c = warp; c < m; c += nw) {
+        const double* zc = Z + (size_t)c * n;
+        double s4 = 0.0;
+        for (int i = k + 1 + lane; i < n; i += 32) s4 += v[i] * zc[i];
+        s4 = warp_sum(s4);
+        if (lane == 0) ptmp[c] = s4;
+      }
+      __syncthreads();
+      const int nk = n - k - 1;
+      for (int t = tid; t < nk * m; t += nt) {
+        const int c = t / nk, i = k + 1 + (t - c * nk);
+        Z[i + (size_t)c * n] -= 2.0 * v[i] * ptmp[c];
+      }
+      __syncthreads();
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      const double inv = 1.0 / W.L[i + (size_t)i * n];
+      for (int c = tid; c < m; c += nt) Z[i + (size_t)c * n] *= inv;
+      __syncthreads();
+      const double* lrow = W.H + (size_t)i * n;  // L[i, k] for k < i, contiguous
+      for (int t = tid; t < i * m; t += nt) {
+        const int c = t / i, k = t - c * i;
+        Z[k + (size_t)c * n] -= lrow[k] * Z[i + (size_t)c * n];
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < n_out * m; idx += nt) {
+      const int r = idx % n_out, c = idx / n_out;
+      T.Y[r + (size_t)c * T.ldy] = (r < n) ? Z[r + (size_t)c * n] * scal[r] : 0.0;
+    }
+    for (int c = tid; c < m; c += nt) T.theta[c] = lam[c];
+    if (tid == 0 && dropped && T.state) T.state[ST_FALLBACK] += 1;
+    (void)nmax;
+    return;
+  }
+}
+
 }  // namespace
 
 size_t rr_work_doubles(int n_max, int m) {
@@ -448,9 +872,24 @@ size_t rr_work_doubles(int n_max, int m) {
          (size_t)m + 16;
 }
 
-void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st) {
+size_t rr_smem_bytes(int n, int m) {
+  return sizeof(double) * ((size_t)n * n + (size_t)n * m + 4 * (size_t)n + 3 * (size_t)m) +
+         sizeof(int) * RRS_THREADS + 64;
+}
+
+void init_rr_kernels() { opt_in_dynamic_smem((const void*)rr_smem_kernel); }
+
+// n_max: the largest pencil any task can have (3m for LOBPCG tasks).
+void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st, int n_max, int m_max) {
   if (ntask <= 0) return;
-  rr_kernel<<<ntask, RR_THREADS, 0, st>>>(d_tasks);
+  const size_t sm = (n_max > 0) ? rr_smem_bytes(n_max, m_max) : (size_t)-1;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (m_max <= RRS_THREADS && sm + 2048 <= (size_t)optin)
+    rr_smem_kernel<<<ntask, RRS_THREADS, sm, st>>>(d_tasks);
+  else
+    rr_kernel<<<ntask, RR_THREADS, 0, st>>>(d_tasks);
 }
 
 }  // namespace dgdft

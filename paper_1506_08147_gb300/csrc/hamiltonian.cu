@@ -23,6 +23,12 @@ template <class real>
 __device__ __forceinline__ bool elem_live(const ElemDev<real>& e) {
   return e.state[ST_ACTIVE] != 0;
 }
+// filt = 1: only elements that precondition with Teter (the others use the
+// learned network this iteration)
+template <class real>
+__device__ __forceinline__ bool elem_live(const ElemDev<real>& e, int filt) {
+  return e.state[ST_ACTIVE] != 0 && (filt == 0 || e.state[ST_TETER] != 0);
+}
 
 // C[p, j] = v_p^T psi_j for the projectors of the element.
 template <class real>
@@ -43,24 +49,30 @@ __global__ void proj_coef_kernel(const ElemDev<real>* __restrict__ elems, BRef<r
   }
 }
 
-template <class real>
-__global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> src, int ncols) {
-  using C = cplx_t<real>;
+// Pass 1.  real: storage of the vectors; TC: arithmetic; TZ: the stored
+// half spectrum.
+template <class real, class TC, class TZ>
+__global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> src, int ncols, int filt) {
+  using C = cplx_t<TC>;
+  using R2 = cplx_t<real>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ElemDev<real>& e = elems[blockIdx.z];
   const int z = blockIdx.x, j = blockIdx.y;
   const int nc = ncols > 0 ? ncols : e.m;
-  if (!elem_live(e) || z >= e.nz || j >= nc) return;
+  if (!elem_live(e, filt) || z >= e.nz || j >= nc) return;
   const int row = e.nxh, ny = e.ny, nh = e.nh;
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + ny * row;
-  const C* plane = reinterpret_cast<const C*>(resolve(e, src) + (size_t)j * e.ng + (size_t)z * e.nx * ny);
+  const R2* plane = reinterpret_cast<const R2*>(resolve(e, src) + (size_t)j * e.ng + (size_t)z * e.nx * ny);
   for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
     const int y = t / nh, k = t - y * nh;
-    buf0[y * row + k] = plane[t];
+    const R2 v = plane[t];
+    buf0[y * row + k] = cmake<C>((TC)v.x, (TC)v.y);
   }
   __syncthreads();
-  int cur = fft_lines<C, false>(buf0, buf1, 0, e.px, ny, row, 1, e.tw_h);
+  const C* tw_h = twp<TC>(e, TW_H);
+  const C* tw_x = twp<TC>(e, TW_X);
+  int cur = fft_lines<C, false>(buf0, buf1, 0, e.px, ny, row, 1, tw_h);
   // even/odd split: X[k] = E[k] + e^{-2 pi i k / nx} O[k], k = 0..nh
   {
     const C* s = cur ? buf1 : buf0;
@@ -69,54 +81,56 @@ __global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
       const int y = t / e.nxh, k = t - y * e.nxh;
       const C zk = s[y * row + (k == nh ? 0 : k)];
       const C zc = cconj(s[y * row + (k == 0 ? 0 : nh - k)]);
-      const C ev = cscale(cadd(zk, zc), (real)0.5);
+      const C ev = cscale(cadd(zk, zc), (TC)0.5);
       const C df = csub(zk, zc);
-      const C od = cmake<C>((real)0.5 * df.y, (real)-0.5 * df.x);  // -i/2 (zk - zc)
-      d[y * row + k] = cadd(ev, cmul(e.tw_x[k], od));
+      const C od = cmake<C>((TC)0.5 * df.y, (TC)-0.5 * df.x);  // -i/2 (zk - zc)
+      d[y * row + k] = cadd(ev, cmul(tw_x[k], od));
     }
     __syncthreads();
     cur ^= 1;
   }
-  cur = fft_lines<C, false>(buf0, buf1, cur, e.py, e.nxh, 1, row, e.tw_y);
+  cur = fft_lines<C, false>(buf0, buf1, cur, e.py, e.nxh, 1, row, twp<TC>(e, TW_Y));
   const C* res = cur ? buf1 : buf0;
-  C* out = e.Z + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
+  cplx_t<TZ>* out = reinterpret_cast<cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
   for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
     const int y = t / e.nxh, k = t - y * e.nxh;
-    out[t] = res[y * row + k];
+    const C v = res[y * row + k];
+    out[t] = cmake<cplx_t<TZ>>((TZ)v.x, (TZ)v.y);
   }
 }
 
 constexpr int ZTILE = 32;
 constexpr int ZROW = ZTILE + 1;
 
-template <class real>
 __device__ __forceinline__ double teter_factor(double s) {
   const double num = 27.0 + s * (18.0 + s * (12.0 + s * 8.0));
   return num / (num + 16.0 * s * s * s * s);
 }
 
-template <class real, int MODE>
+// Pass 2, arithmetic and storage in TZ.
+template <class real, class TZ, int MODE>
 __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols,
-                              const double* __restrict__ tkin_override) {
-  using C = cplx_t<real>;
+                              const double* __restrict__ tkin_override, int filt) {
+  using C = cplx_t<TZ>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ElemDev<real>& e = elems[blockIdx.z];
   const int j = blockIdx.y;
   const int nc = ncols > 0 ? ncols : e.m;
   const int nplane = e.nxh * e.ny;
   const int c0 = blockIdx.x * ZTILE;
-  if (!elem_live(e) || j >= nc || c0 >= nplane) return;
+  if (!elem_live(e, filt) || j >= nc || c0 >= nplane) return;
   const int nz = e.nz;
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + nz * ZROW;
-  C* zj = e.Z + (size_t)j * e.nspec;
+  C* zj = reinterpret_cast<C*>(e.Z) + (size_t)j * e.nspec;
   for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
     const int z = t / ZTILE, cc = t - z * ZTILE;
     const int c = c0 + cc;
     buf0[z * ZROW + cc] = (c < nplane) ? zj[(size_t)z * nplane + c] : cmake<C>(0, 0);
   }
   __syncthreads();
-  int cur = fft_lines<C, false>(buf0, buf1, 0, e.pz, ZTILE, 1, ZROW, e.tw_z);
+  const C* tw_z = twp<TZ>(e, TW_Z);
+  int cur = fft_lines<C, false>(buf0, buf1, 0, e.pz, ZTILE, 1, ZROW, tw_z);
   {
     C* s = cur ? buf1 : buf0;
     double tk = 1.0;
@@ -128,13 +142,13 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
       if (c >= nplane) continue;
       const int y = c / e.nxh, kx = c - y * e.nxh;
       const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
-      double f = (MODE == ZM_KINETIC) ? g : teter_factor<real>(g * inv_tk);
+      double f = (MODE == ZM_KINETIC) ? g : teter_factor(g * inv_tk);
       f *= e.scale;
-      s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (real)f);
+      s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (TZ)f);
     }
     __syncthreads();
   }
-  cur = fft_lines<C, true>(buf0, buf1, cur, e.pz, ZTILE, 1, ZROW, e.tw_z);
+  cur = fft_lines<C, true>(buf0, buf1, cur, e.pz, ZTILE, 1, ZROW, tw_z);
   const C* res = cur ? buf1 : buf0;
   for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
     const int z = t / ZTILE, cc = t - z * ZTILE;
@@ -143,25 +157,29 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
   }
 }
 
-template <class real, int MODE>
+// Pass 3: Z (TZ) -> arithmetic TC -> vectors (real), with the epilogue.
+template <class real, class TZ, class TC, int MODE>
 __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> dst,
-                              BRef<real> xsrc, int ncols) {
-  using C = cplx_t<real>;
+                              BRef<real> xsrc, int ncols, int filt) {
+  using C = cplx_t<TC>;
+  using R2 = cplx_t<real>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ElemDev<real>& e = elems[blockIdx.z];
   const int z = blockIdx.x, j = blockIdx.y;
   const int nc = ncols > 0 ? ncols : e.m;
-  if (!elem_live(e) || z >= e.nz || j >= nc) return;
+  if (!elem_live(e, filt) || z >= e.nz || j >= nc) return;
   const int row = e.nxh, ny = e.ny, nh = e.nh;
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + ny * row;
-  const C* in = e.Z + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
+  const cplx_t<TZ>* in = reinterpret_cast<const cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
   for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
     const int y = t / e.nxh, k = t - y * e.nxh;
-    buf0[y * row + k] = in[t];
+    const cplx_t<TZ> v = in[t];
+    buf0[y * row + k] = cmake<C>((TC)v.x, (TC)v.y);
   }
   __syncthreads();
-  int cur = fft_lines<C, true>(buf0, buf1, 0, e.py, e.nxh, 1, row, e.tw_y);
+  const C* tw_x = twp<TC>(e, TW_X);
+  int cur = fft_lines<C, true>(buf0, buf1, 0, e.py, e.nxh, 1, row, twp<TC>(e, TW_Y));
   // recombine the half spectrum into E + i O for the length-nh inverse
   {
     const C* s = cur ? buf1 : buf0;
@@ -170,14 +188,14 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
       const int y = t / nh, k = t - y * nh;
       const C xk = s[y * row + k];
       const C xc = cconj(s[y * row + nh - k]);
-      const C ev = cscale(cadd(xk, xc), (real)0.5);
-      const C od = cmul(cscale(csub(xk, xc), (real)0.5), cconj(e.tw_x[k]));
+      const C ev = cscale(cadd(xk, xc), (TC)0.5);
+      const C od = cmul(cscale(csub(xk, xc), (TC)0.5), cconj(tw_x[k]));
       d[y * row + k] = cmake<C>(ev.x - od.y, ev.y + od.x);
     }
     __syncthreads();
     cur ^= 1;
   }
-  cur = fft_lines<C, true>(buf0, buf1, cur, e.px, ny, row, 1, e.tw_h);
+  cur = fft_lines<C, true>(buf0, buf1, cur, e.px, ny, row, 1, twp<TC>(e, TW_H));
   C* res = cur ? buf1 : buf0;
   const size_t plane_off = (size_t)j * e.ng + (size_t)z * e.nx * ny;
   if (MODE == XI_HAMILTONIAN) {
@@ -185,79 +203,108 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     if (e.n_sup > 0) {
       const int sb = e.s_plane[z], se = e.s_plane[z + 1];
       const real* cj = e.Ccoef + (size_t)j * e.n_proj;
-      real* rres = reinterpret_cast<real*>(res);
+      TC* rres = reinterpret_cast<TC*>(res);
       for (int s = sb + threadIdx.x; s < se; s += blockDim.x) {
-        real acc = 0;
-        for (int q = e.s_ptr[s]; q < e.s_ptr[s + 1]; ++q) acc += e.s_gv[q] * cj[e.s_proj[q]];
+        TC acc = 0;
+        for (int q = e.s_ptr[s]; q < e.s_ptr[s + 1]; ++q) acc += (TC)e.s_gv[q] * (TC)cj[e.s_proj[q]];
         const int off = e.s_off[s];
         const int y = off / e.nx, x = off - y * e.nx;
         rres[2 * (y * row) + x] += acc;
       }
       __syncthreads();
     }
-    const C* xp = reinterpret_cast<const C*>(resolve(e, xsrc) + plane_off);
-    const C* vp = reinterpret_cast<const C*>(e.V + (size_t)z * e.nx * ny);
-    C* op = reinterpret_cast<C*>(resolve(e, dst) + plane_off);
+    const R2* xp = reinterpret_cast<const R2*>(resolve(e, xsrc) + plane_off);
+    const R2* vp = reinterpret_cast<const R2*>(e.V + (size_t)z * e.nx * ny);
+    R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
       const int y = t / nh, k = t - y * nh;
       const C kv = res[y * row + k];
-      const C xv = xp[t];
-      const C vv = vp[t];
-      op[t] = cmake<C>(kv.x + vv.x * xv.x, kv.y + vv.y * xv.y);
+      const R2 xv = xp[t];
+      const R2 vv = vp[t];
+      op[t] = cmake<R2>((real)(kv.x + (TC)vv.x * (TC)xv.x), (real)(kv.y + (TC)vv.y * (TC)xv.y));
     }
   } else {
-    C* op = reinterpret_cast<C*>(resolve(e, dst) + plane_off);
+    R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
       const int y = t / nh, k = t - y * nh;
-      op[t] = res[y * row + k];
+      const C v = res[y * row + k];
+      op[t] = cmake<R2>((real)v.x, (real)v.y);
     }
   }
 }
 
-template <class real> size_t plane_smem(const BatchShape& s) {
-  return 2 * sizeof(cplx_t<real>) * (size_t)s.max_ny * s.max_nxh;
+template <class T> size_t plane_smem(const BatchShape& s) {
+  return 2 * sizeof(cplx_t<T>) * (size_t)s.max_ny * s.max_nxh;
 }
-template <class real> size_t zcol_smem(const BatchShape& s) {
-  return 2 * sizeof(cplx_t<real>) * (size_t)s.max_nz * ZROW;
+template <class T> size_t zcol_smem(const BatchShape& s) {
+  return 2 * sizeof(cplx_t<T>) * (size_t)s.max_nz * ZROW;
 }
 
 }  // namespace
 
-template <class real>
-void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st) {
+template <class real, class F>
+void apply_h_prec(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st) {
   const BatchShape& s = b.s;
   const int nc = ncols > 0 ? ncols : s.max_m;
   if (s.max_nproj > 0)
     proj_coef_kernel<real><<<dim3(s.max_nproj, 1, s.nel), 128, 0, st>>>(b.d_elems, src, ncols);
-  const size_t sp = plane_smem<real>(s), sz = zcol_smem<real>(s);
-  xy_fwd_kernel<real><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, src, ncols);
-  z_mult_kernel<real, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, sz, st>>>(
-      b.d_elems, ncols, nullptr);
-  xy_inv_kernel<real, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, dst, src,
-                                                                                   ncols);
+  xy_fwd_kernel<real, F, F><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<F>(s), st>>>(b.d_elems, src, ncols, 0);
+  z_mult_kernel<real, F, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, zcol_smem<F>(s),
+                                       st>>>(b.d_elems, ncols, nullptr, 0);
+  xy_inv_kernel<real, F, real, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<real>(s), st>>>(
+      b.d_elems, dst, src, ncols, 0);
 }
 
+// fwd64: run the forward transform (passes 1-2) in FP64 with an FP64
+// intermediate even for FP32 vectors (the rounding of the forward transform
+// is what |G|^2/2 amplifies); pass 3 stays in the working precision.
+template <class real>
+void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st,
+                    bool fwd64) {
+  if (fwd64)
+    apply_h_prec<real, double>(b, src, dst, ncols, st);
+  else
+    apply_h_prec<real, real>(b, src, dst, ncols, st);
+}
+
+// The preconditioner's accuracy does not limit convergence: all passes run
+// in the working precision.
 template <class real>
 void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const double* tkin_override,
-                  int ncols, cudaStream_t st) {
+                  int ncols, cudaStream_t st, int only_teter_elems) {
   const BatchShape& s = b.s;
   const int nc = ncols > 0 ? ncols : s.max_m;
-  const size_t sp = plane_smem<real>(s), sz = zcol_smem<real>(s);
-  xy_fwd_kernel<real><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, src, ncols);
-  z_mult_kernel<real, ZM_TETER><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, sz, st>>>(
-      b.d_elems, ncols, tkin_override);
-  xy_inv_kernel<real, XI_PLAIN><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, dst, src, ncols);
+  const int f = only_teter_elems;
+  xy_fwd_kernel<real, real, real><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<real>(s), st>>>(b.d_elems, src,
+                                                                                               ncols, f);
+  z_mult_kernel<real, real, ZM_TETER><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256,
+                                        zcol_smem<real>(s), st>>>(b.d_elems, ncols, tkin_override, f);
+  xy_inv_kernel<real, real, real, XI_PLAIN><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<real>(s), st>>>(
+      b.d_elems, dst, src, ncols, f);
 }
 
 // Allow the plane and column kernels the full opt-in shared memory once.
 template <class real> static void opt_in_smem_t() {
-  const int mx = 227 * 1024;
-  cudaFuncSetAttribute(xy_fwd_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(xy_inv_kernel<real, XI_HAMILTONIAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(xy_inv_kernel<real, XI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(z_mult_kernel<real, ZM_KINETIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(z_mult_kernel<real, ZM_TETER>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  opt_in_dynamic_smem((const void*)xy_fwd_kernel<real, double, double>);
+  opt_in_dynamic_smem((const void*)xy_fwd_kernel<real, real, real>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<real, double, real, XI_HAMILTONIAN>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<real, real, real, XI_HAMILTONIAN>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<real, real, real, XI_PLAIN>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<real, double, ZM_KINETIC>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<real, real, ZM_KINETIC>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<real, real, ZM_TETER>);
 }
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum minus the kernel's static shared memory.
+void opt_in_dynamic_smem(const void* kernel) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 void init_hamiltonian_kernels() {
   opt_in_smem_t<double>();
   opt_in_smem_t<float>();
@@ -267,17 +314,18 @@ void init_hamiltonian_kernels() {
 // 2: xy inverse with epilogue), for stage timing.
 template <class real>
 void launch_h_pass(const Batch<real>& b, int pass, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st) {
+  using F = real;
+  using I = real;
   const BatchShape& s = b.s;
   const int nc = ncols > 0 ? ncols : s.max_m;
-  const size_t sp = plane_smem<real>(s), sz = zcol_smem<real>(s);
   if (pass == 0)
-    xy_fwd_kernel<real><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, src, ncols);
+    xy_fwd_kernel<real, F, F><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<F>(s), st>>>(b.d_elems, src, ncols, 0);
   else if (pass == 1)
-    z_mult_kernel<real, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, sz, st>>>(
-        b.d_elems, ncols, nullptr);
+    z_mult_kernel<real, F, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256,
+                                         zcol_smem<F>(s), st>>>(b.d_elems, ncols, nullptr, 0);
   else
-    xy_inv_kernel<real, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, sp, st>>>(b.d_elems, dst, src,
-                                                                                     ncols);
+    xy_inv_kernel<real, F, I, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<I>(s), st>>>(
+        b.d_elems, dst, src, ncols, 0);
 }
 template void launch_h_pass<double>(const Batch<double>&, int, BRef<double>, BRef<double>, int, cudaStream_t);
 template void launch_h_pass<float>(const Batch<float>&, int, BRef<float>, BRef<float>, int, cudaStream_t);
@@ -290,11 +338,11 @@ void launch_proj_coef(const Batch<real>& b, BRef<real> src, int ncols, cudaStrea
 template void launch_proj_coef<double>(const Batch<double>&, BRef<double>, int, cudaStream_t);
 template void launch_proj_coef<float>(const Batch<float>&, BRef<float>, int, cudaStream_t);
 
-template void launch_apply_h<double>(const Batch<double>&, BRef<double>, BRef<double>, int, cudaStream_t);
-template void launch_apply_h<float>(const Batch<float>&, BRef<float>, BRef<float>, int, cudaStream_t);
+template void launch_apply_h<double>(const Batch<double>&, BRef<double>, BRef<double>, int, cudaStream_t, bool);
+template void launch_apply_h<float>(const Batch<float>&, BRef<float>, BRef<float>, int, cudaStream_t, bool);
 template void launch_teter<double>(const Batch<double>&, BRef<double>, BRef<double>, const double*, int,
-                                   cudaStream_t);
+                                   cudaStream_t, int);
 template void launch_teter<float>(const Batch<float>&, BRef<float>, BRef<float>, const double*, int,
-                                  cudaStream_t);
+                                  cudaStream_t, int);
 
 }  // namespace dgdft

@@ -43,12 +43,14 @@ enum { XI_HAMILTONIAN = 0, XI_PLAIN = 1 };
 
 // hamiltonian.cu
 template <class real>
-void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st);
+void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st,
+                    bool fwd64 = false);
 template <class real>
 void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const double* tkin_override,
-                  int ncols, cudaStream_t st);
+                  int ncols, cudaStream_t st, int only_teter_elems = 0);
 
 void init_hamiltonian_kernels();
+void opt_in_dynamic_smem(const void* kernel);
 template <class real>
 void launch_proj_coef(const Batch<real>& b, BRef<real> src, int ncols, cudaStream_t st);
 template <class real>
@@ -57,7 +59,7 @@ void launch_h_pass(const Batch<real>& b, int pass, BRef<real> src, BRef<real> ds
 // blas.cu
 // Gram products U_a^T V_b over the rows of each element, split over row
 // chunks; FP64 partial sums are reduced in a fixed order.
-enum { OUT_GRAM_A = 0, OUT_GRAM_B = 1, OUT_GXW = 2, OUT_PTR = 3 };
+enum { OUT_GRAM_A = 0, OUT_GRAM_B = 1, OUT_GXW = 2, OUT_PTR = 3, OUT_Y = 4 };
 constexpr int MAX_PAIRS = 12;
 template <class real> struct GramJob {
   int npairs = 0;
@@ -105,6 +107,9 @@ void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStrea
 // End of an iteration: flip the X/P/HX/HP buffers, mark P valid.
 template <class real>
 void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st);
+// theta = 0 (mode 0) or the Rayleigh quotients from the residual sums (mode 1)
+template <class real>
+void launch_theta(const Batch<real>& b, int nchunk, int mode, cudaStream_t st);
 
 // dense.cu: FP64 Rayleigh-Ritz on one CTA per task.
 enum { RR_FIXED = 0, RR_INITIAL = 1, RR_LOBPCG = 2 };
@@ -123,7 +128,10 @@ struct RRTask {
   double cond_max;   // Cholesky condition limit on the equilibrated B
 };
 size_t rr_work_doubles(int n_max, int m);
-void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st);
+// n_max, m_max bound the tasks' pencil sizes; pencils that fit use the
+// shared-memory kernel.  n_max <= 0 forces the global-memory kernel.
+void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st, int n_max, int m_max);
+void init_rr_kernels();
 
 // solver-level helpers are in solver.cu
 

@@ -11,8 +11,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <random>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -20,6 +22,7 @@
 #include "../../include/dgdft_alb.h"
 #include "../../include/dgdft_alb_steps.h"
 #include "internal.h"
+#include "learned.h"
 
 using namespace dgdft;
 
@@ -132,6 +135,7 @@ struct dgdft_alb_ctx {
   void* cache = nullptr;
   void (*cache_free)(void*) = nullptr;
   std::vector<int> cache_proj_version;
+  ConvNet* net = nullptr;  // learned preconditioner, created on first use
   void drop_cache() {
     if (cache && cache_free) cache_free(cache);
     cache = nullptr;
@@ -174,13 +178,13 @@ size_t elem_bytes(const ElemHost& h) {
   const size_t np = h.pgamma.size(), nnz = h.pidx.size();
   Sizer s;
   s.add(ng * sizeof(real));                               // V
-  s.add(sizeof(cplx_t<real>) * (d.nx / 2 + d.nx + d.ny + d.nz + 4));
+  s.add((sizeof(cplx_t<real>) + sizeof(double2)) * (d.nx / 2 + d.nx + d.ny + d.nz + 4));
   s.add(sizeof(double) * (nxh + d.ny + d.nz));
   s.add(sizeof(int) * (np + 1) + sizeof(int) * nnz + sizeof(real) * nnz + sizeof(double) * np);
   s.add(sizeof(int) * (d.nz + 1) + sizeof(int) * (3 * nnz + 1) + sizeof(real) * nnz);
   s.add(sizeof(real) * np * m);
   for (int i = 0; i < 10; ++i) s.add(sizeof(real) * ng * m);
-  s.add(sizeof(cplx_t<real>) * nspec * m);
+  s.add(sizeof(double2) * nspec * m);
   s.add(sizeof(double) * (18 * m * m + m * m + 3 * m * m + 3 * m));
   s.add(sizeof(double) * rr_work_doubles(3 * (int)m, (int)m));
   s.add(sizeof(double) * m * nchunk_rows((int)ng) * 4);
@@ -206,9 +210,35 @@ template <class real> struct Wave {
   Batch<real> batch;
   int rnchunk = 1;
   std::vector<int> h_state;
+  // learned preconditioner buffers (FP32 waves with a network, uniform grids)
+  bool learned = false;
+  int gnz = 0, gny = 0, gnx = 0;
+  float *nn_in = nullptr, *nn_out = nullptr, *nn_tmp0 = nullptr, *nn_tmp1 = nullptr;
 
   ~Wave() {
     if (arena.base) cudaFree(arena.base);
+    for (float* p : {nn_in, nn_out, nn_tmp0, nn_tmp1})
+      if (p) cudaFree(p);
+  }
+
+  dgdft_status setup_learned() {
+    if (!std::is_same<real, float>::value || ctx->cfg.precond != DGDFT_PRECOND_LEARNED) return DGDFT_OK;
+    if (!ctx->net || !ctx->net->ready) return ctx->fail(DGDFT_ESTATE, "learned preconditioner selected but no network");
+    const dgdft_element_desc& d0 = ctx->el[ids[0]].d;
+    for (int id : ids) {
+      const dgdft_element_desc& d = ctx->el[id].d;
+      if (d.nx != d0.nx || d.ny != d0.ny || d.nz != d0.nz) return DGDFT_OK;  // uneven grids: Teter only
+    }
+    gnz = d0.nz;
+    gny = d0.ny;
+    gnx = d0.nx;
+    const size_t samples = (size_t)batch.s.nel * batch.s.max_m, ng = (size_t)gnx * gny * gnz;
+    if (cudaMalloc(&nn_in, sizeof(float) * samples * 2 * ng) || cudaMalloc(&nn_out, sizeof(float) * samples * ng) ||
+        cudaMalloc(&nn_tmp0, sizeof(float) * samples * 16 * ng) ||
+        cudaMalloc(&nn_tmp1, sizeof(float) * samples * 16 * ng))
+      return ctx->fail(DGDFT_ENOMEM, "learned preconditioner buffers");
+    learned = true;
+    return DGDFT_OK;
   }
 
   dgdft_status build(dgdft_alb_ctx* c, const std::vector<int>& elem_ids, double cond_max) {
@@ -274,7 +304,7 @@ template <class real> struct Wave {
     CK(ctx_copy(ctx, d_rr_lob, rr_lob.data(), sizeof(RRTask) * nel, cudaMemcpyHostToDevice));
     batch.d_elems = d_elems;
     batch.s = s;
-    return DGDFT_OK;
+    return setup_learned();
   }
 
   template <class T> T* take(size_t count) { return (T*)arena.take(sizeof(T) * std::max<size_t>(count, 1)); }
@@ -306,19 +336,28 @@ template <class real> struct Wave {
     const size_t ng = E.ng, m = E.m;
     // potential: converted from the resident FP64 copy at every solve
     E.V = take<real>(ng);
-    // twiddles
-    auto put_tw = [&](int n, int count) -> const C* {
+    // twiddles, working precision and FP64
+    auto put_tw = [&](int n, int count, int axis) -> bool {
       std::vector<double> t = twiddles(n, count);
       std::vector<C> tc(count);
       for (int q = 0; q < count; ++q) tc[q] = cmake<C>((real)t[2 * q], (real)t[2 * q + 1]);
       C* dp = take<C>(count);
-      if (put(dp, tc.data(), count) != DGDFT_OK) return nullptr;
-      return dp;
+      if (!dp || put(dp, tc.data(), count) != DGDFT_OK) return false;
+      E.tw[axis] = dp;
+      if (sizeof(real) == sizeof(double)) {
+        E.tw64[axis] = reinterpret_cast<const double2*>(dp);
+      } else {
+        std::vector<double2> td(count);
+        for (int q = 0; q < count; ++q) td[q] = make_double2(t[2 * q], t[2 * q + 1]);
+        double2* dd = take<double2>(count);
+        if (!dd || put(dd, td.data(), count) != DGDFT_OK) return false;
+        E.tw64[axis] = dd;
+      }
+      return true;
     };
-    E.tw_h = put_tw(E.nh, E.nh);
-    E.tw_x = put_tw(d.nx, E.nh + 1);
-    E.tw_y = put_tw(d.ny, d.ny);
-    E.tw_z = put_tw(d.nz, d.nz);
+    if (!put_tw(E.nh, E.nh, TW_H) || !put_tw(d.nx, E.nh + 1, TW_X) || !put_tw(d.ny, d.ny, TW_Y) ||
+        !put_tw(d.nz, d.nz, TW_Z))
+      return ctx->fail(DGDFT_ECUDA, "twiddle upload");
     auto put_g = [&](const std::vector<double>& g) -> const double* {
       double* dp = take<double>(g.size());
       if (put(dp, g.data(), g.size()) != DGDFT_OK) return nullptr;
@@ -327,7 +366,7 @@ template <class real> struct Wave {
     E.gx2 = put_g(kinetic_axis(d.nx, d.Lx, true));
     E.gy2 = put_g(kinetic_axis(d.ny, d.Ly, false));
     E.gz2 = put_g(kinetic_axis(d.nz, d.Lz, false));
-    if (!E.tw_h || !E.tw_x || !E.tw_y || !E.tw_z || !E.gx2 || !E.gy2 || !E.gz2) return DGDFT_ECUDA;
+    if (!E.gx2 || !E.gy2 || !E.gz2) return DGDFT_ECUDA;
     // projectors, CSR by projector
     const int np = (int)eh.pgamma.size();
     const size_t nnz = eh.pidx.size();
@@ -389,7 +428,7 @@ template <class real> struct Wave {
       E.blk[b][0] = take<real>(ng * m);
       E.blk[b][1] = (b < NDBL) ? take<real>(ng * m) : E.blk[b][0];
     }
-    E.Z = take<C>((size_t)E.nspec * m);
+    E.Z = take<double2>((size_t)E.nspec * m);  // FP64 intermediate of the forward transform
     E.gram = take<double>(18 * m * m);
     E.gxw = take<double>(m * m);
     E.Y = take<double>(3 * m * m);
@@ -439,12 +478,17 @@ template <class real> struct Wave {
     return DGDFT_OK;
   }
 
-  dgdft_status reset_states(double tol) {
+  // resume: elements already converged stay inactive with their results
+  dgdft_status reset_states(double tol, bool resume = false) {
     const int nel = (int)ids.size();
     for (int i = 0; i < nel; ++i) {
       int* s = &h_state[(size_t)i * STATE_WORDS];
-      std::fill(s, s + STATE_WORDS, 0);
-      s[ST_ACTIVE] = 1;
+      const bool keep = resume && s[ST_CONVERGED];
+      if (!keep) {
+        std::fill(s, s + STATE_WORDS, 0);
+        s[ST_ACTIVE] = 1;
+        s[ST_TETER] = learned ? 0 : 1;
+      }
       h[i].tol = tol;
     }
     CK(ctx_copy(ctx, d_elems, h.data(), sizeof(ElemDev<real>) * nel, cudaMemcpyHostToDevice));
@@ -461,6 +505,60 @@ template <class real> struct Wave {
     CK(cudaStreamSynchronize(ctx->stream));
     return DGDFT_OK;
   }
+
+  bool fwd64() const { return ctx->cfg.h_fp64_forward != 0; }
+
+  // P <- P - [X W] ([X W]^T P) and HP by the same transform.  Near
+  // convergence P points almost along W; forming X' = [X W P] Y with the
+  // large, cancelling coefficients that such a basis needs would leave FP32
+  // rounding of order |Y| u in X', which H amplifies into a residual floor.
+  // C = [X W]^T P is staged in the Rayleigh-Ritz coefficient buffer.
+  void orthogonalise_p(cudaStream_t st) {
+    GramJob<real> g;
+    g.npairs = 2;
+    g.a[0] = bref<real>(BX);
+    g.b[0] = bref<real>(BP);
+    g.a[1] = bref<real>(BW);
+    g.b[1] = bref<real>(BP);
+    for (int k = 0; k < 2; ++k) {
+      g.needs_p[k] = 1;
+      g.out_id[k] = OUT_GRAM_A;  // placed below, then moved: see ld_out / brow
+      g.bcol[k] = 0;
+    }
+    g.brow[0] = 0;
+    g.brow[1] = 1;
+    g.out_id[0] = g.out_id[1] = OUT_Y;
+    launch_gram<real>(batch, g, partial, partial_cap, st);
+    TsmmJob<real> t;
+    t.nin = 2;
+    t.in[0] = bref<real>(BX);
+    t.in[1] = bref<real>(BW);
+    t.yrow[0] = 0;
+    t.yrow[1] = 1;
+    t.y_id = Y_RR;
+    t.out = bref<real>(BP);
+    t.needs_p[0] = t.needs_p[1] = 1;
+    t.alpha = -1.0;
+    t.beta = 1.0;
+    launch_tsmm<real>(batch, t, st);
+    t.in[0] = bref<real>(BHX);
+    t.in[1] = bref<real>(BHW);
+    t.out = bref<real>(BHP);
+    launch_tsmm<real>(batch, t, st);
+  }
+
+  // W = T(R): the learned network for elements that use it, Teter for the rest
+  void precondition(cudaStream_t st) {
+    if constexpr (std::is_same<real, float>::value) {
+      if (learned) {
+        learned_precondition(batch, *ctx->net, rnchunk, gnz, gny, gnx, nn_in, nn_out, nn_tmp0, nn_tmp1, st);
+        launch_teter<real>(batch, bref<real>(BW), bref<real>(BW), nullptr, 0, st, 1);
+        return;
+      }
+    }
+    launch_teter<real>(batch, bref<real>(BW), bref<real>(BW), nullptr, 0, st);
+  }
+  const bool trace_ = std::getenv("DGDFT_TRACE") != nullptr;
 
   // Tensor-core Gram for the FP32 stage when the pencil fits one TMEM
   // accumulator (3m <= 256); returns false when the SIMT kernel must run.
@@ -499,7 +597,7 @@ template <class real> struct Wave {
   }
 
   void enqueue_initial(cudaStream_t st) {
-    launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st);
+    launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st, fwd64());
     GramJob<real> g;
     g.npairs = 2;
     g.a[0] = bref<real>(BX);
@@ -510,7 +608,7 @@ template <class real> struct Wave {
     g.out_id[1] = OUT_GRAM_B;
     for (int k = 0; k < 2; ++k) g.needs_p[k] = g.brow[k] = g.bcol[k] = 0;
     launch_gram<real>(batch, g, partial, partial_cap, st);
-    launch_rr(d_rr_init, batch.s.nel, st);
+    launch_rr(d_rr_init, batch.s.nel, st, batch.s.max_m, batch.s.max_m);
     TsmmJob<real> t;
     t.nin = 1;
     t.in[0] = bref<real>(BX);
@@ -526,7 +624,7 @@ template <class real> struct Wave {
     if (batch.s.max_nproj > 0) launch_proj_coef<real>(batch, bref<real>(BX), 0, st);
     launch_residual<real>(batch, rnchunk, st);
     launch_post_residual<real>(batch, rnchunk, maxit, st);
-    launch_teter<real>(batch, bref<real>(BW), bref<real>(BW), nullptr, 0, st);
+    precondition(st);
     {
       GramJob<real> g;
       g.npairs = 1;
@@ -545,9 +643,10 @@ template <class real> struct Wave {
       t.beta = 1.0;
       launch_tsmm<real>(batch, t, st);
     }
-    launch_apply_h<real>(batch, bref<real>(BW), bref<real>(BHW), 0, st);
+    launch_apply_h<real>(batch, bref<real>(BW), bref<real>(BHW), 0, st, fwd64());
+    if (std::is_same<real, float>::value) orthogonalise_p(st);
     if (!tc_gram(0, st)) launch_gram<real>(batch, gram12(), partial, partial_cap, st);
-    launch_rr(d_rr_lob, batch.s.nel, st);
+    launch_rr(d_rr_lob, batch.s.nel, st, 3 * batch.s.max_m, batch.s.max_m);
     {
       TsmmJob<real> t;
       t.nin = 3;
@@ -560,11 +659,19 @@ template <class real> struct Wave {
       t.needs_p[2] = 1;
       t.out = bref<real>(BX, 1);
       launch_tsmm<real>(batch, t, st);
-      t.in[0] = bref<real>(BHX);
-      t.in[1] = bref<real>(BHW);
-      t.in[2] = bref<real>(BHP);
-      t.out = bref<real>(BHX, 1);
-      launch_tsmm<real>(batch, t, st);
+      if (std::is_same<real, double>::value) {
+        t.in[0] = bref<real>(BHX);
+        t.in[1] = bref<real>(BHW);
+        t.in[2] = bref<real>(BHP);
+        t.out = bref<real>(BHX, 1);
+        launch_tsmm<real>(batch, t, st);
+      } else {
+        // FP32: HX is recomputed as H X rather than updated as [HX HW HP] Y,
+        // whose rounding grows with |Y| |HW| once [X W P] is nearly dependent
+        // and would leave HX inconsistent with X (the residual then stalls or
+        // diverges near 1e-4 Ha)
+        launch_apply_h<real>(batch, bref<real>(BX, 1), bref<real>(BHX, 1), 0, st, fwd64());
+      }
       TsmmJob<real> u;
       u.nin = 2;
       u.in[0] = bref<real>(BW);
@@ -583,10 +690,28 @@ template <class real> struct Wave {
   }
 
   // LOBPCG for every element of the wave; stall_window > 0 stops an element
-  // whose max residual has not halved over that many polls.
-  dgdft_status run(double tol, int maxit, int stall_window, std::vector<double>* res_out) {
+  // whose max residual has stopped improving over that many polls.
+  // FP64 check of the current block without iterating: H X in the wave's
+  // arithmetic, Rayleigh quotients as theta, residuals and convergence.
+  dgdft_status verify(double tol) {
     cudaStream_t st = ctx->stream;
     dgdft_status s = reset_states(tol);
+    if (s != DGDFT_OK) return s;
+    launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st, fwd64());
+    launch_theta<real>(batch, rnchunk, 0, st);
+    launch_residual<real>(batch, rnchunk, st);
+    launch_theta<real>(batch, rnchunk, 1, st);
+    if (batch.s.max_nproj > 0) launch_proj_coef<real>(batch, bref<real>(BX), 0, st);
+    launch_residual<real>(batch, rnchunk, st);
+    launch_post_residual<real>(batch, rnchunk, 1 << 30, st);
+    CK(cudaGetLastError());
+    return read_states();
+  }
+
+  dgdft_status run(double tol, int maxit, int stall_window, std::vector<double>* res_out, int refresh_every = 0,
+                   bool resume = false) {
+    cudaStream_t st = ctx->stream;
+    dgdft_status s = reset_states(tol, resume);
     if (s != DGDFT_OK) return s;
     enqueue_initial(st);
     CK(cudaGetLastError());
@@ -605,13 +730,27 @@ template <class real> struct Wave {
     std::vector<double> resbuf;
     int launched = 0;
     dgdft_status rs = DGDFT_OK;
+    int since_refresh = 0;
     while (launched <= maxit + 1) {
-      for (int k = 0; k < every && launched <= maxit + 1; ++k, ++launched) {
+      if (refresh_every > 0 && since_refresh >= refresh_every) {
+        // recompute HX = H X: the updates HX <- [HX HW HP] Y accumulate
+        // rounding in the working precision
+        launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st, fwd64());
+        since_refresh = 0;
+      }
+      for (int k = 0; k < every && launched <= maxit + 1; ++k, ++launched, ++since_refresh) {
         ce = cudaGraphLaunch(exec, st);
         if (ce != cudaSuccess) break;
       }
       if (ce != cudaSuccess) break;
       if ((rs = read_states()) != DGDFT_OK) break;
+      if (trace_) {
+        // diagnostic trace of element 0 (DGDFT_TRACE set in the environment)
+        std::vector<double> r0(h[0].J);
+        if (ctx_copy(ctx, r0.data(), h[0].res, sizeof(double) * h[0].J, cudaMemcpyDeviceToHost) == cudaSuccess)
+          std::fprintf(stderr, "[dgdft] %s it=%d active=%d max_res=%.3e\n", sizeof(real) == 4 ? "fp32" : "fp64",
+                       h_state[ST_ITER], h_state[ST_ACTIVE], *std::max_element(r0.begin(), r0.end()));
+      }
       bool any = false;
       for (int i = 0; i < nel; ++i) {
         int* sw = &h_state[(size_t)i * STATE_WORDS];
@@ -624,7 +763,24 @@ template <class real> struct Wave {
           const double mx = *std::max_element(resbuf.begin(), resbuf.end());
           hist[i].push_back(mx);
           const size_t L = hist[i].size();
-          if (L > (size_t)stall_window && mx > 0.5 * hist[i][L - 1 - stall_window]) {
+          // stalled: the best residual of the last `stall_window` polls is not
+          // 5% below the best one before them (the FP32 floor has been reached)
+          bool stalled = false;
+          if (L > (size_t)stall_window) {
+            const double before = *std::min_element(hist[i].begin(), hist[i].end() - stall_window);
+            const double recent = *std::min_element(hist[i].end() - stall_window, hist[i].end());
+            stalled = recent > 0.95 * before;
+          }
+          if (stalled && learned && !sw[ST_TETER]) {
+            // the learned preconditioner stalled: fall back to Teter
+            int one = 1;
+            ce = ctx_copy(ctx, h[i].state + ST_TETER, &one, sizeof(int), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) break;
+            int fb = sw[ST_FALLBACK] + 1;
+            ce = ctx_copy(ctx, h[i].state + ST_FALLBACK, &fb, sizeof(int), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) break;
+            hist[i].clear();
+          } else if (stalled) {
             int zero = 0;
             ce = ctx_copy(ctx, h[i].state + ST_ACTIVE, &zero, sizeof(int), cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) break;
@@ -744,7 +900,7 @@ dgdft_status alb_orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, int i, cons
   g.ld_out = J;
   g.out_ptr = G;
   launch_gram<double>(one, g, w.partial, w.partial_cap, st);
-  launch_rr(dt, 1, st);
+  launch_rr(dt, 1, st, J, J);
   TsmmJob<double> u;
   u.nin = 1;
   u.in[0] = bptr<double>(phit);
@@ -760,7 +916,7 @@ dgdft_status alb_orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, int i, cons
   g.b[0] = bptr<double>(U);
   g.out_ptr = G2;
   launch_gram<double>(one, g, w.partial, w.partial_cap, st);
-  launch_rr(dt + 1, 1, st);
+  launch_rr(dt + 1, 1, st, J, J);
   u.in[0] = bptr<double>(U);
   u.y_ptr = Y2;
   u.out = bptr<double>(phi_dev_out);
@@ -784,7 +940,8 @@ dgdft_status copy_block_to(Wave<real>& w, int i, Wave<double>& dst, int di, cuda
 }
 
 dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, double seconds,
-                         const std::vector<int>& extra_iters, const std::vector<int>& extra_fb) {
+                         const std::vector<int>& extra_iters, const std::vector<int>& extra_fb,
+                         const std::vector<double>& bulk_res) {
   for (size_t i = 0; i < w.ids.size(); ++i) {
     ElemHost& eh = ctx->el[w.ids[i]];
     const ElemDev<double>& E = w.h[i];
@@ -814,6 +971,8 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     for (double r : eh.resid) mx = std::max(mx, r);
     eh.rep.iterations = sw[ST_ITER] + (extra_iters.empty() ? 0 : extra_iters[i]);
     eh.rep.fallbacks = sw[ST_FALLBACK] + (extra_fb.empty() ? 0 : extra_fb[i]);
+    eh.rep.iterations_bulk = extra_iters.empty() ? 0 : extra_iters[i];
+    eh.rep.resid_bulk = bulk_res.empty() ? 0.0 : bulk_res[i];
     eh.rep.max_resid = mx;
     eh.rep.wave = wave_idx;
     eh.rep.seconds = seconds;
@@ -845,7 +1004,7 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
     dgdft_status s;
     if (mixed) {
       wp->w32.reset(new Wave<float>());
-      if ((s = wp->w32->build(ctx, ids, 1e7)) != DGDFT_OK) return s;
+      if ((s = wp->w32->build(ctx, ids, 1e4)) != DGDFT_OK) return s;
     }
     wp->w64.reset(new Wave<double>());
     if ((s = wp->w64->build(ctx, ids, 1e14)) != DGDFT_OK) return s;
@@ -859,15 +1018,28 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
   }
   Wave<double>& w64 = *wp->w64;
   std::vector<int> it32, fb32;
+  std::vector<double> res32;
   dgdft_status s;
   if (mixed) {
     Wave<float>& w32 = *wp->w32;
     if ((s = w32.load_inputs()) != DGDFT_OK) return s;
     // stage 1: FP32 storage and arithmetic, FP64 Rayleigh-Ritz, to a
     // tolerance above the FP32 residual floor (or until progress stalls)
-    const double tol1 = std::max(10.0 * c.tol, 1e-5);
-    if ((s = w32.run(tol1, c.maxit, 6, nullptr)) != DGDFT_OK) return s;
-    // stage 2 starts from the FP32 Ritz block; V_eff is reloaded in FP64
+    // the FP32 stage aims below tol: its residual floor (~4e-7 Ha from FP32
+    // storage, ~2e-7 from the H apply) leaves room under 1e-6
+    const double tol1 = 0.6 * c.tol;
+    std::vector<double> r32;
+    if ((s = w32.run(tol1, c.maxit, 8, &r32, 0)) != DGDFT_OK) return s;
+    {
+      size_t off = 0;
+      for (size_t i = 0; i < ids.size(); ++i) {
+        const int m = w32.h[i].m, J = w32.h[i].J;
+        res32.push_back(*std::max_element(r32.begin() + off, r32.begin() + off + J));
+        off += m;
+      }
+    }
+    // FP64 check from the FP32 Ritz block; LOBPCG continues in FP64 only for
+    // the elements that miss tol
     for (size_t i = 0; i < ids.size(); ++i) {
       ElemHost& eh = ctx->el[ids[i]];
       launch_convert<double, double>(eh.d_veff, const_cast<double*>(w64.h[i].V), (size_t)eh.ng(), ctx->stream);
@@ -876,12 +1048,16 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
       fb32.push_back(w32.h_state[i * STATE_WORDS + ST_FALLBACK]);
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    if ((s = w64.verify(c.tol)) != DGDFT_OK) return s;
+    bool all = true;
+    for (size_t i = 0; i < ids.size(); ++i) all = all && w64.h_state[i * STATE_WORDS + ST_CONVERGED];
+    if (!all && (s = w64.run(c.tol, c.maxit, 0, nullptr, 0, true)) != DGDFT_OK) return s;
   } else {
     if ((s = w64.load_inputs()) != DGDFT_OK) return s;
+    if ((s = w64.run(c.tol, c.maxit, 0, nullptr)) != DGDFT_OK) return s;
   }
-  if ((s = w64.run(c.tol, c.maxit, 0, nullptr)) != DGDFT_OK) return s;
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32);
+  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32);
 }
 
 }  // namespace
@@ -949,8 +1125,19 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   }
   init_hamiltonian_kernels();
   init_tc_gram_kernel();
+  init_rr_kernels();
+  cudaGetLastError();  // attribute queries above must not leave an error behind
   ctx->el.resize(n_elem);
   for (int i = 0; i < n_elem; ++i) ctx->el[i].d = elems[i];
+  if (cfg->precond_weights) {
+    ctx->net = new ConvNet();
+    std::string e = ctx->net->init(0, ctx->stream);
+    if (e.empty()) e = ctx->net->load_file(cfg->precond_weights, ctx->stream);
+    if (!e.empty()) {
+      dgdft_alb_destroy(ctx.release());
+      return DGDFT_EINVAL;
+    }
+  }
   *out = ctx.release();
   return DGDFT_OK;
 }
@@ -1115,6 +1302,7 @@ void dgdft_alb_destroy(dgdft_alb_ctx* ctx) {
   cudaSetDevice(ctx->device);
   ctx->drop_cache();
   for (ElemHost& eh : ctx->el) eh.release();
+  delete ctx->net;
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -1293,7 +1481,9 @@ dgdft_status time_stage_t(dgdft_alb_ctx* ctx, Wave<real>& w, int stage, int reps
       case DGDFT_STAGE_XY_FWD: launch_h_pass<real>(w.batch, 0, bref<real>(BW), bref<real>(BHW), 0, st); break;
       case DGDFT_STAGE_Z_MULT: launch_h_pass<real>(w.batch, 1, bref<real>(BW), bref<real>(BHW), 0, st); break;
       case DGDFT_STAGE_XY_INV: launch_h_pass<real>(w.batch, 2, bref<real>(BW), bref<real>(BHW), 0, st); break;
-      case DGDFT_STAGE_GRAM: launch_gram<real>(w.batch, w.gram12(), w.partial, w.partial_cap, st); break;
+      case DGDFT_STAGE_GRAM:
+        if (!w.tc_gram(0, st)) launch_gram<real>(w.batch, w.gram12(), w.partial, w.partial_cap, st);
+        break;
       case DGDFT_STAGE_UPDATE: {
         TsmmJob<real> t;
         t.nin = 3;
@@ -1307,7 +1497,7 @@ dgdft_status time_stage_t(dgdft_alb_ctx* ctx, Wave<real>& w, int stage, int reps
         launch_tsmm<real>(w.batch, t, st);
         break;
       }
-      case DGDFT_STAGE_RR: launch_rr(w.d_rr_lob, nel, st); break;
+      case DGDFT_STAGE_RR: launch_rr(w.d_rr_lob, nel, st, 3 * w.batch.s.max_m, w.batch.s.max_m); break;
       default: launch_residual<real>(w.batch, w.rnchunk, st); break;
     }
   };
@@ -1406,7 +1596,7 @@ dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int n, int m, const dou
   if (e == cudaSuccess) e = ctx_copy(ctx, db, b, sizeof(double) * nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = ctx_copy(ctx, dt, &t, sizeof(t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    launch_rr(dt, 1, ctx->stream);
+    launch_rr(dt, 1, ctx->stream, n, m);
     e = cudaStreamSynchronize(ctx->stream);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -1439,6 +1629,243 @@ dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int
   if ((s = alb_orthonormalise(ctx, w, 0, xs, J, out)) != DGDFT_OK) return s;
   CK(ctx_copy(ctx, phi, out, sizeof(double) * (size_t)eh.ne() * J,
                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return DGDFT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------ learned preconditioner
+
+namespace {
+
+dgdft_status ensure_net(dgdft_alb_ctx* ctx, uint64_t seed, bool reinit) {
+  CK(cudaSetDevice(ctx->device));
+  if (!ctx->net) ctx->net = new ConvNet();
+  if (!ctx->net->ready || reinit) {
+    std::string e = ctx->net->init(seed, ctx->stream);
+    if (!e.empty()) return ctx->fail(DGDFT_ENOMEM, e);
+  }
+  return DGDFT_OK;
+}
+
+// A device view of caller data: the caller's pointer when on_device, else a
+// temporary device copy (freed by the guard).
+struct DevView {
+  const void* ptr = nullptr;
+  void* owned = nullptr;
+  ~DevView() {
+    if (owned) cudaFree(owned);
+  }
+};
+
+dgdft_status dev_view(dgdft_alb_ctx* ctx, const void* src, size_t bytes, int on_device, DevView& v) {
+  if (on_device) {
+    v.ptr = src;
+    return DGDFT_OK;
+  }
+  CK(cudaMalloc(&v.owned, bytes));
+  CK(ctx_copy(ctx, v.owned, src, bytes, cudaMemcpyHostToDevice));
+  v.ptr = v.owned;
+  return DGDFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgdft_status dgdft_alb_precond_init(dgdft_alb_ctx* ctx, uint64_t seed) {
+  if (!ctx) return DGDFT_EINVAL;
+  return ensure_net(ctx, seed, true);
+}
+
+dgdft_status dgdft_alb_precond_set_params(dgdft_alb_ctx* ctx, const float* params) {
+  if (!ctx || !params) return DGDFT_EINVAL;
+  for (size_t i = 0; i < convnet_total_params(); ++i)
+    if (!std::isfinite(params[i])) return ctx->fail(DGDFT_EINVAL, "non-finite network parameter");
+  dgdft_status s = ensure_net(ctx, 0, false);
+  if (s != DGDFT_OK) return s;
+  std::string e = ctx->net->set_params(params, ctx->stream);
+  return e.empty() ? DGDFT_OK : ctx->fail(DGDFT_ECUDA, e);
+}
+
+dgdft_status dgdft_alb_precond_get_params(dgdft_alb_ctx* ctx, float* params) {
+  if (!ctx || !params) return DGDFT_EINVAL;
+  if (!ctx->net || !ctx->net->ready) return ctx->fail(DGDFT_ESTATE, "no network");
+  std::string e = ctx->net->get_params(params, ctx->stream);
+  return e.empty() ? DGDFT_OK : ctx->fail(DGDFT_ECUDA, e);
+}
+
+dgdft_status dgdft_alb_precond_save(dgdft_alb_ctx* ctx, const char* path) {
+  if (!ctx || !path) return DGDFT_EINVAL;
+  if (!ctx->net || !ctx->net->ready) return ctx->fail(DGDFT_ESTATE, "no network");
+  std::string e = ctx->net->save_file(path, ctx->stream);
+  return e.empty() ? DGDFT_OK : ctx->fail(DGDFT_EINVAL, e);
+}
+
+dgdft_status dgdft_alb_precond_load(dgdft_alb_ctx* ctx, const char* path) {
+  if (!ctx || !path) return DGDFT_EINVAL;
+  dgdft_status s = ensure_net(ctx, 0, false);
+  if (s != DGDFT_OK) return s;
+  std::string e = ctx->net->load_file(path, ctx->stream);
+  return e.empty() ? DGDFT_OK : ctx->fail(DGDFT_EINVAL, e);
+}
+
+dgdft_status dgdft_alb_precond_forward(dgdft_alb_ctx* ctx, int B, int nz, int ny, int nx, const float* in,
+                                       float* out, int on_device) {
+  if (!ctx || !in || !out || B < 1 || nz < 1 || ny < 1 || nx < 1) return DGDFT_EINVAL;
+  if (!ctx->net || !ctx->net->ready) return ctx->fail(DGDFT_ESTATE, "no network");
+  const size_t pts = (size_t)nz * ny * nx;
+  DevView vin;
+  dgdft_status s = dev_view(ctx, in, sizeof(float) * 2 * B * pts, on_device, vin);
+  if (s != DGDFT_OK) return s;
+  float *tmp = nullptr, *dout = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(float) * (2 * (size_t)B * 16 * pts + (size_t)B * pts)));
+  std::unique_ptr<void, decltype(&cudaFree)> guard(tmp, &cudaFree);
+  dout = tmp + 2 * (size_t)B * 16 * pts;
+  ctx->net->forward((const float*)vin.ptr, dout, B, nz, ny, nx, nullptr, tmp, tmp + (size_t)B * 16 * pts,
+                    ctx->stream);
+  CK(cudaGetLastError());
+  CK(ctx_copy(ctx, out, dout, sizeof(float) * B * pts, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return DGDFT_OK;
+}
+
+dgdft_status dgdft_alb_precond_loss_grad(dgdft_alb_ctx* ctx, int B, int nz, int ny, int nx, int lo, int hi,
+                                         const float* in, const float* tgt, double* loss, float* grads,
+                                         int on_device) {
+  if (!ctx || !in || !tgt || !loss || !grads || B < 1 || nz < 1 || ny < 1 || nx < 1) return DGDFT_EINVAL;
+  if (lo < 0 || hi <= lo || hi > nz || hi > ny || hi > nx) return DGDFT_EINVAL;
+  if (!ctx->net || !ctx->net->ready) return ctx->fail(DGDFT_ESTATE, "no network");
+  const size_t pts = (size_t)nz * ny * nx;
+  DevView vin, vt;
+  dgdft_status s = dev_view(ctx, in, sizeof(float) * 2 * B * pts, on_device, vin);
+  if (s == DGDFT_OK) s = dev_view(ctx, tgt, sizeof(float) * B * pts, on_device, vt);
+  if (s != DGDFT_OK) return s;
+  std::string e = ctx->net->loss_and_grad((const float*)vin.ptr, (const float*)vt.ptr, B, nz, ny, nx, lo, hi, loss,
+                                          ctx->stream);
+  if (!e.empty()) return ctx->fail(DGDFT_ECUDA, e);
+  size_t off = 0;
+  for (int l = 0; l < kConvLayers; ++l) {
+    const size_t n = conv_param_count(l);
+    CK(ctx_copy(ctx, grads + off, ctx->net->grad[l], n * sizeof(float), cudaMemcpyDeviceToHost));
+    off += n;
+  }
+  return DGDFT_OK;
+}
+
+dgdft_status dgdft_alb_precond_train(dgdft_alb_ctx* ctx, int nfields, int nz, int ny, int nx, const float* r,
+                                     const float* v, const float* t, int crop, int batch, int steps, double lr,
+                                     uint64_t seed, double* loss_first, double* loss_last) {
+  if (!ctx || !r || !v || !t || nfields < 1 || crop < 9 || batch < 1 || steps < 1 || !(lr > 0.0))
+    return DGDFT_EINVAL;
+  dgdft_status s = ensure_net(ctx, seed, false);
+  if (s != DGDFT_OK) return s;
+  const size_t pts = (size_t)nz * ny * nx, cpts = (size_t)crop * crop * crop;
+  float* buf = nullptr;
+  CK(cudaMalloc(&buf, sizeof(float) * (3 * (size_t)batch * cpts + nfields) + sizeof(int) * 4 * batch));
+  std::unique_ptr<void, decltype(&cudaFree)> guard(buf, &cudaFree);
+  float* in = buf;
+  float* tgt = in + 2 * (size_t)batch * cpts;
+  float* rms = tgt + (size_t)batch * cpts;
+  int* offs = reinterpret_cast<int*>(rms + nfields);
+  field_rms(r, nfields, pts, rms, ctx->stream);
+  std::mt19937_64 gen(seed ^ 0x5DEECE66DULL);
+  std::vector<int> h_offs(4 * (size_t)batch);
+  double first = 0.0, last = 0.0;
+  const int avg = std::min(10, steps);
+  for (int it = 0; it < steps; ++it) {
+    for (int b = 0; b < batch; ++b) {
+      h_offs[4 * b] = (int)(gen() % (uint64_t)nfields);
+      h_offs[4 * b + 1] = (int)(gen() % (uint64_t)nz);
+      h_offs[4 * b + 2] = (int)(gen() % (uint64_t)ny);
+      h_offs[4 * b + 3] = (int)(gen() % (uint64_t)nx);
+    }
+    CK(cudaMemcpyAsync(offs, h_offs.data(), sizeof(int) * 4 * batch, cudaMemcpyHostToDevice, ctx->stream));
+    gather_crops(r, v, t, rms, offs, batch, crop, nz, ny, nx, in, tgt, ctx->stream);
+    double loss = 0.0;
+    std::string e = ctx->net->loss_and_grad(in, tgt, batch, crop, crop, crop, 4, crop - 4, &loss, ctx->stream);
+    if (!e.empty()) return ctx->fail(DGDFT_ECUDA, e);
+    if (!std::isfinite(loss)) return ctx->fail(DGDFT_ENOTCONV, "training loss is not finite");
+    ctx->net->adam((float)lr, ctx->stream);
+    if (it < avg) first += loss / avg;
+    if (it >= steps - avg) last += loss / avg;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  if (loss_first) *loss_first = first;
+  if (loss_last) *loss_last = last;
+  return DGDFT_OK;
+}
+
+dgdft_status dgdft_alb_precond_make_data(dgdft_alb_ctx* ctx, int elem, int nsnap, const int* snap_iters,
+                                         float* r_out, float* t_out, double* sigma_out, int* cg_iters) {
+  if (!ctx || !snap_iters || !r_out || !t_out || nsnap < 1 || elem < 0 || elem >= (int)ctx->el.size())
+    return DGDFT_EINVAL;
+  for (int q = 0; q < nsnap; ++q)
+    if (snap_iters[q] < 1) return DGDFT_EINVAL;
+  Wave<double> w;
+  dgdft_status s = with_step_wave<double>(ctx, elem, w);
+  if (s != DGDFT_OK) return s;
+  ElemDev<double>& E = w.h[0];
+  const int ng = E.ng, m = E.m;
+  const size_t nb = (size_t)ng * m;
+  cudaStream_t st = ctx->stream;
+  double* small = nullptr;
+  CK(cudaMalloc(&small, sizeof(double) * (64 * (size_t)m + 7 * (size_t)m)));
+  std::unique_ptr<void, decltype(&cudaFree)> guard(small, &cudaFree);
+  double* part = small;
+  double* rr = part + 64 * m;
+  double* rrn = rr + m;
+  double* pap = rrn + m;
+  double* alpha = pap + m;
+  double* nalpha = alpha + m;
+  double* beta = nalpha + m;
+  double* negsig = beta + m;
+  for (int q = 0; q < nsnap; ++q) {
+    if ((s = w.load_inputs()) != DGDFT_OK) return s;
+    if ((s = w.run(0.0, snap_iters[q], 0, nullptr)) != DGDFT_OK) return s;
+    double theta0 = 0.0;
+    CK(ctx_copy(ctx, &theta0, E.theta, sizeof(double), cudaMemcpyDeviceToHost));
+    const double sigma = theta0 - 1.0;
+    if (sigma_out) sigma_out[q] = sigma;
+    double* R = E.blk[BW][0];
+    launch_convert<double, float>(R, r_out + (size_t)q * nb, nb, st);
+    // CG on (H - sigma I) t = r for all m columns at once
+    if ((s = w.reset_states(0.0)) != DGDFT_OK) return s;
+    double* T = E.blk[BP][1];
+    double* RC = E.blk[BHW][0];
+    double* P = E.blk[BHP][1];
+    double* AP = E.blk[BP][0];
+    CK(cudaMemsetAsync(T, 0, sizeof(double) * nb, st));
+    CK(cudaMemcpyAsync(RC, R, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(P, R, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> hs(m, -sigma);
+    CK(cudaMemcpyAsync(negsig, hs.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    col_dot(RC, RC, ng, m, part, rr, st);
+    std::vector<double> b2(m), cur(m);
+    CK(ctx_copy(ctx, b2.data(), rr, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    int it = 0;
+    for (; it < 1000; ++it) {
+      launch_apply_h<double>(w.batch, bptr<double>(P), bptr<double>(AP), m, st);
+      col_axpby(negsig, P, nullptr, AP, ng, m, st);
+      col_dot(P, AP, ng, m, part, pap, st);
+      cg_alpha(rr, pap, alpha, nalpha, m, st);
+      col_axpby(alpha, P, nullptr, T, ng, m, st);
+      col_axpby(nalpha, AP, nullptr, RC, ng, m, st);
+      col_dot(RC, RC, ng, m, part, rrn, st);
+      cg_beta(rr, rrn, beta, m, st);
+      col_axpby(nullptr, RC, beta, P, ng, m, st);
+      if (it % 10 == 9) {
+        CK(ctx_copy(ctx, cur.data(), rr, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        double worst = 0.0;
+        for (int j = 0; j < m; ++j) worst = std::max(worst, std::sqrt(cur[j] / std::max(b2[j], 1e-300)));
+        if (worst <= 1e-10) break;
+      }
+    }
+    CK(cudaGetLastError());
+    if (cg_iters) cg_iters[q] = it + 1;
+    launch_convert<double, float>(T, t_out + (size_t)q * nb, nb, st);
+    CK(cudaStreamSynchronize(st));
+  }
   return DGDFT_OK;
 }
 

@@ -3,9 +3,11 @@
 // C = U^T V over the N_g rows of each element, where U is a concatenation of
 // up to 6 column blocks (the MMA M side, padded to 128) and V of up to 3
 // blocks (the N side).  Every FP32 value x is split into bf16 parts
-// hi = bf16(x), lo = bf16(x - hi) and the product is accumulated in FP32 in
-// tensor memory as hi*hi + hi*lo + lo*hi (the dropped lo*lo term is ~2^-16
-// relative), so the FP32 data keep ~16 significant bits per product.
+// hi = bf16(x), lo = bf16(x - hi) and the product (hi + lo)(hi + lo) is
+// accumulated in FP32 in tensor memory as four bf16 products.  The lo*lo
+// term is kept: it is always positive on the diagonal of S^T S, so dropping
+// it would bias the overlap matrix by ~2^-18 relative; what remains is the
+// random rounding of lo (~2^-17 relative per value).
 //
 // Each CTA (128 threads) owns one 128-row M tile and one chunk of rows:
 //   * threads load FP32 from HBM (coalesced along rows), split, and store the
@@ -28,7 +30,7 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int TC_KC = 64;                    // rows (K) per stage: one 128-byte bf16 row
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr int TC_NMAX = 256;                 // accumulator columns (N <= 256)
 constexpr int A_BYTES = TC_M * TC_KC * 2;    // one bf16 part of the A tile: 16 KB
 constexpr uint32_t SPIN_LIMIT = 1u << 26;
@@ -178,6 +180,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int mt = blockIdx.y;
   if (mt * TC_M >= M_total) return;
   const int rows = e.ng;
+  // float2 loads need every column to start on an 8-byte boundary: even N_g
+  // (always true for solver blocks, nx being even) and k0 even
+  const bool vec2 = (rows & 1) == 0;
   const int k_beg = blockIdx.x * args.kchunk;
   const int k_end = min(rows, k_beg + args.kchunk);
   const int nsteps = (k_end > k_beg) ? (k_end - k_beg + TC_KC - 1) / TC_KC : 0;
@@ -218,40 +223,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (abort_flag) break;
     const int k0 = k_beg + c * TC_KC;
-    // A tile: 128 columns of U x 64 rows; each warp handles 8 columns per pass,
-    // lanes read two consecutive rows (float2) of one column.
-    for (int q = warp; q < TC_M; q += 4) {
-      const int col = mt * TC_M + q;
-      const float* src = (col < M_total) ? side_col(e, args.a, col) : nullptr;
-      const int k = 2 * lane;
-      float x0 = 0.f, x1 = 0.f;
-      if (src) {
-        const int g = k0 + k;
-        if (g + 1 < k_end) {
-          const float2 v = *reinterpret_cast<const float2*>(src + g);
-          x0 = v.x;
-          x1 = v.y;
-        } else if (g < k_end) {
-          x0 = src[g];
+    // A tile (128 columns) then B tile (N columns), 64 rows each: every warp
+    // takes columns warp, warp + NW, ...; lanes read two consecutive rows of a
+    // column.  Eight columns' loads are issued before any is converted so the
+    // loads overlap instead of forming a dependent chain.
+    constexpr int NW = TC_THREADS / 32;
+    constexpr int BATCH = 8;
+    const int k = 2 * lane;
+    const int g = k0 + k;
+    for (int side = 0; side < 2; ++side) {
+      const int ncol = side ? N : TC_M;
+      unsigned char* hi = side ? b_hi : a_hi;
+      unsigned char* lo = side ? b_lo : a_lo;
+      for (int q0 = warp; q0 < ncol; q0 += NW * BATCH) {
+        float2 v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+          const int q = q0 + u * NW;
+          const float* src = nullptr;
+          if (q < ncol) {
+            if (side) {
+              src = (q < N_real) ? side_col(e, args.b, q) : nullptr;
+            } else {
+              const int col = mt * TC_M + q;
+              src = (col < M_total) ? side_col(e, args.a, col) : nullptr;
+            }
+          }
+          v[u] = make_float2(0.f, 0.f);
+          if (src) {
+            if (vec2 && g + 1 < k_end) {
+              v[u] = *reinterpret_cast<const float2*>(src + g);
+            } else {
+              if (g < k_end) v[u].x = src[g];
+              if (g + 1 < k_end) v[u].y = src[g + 1];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+          const int q = q0 + u * NW;
+          if (q < ncol) split_store2(hi, lo, q, k, v[u].x, v[u].y);
         }
       }
-      split_store2(a_hi, a_lo, q, k, x0, x1);
-    }
-    for (int q = warp; q < N; q += 4) {
-      const float* src = (q < N_real) ? side_col(e, args.b, q) : nullptr;
-      const int k = 2 * lane;
-      float x0 = 0.f, x1 = 0.f;
-      if (src) {
-        const int g = k0 + k;
-        if (g + 1 < k_end) {
-          const float2 v = *reinterpret_cast<const float2*>(src + g);
-          x0 = v.x;
-          x1 = v.y;
-        } else if (g < k_end) {
-          x0 = src[g];
-        }
-      }
-      split_store2(b_hi, b_lo, q, k, x0, x1);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -265,6 +278,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mma_bf16(tmem, sw128_desc(ah + koff), sw128_desc(bh + koff), idesc, acc0);
         mma_bf16(tmem, sw128_desc(ah + koff), sw128_desc(bl + koff), idesc, 1u);
         mma_bf16(tmem, sw128_desc(al + koff), sw128_desc(bh + koff), idesc, 1u);
+        mma_bf16(tmem, sw128_desc(al + koff), sw128_desc(bl + koff), idesc, 1u);
       }
       mma_commit(&bars[s]);
     }
@@ -280,10 +294,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   double* out = partial + blockIdx.z * args.pstride +
                 ((size_t)blockIdx.x * args.tiles_m + mt) * ((size_t)TC_M * TC_NMAX);
   if (ok) {
-    const int row = warp * 32 + lane;  // TMEM lane = M index within the tile
-    for (int c0 = 0; c0 < N; c0 += 16) {
+    // a warp reads the TMEM lanes of its quarter (warp % 4); warps w and w + 4
+    // take alternate 16-column groups
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;  // TMEM lane = M index within the tile
+    for (int c0 = 16 * half; c0 < N; c0 += 32) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j) out[(size_t)row * TC_NMAX + c0 + j] = (nsteps > 0) ? (double)v[j] : 0.0;
     }
@@ -335,7 +352,7 @@ size_t tc_gram_smem_bytes(int n_cols) {
 }
 
 void init_tc_gram_kernel() {
-  cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  opt_in_dynamic_smem((const void*)tc_gram_kernel);
 }
 
 // LOBPCG Gram blocks of the FP32 stage: mode 0 -> A, B from [S HS]^T S;

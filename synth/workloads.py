@@ -138,6 +138,32 @@ def config2(elems=None):
     return _monolayer_elements(2, 12, 12, 6, 6, (48, 64, 40), 48, 40, 1e-6, elems)
 
 
+def config4(perturbation: int, elems=(0,)):
+    """Elements of the 576-atom monolayer geometry with its own seeded
+    +-0.2 bohr perturbation (perturbation = 0..63): training geometries of
+    the learned preconditioner."""
+    atoms, cell = monolayer(12, 12, perturb=0.2, gen=rng(4, 3, perturbation))
+    gamma = rng(4, 1, perturbation).uniform(0.5, 2.0, size=(len(atoms), 2))
+    nex = ney = 6
+    nq = (48, 64, 40)
+    ex_w, ey_w = cell[0] / nex, cell[1] / ney
+    lq = np.array([3 * ex_w, 3 * ey_w, cell[2]])
+    h = lq / np.asarray(nq)
+    ngrid = tuple(int(round(c / hh)) for c, hh in zip(cell, h))
+    co = fields.local_potential_coeffs(atoms, cell, ngrid)
+    e_lo, e_hi = element_box(nq)
+    out = []
+    for k in elems:
+        ix, iy = k % nex, k // nex
+        origin = np.mod(np.array([(ix - 1) * ex_w, (iy - 1) * ey_w, 0.0]), cell)
+        v = fields.eval_series(co, origin, h, nq)
+        rp, idx, val, gam = fields.kb_projectors(atoms, cell, origin, h, nq, gamma)
+        out.append(ElementInput(n=tuple(nq), L=tuple(lq), veff=v, proj_row_ptr=rp, proj_idx=idx,
+                                proj_val=val, proj_gamma=gam, e_lo=e_lo, e_hi=e_hi, m=48, J=40,
+                                tol=1e-6, seed_key=(4, 2, perturbation, k)))
+    return out
+
+
 def config5(elems=None):
     """216 extended elements of the 3,456-atom monolayer (24 x 9 elements)."""
     return _monolayer_elements(5, 48, 18, 24, 9, (48, 64, 48), 144, 120, 1e-6, elems)

@@ -46,6 +46,7 @@ def config2(elems):
 
 
 if __name__ == "__main__":
-    config1()
+    if "--skip-config1" not in sys.argv:
+        config1()
     if "--config2" in sys.argv:
-        config2([0])
+        config2([0, 7])
