@@ -60,6 +60,27 @@ dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int
  * values).  DGDFT_ESTATE before a solve. */
 dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device);
 
+/* Gram product C = U^T V in FP64 that allocates nothing.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory while
+ * they run (a custom pool that must not fragment, allocator-free real-time
+ * loops, frameworks that forbid allocation during graph recording).  It
+ * needs no context.  u is ng x p, v is ng x q, c is p x q, all column-major
+ * FP64 *device* pointers on the current device, owned by the caller; the
+ * work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without waiting for it.
+ * Limits: 1 <= p, q <= 256 and ng >= 1; anything else returns DGDFT_EINVAL
+ * before any GPU work.  The split-K partial sums live in one fixed 8 MiB
+ * device array inside the library, held by every GPU that loads it until
+ * the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress), so make the first call on each
+ * device outside any stream capture.  Every call reuses the same array:
+ * calls that can overlap on the GPU (different streams, or the same
+ * stream from different host threads without ordering) race and corrupt
+ * each other's results; serialise them.  Returns DGDFT_ECUDA if the launch
+ * fails.  No cudaMalloc, cudaFree or allocating library call is made. */
+dgdft_status dgdft_alb_gram_noalloc(int ng, int p, int q, const double* u, const double* v, double* c,
+                                    void* stream);
+
 /* ---- Learned preconditioner (the chosen form's replacement of the Teter
  * preconditioner of Sec. II.B, operation 5).  A 3-D convolutional network:
  * inputs (r / rms(r), V_eff), 4 layers of 3x3x3 circular convolutions,

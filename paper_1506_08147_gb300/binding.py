@@ -64,6 +64,7 @@ _SIGS = {
     "dgdft_alb_get_block": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "dgdft_alb_time_stage": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int)]),
+    "dgdft_alb_gram_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, _P, _P]),
     "dgdft_alb_precond_init": (C.c_int, [_P, C.c_uint64]),
     "dgdft_alb_precond_set_params": (C.c_int, [_P, _P]),
     "dgdft_alb_precond_get_params": (C.c_int, [_P, _P]),
