@@ -155,7 +155,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
-                    stream=stream.cuda_stream, simt_only=args.simt, h_fp64_forward=args.fwd64)
+                    stream=stream.cuda_stream, tc_gram=args.tc_gram, h_fp64_forward=args.fwd64)
     dev_x0 = []
     for k, e in enumerate(els):
         B.load_element(ctx, k, e)
@@ -404,7 +404,8 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=3)
-    ap.add_argument("--simt", action="store_true", help="SIMT kernels only (no tcgen05)")
+    ap.add_argument("--tc-gram", action="store_true",
+                    help="tcgen05 split-BF16 Gram in the FP32 stage (default: compensated SIMT)")
     ap.add_argument("--fwd64", action="store_true", help="FP64 forward FFT in the FP32 stage's H apply")
     args = ap.parse_args()
     if args.impl == "reference":

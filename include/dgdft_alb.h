@@ -91,8 +91,13 @@ typedef struct {
   int device;             /* CUDA device ordinal; -1 = current device         */
   int keep_block;         /* 1: keep each converged N_g x m Ritz block on the
                              host after solve (for dgdft_alb_get_block)        */
-  int bulk_kernels;       /* 0: tcgen05 tensor-core kernels for the FP32 stage
-                             where the shapes allow (3m <= 256); 1: SIMT only */
+  int bulk_kernels;       /* Gram products of the FP32 stage.  0: SIMT FP32
+                             with compensated accumulation (~2e-7 relative);
+                             1: tcgen05 split-BF16 tensor-core kernel where
+                             the shapes allow (3m <= 256): faster per call,
+                             but its FP32 tensor-memory accumulation gives
+                             ~1e-5 relative, so the FP32 stage stalls higher
+                             and leaves more iterations to FP64           */
   int h_fp64_forward;     /* 1: the FP32 stage's H apply runs its forward FFT
                              in FP64 (lower noise, ~10x slower passes)        */
   const char* autotune_cache;   /* optional JSON path; NULL = none            */

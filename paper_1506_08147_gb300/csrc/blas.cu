@@ -18,6 +18,7 @@ namespace {
 constexpr int TILE = 64;   // output tile edge
 constexpr int KS = 32;     // rows staged per shared-memory step (Gram)
 constexpr int KU = 16;     // inner dimension staged per step (update)
+constexpr double SHIFT_RES = 5e-2;  // residual below which the FP32 shift follows the Ritz values
 
 template <class real>
 __device__ __forceinline__ int ld_of(const ElemDev<real>& e, const BRef<real>& r, int ld_in, int rows) {
@@ -52,10 +53,14 @@ __global__ void __launch_bounds__(256) gram_kernel(const ElemDev<real>* __restri
   const int k_beg = blockIdx.x * kchunk;
   const int k_end = min(rows, k_beg + kchunk);
   real acc[4][4];
+  // FP32: each KS-row step is summed in FP32 and folded into a compensated
+  // (hi, lo) pair, so rounding does not grow with the chunk length (the
+  // Gram entries carry residual information ~1e-6 of their size)
+  real chi[4][4], clo[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = chi[i][j] = clo[i][j] = 0;
   for (int k0 = k_beg; k0 < k_end; k0 += KS) {
     for (int i = threadIdx.x; i < KS * TILE; i += blockDim.x) {
       const int c = i / KS, r = i - c * KS;
@@ -78,13 +83,27 @@ __global__ void __launch_bounds__(256) gram_kernel(const ElemDev<real>* __restri
         for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
     }
     __syncthreads();
+    if constexpr (sizeof(real) == sizeof(float)) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          // Knuth's two-sum of chi + acc: exact error term into clo
+          const real sum = chi[i][j] + acc[i][j];
+          const real bp = sum - chi[i][j];
+          clo[i][j] += (chi[i][j] - (sum - bp)) + (acc[i][j] - bp);
+          chi[i][j] = sum;
+          acc[i][j] = 0;
+        }
+    }
   }
   double* out = partial + blockIdx.z * pstride +
                 ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (TILE * TILE);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * TILE + tx * 4 + j] = (double)acc[i][j];
+    for (int j = 0; j < 4; ++j)
+      out[(ty * 4 + i) * TILE + tx * 4 + j] = (double)acc[i][j] + (double)chi[i][j] + (double)clo[i][j];
 }
 
 template <class real>
@@ -108,7 +127,6 @@ __global__ void gram_reduce_kernel(const ElemDev<real>* __restrict__ elems, Gram
     case OUT_GRAM_A: out = e.gram; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
     case OUT_GRAM_B: out = e.gram + (size_t)9 * e.m * e.m; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
     case OUT_GXW: out = e.gxw; ld = job.ld_out > 0 ? job.ld_out : e.m; break;
-    case OUT_Y: out = e.Y; ld = job.ld_out > 0 ? job.ld_out : 3 * e.m; break;
     default: out = job.out_ptr; ld = job.ld_out; break;
   }
   const double* base = partial + blockIdx.z * pstride + (size_t)blockIdx.x * (TILE * TILE);
@@ -255,7 +273,8 @@ __global__ void post_residual_kernel(const ElemDev<real>* __restrict__ elems, in
     }
     const double res = sqrt(s[0] / s[1]);
     e.res[j] = res;
-    e.tkin[j] = (s[2] - s[3] - nl) / s[1];
+    // x.Hx was taken with H - sigma I
+    e.tkin[j] = (s[2] + e.sigma[0] * s[1] - s[3] - nl) / s[1];
     if (!isfinite(res)) bad = 1;
     if (j < e.J) mx = fmax(mx, res);
   }
@@ -279,6 +298,44 @@ __global__ void post_residual_kernel(const ElemDev<real>* __restrict__ elems, in
     } else {
       st[ST_ITER] += 1;
     }
+    if constexpr (sizeof(real) == sizeof(float)) {
+      // Re-centre the spectral shift on the Ritz values once they have
+      // settled: the Gram entries that carry the residual information
+      // ((H - sigma) x_i against the basis) then shrink from |theta| to
+      // |theta - sigma|, and with them the FP32 rounding of those sums.
+      double d = 0.0;
+      if (st[ST_ACTIVE] && mx < SHIFT_RES) {
+        const double lo = e.theta[0], hi = e.theta[e.m - 1];
+        const double mid = 0.5 * (lo + hi);
+        if (fabs(mid) > 0.25 * (hi - lo) + 1e-3) d = mid;
+      }
+      e.sigma[1] = d;
+      if (d != 0.0) {
+        e.sigma[0] += d;
+        for (int j = 0; j < e.m; ++j) e.theta[j] -= d;
+      }
+    }
+  }
+}
+
+// After a change d of the shift: HX -= d X and HP -= d P, keeping the stored
+// H-images equal to (H - sigma I) applied to their blocks.
+template <class real>
+__global__ void __launch_bounds__(256) shift_kernel(const ElemDev<real>* __restrict__ elems) {
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const double d = e.sigma[1];
+  if (d == 0.0) return;
+  const real dr = (real)d;
+  const size_t n = (size_t)e.ng * e.m;
+  const bool has_p = e.state[ST_HAS_P] != 0;
+  real* hx = cur_blk(e, BHX);
+  const real* x = cur_blk(e, BX);
+  real* hp = cur_blk(e, BHP);
+  const real* p = cur_blk(e, BP);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    hx[i] -= dr * x[i];
+    if (has_p) hp[i] -= dr * p[i];
   }
 }
 
@@ -357,6 +414,12 @@ void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStrea
 }
 
 template <class real>
+void launch_shift(const Batch<real>& b, cudaStream_t st) {
+  const int per_elem = std::max(8, 1216 / std::max(1, b.s.nel));
+  shift_kernel<real><<<dim3(per_elem, 1, b.s.nel), 256, 0, st>>>(b.d_elems);
+}
+
+template <class real>
 void launch_theta(const Batch<real>& b, int nchunk, int mode, cudaStream_t st) {
   theta_kernel<real><<<dim3(1, 1, b.s.nel), 128, 0, st>>>(b.d_elems, nchunk, mode);
 }
@@ -373,7 +436,8 @@ void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st) {
   template void launch_residual<real>(const Batch<real>&, int, cudaStream_t);                        \
   template void launch_post_residual<real>(const Batch<real>&, int, int, cudaStream_t);              \
   template void launch_iter_finish<real>(const Batch<real>&, int, cudaStream_t);                    \
-  template void launch_theta<real>(const Batch<real>&, int, int, cudaStream_t);
+  template void launch_theta<real>(const Batch<real>&, int, int, cudaStream_t);                     \
+  template void launch_shift<real>(const Batch<real>&, cudaStream_t);
 DGDFT_INST(double)
 DGDFT_INST(float)
 #undef DGDFT_INST

@@ -101,6 +101,10 @@ template <class real> struct ElemDev {
   double* theta;            // m
   double* res;              // m
   double* tkin;             // m
+  // spectral shift of the FP32 stage: [0] sigma, [1] the change made this
+  // iteration.  Kernels of the FP32 stage apply H - sigma I, so Ritz values
+  // and H-images are stored relative to sigma (always 0 for FP64 waves).
+  double* sigma;
   double* rr_work;          // dense eigensolver workspace
   double* rpart;            // residual partial sums
   int* state;               // STATE_WORDS

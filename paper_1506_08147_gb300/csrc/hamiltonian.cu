@@ -216,12 +216,13 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     const R2* xp = reinterpret_cast<const R2*>(resolve(e, xsrc) + plane_off);
     const R2* vp = reinterpret_cast<const R2*>(e.V + (size_t)z * e.nx * ny);
     R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);
+    const TC sg = (TC)e.sigma[0];  // 0 except in the shifted FP32 stage
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
       const int y = t / nh, k = t - y * nh;
       const C kv = res[y * row + k];
       const R2 xv = xp[t];
       const R2 vv = vp[t];
-      op[t] = cmake<R2>((real)(kv.x + (TC)vv.x * (TC)xv.x), (real)(kv.y + (TC)vv.y * (TC)xv.y));
+      op[t] = cmake<R2>((real)(kv.x + ((TC)vv.x - sg) * (TC)xv.x), (real)(kv.y + ((TC)vv.y - sg) * (TC)xv.y));
     }
   } else {
     R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);

@@ -59,7 +59,7 @@ void launch_h_pass(const Batch<real>& b, int pass, BRef<real> src, BRef<real> ds
 // blas.cu
 // Gram products U_a^T V_b over the rows of each element, split over row
 // chunks; FP64 partial sums are reduced in a fixed order.
-enum { OUT_GRAM_A = 0, OUT_GRAM_B = 1, OUT_GXW = 2, OUT_PTR = 3, OUT_Y = 4 };
+enum { OUT_GRAM_A = 0, OUT_GRAM_B = 1, OUT_GXW = 2, OUT_PTR = 3 };
 constexpr int MAX_PAIRS = 12;
 template <class real> struct GramJob {
   int npairs = 0;
@@ -107,6 +107,10 @@ void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStrea
 // End of an iteration: flip the X/P/HX/HP buffers, mark P valid.
 template <class real>
 void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st);
+// FP32 stage: HX -= d X, HP -= d P for elements whose shift moved by d this
+// iteration (post_residual decides d).
+template <class real>
+void launch_shift(const Batch<real>& b, cudaStream_t st);
 // theta = 0 (mode 0) or the Rayleigh quotients from the residual sums (mode 1)
 template <class real>
 void launch_theta(const Batch<real>& b, int nchunk, int mode, cudaStream_t st);

@@ -185,7 +185,7 @@ size_t elem_bytes(const ElemHost& h) {
   s.add(sizeof(real) * np * m);
   for (int i = 0; i < 10; ++i) s.add(sizeof(real) * ng * m);
   s.add(sizeof(double2) * nspec * m);
-  s.add(sizeof(double) * (18 * m * m + m * m + 3 * m * m + 3 * m));
+  s.add(sizeof(double) * (18 * m * m + m * m + 3 * m * m + 3 * m + 2));
   s.add(sizeof(double) * rr_work_doubles(3 * (int)m, (int)m));
   s.add(sizeof(double) * m * nchunk_rows((int)ng) * 4);
   s.add(sizeof(int) * STATE_WORDS);
@@ -214,11 +214,66 @@ template <class real> struct Wave {
   bool learned = false;
   int gnz = 0, gny = 0, gnx = 0;
   float *nn_in = nullptr, *nn_out = nullptr, *nn_tmp0 = nullptr, *nn_tmp1 = nullptr;
+  // Two half-batches iterated on two streams, the second half a
+  // half-iteration behind: the Rayleigh-Ritz kernel of one half (one CTA per
+  // element, bound by the FP64 pipe of few SMs) then runs beside the
+  // bandwidth-bound kernels of the other half instead of leaving most SMs idle.
+  struct SubView {
+    Batch<real> batch;
+    RRTask *rr_init = nullptr, *rr_lob = nullptr;
+    double* partial = nullptr;
+    size_t partial_cap = 0;
+  };
+  SubView full, sub[2];
+  bool split = false;
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   ~Wave() {
     if (arena.base) cudaFree(arena.base);
     for (float* p : {nn_in, nn_out, nn_tmp0, nn_tmp1})
       if (p) cudaFree(p);
+    if (st2) cudaStreamDestroy(st2);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
+
+  void use(const SubView& v) {
+    batch = v.batch;
+    d_rr_init = v.rr_init;
+    d_rr_lob = v.rr_lob;
+    partial = v.partial;
+    partial_cap = v.partial_cap;
+  }
+
+  // Half-batch views; split only FP32 waves of >= 2 elements without the
+  // learned preconditioner (its scratch is shared by the wave).
+  dgdft_status setup_split() {
+    full.batch = batch;
+    full.rr_init = d_rr_init;
+    full.rr_lob = d_rr_lob;
+    full.partial = partial;
+    full.partial_cap = partial_cap;
+    const int nel = batch.s.nel;
+    if (!std::is_same<real, float>::value || learned || nel < 2) return DGDFT_OK;
+    const int h0 = nel / 2;
+    const size_t per = partial_cap / nel;
+    for (int k = 0; k < 2; ++k) {
+      const int off = k ? h0 : 0, cnt = k ? nel - h0 : h0;
+      SubView& v = sub[k];
+      v.batch = batch;
+      v.batch.d_elems = d_elems + off;
+      v.batch.s.nel = cnt;
+      v.rr_init = d_rr_init + off;
+      v.rr_lob = d_rr_lob + off;
+      v.partial = partial + per * off;
+      v.partial_cap = per * cnt;
+    }
+    CK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    split = true;
+    return DGDFT_OK;
   }
 
   dgdft_status setup_learned() {
@@ -304,7 +359,9 @@ template <class real> struct Wave {
     CK(ctx_copy(ctx, d_rr_lob, rr_lob.data(), sizeof(RRTask) * nel, cudaMemcpyHostToDevice));
     batch.d_elems = d_elems;
     batch.s = s;
-    return setup_learned();
+    dgdft_status ls = setup_learned();
+    if (ls != DGDFT_OK) return ls;
+    return setup_split();
   }
 
   template <class T> T* take(size_t count) { return (T*)arena.take(sizeof(T) * std::max<size_t>(count, 1)); }
@@ -435,10 +492,16 @@ template <class real> struct Wave {
     E.theta = take<double>(m);
     E.res = take<double>(m);
     E.tkin = take<double>(m);
+    E.sigma = take<double>(2);
     E.rr_work = take<double>(rr_work_doubles(3 * (int)m, (int)m));
     E.rpart = take<double>(m * rnchunk * 4);
     E.state = take<int>(STATE_WORDS);
-    if (!E.state || !E.rpart || !E.rr_work || !E.Z) return ctx->fail(DGDFT_ENOMEM, "wave arena exhausted");
+    if (!E.state || !E.rpart || !E.rr_work || !E.Z || !E.sigma)
+      return ctx->fail(DGDFT_ENOMEM, "wave arena exhausted");
+    {
+      const double zero2[2] = {0.0, 0.0};
+      if (put(E.sigma, zero2, 2) != DGDFT_OK) return DGDFT_ECUDA;
+    }
     return DGDFT_OK;
   }
 
@@ -488,6 +551,7 @@ template <class real> struct Wave {
         std::fill(s, s + STATE_WORDS, 0);
         s[ST_ACTIVE] = 1;
         s[ST_TETER] = learned ? 0 : 1;
+        CK(cudaMemsetAsync(h[i].sigma, 0, 2 * sizeof(double), ctx->stream));
       }
       h[i].tol = tol;
     }
@@ -508,45 +572,6 @@ template <class real> struct Wave {
 
   bool fwd64() const { return ctx->cfg.h_fp64_forward != 0; }
 
-  // P <- P - [X W] ([X W]^T P) and HP by the same transform.  Near
-  // convergence P points almost along W; forming X' = [X W P] Y with the
-  // large, cancelling coefficients that such a basis needs would leave FP32
-  // rounding of order |Y| u in X', which H amplifies into a residual floor.
-  // C = [X W]^T P is staged in the Rayleigh-Ritz coefficient buffer.
-  void orthogonalise_p(cudaStream_t st) {
-    GramJob<real> g;
-    g.npairs = 2;
-    g.a[0] = bref<real>(BX);
-    g.b[0] = bref<real>(BP);
-    g.a[1] = bref<real>(BW);
-    g.b[1] = bref<real>(BP);
-    for (int k = 0; k < 2; ++k) {
-      g.needs_p[k] = 1;
-      g.out_id[k] = OUT_GRAM_A;  // placed below, then moved: see ld_out / brow
-      g.bcol[k] = 0;
-    }
-    g.brow[0] = 0;
-    g.brow[1] = 1;
-    g.out_id[0] = g.out_id[1] = OUT_Y;
-    launch_gram<real>(batch, g, partial, partial_cap, st);
-    TsmmJob<real> t;
-    t.nin = 2;
-    t.in[0] = bref<real>(BX);
-    t.in[1] = bref<real>(BW);
-    t.yrow[0] = 0;
-    t.yrow[1] = 1;
-    t.y_id = Y_RR;
-    t.out = bref<real>(BP);
-    t.needs_p[0] = t.needs_p[1] = 1;
-    t.alpha = -1.0;
-    t.beta = 1.0;
-    launch_tsmm<real>(batch, t, st);
-    t.in[0] = bref<real>(BHX);
-    t.in[1] = bref<real>(BHW);
-    t.out = bref<real>(BHP);
-    launch_tsmm<real>(batch, t, st);
-  }
-
   // W = T(R): the learned network for elements that use it, Teter for the rest
   void precondition(cudaStream_t st) {
     if constexpr (std::is_same<real, float>::value) {
@@ -564,7 +589,7 @@ template <class real> struct Wave {
   // accumulator (3m <= 256); returns false when the SIMT kernel must run.
   bool tc_gram(int mode, cudaStream_t st) {
     if constexpr (std::is_same<real, float>::value) {
-      if (ctx->cfg.bulk_kernels == 0 && 3 * batch.s.max_m <= 256) {
+      if (ctx->cfg.bulk_kernels == 1 && 3 * batch.s.max_m <= 256) {
         launch_tc_gram(batch, mode, partial, partial_cap, st);
         return true;
       }
@@ -576,8 +601,11 @@ template <class real> struct Wave {
 
   GramJob<real> gram12() const {
     GramJob<real> g;
-    const int A_[6][4] = {{BX, BHX, 0, 0}, {BX, BHW, 0, 1}, {BX, BHP, 0, 2},
-                          {BW, BHW, 1, 1}, {BW, BHP, 1, 2}, {BP, BHP, 2, 2}};
+    // A(i, j) for block(i) < block(j) is taken as (H s_i)^T s_j, H on the
+    // earlier block: (H x)^T w = theta x^T w + r^T w is small, so its rounding
+    // is small too, while x^T (H w) sums large terms that cancel.
+    const int A_[6][4] = {{BHX, BX, 0, 0}, {BHX, BW, 0, 1}, {BHX, BP, 0, 2},
+                          {BHW, BW, 1, 1}, {BHW, BP, 1, 2}, {BHP, BP, 2, 2}};
     const int B_[6][4] = {{BX, BX, 0, 0}, {BX, BW, 0, 1}, {BX, BP, 0, 2},
                           {BW, BW, 1, 1}, {BW, BP, 1, 2}, {BP, BP, 2, 2}};
     g.npairs = 12;
@@ -587,7 +615,7 @@ template <class real> struct Wave {
         const int k = q + 6 * h2;
         g.a[k] = bref<real>(T[q][0]);
         g.b[k] = bref<real>(T[q][1]);
-        g.needs_p[k] = (T[q][0] == BP || T[q][1] == BP || T[q][1] == BHP);
+        g.needs_p[k] = (T[q][0] == BP || T[q][0] == BHP || T[q][1] == BP || T[q][1] == BHP);
         g.out_id[k] = h2 ? OUT_GRAM_B : OUT_GRAM_A;
         g.brow[k] = T[q][2];
         g.bcol[k] = T[q][3];
@@ -621,9 +649,16 @@ template <class real> struct Wave {
   }
 
   void enqueue_iteration(cudaStream_t st, int maxit) {
+    enqueue_front(st, maxit);
+    enqueue_back(st);
+  }
+
+  // Residual, preconditioner, W and HW, Gram products (operations 1, 2, 5).
+  void enqueue_front(cudaStream_t st, int maxit) {
     if (batch.s.max_nproj > 0) launch_proj_coef<real>(batch, bref<real>(BX), 0, st);
     launch_residual<real>(batch, rnchunk, st);
     launch_post_residual<real>(batch, rnchunk, maxit, st);
+    if (std::is_same<real, float>::value) launch_shift<real>(batch, st);
     precondition(st);
     {
       GramJob<real> g;
@@ -644,8 +679,11 @@ template <class real> struct Wave {
       launch_tsmm<real>(batch, t, st);
     }
     launch_apply_h<real>(batch, bref<real>(BW), bref<real>(BHW), 0, st, fwd64());
-    if (std::is_same<real, float>::value) orthogonalise_p(st);
     if (!tc_gram(0, st)) launch_gram<real>(batch, gram12(), partial, partial_cap, st);
+  }
+
+  // Rayleigh-Ritz and the block updates (operations 3, 4; H X for FP32).
+  void enqueue_back(cudaStream_t st) {
     launch_rr(d_rr_lob, batch.s.nel, st, 3 * batch.s.max_m, batch.s.max_m);
     {
       TsmmJob<real> t;
@@ -715,15 +753,48 @@ template <class real> struct Wave {
     if (s != DGDFT_OK) return s;
     enqueue_initial(st);
     CK(cudaGetLastError());
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    enqueue_iteration(st, maxit);
-    cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    if (ce != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "graph capture: " + cuda_err_string(ce));
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "graph instantiate: " + cuda_err_string(ce));
+    cudaGraphExec_t exec = nullptr, exec2 = nullptr;
+    cudaError_t ce = cudaSuccess;
+    auto capture = [&](cudaStream_t cs, int which, int order, cudaGraphExec_t* out) -> cudaError_t {
+      cudaGraph_t graph = nullptr;
+      if (which >= 0) use(sub[which]);
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return e;
+      if (order == 0) {
+        enqueue_front(cs, maxit);
+        enqueue_back(cs);
+      } else {
+        enqueue_back(cs);
+        enqueue_front(cs, maxit);
+      }
+      e = cudaStreamEndCapture(cs, &graph);
+      use(full);
+      if (e != cudaSuccess) return e;
+      e = cudaGraphInstantiate(out, graph, 0);
+      cudaGraphDestroy(graph);
+      return e;
+    };
+    if (!split) {
+      ce = capture(st, -1, 0, &exec);
+    } else {
+      // the second half starts with its front part, then iterates
+      // back + front: half an iteration behind the first half
+      CK(cudaEventRecord(ev_fork, st));
+      CK(cudaStreamWaitEvent(st2, ev_fork, 0));
+      use(sub[1]);
+      enqueue_front(st2, maxit);
+      use(full);
+      ce = capture(st, 0, 0, &exec);
+      if (ce == cudaSuccess) ce = capture(st2, 1, 1, &exec2);
+    }
+    if (ce != cudaSuccess) {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (split) {
+        cudaEventRecord(ev_join, st2);
+        cudaStreamWaitEvent(st, ev_join, 0);
+      }
+      return ctx->fail(DGDFT_ECUDA, "graph capture: " + cuda_err_string(ce));
+    }
     const int nel = (int)ids.size();
     const int every = std::max(1, ctx->cfg.check_every);
     std::vector<std::vector<double>> hist(nel);
@@ -732,7 +803,7 @@ template <class real> struct Wave {
     dgdft_status rs = DGDFT_OK;
     int since_refresh = 0;
     while (launched <= maxit + 1) {
-      if (refresh_every > 0 && since_refresh >= refresh_every) {
+      if (refresh_every > 0 && !split && since_refresh >= refresh_every) {
         // recompute HX = H X: the updates HX <- [HX HW HP] Y accumulate
         // rounding in the working precision
         launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st, fwd64());
@@ -740,9 +811,14 @@ template <class real> struct Wave {
       }
       for (int k = 0; k < every && launched <= maxit + 1; ++k, ++launched, ++since_refresh) {
         ce = cudaGraphLaunch(exec, st);
+        if (ce == cudaSuccess && split) ce = cudaGraphLaunch(exec2, st2);
         if (ce != cudaSuccess) break;
       }
       if (ce != cudaSuccess) break;
+      if (split) {
+        ce = cudaStreamSynchronize(st2);
+        if (ce != cudaSuccess) break;
+      }
       if ((rs = read_states()) != DGDFT_OK) break;
       if (trace_) {
         // diagnostic trace of element 0 (DGDFT_TRACE set in the environment)
@@ -790,6 +866,12 @@ template <class real> struct Wave {
       if (ce != cudaSuccess || !any) break;
     }
     cudaGraphExecDestroy(exec);
+    if (exec2) cudaGraphExecDestroy(exec2);
+    if (split) {
+      // later work on the caller's stream sees the second half's results
+      cudaEventRecord(ev_join, st2);
+      cudaStreamWaitEvent(st, ev_join, 0);
+    }
     if (ce != cudaSuccess) return ctx->fail(DGDFT_ECUDA, "LOBPCG iteration: " + cuda_err_string(ce));
     if (rs != DGDFT_OK) return rs;
     CK(cudaStreamSynchronize(st));
@@ -1004,7 +1086,11 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
     dgdft_status s;
     if (mixed) {
       wp->w32.reset(new Wave<float>());
-      if ((s = wp->w32->build(ctx, ids, 1e4)) != DGDFT_OK) return s;
+      // Cholesky condition limit of the FP32 stage's pencil: the compensated
+      // SIMT Gram is accurate to ~2e-7 relative and tolerates nearly dependent
+      // [X W P]; the tensor-core Gram (~1e-5) does not
+      const double cond32 = c.bulk_kernels == 1 ? 1e4 : 1e6;
+      if ((s = wp->w32->build(ctx, ids, cond32)) != DGDFT_OK) return s;
     }
     wp->w64.reset(new Wave<double>());
     if ((s = wp->w64->build(ctx, ids, 1e14)) != DGDFT_OK) return s;
@@ -1023,13 +1109,13 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
   if (mixed) {
     Wave<float>& w32 = *wp->w32;
     if ((s = w32.load_inputs()) != DGDFT_OK) return s;
-    // stage 1: FP32 storage and arithmetic, FP64 Rayleigh-Ritz, to a
-    // tolerance above the FP32 residual floor (or until progress stalls)
-    // the FP32 stage aims below tol: its residual floor (~4e-7 Ha from FP32
-    // storage, ~2e-7 from the H apply) leaves room under 1e-6
+    // stage 1: FP32 storage and arithmetic, FP64 Rayleigh-Ritz.  It aims
+    // below tol and ends an element when its residual stops improving: the
+    // FP32 H apply leaves a floor near 2e-6 Ha (FFT rounding amplified by
+    // |G|^2/2), from which FP64 needs a few iterations
     const double tol1 = 0.6 * c.tol;
     std::vector<double> r32;
-    if ((s = w32.run(tol1, c.maxit, 8, &r32, 0)) != DGDFT_OK) return s;
+    if ((s = w32.run(tol1, c.maxit, 5, &r32, 0)) != DGDFT_OK) return s;
     {
       size_t off = 0;
       for (size_t i = 0; i < ids.size(); ++i) {
@@ -1404,7 +1490,7 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
   int* dstate = nullptr;
   const size_t tiles = ((p + 63) / 64) * ((q + 63) / 64);
   bool use_tc = false;
-  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 0 && q <= 256;
+  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 1 && q <= 256;
   const size_t pcap = use_tc ? ((size_t)(ng + 2047) / 2048) * ((p + 127) / 128) * 128 * 256
                              : ((size_t)(ng + 2047) / 2048) * tiles * 4096;
   CK(cudaMalloc(&du, sizeof(real) * (size_t)ng * p));

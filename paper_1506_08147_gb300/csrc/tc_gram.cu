@@ -334,7 +334,9 @@ __global__ void tc_gram_reduce_kernel(const ElemDev<float>* __restrict__ elems, 
       if (r < 3 * m) {
         e.gram[(size_t)9 * m * m + c + (size_t)r * ld] = s;  // B(c, r) = S_c . S_r
       } else {
-        e.gram[c + (size_t)(r - 3 * m) * ld] = s;            // A(c, j) = S_c . (HS)_j
+        // A(j, c) = (HS)_j . S_c: in the upper block triangle H falls on the
+        // earlier block, whose H-image after the shift is the small one
+        e.gram[(r - 3 * m) + (size_t)c * ld] = s;
       }
     } else if (out_mode == 1) {
       e.gxw[c + (size_t)r * m] = s;  // (X^T W)(c, r) = X_c . W_r
