@@ -27,7 +27,7 @@ namespace {
 constexpr int RR_THREADS = 256;
 
 struct RRWork {
-  double *L, *C, *H, *Z, *d, *e, *scal, *lam, *ptmp, *tri;
+  double *L, *C, *H, *Z, *d, *e, *scal, *lam, *ptmp, *tri, *shift;
   int* cstart;
 };
 
@@ -43,7 +43,8 @@ __device__ RRWork carve(double* w, int n, int m) {
   r.lam = r.scal + n;
   r.ptmp = r.lam + m;
   r.tri = r.ptmp + n;                       // 5 n per eigenvector slot
-  r.cstart = reinterpret_cast<int*>(r.tri + (size_t)5 * n * m);
+  r.shift = r.tri + (size_t)5 * n * m;
+  r.cstart = reinterpret_cast<int*>(r.shift + m);
   return r;
 }
 
@@ -148,6 +149,103 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
   h *= 0x297A2D39u;
   h ^= h >> 15;
   return (double)(h & 0xFFFFFF) / (double)0x800000 - 1.0;
+}
+
+// Eigenvectors of the symmetric tridiagonal (d, e) for the m lowest
+// eigenvalue estimates lam[] by inverse iteration, all vectors at once
+// (thread q owns vector q, column q of Z).  Estimates closer than ortol form
+// clusters: their shifts are kept at least 10 eps |T| apart and after every
+// step the cluster's vectors are orthogonalised by modified Gram-Schmidt
+// (inverse iteration alone cannot separate them).  Isolated vectors take
+// the Rayleigh quotient as the shift after the first step (cubic
+// convergence from a rough start).  On return the columns are orthonormal
+// and lam[] holds their Rayleigh quotients.  shift, dots: m doubles; tri:
+// 5 n doubles per vector; cstart: m ints.  Every thread of the block calls.
+__device__ void tri_eigvecs(const double* d, const double* e, int n, int m, double* lam, double* Z, int ldz,
+                            int* cstart, double* shift, double* dots, double* tri, double ortol, double gnorm,
+                            double* red, unsigned seed) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const double eps = DBL_EPSILON;
+  const double sep = 10.0 * eps * fmax(gnorm, 1e-300);
+  __shared__ int any_cluster;
+  if (tid == 0) {
+    any_cluster = 0;
+    for (int i = 0; i < m; ++i) {
+      const bool joins = i > 0 && lam[i] - lam[i - 1] <= ortol;
+      cstart[i] = joins ? cstart[i - 1] : i;
+      shift[i] = joins ? fmax(lam[i], shift[i - 1] + sep) : lam[i];
+      any_cluster |= joins;
+    }
+  }
+  __syncthreads();
+  for (int it = 0; it < 3; ++it) {
+    for (int q = tid; q < m; q += nt) {
+      double* b = Z + (size_t)q * ldz;
+      double* u0 = tri + (size_t)5 * n * q;
+      const bool single = cstart[q] == q && (q + 1 >= m || cstart[q + 1] != q);
+      if (it == 0)
+        for (int i = 0; i < n; ++i) b[i] = hash_unit(i, q + 7919u * seed);
+      double lq = shift[q];
+      if (single && it > 0) {
+        double rq = 0.0;
+        for (int i = 0; i < n; ++i) {
+          double t = d[i] * b[i];
+          if (i > 0) t += e[i - 1] * b[i - 1];
+          if (i + 1 < n) t += e[i] * b[i + 1];
+          rq += b[i] * t;
+        }
+        lq = rq;
+      }
+      tri_solve(d, e, n, lq, b, u0, u0 + n, u0 + 2 * n, u0 + 3 * n, eps * fmax(gnorm, 1e-300));
+      double nb = 0.0;
+      for (int i = 0; i < n; ++i) nb += b[i] * b[i];
+      nb = 1.0 / sqrt(nb);
+      for (int i = 0; i < n; ++i) b[i] *= nb;
+    }
+    __syncthreads();
+    if (!any_cluster) continue;
+    for (int j = 0; j < m; ++j) {
+      const bool clustered = (cstart[j] != j) || (j + 1 < m && cstart[j + 1] == cstart[j]);
+      if (!clustered) continue;  // uniform across the block
+      double* zj = Z + (size_t)j * ldz;
+      double part = 0.0;
+      for (int i = tid; i < n; i += nt) part += zj[i] * zj[i];
+      const double inv = 1.0 / sqrt(block_sum(part, red));
+      for (int i = tid; i < n; i += nt) zj[i] *= inv;
+      __syncthreads();
+      int kend = j + 1;
+      while (kend < m && cstart[kend] == cstart[j]) ++kend;
+      for (int k = j + 1 + warp; k < kend; k += nw) {
+        const double* zk = Z + (size_t)k * ldz;
+        double s2 = 0.0;
+        for (int i = lane; i < n; i += 32) s2 += zj[i] * zk[i];
+        s2 = warp_sum(s2);
+        if (lane == 0) dots[k] = s2;
+      }
+      __syncthreads();
+      const int rest = kend - j - 1;
+      for (int t = tid; t < rest * n; t += nt) {
+        const int k = j + 1 + t / n, i = t - (k - j - 1) * n;
+        Z[i + (size_t)k * ldz] -= dots[k] * zj[i];
+      }
+      __syncthreads();
+    }
+  }
+  // eigenvalues as FP64 Rayleigh quotients z^T T z of the unit vectors
+  for (int j = warp; j < m; j += nw) {
+    const double* zj = Z + (size_t)j * ldz;
+    double s5 = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      double t = d[i] * zj[i];
+      if (i > 0) t += e[i - 1] * zj[i - 1];
+      if (i + 1 < n) t += e[i] * zj[i + 1];
+      s5 += zj[i] * t;
+    }
+    s5 = warp_sum(s5);
+    if (lane == 0) lam[j] = s5;
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict__ tasks) {
@@ -375,77 +473,9 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
       W.lam[i] = 0.5 * (lo + hi);
     }
     __syncthreads();
-    // 6. inverse iteration, one thread per eigenvalue.  Eigenvalues closer
-    // than 1e-7 |T| form a cluster whose vectors one thread computes in
-    // turn, orthogonalising against the cluster (inverse iteration alone
-    // cannot separate them); all other vectors are accurate to ~eps |T| / gap
-    // on their own.  A modified Gram-Schmidt pass over all m vectors follows.
-    const double ortol = 1e-7 * gnorm;
-    if (tid == 0) {
-      for (int i = 0; i < m; ++i)
-        W.cstart[i] = (i == 0 || W.lam[i] - W.lam[i - 1] > ortol) ? i : W.cstart[i - 1];
-    }
-    __syncthreads();
-    const double sep = 10.0 * eps * gnorm;
-    for (int s = tid; s < m; s += nt) {
-      if (W.cstart[s] != s) continue;
-      double lam_prev = -DBL_MAX;
-      for (int q = s; q < m && W.cstart[q] == s; ++q) {
-        double lam = W.lam[q];
-        if (q > s && lam - lam_prev < sep) lam = lam_prev + sep;
-        lam_prev = lam;
-        double* b = W.Z + (size_t)q * n;
-        double* u0 = W.tri + (size_t)5 * n * q;
-        double* u1 = u0 + n;
-        double* u2 = u1 + n;
-        double* mul = u2 + n;
-        for (int i = 0; i < n; ++i) b[i] = hash_unit(i, q + 7919u * blockIdx.x);
-        for (int it = 0; it < 3; ++it) {
-          double nb = 0.0;
-          for (int i = 0; i < n; ++i) nb += b[i] * b[i];
-          nb = 1.0 / sqrt(nb);
-          for (int i = 0; i < n; ++i) b[i] *= nb;
-          tri_solve(W.d, W.e, n, lam, b, u0, u1, u2, mul, eps * fmax(gnorm, 1e-300));
-          for (int p = s; p < q; ++p) {
-            const double* zp = W.Z + (size_t)p * n;
-            double dp = 0.0;
-            for (int i = 0; i < n; ++i) dp += zp[i] * b[i];
-            for (int i = 0; i < n; ++i) b[i] -= dp * zp[i];
-          }
-        }
-        double nb = 0.0;
-        for (int i = 0; i < n; ++i) nb += b[i] * b[i];
-        nb = 1.0 / sqrt(nb);
-        for (int i = 0; i < n; ++i) b[i] *= nb;
-      }
-    }
-    __syncthreads();
-    {
-      // modified Gram-Schmidt over the m vectors (columns of Z, length n)
-      const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-      for (int j = 0; j < m; ++j) {
-        double* zj = W.Z + (size_t)j * n;
-        double part = 0.0;
-        for (int i = tid; i < n; i += nt) part += zj[i] * zj[i];
-        const double inv = 1.0 / sqrt(block_sum(part, red));
-        for (int i = tid; i < n; i += nt) zj[i] *= inv;
-        __syncthreads();
-        for (int k = j + 1 + warp; k < m; k += nw) {
-          const double* zk = W.Z + (size_t)k * n;
-          double s2 = 0.0;
-          for (int i = lane; i < n; i += 32) s2 += zj[i] * zk[i];
-          s2 = warp_sum(s2);
-          if (lane == 0) W.ptmp[k] = s2;
-        }
-        __syncthreads();
-        const int rest = m - j - 1;
-        for (int t = tid; t < rest * n; t += nt) {
-          const int k = j + 1 + t / n, i = t - (k - j - 1) * n;
-          W.Z[i + (size_t)k * n] -= W.ptmp[k] * zj[i];
-        }
-        __syncthreads();
-      }
-    }
+    // 6. eigenvectors of the tridiagonal by inverse iteration
+    tri_eigvecs(W.d, W.e, n, m, W.lam, W.Z, n, W.cstart, W.shift, W.ptmp, W.tri, 1e-7 * gnorm, gnorm, red,
+                blockIdx.x);
     // 7. back-transformation by the reflectors, then Y = D L^-T Z
     for (int k = n - 3; k >= 0; --k) {
       const double* v = W.H + (size_t)k * n;
@@ -734,97 +764,9 @@ __global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __re
       }
     }
     __syncthreads();
-    // 5. inverse iteration (one thread per eigenvalue); shifts closer than the
-    // FP32 location accuracy form clusters orthogonalised in turn
-    const double ortol = 1e-5 * gnorm;
-    if (tid == 0) {
-      for (int i = 0; i < m; ++i)
-        W.cstart[i] = (i == 0 || lam[i] - lam[i - 1] > ortol) ? i : W.cstart[i - 1];
-    }
-    __syncthreads();
-    const double sep = 10.0 * eps * gnorm;
-    for (int s0 = tid; s0 < m; s0 += nt) {
-      if (W.cstart[s0] != s0) continue;
-      const bool single = (s0 + 1 >= m) || (W.cstart[s0 + 1] != s0);
-      double lam_prev = -DBL_MAX;
-      for (int q = s0; q < m && W.cstart[q] == s0; ++q) {
-        double lq = lam[q];
-        if (q > s0 && lq - lam_prev < sep) lq = lam_prev + sep;
-        lam_prev = lq;
-        double* b = Z + (size_t)q * n;
-        double* u0 = W.tri + (size_t)5 * n * q;
-        double* u1 = u0 + n;
-        double* u2 = u1 + n;
-        double* mul = u2 + n;
-        for (int i = 0; i < n; ++i) b[i] = hash_unit(i, q + 7919u * blockIdx.x);
-        for (int it = 0; it < 4; ++it) {
-          double nb = 0.0;
-          for (int i = 0; i < n; ++i) nb += b[i] * b[i];
-          nb = 1.0 / sqrt(nb);
-          for (int i = 0; i < n; ++i) b[i] *= nb;
-          if (single && it > 0) {
-            // Rayleigh-quotient shift from the current unit vector (cubic
-            // convergence from the FP32-located start)
-            double rq = 0.0;
-            for (int i = 0; i < n; ++i) {
-              double t = d[i] * b[i];
-              if (i > 0) t += e[i - 1] * b[i - 1];
-              if (i + 1 < n) t += e[i] * b[i + 1];
-              rq += b[i] * t;
-            }
-            lq = rq;
-          }
-          tri_solve(d, e, n, lq, b, u0, u1, u2, mul, eps * fmax(gnorm, 1e-300));
-          for (int p = s0; p < q; ++p) {
-            const double* zp = Z + (size_t)p * n;
-            double dp = 0.0;
-            for (int i = 0; i < n; ++i) dp += zp[i] * b[i];
-            for (int i = 0; i < n; ++i) b[i] -= dp * zp[i];
-          }
-        }
-        double nb = 0.0;
-        for (int i = 0; i < n; ++i) nb += b[i] * b[i];
-        nb = 1.0 / sqrt(nb);
-        for (int i = 0; i < n; ++i) b[i] *= nb;
-      }
-    }
-    __syncthreads();
-    for (int j = 0; j < m; ++j) {  // modified Gram-Schmidt over the m vectors
-      double* zj = Z + (size_t)j * n;
-      double part = 0.0;
-      for (int i = tid; i < n; i += nt) part += zj[i] * zj[i];
-      const double inv = 1.0 / sqrt(block_sum(part, red));
-      for (int i = tid; i < n; i += nt) zj[i] *= inv;
-      __syncthreads();
-      for (int k = j + 1 + warp; k < m; k += nw) {
-        const double* zk = Z + (size_t)k * n;
-        double s3 = 0.0;
-        for (int i = lane; i < n; i += 32) s3 += zj[i] * zk[i];
-        s3 = warp_sum(s3);
-        if (lane == 0) ptmp[k] = s3;
-      }
-      __syncthreads();
-      const int rest = m - j - 1;
-      for (int t = tid; t < rest * n; t += nt) {
-        const int k = j + 1 + t / n, i = t - (k - j - 1) * n;
-        Z[i + (size_t)k * n] -= ptmp[k] * zj[i];
-      }
-      __syncthreads();
-    }
-    // eigenvalues as FP64 Rayleigh quotients z^T T z of the unit vectors
-    for (int j = warp; j < m; j += nw) {
-      const double* zj = Z + (size_t)j * n;
-      double s5 = 0.0;
-      for (int i = lane; i < n; i += 32) {
-        double t = d[i] * zj[i];
-        if (i > 0) t += e[i - 1] * zj[i - 1];
-        if (i + 1 < n) t += e[i] * zj[i + 1];
-        s5 += zj[i] * t;
-      }
-      s5 = warp_sum(s5);
-      if (lane == 0) lam[j] = s5;
-    }
-    __syncthreads();
+    // 5. eigenvectors by inverse iteration; shifts closer than the FP32
+    // location accuracy form clusters, orthogonalised within the cluster
+    tri_eigvecs(d, e, n, m, lam, Z, n, W.cstart, lo_s, hi_s, W.tri, 1e-5 * gnorm, gnorm, red, blockIdx.x);
     // 6. back-transformation, then Y = D L^-T Z (right-looking)
     for (int k = n - 3; k >= 0; --k) {
       const double* v = S + (size_t)k * n;
@@ -869,7 +811,7 @@ __global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __re
 
 size_t rr_work_doubles(int n_max, int m) {
   return (size_t)3 * n_max * n_max + (size_t)n_max * m + 4 * (size_t)n_max + m + (size_t)5 * n_max * m +
-         (size_t)m + 16;
+         (size_t)2 * m + 16;
 }
 
 size_t rr_smem_bytes(int n, int m) {
