@@ -106,6 +106,120 @@ __global__ void __launch_bounds__(256) gram_kernel(const ElemDev<real>* __restri
       out[(ty * 4 + i) * TILE + tx * 4 + j] = (double)acc[i][j] + (double)chi[i][j] + (double)clo[i][j];
 }
 
+// FP32 Gram products for blocks of at most 48 columns (the LOBPCG pencil at
+// m <= 48): one 48 x 48 output tile per CTA of 144 threads (4 x 4 outputs
+// each), the pairs of one row chunk adjacent in the grid so the blocks they
+// share come from L2.  Operands are staged column-major (rows contiguous)
+// by double-buffered cp.async; each thread reads 4 rows of a column as one
+// float4, with the 16-byte chunks of a column XOR-swizzled by column group
+// so the twelve column groups of a warp hit distinct banks.  Accumulation
+// as in gram_kernel: FP32 per 32-row stage, folded into a two-sum
+// compensated pair.  Partials use gram_kernel's 64 x 64 layout.
+// grid: (npairs, nchunk, nel); block 144.
+constexpr int G48 = 48;
+constexpr int GK = 32;  // rows per stage
+
+__device__ __forceinline__ int g48_off(int c, int r) {
+  return c * GK + ((((r >> 2) ^ ((c >> 2) & 7)) << 2) | (r & 3));
+}
+
+__global__ void __launch_bounds__(144) gram48_kernel(const ElemDev<float>* __restrict__ elems,
+                                                      GramJob<float> job, double* __restrict__ partial,
+                                                      size_t pstride, int kchunk) {
+  __shared__ __align__(16) float As[2][G48 * GK];
+  __shared__ __align__(16) float Bs[2][G48 * GK];
+  const ElemDev<float>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int pair = blockIdx.x;
+  if (job.needs_p[pair] && !e.state[ST_HAS_P]) return;
+  const int ca = job.ncols_a > 0 ? job.ncols_a : e.m;
+  const int cb = job.ncols_b > 0 ? job.ncols_b : e.m;
+  const int rows = job.rows > 0 ? job.rows : e.ng;
+  const float* A = resolve(e, job.a[pair]);
+  const float* B = resolve(e, job.b[pair]);
+  const int lda = ld_of(e, job.a[pair], job.ld_in, rows);
+  const int ldb = ld_of(e, job.b[pair], job.ld_in, rows);
+  const int tx = threadIdx.x % 12, ty = threadIdx.x / 12;
+  const int k_beg = blockIdx.y * kchunk;
+  const int k_end = min(rows, k_beg + kchunk);
+  // 16-byte copies need 16-byte aligned column starts
+  const bool vec = ((lda | ldb | k_beg) & 3) == 0 && ((((uintptr_t)A) | ((uintptr_t)B)) & 15) == 0;
+  auto load_stage = [&](int buf, int k0) {
+    for (int t = threadIdx.x; t < 2 * G48 * (GK / 4); t += blockDim.x) {
+      const int op = t / (G48 * (GK / 4));
+      const int rem = t - op * (G48 * (GK / 4));
+      const int c = rem / (GK / 4), q = rem - c * (GK / 4);
+      const float* src = op ? B : A;
+      const int ld = op ? ldb : lda;
+      const int cc = op ? cb : ca;
+      float* dst = (op ? Bs[buf] : As[buf]) + g48_off(c, 4 * q);
+      const int k = k0 + 4 * q;
+      const int nv = (c < cc) ? max(0, min(4, k_end - k)) : 0;
+      const float* g = nv ? src + (size_t)c * ld + k : src;
+      if (vec) {
+        cp_async16(dst, g, 4 * nv);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cp_async4(dst + u, u < nv ? g + u : src, u < nv ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  float acc[4][4], chi[4][4], clo[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = chi[i][j] = clo[i][j] = 0.f;
+  const int nst = (k_end > k_beg) ? (k_end - k_beg + GK - 1) / GK : 0;
+  if (nst > 0) load_stage(0, k_beg);
+  for (int st = 0; st < nst; ++st) {
+    if (st + 1 < nst) {
+      load_stage((st + 1) & 1, k_beg + (st + 1) * GK);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* as = As[st & 1];
+    const float* bs = Bs[st & 1];
+#pragma unroll 2
+    for (int r = 0; r < GK; r += 4) {
+      float4 a4[4], b4[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a4[i] = *reinterpret_cast<const float4*>(as + g48_off(ty * 4 + i, r));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b4[j] = *reinterpret_cast<const float4*>(bs + g48_off(tx * 4 + j, r));
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float t = acc[i][j];
+          t = fmaf(a4[i].x, b4[j].x, t);
+          t = fmaf(a4[i].y, b4[j].y, t);
+          t = fmaf(a4[i].z, b4[j].z, t);
+          t = fmaf(a4[i].w, b4[j].w, t);
+          acc[i][j] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float sum = chi[i][j] + acc[i][j];
+        const float bp = sum - chi[i][j];
+        clo[i][j] += (chi[i][j] - (sum - bp)) + (acc[i][j] - bp);
+        chi[i][j] = sum;
+        acc[i][j] = 0.f;
+      }
+  }
+  double* out = partial + blockIdx.z * pstride + ((size_t)blockIdx.y * gridDim.x + pair) * (TILE * TILE);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * TILE + tx * 4 + j] = (double)chi[i][j] + (double)clo[i][j];
+}
+
 template <class real>
 __global__ void gram_reduce_kernel(const ElemDev<real>* __restrict__ elems, GramJob<real> job,
                                    const double* __restrict__ partial, size_t pstride, int nchunk,
@@ -213,6 +327,171 @@ __global__ void __launch_bounds__(256) tsmm_kernel(const ElemDev<real>* __restri
       *o = v;
     }
   }
+}
+
+// FP32 block update out = alpha sum_i in_i Y_i + beta out (and optionally
+// out2 = the partial sum over inputs i >= from2) for up to 48 output
+// columns per CTA tile: 128 rows x 48 columns per CTA of 128 threads, each
+// thread 4 rows x 12 columns.  Y (all inputs' rows x 48 columns) is
+// converted to FP32 into shared memory once per CTA; the input rows stream
+// through a double-buffered cp.async stage of TK k-values x 128 rows.
+// grid: (row-tile groups, column tiles, nel); block 128.
+constexpr int TS_THREADS = 128;
+constexpr int TS_CT = 48;
+constexpr int TS_TR = 128;
+constexpr int TS_TK = 16;
+
+__global__ void __launch_bounds__(TS_THREADS, 4) tsmm_rows_kernel(const ElemDev<float>* __restrict__ elems,
+                                                               TsmmJob<float> job) {
+  extern __shared__ __align__(16) float tsm[];
+  const ElemDev<float>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int nc = job.ncols > 0 ? job.ncols : e.m;
+  const int rows = job.rows > 0 ? job.rows : e.ng;
+  const int c0 = blockIdx.y * TS_CT;
+  if (c0 >= nc) return;
+  const double* Y;
+  int ldy;
+  switch (job.y_id) {
+    case Y_RR: Y = e.Y; ldy = job.ldy > 0 ? job.ldy : 3 * e.m; break;
+    case Y_GXW: Y = e.gxw; ldy = job.ldy > 0 ? job.ldy : e.m; break;
+    default: Y = job.y_ptr; ldy = job.ldy; break;
+  }
+  const float* Yf = (job.y_id == Y_RR) ? e.Yf : nullptr;  // FP32 copy written by Rayleigh-Ritz
+  const bool has_p = e.state[ST_HAS_P] != 0;
+  const int ycol0 = job.ycol * nc + c0;
+  const int ktot = job.nin * nc;
+  float* ys = tsm;                                   // ktot x TS_CT
+  float* ss = tsm + (size_t)ktot * TS_CT;            // 2 x TS_TK x TS_TR
+  for (int t = threadIdx.x; t < ktot * TS_CT; t += blockDim.x) {
+    const int c = t / ktot, kk = t - c * ktot;
+    const int in = kk / nc, k = kk - in * nc;
+    float v = 0.f;
+    if (c0 + c < nc) {
+      const size_t yi = (job.yrow[in] * nc + k) + (size_t)(ycol0 + c) * ldy;
+      v = Yf ? Yf[yi] : (float)Y[yi];
+    }
+    ys[kk * TS_CT + c] = v;
+  }
+  // inputs in the order they are summed (last first), P skipped without P
+  int act[3], nact = 0;
+  for (int in = job.nin - 1; in >= 0; --in)
+    if (!(job.needs_p[in] && !has_p)) act[nact++] = in;
+  // out2 is complete after the last active input with index >= from2
+  int q2 = -1;
+  for (int q = 0; q < nact; ++q)
+    if (job.from2 >= 0 && act[q] >= job.from2) q2 = q;
+  const int cpi = (nc + TS_TK - 1) / TS_TK;  // stages per input
+  const int nstage = nact * cpi;
+  const int tr = threadIdx.x >> 2, tc = threadIdx.x & 3;
+  const int ncol = min(TS_CT, nc - c0);
+  const float alpha = (float)job.alpha, beta = (float)job.beta;
+  float* O = resolve(e, job.out);
+  const int ldo = ld_of(e, job.out, job.ld_in, rows);
+  float* O2 = job.from2 >= 0 ? resolve(e, job.out2) : nullptr;
+  const int ld2 = job.from2 >= 0 ? ld_of(e, job.out2, job.ld_in, rows) : 0;
+  bool vec = true;
+  for (int q = 0; q < nact; ++q) {
+    const float* S = resolve(e, job.in[act[q]]);
+    vec = vec && (ld_of(e, job.in[act[q]], job.ld_in, rows) & 3) == 0 && (((uintptr_t)S) & 15) == 0;
+  }
+  __syncthreads();
+  for (int rt = blockIdx.x; rt * TS_TR < rows; rt += gridDim.x) {
+    const int row0 = rt * TS_TR;
+    auto load_stage = [&](int buf, int stg) {
+      const int in = act[stg / cpi], k0 = (stg % cpi) * TS_TK;
+      const float* S = resolve(e, job.in[in]);
+      const int lds = ld_of(e, job.in[in], job.ld_in, rows);
+      float* dst0 = ss + (size_t)buf * TS_TK * TS_TR;
+      for (int t = threadIdx.x; t < TS_TK * (TS_TR / 4); t += blockDim.x) {
+        const int kk = t / (TS_TR / 4), q = t - kk * (TS_TR / 4);
+        const int k = k0 + kk, r = row0 + 4 * q;
+        const int nv = (k < nc) ? max(0, min(4, rows - r)) : 0;
+        const float* g = nv ? S + (size_t)k * lds + r : S;
+        float* dst = dst0 + kk * TS_TR + 4 * q;
+        if (vec) {
+          cp_async16(dst, g, 4 * nv);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cp_async4(dst + u, u < nv ? g + u : S, u < nv ? 4 : 0);
+        }
+      }
+      cp_async_commit();
+    };
+    float acc[4][12];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[i][j] = 0.f;
+    if (nstage > 0) load_stage(0, 0);
+    for (int stg = 0; stg < nstage; ++stg) {
+      if (stg + 1 < nstage) {
+        load_stage((stg + 1) & 1, stg + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const int in = act[stg / cpi], k0 = (stg % cpi) * TS_TK;
+      const float* sb = ss + (size_t)(stg & 1) * TS_TK * TS_TR + 4 * tr;
+      const float* yb = ys + ((size_t)in * nc + k0) * TS_CT + 12 * tc;
+      const int kn = min(TS_TK, nc - k0);
+#pragma unroll 4
+      for (int kk = 0; kk < kn; ++kk) {
+        const float4 s4 = *reinterpret_cast<const float4*>(sb + kk * TS_TR);
+        const float4* y4 = reinterpret_cast<const float4*>(yb + (size_t)kk * TS_CT);
+        const float4 ya = y4[0], yb4 = y4[1], yc = y4[2];
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        const float yv[12] = {ya.x, ya.y, ya.z, ya.w, yb4.x, yb4.y, yb4.z, yb4.w, yc.x, yc.y, yc.z, yc.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 12; ++j) acc[i][j] = fmaf(sv[i], yv[j], acc[i][j]);
+      }
+      __syncthreads();
+      if (O2 && (stg % cpi) == cpi - 1 && stg / cpi == q2) {
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+          const int c = 12 * tc + j;
+          if (c >= ncol) continue;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = row0 + 4 * tr + i;
+            if (r < rows) O2[(size_t)(c0 + c) * ld2 + r] = acc[i][j];
+          }
+        }
+      }
+    }
+    if (O2 && q2 < 0) {
+      // every input at or after from2 was skipped: out2 = 0
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        const int c = 12 * tc + j;
+        if (c >= ncol) continue;
+        for (int i = 0; i < 4; ++i) {
+          const int r = row0 + 4 * tr + i;
+          if (r < rows) O2[(size_t)(c0 + c) * ld2 + r] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const int c = 12 * tc + j;
+      if (c >= ncol) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = row0 + 4 * tr + i;
+        if (r < rows) {
+          float* o = O + (size_t)(c0 + c) * ldo + r;
+          *o = (beta == 0.f) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *o;
+        }
+      }
+    }
+  }
+}
+
+size_t tsmm_rows_smem(int nin, int nc) {
+  return sizeof(float) * ((size_t)nin * nc * TS_CT + 2 * (size_t)TS_TK * TS_TR);
 }
 
 // R = HX - X diag(theta) into W; partial sums (r.r, x.x, x.Hx, x.V x).
@@ -388,8 +667,14 @@ void launch_gram(const Batch<real>& b, const GramJob<real>& job, double* partial
     nchunk = (rows + kchunk - 1) / kchunk;
   }
   const size_t pstride = (size_t)nchunk * ny * TILE * TILE;
-  gram_kernel<real><<<dim3(nchunk, ny, s.nel), 256, 0, st>>>(b.d_elems, job, partial, pstride, kchunk,
-                                                             tiles_a, tiles_b);
+  if (std::is_same<real, float>::value && ca <= G48 && cb <= G48) {
+    gram48_kernel<<<dim3(ny, nchunk, s.nel), 144, 0, st>>>(
+        reinterpret_cast<const ElemDev<float>*>(b.d_elems), *reinterpret_cast<const GramJob<float>*>(&job), partial,
+        pstride, kchunk);
+  } else {
+    gram_kernel<real><<<dim3(nchunk, ny, s.nel), 256, 0, st>>>(b.d_elems, job, partial, pstride, kchunk,
+                                                               tiles_a, tiles_b);
+  }
   gram_reduce_kernel<real><<<dim3(ny, 1, s.nel), 256, 0, st>>>(b.d_elems, job, partial, pstride, nchunk,
                                                                tiles_a, tiles_b);
 }
@@ -398,6 +683,17 @@ template <class real>
 void launch_tsmm(const Batch<real>& b, const TsmmJob<real>& job, cudaStream_t st) {
   const BatchShape& s = b.s;
   const int nc = job.ncols > 0 ? job.ncols : s.max_m;
+  if constexpr (std::is_same<real, float>::value) {
+    const size_t smem = tsmm_rows_smem(job.nin, nc);
+    if (smem <= 160 * 1024) {
+      const int rows = job.rows > 0 ? job.rows : s.max_ng;
+      // two 128-row tiles per CTA: the Y staging is amortised, the grid
+      // stays many times the SM count
+      const int gx = std::max(1, (rows + 2 * TS_TR - 1) / (2 * TS_TR));
+      tsmm_rows_kernel<<<dim3(gx, (nc + TS_CT - 1) / TS_CT, s.nel), TS_THREADS, smem, st>>>(b.d_elems, job);
+      return;
+    }
+  }
   const int rows = job.rows > 0 ? job.rows : s.max_ng;
   tsmm_kernel<real><<<dim3((rows + TILE - 1) / TILE, (nc + TILE - 1) / TILE, s.nel), 256, 0, st>>>(
       b.d_elems, job);
@@ -428,6 +724,8 @@ template <class real>
 void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st) {
   iter_finish_kernel<real><<<(b.s.nel + 127) / 128, 128, 0, st>>>(b.d_elems, b.s.nel, set_p);
 }
+
+void init_blas_kernels() { opt_in_dynamic_smem((const void*)tsmm_rows_kernel); }
 
 #define DGDFT_INST(real)                                                                             \
   template void launch_gram<real>(const Batch<real>&, const GramJob<real>&, double*, size_t,         \

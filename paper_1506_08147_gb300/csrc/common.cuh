@@ -76,6 +76,9 @@ template <class real> struct ElemDev {
   const double* gx2;        // (2 pi kx / Lx)^2 / 2, kx = 0..nh
   const double* gy2;        // (2 pi f_y / Ly)^2 / 2 over y index (|f| <= ny/2)
   const double* gz2;
+  const float* gx2f;        // the same symbols in FP32 (FP32 stage arithmetic)
+  const float* gy2f;
+  const float* gz2f;
   const real* V;            // V_eff^{Q_K}, N_g
   // Kleinman-Bylander projectors, CSR by projector
   int n_proj;
@@ -98,6 +101,7 @@ template <class real> struct ElemDev {
   double* gram;             // 2 x (3m)^2: A then B (ld 3m)
   double* gxw;              // m x m: X^T W
   double* Y;                // 3m x m Rayleigh-Ritz coefficients
+  float* Yf;                // the same in FP32 (FP32 waves: read by the block updates)
   double* theta;            // m
   double* res;              // m
   double* tkin;             // m
@@ -109,6 +113,24 @@ template <class real> struct ElemDev {
   double* rpart;            // residual partial sums
   int* state;               // STATE_WORDS
 };
+
+// Asynchronous global -> shared copies (cp.async).  src_bytes < size fills
+// the rest of the destination with zeros (src must still be a valid address).
+__device__ __forceinline__ uint32_t shared_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(shared_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(shared_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

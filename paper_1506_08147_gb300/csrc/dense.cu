@@ -332,11 +332,23 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
       __syncthreads();
     }
     bool fail = sflag != 0;
-    if (!fail && (pmax / pmin) * (pmax / pmin) > T.cond_max) fail = true;
+    // the last LOBPCG resort (X alone) takes any positive-definite B: its
+    // Rayleigh-Ritz re-orthonormalises a block that has drifted
+    const bool last_resort = T.mode == RR_LOBPCG && n == m;
+    if (!fail && !last_resort && (pmax / pmin) * (pmax / pmin) > T.cond_max) fail = true;
     __syncthreads();
     if (fail) {
       if (T.mode == RR_LOBPCG && n == 3 * m) {
         n = 2 * m;
+        dropped = true;
+        __syncthreads();
+        continue;
+      }
+      if (T.mode == RR_LOBPCG && n == 2 * m) {
+        // [X W] is numerically dependent too (W nearly inside span X or
+        // its columns nearly parallel): Rayleigh-Ritz on X alone, a
+        // rotation of the current block; the next iteration brings a new W
+        n = m;
         dropped = true;
         __syncthreads();
         continue;
@@ -506,7 +518,9 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
     __syncthreads();
     for (int idx = tid; idx < n_out * m; idx += nt) {
       const int r = idx % n_out, c = idx / n_out;
-      T.Y[r + (size_t)c * T.ldy] = (r < n) ? W.Z[r + (size_t)c * n] * W.scal[r] : 0.0;
+      const double y = (r < n) ? W.Z[r + (size_t)c * n] * W.scal[r] : 0.0;
+      T.Y[r + (size_t)c * T.ldy] = y;
+      if (T.Yf) T.Yf[r + (size_t)c * T.ldy] = (float)y;
     }
     for (int c = tid; c < m; c += nt) T.theta[c] = W.lam[c];
     if (tid == 0 && dropped && T.state) T.state[ST_FALLBACK] += 1;
@@ -605,11 +619,23 @@ __global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __re
       __syncthreads();
     }
     bool fail = sflag != 0;
-    if (!fail && (pmax / pmin) * (pmax / pmin) > T.cond_max) fail = true;
+    // the last LOBPCG resort (X alone) takes any positive-definite B: its
+    // Rayleigh-Ritz re-orthonormalises a block that has drifted
+    const bool last_resort = T.mode == RR_LOBPCG && n == m;
+    if (!fail && !last_resort && (pmax / pmin) * (pmax / pmin) > T.cond_max) fail = true;
     __syncthreads();
     if (fail) {
       if (T.mode == RR_LOBPCG && n == 3 * m) {
         n = 2 * m;
+        dropped = true;
+        __syncthreads();
+        continue;
+      }
+      if (T.mode == RR_LOBPCG && n == 2 * m) {
+        // [X W] is numerically dependent too (W nearly inside span X or
+        // its columns nearly parallel): Rayleigh-Ritz on X alone, a
+        // rotation of the current block; the next iteration brings a new W
+        n = m;
         dropped = true;
         __syncthreads();
         continue;
@@ -798,7 +824,9 @@ __global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __re
     }
     for (int idx = tid; idx < n_out * m; idx += nt) {
       const int r = idx % n_out, c = idx / n_out;
-      T.Y[r + (size_t)c * T.ldy] = (r < n) ? Z[r + (size_t)c * n] * scal[r] : 0.0;
+      const double y = (r < n) ? Z[r + (size_t)c * n] * scal[r] : 0.0;
+      T.Y[r + (size_t)c * T.ldy] = y;
+      if (T.Yf) T.Yf[r + (size_t)c * T.ldy] = (float)y;
     }
     for (int c = tid; c < m; c += nt) T.theta[c] = lam[c];
     if (tid == 0 && dropped && T.state) T.state[ST_FALLBACK] += 1;

@@ -136,15 +136,34 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
     double tk = 1.0;
     if (MODE == ZM_TETER) tk = tkin_override ? tkin_override[j] : e.tkin[j];
     const double inv_tk = 1.0 / fmax(tk, 1e-8);
-    for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
-      const int gz = t / ZTILE, cc = t - gz * ZTILE;
-      const int c = c0 + cc;
-      if (c >= nplane) continue;
-      const int y = c / e.nxh, kx = c - y * e.nxh;
-      const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
-      double f = (MODE == ZM_KINETIC) ? g : teter_factor(g * inv_tk);
-      f *= e.scale;
-      s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (TZ)f);
+    if constexpr (sizeof(TZ) == sizeof(float)) {
+      // FP32 symbols and Teter factor: no FP64 arithmetic per point
+      const float inv_tkf = (float)inv_tk, scalef = (float)e.scale;
+      for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
+        const int gz = t / ZTILE, cc = t - gz * ZTILE;
+        const int c = c0 + cc;
+        if (c >= nplane) continue;
+        const int y = c / e.nxh, kx = c - y * e.nxh;
+        const float g = e.gx2f[kx] + e.gy2f[y] + e.gz2f[gz];
+        float f = g;
+        if (MODE == ZM_TETER) {
+          const float sv = g * inv_tkf;
+          const float num = 27.0f + sv * (18.0f + sv * (12.0f + sv * 8.0f));
+          f = num / (num + 16.0f * sv * sv * sv * sv);
+        }
+        s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (TZ)(f * scalef));
+      }
+    } else {
+      for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
+        const int gz = t / ZTILE, cc = t - gz * ZTILE;
+        const int c = c0 + cc;
+        if (c >= nplane) continue;
+        const int y = c / e.nxh, kx = c - y * e.nxh;
+        const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
+        double f = (MODE == ZM_KINETIC) ? g : teter_factor(g * inv_tk);
+        f *= e.scale;
+        s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (TZ)f);
+      }
     }
     __syncthreads();
   }

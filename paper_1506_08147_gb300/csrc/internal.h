@@ -93,9 +93,14 @@ template <class real> struct TsmmJob {
   int ld_in = 0;             // explicit pointer leading dim (<= 0: rows)
   BRef<real> out;
   double alpha = 1.0, beta = 0.0;
+  // optional second output: out2 = sum over inputs i >= from2 of in_i Y_i
+  // (alpha 1, beta 0), written on the way to out; from2 < 0: none
+  int from2 = -1;
+  BRef<real> out2;
 };
 template <class real>
 void launch_tsmm(const Batch<real>& b, const TsmmJob<real>& job, cudaStream_t st);
+void init_blas_kernels();
 
 // Residual R = HX - X diag(theta) into W, with per-column partial sums.
 template <class real>
@@ -125,6 +130,7 @@ struct RRTask {
   int n_fixed;
   int m;             // eigenpairs wanted (lowest)
   double* Y;         // n x m output (ldy); LOBPCG rows of a dropped P are zeroed
+  float* Yf;         // optional FP32 copy of Y (same layout), or nullptr
   int ldy;
   double* theta;     // m
   double* work;      // rr_work_doubles(n_max, m) doubles

@@ -180,6 +180,7 @@ size_t elem_bytes(const ElemHost& h) {
   s.add(ng * sizeof(real));                               // V
   s.add((sizeof(cplx_t<real>) + sizeof(double2)) * (d.nx / 2 + d.nx + d.ny + d.nz + 4));
   s.add(sizeof(double) * (nxh + d.ny + d.nz));
+  s.add(sizeof(float) * (nxh + d.ny + d.nz + 3 * m * m) + 4 * ALIGN);
   s.add(sizeof(int) * (np + 1) + sizeof(int) * nnz + sizeof(real) * nnz + sizeof(double) * np);
   s.add(sizeof(int) * (d.nz + 1) + sizeof(int) * (3 * nnz + 1) + sizeof(real) * nnz);
   s.add(sizeof(real) * np * m);
@@ -345,6 +346,7 @@ template <class real> struct Wave {
       t.n_fixed = E.m;
       t.m = E.m;
       t.Y = E.Y;
+      t.Yf = E.Yf;
       t.ldy = 3 * E.m;
       t.theta = E.theta;
       t.work = E.rr_work;
@@ -424,6 +426,16 @@ template <class real> struct Wave {
     E.gy2 = put_g(kinetic_axis(d.ny, d.Ly, false));
     E.gz2 = put_g(kinetic_axis(d.nz, d.Lz, false));
     if (!E.gx2 || !E.gy2 || !E.gz2) return DGDFT_ECUDA;
+    auto put_gf = [&](const std::vector<double>& g) -> const float* {
+      std::vector<float> gf(g.begin(), g.end());
+      float* dp = take<float>(gf.size());
+      if (put(dp, gf.data(), gf.size()) != DGDFT_OK) return nullptr;
+      return dp;
+    };
+    E.gx2f = put_gf(kinetic_axis(d.nx, d.Lx, true));
+    E.gy2f = put_gf(kinetic_axis(d.ny, d.Ly, false));
+    E.gz2f = put_gf(kinetic_axis(d.nz, d.Lz, false));
+    if (!E.gx2f || !E.gy2f || !E.gz2f) return DGDFT_ECUDA;
     // projectors, CSR by projector
     const int np = (int)eh.pgamma.size();
     const size_t nnz = eh.pidx.size();
@@ -489,6 +501,7 @@ template <class real> struct Wave {
     E.gram = take<double>(18 * m * m);
     E.gxw = take<double>(m * m);
     E.Y = take<double>(3 * m * m);
+    E.Yf = std::is_same<real, float>::value ? take<float>(3 * m * m) : nullptr;
     E.theta = take<double>(m);
     E.res = take<double>(m);
     E.tkin = take<double>(m);
@@ -696,7 +709,14 @@ template <class real> struct Wave {
       t.yrow[2] = 2;
       t.needs_p[2] = 1;
       t.out = bref<real>(BX, 1);
+      constexpr bool f32 = std::is_same<real, float>::value;
+      if (f32) {
+        // P' = [W P] Y_wp is the partial sum on the way to X' = X Y_x + P'
+        t.from2 = 1;
+        t.out2 = bref<real>(BP, 1);
+      }
       launch_tsmm<real>(batch, t, st);
+      t.from2 = -1;
       if (std::is_same<real, double>::value) {
         t.in[0] = bref<real>(BHX);
         t.in[1] = bref<real>(BHW);
@@ -718,7 +738,7 @@ template <class real> struct Wave {
       u.yrow[1] = 2;
       u.needs_p[1] = 1;
       u.out = bref<real>(BP, 1);
-      launch_tsmm<real>(batch, u, st);
+      if (!f32) launch_tsmm<real>(batch, u, st);
       u.in[0] = bref<real>(BHW);
       u.in[1] = bref<real>(BHP);
       u.out = bref<real>(BHP, 1);
@@ -840,12 +860,14 @@ template <class real> struct Wave {
           hist[i].push_back(mx);
           const size_t L = hist[i].size();
           // stalled: the best residual of the last `stall_window` polls is not
-          // 5% below the best one before them (the FP32 floor has been reached)
+          // 5% below the best one before them (the FP32 floor has been
+          // reached).  Only near the floor: early plateaus (a random start
+          // still sorting its subspace) are not stalls.
           bool stalled = false;
           if (L > (size_t)stall_window) {
             const double before = *std::min_element(hist[i].begin(), hist[i].end() - stall_window);
             const double recent = *std::min_element(hist[i].end() - stall_window, hist[i].end());
-            stalled = recent > 0.95 * before;
+            stalled = recent > 0.95 * before && recent < std::max(100.0 * tol, 1e-5);
           }
           if (stalled && learned && !sw[ST_TETER]) {
             // the learned preconditioner stalled: fall back to Teter
@@ -1134,10 +1156,31 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
       fb32.push_back(w32.h_state[i * STATE_WORDS + ST_FALLBACK]);
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    if (std::getenv("DGDFT_TRACE")) {
+      for (size_t i = 0; i < ids.size(); ++i) {
+        const int* sw = &w32.h_state[i * STATE_WORDS];
+        if (sw[ST_ERROR] || sw[ST_ITER] < 50)
+          std::fprintf(stderr, "[dgdft] fp32 element %zu: iter %d err %d fallback %d converged %d\n", i, sw[ST_ITER],
+                       sw[ST_ERROR], sw[ST_FALLBACK], sw[ST_CONVERGED]);
+      }
+    }
+    auto t1 = std::chrono::steady_clock::now();
     if ((s = w64.verify(c.tol)) != DGDFT_OK) return s;
     bool all = true;
-    for (size_t i = 0; i < ids.size(); ++i) all = all && w64.h_state[i * STATE_WORDS + ST_CONVERGED];
+    int nconv = 0;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      all = all && w64.h_state[i * STATE_WORDS + ST_CONVERGED];
+      nconv += w64.h_state[i * STATE_WORDS + ST_CONVERGED] != 0;
+    }
+    auto t2 = std::chrono::steady_clock::now();
     if (!all && (s = w64.run(c.tol, c.maxit, 0, nullptr, 0, true)) != DGDFT_OK) return s;
+    if (std::getenv("DGDFT_TRACE")) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      auto t3 = std::chrono::steady_clock::now();
+      std::fprintf(stderr, "[dgdft] fp32 stage %.3f s, verify %.3f s (%d/%zu pass), fp64 stage %.3f s\n",
+                   std::chrono::duration<double>(t1 - t0).count(), std::chrono::duration<double>(t2 - t1).count(),
+                   nconv, ids.size(), std::chrono::duration<double>(t3 - t2).count());
+    }
   } else {
     if ((s = w64.load_inputs()) != DGDFT_OK) return s;
     if ((s = w64.run(c.tol, c.maxit, 0, nullptr)) != DGDFT_OK) return s;
@@ -1212,6 +1255,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   init_hamiltonian_kernels();
   init_tc_gram_kernel();
   init_rr_kernels();
+  init_blas_kernels();
   cudaGetLastError();  // attribute queries above must not leave an error behind
   ctx->el.resize(n_elem);
   for (int i = 0; i < n_elem; ++i) ctx->el[i].d = elems[i];
