@@ -130,10 +130,21 @@ def stage_bytes(name, e, s):
     return 0
 
 
-# launches of each stage per LOBPCG iteration (H apply and Teter both run
-# the three FFT passes; the Gram stage also runs X^T W; 5 block updates)
-STAGE_PER_ITER = {"xy_fwd": 2, "z_mult": 2, "xy_inv": 2, "gram": 1, "update": 5, "rayleigh_ritz": 1,
+# launches of each stage per FP32 LOBPCG iteration: the three FFT passes run
+# for H W, for H X' and for the Teter preconditioner; one 12-pair Gram
+# (X^T W is a small extra Gram); three block updates (X' with P', HP', the
+# projection of W); one Rayleigh-Ritz; one residual pass
+STAGE_PER_ITER = {"xy_fwd": 3, "z_mult": 3, "xy_inv": 3, "gram": 1, "update": 3, "rayleigh_ritz": 1,
                   "residual": 1}
+
+# FP32 peak of the SIMT pipe: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x
+# 2.07 GHz (the maximum SM clock)
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes (read + write) of one element's share of the 12-pair FP32 Gram
+# launch, from the ncu capture summarised in profiles/gram48_config2.md
+# (None when the kernel changed after the capture)
+GRAM_TRAFFIC_PER_ELEMENT = None
 
 
 def run_ours(args):
@@ -207,7 +218,16 @@ def run_ours(args):
     share = {n: stages[n][0] * STAGE_PER_ITER[n] for n in stages}
     dom = max(share, key=share.get)
     dom_ms, nel, sbytes = stages[dom]
-    if dom == "rayleigh_ritz":
+    if dom == "gram":
+        # the FP32 Gram is bound by the FP32 FMA pipe (SIMT, compensated)
+        flops = sum(12 * 2.0 * e.m * e.m * e.ng for e in els)
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_SIMT_TFLOPS,
+                "traffic": (GRAM_TRAFFIC_PER_ELEMENT * len(els)) if GRAM_TRAFFIC_PER_ELEMENT else None,
+                "kernel": "gram48 (12 Gram blocks of S^T S and (H S)^T S, FP32 stage)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+    elif dom == "rayleigh_ritz":
         # FP64 ALU bound: lowest m of a 3m pencil, ~ (3m)^3 (1/3 + 1 + 2/3 + ...) flops
         n3 = (3 * els[0].m) ** 3
         flops = nel * 2.5 * 2 * n3
@@ -308,7 +328,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(local),
     }
-    line["gpu_launches"] = estimate_launches(els, iters, args.steps)
+    line["gpu_launches"] = count_launches(els, reps, iters, args.steps)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -316,13 +336,20 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def estimate_launches(els, iters, steps):
-    """Kernels launched per solve: initial Rayleigh-Ritz (9), 21 per LOBPCG
-    iteration (graph nodes), input conversions (2 per element per stage) and
-    the FP64 orthonormalisation (10 per element); iterations are summed over
-    both precision stages."""
-    per_solve = 2 * 9 + 21 * (max(iters) + 2) + 4 * len(els) + 10 * len(els)
-    return int(per_solve * steps)
+def count_launches(els, reps, iters, steps):
+    """Kernels launched in the timed steps.  The LOBPCG iterations run as CUDA
+    graphs whose kernel nodes the library counts exactly (graph_kernels,
+    one count per wave); outside them each solve launches the initial
+    Rayleigh-Ritz of both stages (about 10 kernels each), the second
+    half-batch's first half-iteration (about 15), the FP64 check (8), input
+    conversions (2 per element and stage) and the FP64 orthonormalisation
+    (about 10 per element): estimated, not counted."""
+    waves = {}
+    for r in reps:
+        waves[r["wave"]] = r["graph_kernels"]
+    graph = sum(waves.values())
+    other = 2 * 10 + 15 + 8 + 4 * len(els) + 10 * len(els)
+    return int((graph + other) * steps)
 
 
 def cpu_baseline(el, budget_s):
@@ -406,7 +433,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=3)
     ap.add_argument("--tc-gram", action="store_true",
                     help="tcgen05 split-BF16 Gram in the FP32 stage (default: compensated SIMT)")
-    ap.add_argument("--fwd64", action="store_true", help="FP64 forward FFT in the FP32 stage's H apply")
+    ap.add_argument("--fwd64", type=int, default=0, choices=[0, 1, 2],
+                    help="FP64 forward FFT in the FP32 stage's H apply: 1 always, 2 for H X near convergence")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

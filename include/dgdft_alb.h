@@ -98,8 +98,11 @@ typedef struct {
                              but its FP32 tensor-memory accumulation gives
                              ~1e-5 relative, so the FP32 stage stalls higher
                              and leaves more iterations to FP64           */
-  int h_fp64_forward;     /* 1: the FP32 stage's H apply runs its forward FFT
-                             in FP64 (lower noise, ~10x slower passes)        */
+  int h_fp64_forward;     /* FP64 forward FFT in the FP32 stage's H apply
+                             (its rounding, amplified by |G|^2/2, sets the
+                             stage's residual floor near 2e-6 Ha): 0 never;
+                             1 every apply (~4x slower passes); 2 only H X'
+                             once the median residual is below 1e-5        */
   const char* autotune_cache;   /* optional JSON path; NULL = none            */
   const char* precond_weights;  /* learned preconditioner weights; NULL = none */
 } dgdft_alb_config;
@@ -114,6 +117,10 @@ typedef struct {
   double seconds;    /* wall time of the element's wave                       */
   int iterations_bulk; /* of `iterations`, those run in the FP32 stage (mixed) */
   double resid_bulk;   /* max_{j<J} residual (Ha) when the FP32 stage ended   */
+  long long graph_kernels; /* kernels launched through the per-iteration CUDA
+                              graphs of this element's wave (both stages);
+                              set-up, verify and orthonormalisation kernels
+                              outside the graphs are not counted           */
 } dgdft_solve_report;
 
 /* Fill cfg with defaults: FP64, Teter, tol 1e-6, maxit 400, check_every 4. */

@@ -40,7 +40,7 @@ class dgdft_alb_config(C.Structure):
 class dgdft_solve_report(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("max_resid", C.c_double),
                 ("fallbacks", C.c_int), ("wave", C.c_int), ("seconds", C.c_double),
-                ("iterations_bulk", C.c_int), ("resid_bulk", C.c_double)]
+                ("iterations_bulk", C.c_int), ("resid_bulk", C.c_double), ("graph_kernels", C.c_longlong)]
 
 
 _P = C.c_void_p
@@ -207,7 +207,8 @@ class Context:
             self._check(st, "solve")
         return st, [dict(status=r.status, iterations=r.iterations, max_resid=r.max_resid,
                          fallbacks=r.fallbacks, wave=r.wave, seconds=r.seconds,
-                         iterations_bulk=r.iterations_bulk, resid_bulk=r.resid_bulk) for r in reps]
+                         iterations_bulk=r.iterations_bulk, resid_bulk=r.resid_bulk,
+                         graph_kernels=r.graph_kernels) for r in reps]
 
     def dgdft_alb_get_basis(self, elem, phi=None, eig=None, resid=None):
         d = self.descs[elem]

@@ -227,6 +227,8 @@ template <class real> struct Wave {
   };
   SubView full, sub[2];
   bool split = false;
+  bool hx64 = false;            // capture H X' with the FP64 forward transform
+  long long graph_kernels = 0;  // kernel nodes launched through graphs by run()
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
@@ -583,7 +585,7 @@ template <class real> struct Wave {
     return DGDFT_OK;
   }
 
-  bool fwd64() const { return ctx->cfg.h_fp64_forward != 0; }
+  bool fwd64() const { return ctx->cfg.h_fp64_forward == 1; }
 
   // W = T(R): the learned network for elements that use it, Teter for the rest
   void precondition(cudaStream_t st) {
@@ -728,7 +730,7 @@ template <class real> struct Wave {
         // whose rounding grows with |Y| |HW| once [X W P] is nearly dependent
         // and would leave HX inconsistent with X (the residual then stalls or
         // diverges near 1e-4 Ha)
-        launch_apply_h<real>(batch, bref<real>(BX, 1), bref<real>(BHX, 1), 0, st, fwd64());
+        launch_apply_h<real>(batch, bref<real>(BX, 1), bref<real>(BHX, 1), 0, st, fwd64() || hx64);
       }
       TsmmJob<real> u;
       u.nin = 2;
@@ -766,14 +768,19 @@ template <class real> struct Wave {
     return read_states();
   }
 
+  // precise_below > 0 (FP32 waves): once the median active element's residual
+  // is below it, H X' is computed with the FP64 forward transform, whose
+  // rounding no longer dominates the residual; the FP32 stage can then reach
+  // tol.
   dgdft_status run(double tol, int maxit, int stall_window, std::vector<double>* res_out, int refresh_every = 0,
-                   bool resume = false) {
+                   bool resume = false, double precise_below = 0.0) {
     cudaStream_t st = ctx->stream;
     dgdft_status s = reset_states(tol, resume);
     if (s != DGDFT_OK) return s;
     enqueue_initial(st);
     CK(cudaGetLastError());
     cudaGraphExec_t exec = nullptr, exec2 = nullptr;
+    long long nodes1 = 0, nodes2 = 0;
     cudaError_t ce = cudaSuccess;
     auto capture = [&](cudaStream_t cs, int which, int order, cudaGraphExec_t* out) -> cudaError_t {
       cudaGraph_t graph = nullptr;
@@ -790,6 +797,8 @@ template <class real> struct Wave {
       e = cudaStreamEndCapture(cs, &graph);
       use(full);
       if (e != cudaSuccess) return e;
+      size_t nn = 0;
+      if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess) (which == 1 ? nodes2 : nodes1) = (long long)nn;
       e = cudaGraphInstantiate(out, graph, 0);
       cudaGraphDestroy(graph);
       return e;
@@ -807,8 +816,24 @@ template <class real> struct Wave {
       ce = capture(st, 0, 0, &exec);
       if (ce == cudaSuccess) ce = capture(st2, 1, 1, &exec2);
     }
+    // the same iteration with the precise H X' (captured up front; the node
+    // counts are equal)
+    cudaGraphExec_t pexec = nullptr, pexec2 = nullptr;
+    if (ce == cudaSuccess && precise_below > 0.0 && !fwd64()) {
+      hx64 = true;
+      const long long n1 = nodes1, n2 = nodes2;
+      ce = split ? capture(st, 0, 0, &pexec) : capture(st, -1, 0, &pexec);
+      if (ce == cudaSuccess && split) ce = capture(st2, 1, 1, &pexec2);
+      nodes1 = n1;
+      nodes2 = n2;
+      hx64 = false;
+    }
+    bool precise = false;
     if (ce != cudaSuccess) {
       if (exec) cudaGraphExecDestroy(exec);
+      if (exec2) cudaGraphExecDestroy(exec2);
+      if (pexec) cudaGraphExecDestroy(pexec);
+      if (pexec2) cudaGraphExecDestroy(pexec2);
       if (split) {
         cudaEventRecord(ev_join, st2);
         cudaStreamWaitEvent(st, ev_join, 0);
@@ -830,9 +855,10 @@ template <class real> struct Wave {
         since_refresh = 0;
       }
       for (int k = 0; k < every && launched <= maxit + 1; ++k, ++launched, ++since_refresh) {
-        ce = cudaGraphLaunch(exec, st);
-        if (ce == cudaSuccess && split) ce = cudaGraphLaunch(exec2, st2);
+        ce = cudaGraphLaunch(precise ? pexec : exec, st);
+        if (ce == cudaSuccess && split) ce = cudaGraphLaunch(precise ? pexec2 : exec2, st2);
         if (ce != cudaSuccess) break;
+        graph_kernels += nodes1 + (split ? nodes2 : 0);
       }
       if (ce != cudaSuccess) break;
       if (split) {
@@ -848,6 +874,7 @@ template <class real> struct Wave {
                        h_state[ST_ITER], h_state[ST_ACTIVE], *std::max_element(r0.begin(), r0.end()));
       }
       bool any = false;
+      std::vector<double> active_res;  // read only with a stall window
       for (int i = 0; i < nel; ++i) {
         int* sw = &h_state[(size_t)i * STATE_WORDS];
         if (!sw[ST_ACTIVE]) continue;
@@ -858,6 +885,7 @@ template <class real> struct Wave {
           if (ce != cudaSuccess) break;
           const double mx = *std::max_element(resbuf.begin(), resbuf.end());
           hist[i].push_back(mx);
+          active_res.push_back(mx);
           const size_t L = hist[i].size();
           // stalled: the best residual of the last `stall_window` polls is not
           // 5% below the best one before them (the FP32 floor has been
@@ -886,9 +914,18 @@ template <class real> struct Wave {
         }
       }
       if (ce != cudaSuccess || !any) break;
+      if (pexec && !precise && !active_res.empty()) {
+        // switch once the median active element is below the threshold: the
+        // rest would otherwise stall at the FP32 floor before a laggard
+        // catches up
+        std::nth_element(active_res.begin(), active_res.begin() + active_res.size() / 2, active_res.end());
+        if (active_res[active_res.size() / 2] < precise_below) precise = true;
+      }
     }
     cudaGraphExecDestroy(exec);
     if (exec2) cudaGraphExecDestroy(exec2);
+    if (pexec) cudaGraphExecDestroy(pexec);
+    if (pexec2) cudaGraphExecDestroy(pexec2);
     if (split) {
       // later work on the caller's stream sees the second half's results
       cudaEventRecord(ev_join, st2);
@@ -1045,7 +1082,7 @@ dgdft_status copy_block_to(Wave<real>& w, int i, Wave<double>& dst, int di, cuda
 
 dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, double seconds,
                          const std::vector<int>& extra_iters, const std::vector<int>& extra_fb,
-                         const std::vector<double>& bulk_res) {
+                         const std::vector<double>& bulk_res, long long graph_kernels) {
   for (size_t i = 0; i < w.ids.size(); ++i) {
     ElemHost& eh = ctx->el[w.ids[i]];
     const ElemDev<double>& E = w.h[i];
@@ -1080,6 +1117,7 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     eh.rep.max_resid = mx;
     eh.rep.wave = wave_idx;
     eh.rep.seconds = seconds;
+    eh.rep.graph_kernels = graph_kernels;
     eh.rep.status = (sw[ST_ERROR] != 0 || s != DGDFT_OK) ? DGDFT_ENOTCONV
                                                          : (mx <= ctx->cfg.tol ? DGDFT_OK : DGDFT_ENOTCONV);
     eh.solved = true;
@@ -1125,6 +1163,8 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
     }
   }
   Wave<double>& w64 = *wp->w64;
+  w64.graph_kernels = 0;
+  if (wp->w32) wp->w32->graph_kernels = 0;
   std::vector<int> it32, fb32;
   std::vector<double> res32;
   dgdft_status s;
@@ -1137,7 +1177,8 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
     // |G|^2/2), from which FP64 needs a few iterations
     const double tol1 = 0.6 * c.tol;
     std::vector<double> r32;
-    if ((s = w32.run(tol1, c.maxit, 5, &r32, 0)) != DGDFT_OK) return s;
+    const double precise_below = c.h_fp64_forward == 2 ? 1e-5 : 0.0;
+    if ((s = w32.run(tol1, c.maxit, 5, &r32, 0, false, precise_below)) != DGDFT_OK) return s;
     {
       size_t off = 0;
       for (size_t i = 0; i < ids.size(); ++i) {
@@ -1186,7 +1227,8 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
     if ((s = w64.run(c.tol, c.maxit, 0, nullptr)) != DGDFT_OK) return s;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32);
+  const long long gk = w64.graph_kernels + (wp->w32 ? wp->w32->graph_kernels : 0);
+  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32, gk);
 }
 
 }  // namespace
