@@ -51,16 +51,25 @@ __device__ __forceinline__ void small_dft(C* v, const C* tw, int n) {
   }
 }
 
+// floor(a / d) for 0 <= a < 2^22 from a rounded reciprocal: (a + 0.5) / d
+// lies at least 0.5 / d from an integer, far beyond the FP32 rounding of
+// the product, so truncation gives the exact quotient.
+__device__ __forceinline__ int fdiv_small(int a, float inv_d) {
+  return __float2int_rz(((float)a + 0.5f) * inv_d);
+}
+
 template <class C, int R, bool INV>
 __device__ __forceinline__ void stage_radix(const C* __restrict__ in, C* __restrict__ out, int n,
                                             int Ns, int nlines, int ls, int es, const C* tw) {
   const int nb = n / R;
   const int total = nlines * nb;
   const int tstep = n / (Ns * R);
+  const float inv_nb = 1.0f / (float)nb, inv_ns = 1.0f / (float)Ns;
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    const int l = b / nb;
+    const int l = fdiv_small(b, inv_nb);
     const int j = b - l * nb;
-    const int k = j % Ns;
+    const int jq = fdiv_small(j, inv_ns);
+    const int k = j - jq * Ns;
     C v[R];
     const C* src = in + l * ls;
 #pragma unroll
@@ -73,7 +82,7 @@ __device__ __forceinline__ void stage_radix(const C* __restrict__ in, C* __restr
       }
     }
     small_dft<C, R, INV>(v, tw, n);
-    const int idxD = (j / Ns) * Ns * R + k;
+    const int idxD = jq * Ns * R + k;
     C* dst = out + l * ls;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es] = v[r];

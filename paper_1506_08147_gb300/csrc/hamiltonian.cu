@@ -61,11 +61,12 @@ __global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
   const int nc = ncols > 0 ? ncols : e.m;
   if (!elem_live(e, filt) || z >= e.nz || j >= nc) return;
   const int row = e.nxh, ny = e.ny, nh = e.nh;
+  const float inv_nh = 1.0f / (float)nh, inv_nxh = 1.0f / (float)e.nxh;
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + ny * row;
   const R2* plane = reinterpret_cast<const R2*>(resolve(e, src) + (size_t)j * e.ng + (size_t)z * e.nx * ny);
   for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-    const int y = t / nh, k = t - y * nh;
+    const int y = fdiv_small(t, inv_nh), k = t - y * nh;
     const R2 v = plane[t];
     buf0[y * row + k] = cmake<C>((TC)v.x, (TC)v.y);
   }
@@ -78,7 +79,7 @@ __global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     const C* s = cur ? buf1 : buf0;
     C* d = cur ? buf0 : buf1;
     for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
-      const int y = t / e.nxh, k = t - y * e.nxh;
+      const int y = fdiv_small(t, inv_nxh), k = t - y * e.nxh;
       const C zk = s[y * row + (k == nh ? 0 : k)];
       const C zc = cconj(s[y * row + (k == 0 ? 0 : nh - k)]);
       const C ev = cscale(cadd(zk, zc), (TC)0.5);
@@ -93,7 +94,7 @@ __global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
   const C* res = cur ? buf1 : buf0;
   cplx_t<TZ>* out = reinterpret_cast<cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
   for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
-    const int y = t / e.nxh, k = t - y * e.nxh;
+    const int y = fdiv_small(t, inv_nxh), k = t - y * e.nxh;
     const C v = res[y * row + k];
     out[t] = cmake<cplx_t<TZ>>((TZ)v.x, (TZ)v.y);
   }
@@ -117,6 +118,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
   const int j = blockIdx.y;
   const int nc = ncols > 0 ? ncols : e.m;
   const int nplane = e.nxh * e.ny;
+  const float inv_nxh = 1.0f / (float)e.nxh;
   const int c0 = blockIdx.x * ZTILE;
   if (!elem_live(e, filt) || j >= nc || c0 >= nplane) return;
   const int nz = e.nz;
@@ -143,7 +145,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
         const int gz = t / ZTILE, cc = t - gz * ZTILE;
         const int c = c0 + cc;
         if (c >= nplane) continue;
-        const int y = c / e.nxh, kx = c - y * e.nxh;
+        const int y = fdiv_small(c, inv_nxh), kx = c - y * e.nxh;
         const float g = e.gx2f[kx] + e.gy2f[y] + e.gz2f[gz];
         float f = g;
         if (MODE == ZM_TETER) {
@@ -158,7 +160,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
         const int gz = t / ZTILE, cc = t - gz * ZTILE;
         const int c = c0 + cc;
         if (c >= nplane) continue;
-        const int y = c / e.nxh, kx = c - y * e.nxh;
+        const int y = fdiv_small(c, inv_nxh), kx = c - y * e.nxh;
         const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
         double f = (MODE == ZM_KINETIC) ? g : teter_factor(g * inv_tk);
         f *= e.scale;
@@ -188,11 +190,12 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
   const int nc = ncols > 0 ? ncols : e.m;
   if (!elem_live(e, filt) || z >= e.nz || j >= nc) return;
   const int row = e.nxh, ny = e.ny, nh = e.nh;
+  const float inv_nh = 1.0f / (float)nh, inv_nxh = 1.0f / (float)e.nxh;
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + ny * row;
   const cplx_t<TZ>* in = reinterpret_cast<const cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
   for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
-    const int y = t / e.nxh, k = t - y * e.nxh;
+    const int y = fdiv_small(t, inv_nxh), k = t - y * e.nxh;
     const cplx_t<TZ> v = in[t];
     buf0[y * row + k] = cmake<C>((TC)v.x, (TC)v.y);
   }
@@ -204,7 +207,7 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     const C* s = cur ? buf1 : buf0;
     C* d = cur ? buf0 : buf1;
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-      const int y = t / nh, k = t - y * nh;
+      const int y = fdiv_small(t, inv_nh), k = t - y * nh;
       const C xk = s[y * row + k];
       const C xc = cconj(s[y * row + nh - k]);
       const C ev = cscale(cadd(xk, xc), (TC)0.5);
@@ -237,7 +240,7 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);
     const TC sg = (TC)e.sigma[0];  // 0 except in the shifted FP32 stage
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-      const int y = t / nh, k = t - y * nh;
+      const int y = fdiv_small(t, inv_nh), k = t - y * nh;
       const C kv = res[y * row + k];
       const R2 xv = xp[t];
       const R2 vv = vp[t];
@@ -246,7 +249,7 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
   } else {
     R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-      const int y = t / nh, k = t - y * nh;
+      const int y = fdiv_small(t, inv_nh), k = t - y * nh;
       const C v = res[y * row + k];
       op[t] = cmake<R2>((real)v.x, (real)v.y);
     }

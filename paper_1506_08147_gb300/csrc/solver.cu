@@ -188,11 +188,9 @@ size_t elem_bytes(const ElemHost& h) {
   s.add(sizeof(double2) * nspec * m);
   s.add(sizeof(double) * (18 * m * m + m * m + 3 * m * m + 3 * m + 2));
   s.add(sizeof(double) * rr_work_doubles(3 * (int)m, (int)m));
-  s.add(sizeof(double) * m * nchunk_rows((int)ng) * 4);
   s.add(sizeof(int) * STATE_WORDS);
-  // share of the Gram partial buffer (12 pairs, 2048-row chunks)
-  const size_t tiles = ((m + 63) / 64) * ((m + 63) / 64);
-  s.add(sizeof(double) * ((ng + 2047) / 2048) * 12 * tiles * 4096);
+  // the residual partial sums and the Gram partial buffer depend on the
+  // wave's largest element and are added by Wave::build
   return s.total + 64 * ALIGN;
 }
 
@@ -316,8 +314,14 @@ template <class real> struct Wave {
       s.max_nproj = std::max(s.max_nproj, (int)eh.pgamma.size());
     }
     rnchunk = nchunk_rows(s.max_ng);
+    const size_t tiles = ((s.max_m + 63) / 64) * ((s.max_m + 63) / 64);
+    const size_t pcap = (size_t)nel * ((s.max_ng + 2047) / 2048) * 12 * tiles * 4096;
     size_t total = 0;
-    for (int id : ids) total += elem_bytes<real>(ctx->el[id]);
+    for (int id : ids) {
+      total += elem_bytes<real>(ctx->el[id]);
+      total += sizeof(double) * (size_t)ctx->el[id].d.n_compute * rnchunk * 4 + ALIGN;  // rpart
+    }
+    total += sizeof(double) * pcap + ALIGN;
     total += (sizeof(ElemDev<real>) + 2 * sizeof(RRTask)) * nel + 4 * ALIGN;
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, total);
@@ -325,11 +329,8 @@ template <class real> struct Wave {
     arena.base = (char*)p;
     arena.cap = total;
     // Gram partials: shared by the wave
-    {
-      size_t tiles = ((s.max_m + 63) / 64) * ((s.max_m + 63) / 64);
-      partial_cap = (size_t)nel * ((s.max_ng + 2047) / 2048) * 12 * tiles * 4096;
-      partial = (double*)arena.take(partial_cap * sizeof(double));
-    }
+    partial_cap = pcap;
+    partial = (double*)arena.take(partial_cap * sizeof(double));
     d_elems = (ElemDev<real>*)arena.take(sizeof(ElemDev<real>) * nel);
     d_rr_init = (RRTask*)arena.take(sizeof(RRTask) * nel);
     d_rr_lob = (RRTask*)arena.take(sizeof(RRTask) * nel);
@@ -891,11 +892,12 @@ template <class real> struct Wave {
           // 5% below the best one before them (the FP32 floor has been
           // reached).  Only near the floor: early plateaus (a random start
           // still sorting its subspace) are not stalls.
-          bool stalled = false;
+          bool stalled = false, near_floor = false;
           if (L > (size_t)stall_window) {
             const double before = *std::min_element(hist[i].begin(), hist[i].end() - stall_window);
             const double recent = *std::min_element(hist[i].end() - stall_window, hist[i].end());
-            stalled = recent > 0.95 * before && recent < std::max(100.0 * tol, 1e-5);
+            stalled = recent > 0.95 * before;
+            near_floor = recent < std::max(100.0 * tol, 1e-5);
           }
           if (stalled && learned && !sw[ST_TETER]) {
             // the learned preconditioner stalled: fall back to Teter
@@ -906,7 +908,7 @@ template <class real> struct Wave {
             ce = ctx_copy(ctx, h[i].state + ST_FALLBACK, &fb, sizeof(int), cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) break;
             hist[i].clear();
-          } else if (stalled) {
+          } else if (stalled && near_floor) {
             int zero = 0;
             ce = ctx_copy(ctx, h[i].state + ST_ACTIVE, &zero, sizeof(int), cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) break;
@@ -1422,8 +1424,13 @@ dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem) {
   size_t acc = 0;
   for (int id : todo) {
     const ElemHost& eh = ctx->el[id];
-    size_t b = elem_bytes<double>(eh);
-    if (ctx->cfg.precision == DGDFT_PREC_MIXED) b += elem_bytes<float>(eh);
+    // plus the element's share of the wave-level buffers (Gram partials and
+    // residual partial sums, sized here by the element itself)
+    const size_t m = (size_t)eh.d.n_compute, ng = (size_t)eh.ng();
+    const size_t shared = sizeof(double) * (((ng + 2047) / 2048) * 12 * ((m + 63) / 64) * ((m + 63) / 64) * 4096 +
+                                            m * (size_t)nchunk_rows((int)ng) * 4);
+    size_t b = elem_bytes<double>(eh) + shared;
+    if (ctx->cfg.precision == DGDFT_PREC_MIXED) b += elem_bytes<float>(eh) + shared;
     if (b > cap) return ctx->fail(DGDFT_ENOMEM, "one element exceeds the device-memory budget");
     if (waves.empty() || acc + b > cap) {
       waves.emplace_back();

@@ -1,0 +1,69 @@
+"""Full mixed-form solves on the uneven and the large-block workloads.
+
+The uneven batch mixes four grid shapes and block sizes m = 32 ... 112 in one
+wave (the kernels then run their general paths: column-tiled updates,
+64-wide Gram tiles, the global-memory Rayleigh-Ritz); the large-monolayer
+element has m = 144, J = 120 and a 432 x 432 pencil.  Each returned block is
+checked with the FP64 oracle's own H: residual, orthonormal ALBs and
+span(ALBs) = span(restricted Ritz block).
+"""
+
+import numpy as np
+import pytest
+
+import __graft_entry__ as entry
+import synth
+from oracle import alb, hamiltonian as H
+from paper_1506_08147_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+# one or two elements of every grid shape, m from 32 to 112
+CONFIG3_PICK = [2, 11, 3, 25, 0, 7]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    entry.build()
+
+
+def check_solution(c, els, tol):
+    for k, e in enumerate(els):
+        phi, eig, res = c.dgdft_alb_get_basis(k)
+        x = c.dgdft_alb_get_block(k)
+        assert np.all(np.isfinite(eig))
+        assert np.max(res) <= tol
+        r = H.apply_h(x[:e.J], e) - eig[:, None] * x[:e.J]
+        assert np.max(np.linalg.norm(r, axis=1)) <= 1.05 * tol
+        np.testing.assert_allclose(phi @ phi.T * e.dv, np.eye(e.J), atol=1e-12)
+        # the span test is as sensitive as the restricted block is ill
+        # conditioned (a middle third of a standalone box can be nearly
+        # rank deficient): FP64 rounding amplified by its condition number
+        xr = alb.restrict(x, e)
+        sv = np.linalg.svd(xr, compute_uv=False)
+        assert alb.sin_max_angle(xr, phi) < max(1e-10, 1e-14 * sv[0] / sv[-1])
+        assert np.all(np.diff(eig) >= -1e-9)
+
+
+def test_solve_config3_uneven_batch():
+    els = synth.config3(elems=CONFIG3_PICK)
+    c = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_MIXED, tol=1e-6, maxit=800,
+                  keep_block=True)
+    for k, e in enumerate(els):
+        B.load_element(c, k, e, synth.initial_block(e))
+    st, rep = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    check_solution(c, els, 1e-6)
+    c.close()
+
+
+def test_solve_config5_large_block():
+    els = synth.config5(elems=[100])
+    c = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_MIXED, tol=1e-6, maxit=800,
+                  keep_block=True)
+    for k, e in enumerate(els):
+        B.load_element(c, k, e, synth.initial_block(e))
+    st, rep = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    check_solution(c, els, 1e-6)
+    c.close()
