@@ -66,6 +66,41 @@ def train(out_path, geometries=64, snaps=(5, 15, 40), steps=3000, batch=8, crop=
     return info
 
 
+def evaluate(weights_path, n_elems=4, log=print):
+    """Mixed-form solves of the first n_elems monolayer elements (config 2,
+    which is not among the training geometries) with Teter and with the
+    network: iterations of the FP32 stage, total iterations, seconds."""
+    import time as _time
+
+    import numpy as np
+
+    import synth
+    from paper_1506_08147_gb300 import binding as B
+
+    els = synth.config2(elems=list(range(n_elems)))
+    out = {}
+    for name, mode in (("teter", B.DGDFT_PRECOND_TETER), ("learned", B.DGDFT_PRECOND_LEARNED)):
+        c = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_MIXED, tol=1e-6, maxit=600,
+                      precond=mode, precond_weights=weights_path if name == "learned" else None)
+        for k, e in enumerate(els):
+            B.load_element(c, k, e, synth.initial_block(e))
+        c.dgdft_alb_solve()  # warm-up (wave build)
+        for k, e in enumerate(els):
+            c.dgdft_alb_set_initial(k, synth.initial_block(e))
+        t0 = _time.time()
+        st, rep = c.dgdft_alb_solve()
+        dt = _time.time() - t0
+        c.close()
+        out[name] = {"status": int(st), "seconds": dt,
+                     "fp32_iterations_mean": float(np.mean([r["iterations_bulk"] for r in rep])),
+                     "iterations_mean": float(np.mean([r["iterations"] for r in rep])),
+                     "iterations_max": int(max(r["iterations"] for r in rep)),
+                     "teter_fallbacks": int(sum(r["fallbacks"] for r in rep)) if name == "learned" else 0,
+                     "max_resid": float(max(r["max_resid"] for r in rep))}
+        log(json.dumps({name: out[name]}))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -76,8 +111,11 @@ def main():
     ap.add_argument("--crop", type=int, default=40)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--eval", type=int, default=0, help="then compare with Teter on this many monolayer elements")
     a = ap.parse_args()
     train(a.out, a.geometries, [int(s) for s in a.snaps.split(",")], a.steps, a.batch, a.crop, a.lr, a.seed)
+    if a.eval > 0:
+        evaluate(a.out, a.eval)
 
 
 if __name__ == "__main__":

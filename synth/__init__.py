@@ -17,6 +17,7 @@ from .workloads import (  # noqa: F401
     config1,
     config2,
     config3,
+    config4,
     config5,
     element_box,
     initial_block,

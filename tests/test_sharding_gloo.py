@@ -63,3 +63,18 @@ def test_partition_single_rank_and_errors():
     assert sharding.partition([], 3) == [[], [], []]
     with pytest.raises(ValueError):
         sharding.partition([1.0], 0)
+
+
+def test_bench_workload_split_two_ranks():
+    """bench.py at 2 ranks: two monolayer replicas, each rank a disjoint half
+    of their 2 x k elements, replica 0 identical to the 1-rank workload."""
+    import bench
+    one, _ = bench.workload(2, 0, 1)
+    r0, _ = bench.workload(2, 0, 2)
+    r1, _ = bench.workload(2, 1, 2)
+    keys0 = {e.seed_key for e in r0}
+    keys1 = {e.seed_key for e in r1}
+    assert not keys0 & keys1
+    assert len(keys0) == len(keys1) == 2
+    assert {e.seed_key for e in one} <= keys0 | keys1
+    assert len(keys0 | keys1) == 4
