@@ -220,6 +220,101 @@ __global__ void __launch_bounds__(144) gram48_kernel(const ElemDev<float>* __res
     for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * TILE + tx * 4 + j] = (double)chi[i][j] + (double)clo[i][j];
 }
 
+// FP64 Gram products for blocks of at most 48 columns (the FP64 stage at
+// m <= 48): the layout of gram48_kernel with 16-row stages of doubles, each
+// thread reading 2 rows of a column as one 16-byte double2 (chunks of a
+// column swizzled by column group as there).  FP64 accumulation; the FP64
+// pipe bounds it, and 48-wide tiles avoid the 64-wide tiles' idle lanes.
+// grid: (npairs, nchunk, nel); block 144.
+constexpr int GKD = 16;  // rows per stage (doubles)
+
+__device__ __forceinline__ int g48d_off(int c, int r) {
+  return c * GKD + ((((r >> 1) ^ ((c >> 2) & 7)) << 1) | (r & 1));
+}
+
+__global__ void __launch_bounds__(144) gram48d_kernel(const ElemDev<double>* __restrict__ elems,
+                                                       GramJob<double> job, double* __restrict__ partial,
+                                                       size_t pstride, int kchunk) {
+  __shared__ __align__(16) double As[2][G48 * GKD];
+  __shared__ __align__(16) double Bs[2][G48 * GKD];
+  const ElemDev<double>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int pair = blockIdx.x;
+  if (job.needs_p[pair] && !e.state[ST_HAS_P]) return;
+  const int ca = job.ncols_a > 0 ? job.ncols_a : e.m;
+  const int cb = job.ncols_b > 0 ? job.ncols_b : e.m;
+  const int rows = job.rows > 0 ? job.rows : e.ng;
+  const double* A = resolve(e, job.a[pair]);
+  const double* B = resolve(e, job.b[pair]);
+  const int lda = ld_of(e, job.a[pair], job.ld_in, rows);
+  const int ldb = ld_of(e, job.b[pair], job.ld_in, rows);
+  const int tx = threadIdx.x % 12, ty = threadIdx.x / 12;
+  const int k_beg = blockIdx.y * kchunk;
+  const int k_end = min(rows, k_beg + kchunk);
+  const bool vec = ((lda | ldb | k_beg) & 1) == 0 && ((((uintptr_t)A) | ((uintptr_t)B)) & 15) == 0;
+  auto load_stage = [&](int buf, int k0) {
+    for (int t = threadIdx.x; t < 2 * G48 * (GKD / 2); t += blockDim.x) {
+      const int op = t / (G48 * (GKD / 2));
+      const int rem = t - op * (G48 * (GKD / 2));
+      const int c = rem / (GKD / 2), q = rem - c * (GKD / 2);
+      const double* src = op ? B : A;
+      const int ld = op ? ldb : lda;
+      const int cc = op ? cb : ca;
+      double* dst = (op ? Bs[buf] : As[buf]) + g48d_off(c, 2 * q);
+      const int k = k0 + 2 * q;
+      const int nv = (c < cc) ? max(0, min(2, k_end - k)) : 0;
+      const double* g = nv ? src + (size_t)c * ld + k : src;
+      if (vec) {
+        cp_async16(dst, g, 8 * nv);
+      } else {
+        // 8-byte pieces: two 4-byte copies each
+        const float* gf = reinterpret_cast<const float*>(g);
+        const float* sf = reinterpret_cast<const float*>(src);
+        float* df = reinterpret_cast<float*>(dst);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cp_async4(df + u, u < 2 * nv ? gf + u : sf, u < 2 * nv ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int nst = (k_end > k_beg) ? (k_end - k_beg + GKD - 1) / GKD : 0;
+  if (nst > 0) load_stage(0, k_beg);
+  for (int st = 0; st < nst; ++st) {
+    if (st + 1 < nst) {
+      load_stage((st + 1) & 1, k_beg + (st + 1) * GKD);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const double* as = As[st & 1];
+    const double* bs = Bs[st & 1];
+#pragma unroll 2
+    for (int r = 0; r < GKD; r += 2) {
+      double2 a2[4], b2[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a2[i] = *reinterpret_cast<const double2*>(as + g48d_off(ty * 4 + i, r));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b2[j] = *reinterpret_cast<const double2*>(bs + g48d_off(tx * 4 + j, r));
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a2[i].y, b2[j].y, fma(a2[i].x, b2[j].x, acc[i][j]));
+    }
+    __syncthreads();
+  }
+  double* out = partial + blockIdx.z * pstride + ((size_t)blockIdx.y * gridDim.x + pair) * (TILE * TILE);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * TILE + tx * 4 + j] = acc[i][j];
+}
+
 template <class real>
 __global__ void gram_reduce_kernel(const ElemDev<real>* __restrict__ elems, GramJob<real> job,
                                    const double* __restrict__ partial, size_t pstride, int nchunk,
@@ -671,6 +766,10 @@ void launch_gram(const Batch<real>& b, const GramJob<real>& job, double* partial
     gram48_kernel<<<dim3(ny, nchunk, s.nel), 144, 0, st>>>(
         reinterpret_cast<const ElemDev<float>*>(b.d_elems), *reinterpret_cast<const GramJob<float>*>(&job), partial,
         pstride, kchunk);
+  } else if (std::is_same<real, double>::value && ca <= G48 && cb <= G48) {
+    gram48d_kernel<<<dim3(ny, nchunk, s.nel), 144, 0, st>>>(
+        reinterpret_cast<const ElemDev<double>*>(b.d_elems), *reinterpret_cast<const GramJob<double>*>(&job),
+        partial, pstride, kchunk);
   } else {
     gram_kernel<real><<<dim3(nchunk, ny, s.nel), 256, 0, st>>>(b.d_elems, job, partial, pstride, kchunk,
                                                                tiles_a, tiles_b);
