@@ -73,7 +73,8 @@ enum {
 
 /* One extended element Q_K and its element E_K. */
 typedef struct {
-  int nx, ny, nz;        /* grid of Q_K (even sizes with factors 2, 3, 5)     */
+  int nx, ny, nz;        /* grid of Q_K: factors 2, 3, 5, nx even,
+                            (nx/2+1)*ny <= 7000, nz <= 400                   */
   double Lx, Ly, Lz;     /* side lengths of Q_K in bohr                       */
   int e_lo[3], e_hi[3];  /* E_K as the half-open grid-index box [lo, hi)      */
   int n_compute;         /* m: eigenpairs computed by LOBPCG (>= n_keep)      */

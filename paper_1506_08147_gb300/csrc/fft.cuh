@@ -51,11 +51,13 @@ __device__ __forceinline__ void small_dft(C* v, const C* tw, int n) {
   }
 }
 
-// floor(a / d) for 0 <= a < 2^22 from a rounded reciprocal: (a + 0.5) / d
-// lies at least 0.5 / d from an integer, far beyond the FP32 rounding of
-// the product, so truncation gives the exact quotient.
-__device__ __forceinline__ int fdiv_small(int a, float inv_d) {
-  return __float2int_rz(((float)a + 0.5f) * inv_d);
+// floor(a / d) for 0 <= a < 2^16, 2 <= d < 2^16 by one high multiply: with
+// M = ceil(2^32 / d), a M / 2^32 = a / d + a (M d - 2^32) / (d 2^32) and the
+// second term is below 1 / d, so the integer part is exact.  M does not fit
+// 32 bits for d = 1, which is marked by M = 0 and handled apart.
+__device__ __forceinline__ unsigned div_magic(unsigned d) { return d > 1u ? 0xFFFFFFFFu / d + 1u : 0u; }
+__device__ __forceinline__ int udiv_small(int a, unsigned magic) {
+  return magic ? (int)__umulhi((unsigned)a, magic) : a;
 }
 
 template <class C, int R, bool INV>
@@ -64,11 +66,11 @@ __device__ __forceinline__ void stage_radix(const C* __restrict__ in, C* __restr
   const int nb = n / R;
   const int total = nlines * nb;
   const int tstep = n / (Ns * R);
-  const float inv_nb = 1.0f / (float)nb, inv_ns = 1.0f / (float)Ns;
+  const unsigned mag_nb = div_magic(nb), mag_ns = div_magic(Ns);
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    const int l = fdiv_small(b, inv_nb);
+    const int l = udiv_small(b, mag_nb);
     const int j = b - l * nb;
-    const int jq = fdiv_small(j, inv_ns);
+    const int jq = udiv_small(j, mag_ns);
     const int k = j - jq * Ns;
     C v[R];
     const C* src = in + l * ls;
@@ -88,6 +90,78 @@ __device__ __forceinline__ void stage_radix(const C* __restrict__ in, C* __restr
     for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es] = v[r];
   }
 }
+
+// Compile-time variant for a line length N known when the kernel is built:
+// the same radix order as the host plan (4s, then 2s, 3s, 5s), every loop
+// bound, stride and twiddle step a constant.
+__host__ __device__ constexpr int ct_nstage(int n) {
+  int s = 0;
+  const int rad[4] = {4, 2, 3, 5};
+  for (int q = 0; q < 4; ++q)
+    while (n % rad[q] == 0) {
+      n /= rad[q];
+      ++s;
+    }
+  return s;
+}
+__host__ __device__ constexpr int ct_radix(int n, int stage) {
+  int s = 0;
+  const int rad[4] = {4, 2, 3, 5};
+  for (int q = 0; q < 4; ++q)
+    while (n % rad[q] == 0) {
+      if (s == stage) return rad[q];
+      n /= rad[q];
+      ++s;
+    }
+  return 1;
+}
+
+template <class C, int R, bool INV, int N, int NS>
+__device__ __forceinline__ void stage_radix_ct(const C* __restrict__ in, C* __restrict__ out, int nlines, int ls,
+                                               int es, const C* tw) {
+  constexpr int nb = N / R;
+  constexpr int tstep = N / (NS * R);
+  const int total = nlines * nb;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int l = b / nb;
+    const int j = b - l * nb;
+    const int jq = j / NS;
+    const int k = j - jq * NS;
+    C v[R];
+    const C* src = in + l * ls;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * es];
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = tw[r * k * tstep];
+        v[r] = cmul(v[r], INV ? cconj(w) : w);
+      }
+    }
+    small_dft<C, R, INV>(v, tw, N);
+    const int idxD = jq * NS * R + k;
+    C* dst = out + l * ls;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(idxD + r * NS) * es] = v[r];
+  }
+}
+
+template <class C, bool INV, int N, int S, int NS>
+__device__ __forceinline__ int fft_ct_stages(C* buf0, C* buf1, int cur, int nlines, int ls, int es, const C* tw) {
+  if constexpr (S >= ct_nstage(N)) {
+    return cur;
+  } else {
+    constexpr int R = ct_radix(N, S);
+    stage_radix_ct<C, R, INV, N, NS>(cur ? buf1 : buf0, cur ? buf0 : buf1, nlines, ls, es, tw);
+    __syncthreads();
+    return fft_ct_stages<C, INV, N, S + 1, NS * R>(buf0, buf1, cur ^ 1, nlines, ls, es, tw);
+  }
+}
+
+// N > 0: the compile-time transform; N == 0: the plan's runtime transform.
+template <class C, bool INV, int N>
+__device__ __forceinline__ int fft_lines_n(C* buf0, C* buf1, int cur, const FftPlan& plan, int nlines, int ls,
+                                           int es, const C* tw);
 
 // Full transform of nlines lines; ping-pongs between bufs[0] and bufs[1]
 // starting from bufs[cur].  Returns the index of the buffer holding the result.
@@ -111,6 +185,15 @@ __device__ int fft_lines(C* buf0, C* buf1, int cur, const FftPlan& plan, int nli
     cur ^= 1;
   }
   return cur;
+}
+
+template <class C, bool INV, int N>
+__device__ __forceinline__ int fft_lines_n(C* buf0, C* buf1, int cur, const FftPlan& plan, int nlines, int ls,
+                                           int es, const C* tw) {
+  if constexpr (N > 0)
+    return fft_ct_stages<C, INV, N, 0, 1>(buf0, buf1, cur, nlines, ls, es, tw);
+  else
+    return fft_lines<C, INV>(buf0, buf1, cur, plan, nlines, ls, es, tw);
 }
 
 }  // namespace dgdft

@@ -51,7 +51,7 @@ __global__ void proj_coef_kernel(const ElemDev<real>* __restrict__ elems, BRef<r
 
 // Pass 1.  real: storage of the vectors; TC: arithmetic; TZ: the stored
 // half spectrum.
-template <class real, class TC, class TZ>
+template <class real, class TC, class TZ, int NH = 0, int NY = 0>
 __global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> src, int ncols, int filt) {
   using C = cplx_t<TC>;
   using R2 = cplx_t<real>;
@@ -60,26 +60,27 @@ __global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
   const int z = blockIdx.x, j = blockIdx.y;
   const int nc = ncols > 0 ? ncols : e.m;
   if (!elem_live(e, filt) || z >= e.nz || j >= nc) return;
-  const int row = e.nxh, ny = e.ny, nh = e.nh;
-  const float inv_nh = 1.0f / (float)nh, inv_nxh = 1.0f / (float)e.nxh;
+  const int nh = NH ? NH : e.nh, ny = NY ? NY : e.ny, nxh = nh + 1, row = nxh;
+  if (NH && (e.nh != NH || e.ny != NY)) return;  // launched only on uniform batches of this grid
+  const unsigned mag_nh = div_magic(nh), mag_nxh = div_magic(nxh);
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + ny * row;
   const R2* plane = reinterpret_cast<const R2*>(resolve(e, src) + (size_t)j * e.ng + (size_t)z * e.nx * ny);
   for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-    const int y = fdiv_small(t, inv_nh), k = t - y * nh;
+    const int y = (NH ? t / nh : udiv_small(t, mag_nh)), k = t - y * nh;
     const R2 v = plane[t];
     buf0[y * row + k] = cmake<C>((TC)v.x, (TC)v.y);
   }
   __syncthreads();
   const C* tw_h = twp<TC>(e, TW_H);
   const C* tw_x = twp<TC>(e, TW_X);
-  int cur = fft_lines<C, false>(buf0, buf1, 0, e.px, ny, row, 1, tw_h);
+  int cur = fft_lines_n<C, false, NH>(buf0, buf1, 0, e.px, ny, row, 1, tw_h);
   // even/odd split: X[k] = E[k] + e^{-2 pi i k / nx} O[k], k = 0..nh
   {
     const C* s = cur ? buf1 : buf0;
     C* d = cur ? buf0 : buf1;
-    for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
-      const int y = fdiv_small(t, inv_nxh), k = t - y * e.nxh;
+    for (int t = threadIdx.x; t < nxh * ny; t += blockDim.x) {
+      const int y = (NH ? t / nxh : udiv_small(t, mag_nxh)), k = t - y * nxh;
       const C zk = s[y * row + (k == nh ? 0 : k)];
       const C zc = cconj(s[y * row + (k == 0 ? 0 : nh - k)]);
       const C ev = cscale(cadd(zk, zc), (TC)0.5);
@@ -90,11 +91,11 @@ __global__ void xy_fwd_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     __syncthreads();
     cur ^= 1;
   }
-  cur = fft_lines<C, false>(buf0, buf1, cur, e.py, e.nxh, 1, row, twp<TC>(e, TW_Y));
+  cur = fft_lines_n<C, false, NY>(buf0, buf1, cur, e.py, nxh, 1, row, twp<TC>(e, TW_Y));
   const C* res = cur ? buf1 : buf0;
-  cplx_t<TZ>* out = reinterpret_cast<cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
-  for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
-    const int y = fdiv_small(t, inv_nxh), k = t - y * e.nxh;
+  cplx_t<TZ>* out = reinterpret_cast<cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * nxh * ny;
+  for (int t = threadIdx.x; t < nxh * ny; t += blockDim.x) {
+    const int y = (NH ? t / nxh : udiv_small(t, mag_nxh)), k = t - y * nxh;
     const C v = res[y * row + k];
     out[t] = cmake<cplx_t<TZ>>((TZ)v.x, (TZ)v.y);
   }
@@ -109,7 +110,7 @@ __device__ __forceinline__ double teter_factor(double s) {
 }
 
 // Pass 2, arithmetic and storage in TZ.
-template <class real, class TZ, int MODE>
+template <class real, class TZ, int MODE, int NZ = 0>
 __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols,
                               const double* __restrict__ tkin_override, int filt) {
   using C = cplx_t<TZ>;
@@ -118,10 +119,11 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
   const int j = blockIdx.y;
   const int nc = ncols > 0 ? ncols : e.m;
   const int nplane = e.nxh * e.ny;
-  const float inv_nxh = 1.0f / (float)e.nxh;
+  const unsigned mag_nxh = div_magic(e.nxh);
   const int c0 = blockIdx.x * ZTILE;
   if (!elem_live(e, filt) || j >= nc || c0 >= nplane) return;
-  const int nz = e.nz;
+  const int nz = NZ ? NZ : e.nz;
+  if (NZ && e.nz != NZ) return;  // launched only on uniform batches of this grid
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + nz * ZROW;
   C* zj = reinterpret_cast<C*>(e.Z) + (size_t)j * e.nspec;
@@ -132,7 +134,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
   }
   __syncthreads();
   const C* tw_z = twp<TZ>(e, TW_Z);
-  int cur = fft_lines<C, false>(buf0, buf1, 0, e.pz, ZTILE, 1, ZROW, tw_z);
+  int cur = fft_lines_n<C, false, NZ>(buf0, buf1, 0, e.pz, ZTILE, 1, ZROW, tw_z);
   {
     C* s = cur ? buf1 : buf0;
     double tk = 1.0;
@@ -145,7 +147,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
         const int gz = t / ZTILE, cc = t - gz * ZTILE;
         const int c = c0 + cc;
         if (c >= nplane) continue;
-        const int y = fdiv_small(c, inv_nxh), kx = c - y * e.nxh;
+        const int y = udiv_small(c, mag_nxh), kx = c - y * e.nxh;
         const float g = e.gx2f[kx] + e.gy2f[y] + e.gz2f[gz];
         float f = g;
         if (MODE == ZM_TETER) {
@@ -160,7 +162,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
         const int gz = t / ZTILE, cc = t - gz * ZTILE;
         const int c = c0 + cc;
         if (c >= nplane) continue;
-        const int y = fdiv_small(c, inv_nxh), kx = c - y * e.nxh;
+        const int y = udiv_small(c, mag_nxh), kx = c - y * e.nxh;
         const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
         double f = (MODE == ZM_KINETIC) ? g : teter_factor(g * inv_tk);
         f *= e.scale;
@@ -169,7 +171,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
     }
     __syncthreads();
   }
-  cur = fft_lines<C, true>(buf0, buf1, cur, e.pz, ZTILE, 1, ZROW, tw_z);
+  cur = fft_lines_n<C, true, NZ>(buf0, buf1, cur, e.pz, ZTILE, 1, ZROW, tw_z);
   const C* res = cur ? buf1 : buf0;
   for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
     const int z = t / ZTILE, cc = t - z * ZTILE;
@@ -179,7 +181,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
 }
 
 // Pass 3: Z (TZ) -> arithmetic TC -> vectors (real), with the epilogue.
-template <class real, class TZ, class TC, int MODE>
+template <class real, class TZ, class TC, int MODE, int NH = 0, int NY = 0>
 __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real> dst,
                               BRef<real> xsrc, int ncols, int filt) {
   using C = cplx_t<TC>;
@@ -189,25 +191,26 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
   const int z = blockIdx.x, j = blockIdx.y;
   const int nc = ncols > 0 ? ncols : e.m;
   if (!elem_live(e, filt) || z >= e.nz || j >= nc) return;
-  const int row = e.nxh, ny = e.ny, nh = e.nh;
-  const float inv_nh = 1.0f / (float)nh, inv_nxh = 1.0f / (float)e.nxh;
+  const int nh = NH ? NH : e.nh, ny = NY ? NY : e.ny, nxh = nh + 1, row = nxh;
+  if (NH && (e.nh != NH || e.ny != NY)) return;  // launched only on uniform batches of this grid
+  const unsigned mag_nh = div_magic(nh), mag_nxh = div_magic(nxh);
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + ny * row;
-  const cplx_t<TZ>* in = reinterpret_cast<const cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * e.nxh * ny;
-  for (int t = threadIdx.x; t < e.nxh * ny; t += blockDim.x) {
-    const int y = fdiv_small(t, inv_nxh), k = t - y * e.nxh;
+  const cplx_t<TZ>* in = reinterpret_cast<const cplx_t<TZ>*>(e.Z) + (size_t)j * e.nspec + (size_t)z * nxh * ny;
+  for (int t = threadIdx.x; t < nxh * ny; t += blockDim.x) {
+    const int y = (NH ? t / nxh : udiv_small(t, mag_nxh)), k = t - y * nxh;
     const cplx_t<TZ> v = in[t];
     buf0[y * row + k] = cmake<C>((TC)v.x, (TC)v.y);
   }
   __syncthreads();
   const C* tw_x = twp<TC>(e, TW_X);
-  int cur = fft_lines<C, true>(buf0, buf1, 0, e.py, e.nxh, 1, row, twp<TC>(e, TW_Y));
+  int cur = fft_lines_n<C, true, NY>(buf0, buf1, 0, e.py, nxh, 1, row, twp<TC>(e, TW_Y));
   // recombine the half spectrum into E + i O for the length-nh inverse
   {
     const C* s = cur ? buf1 : buf0;
     C* d = cur ? buf0 : buf1;
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-      const int y = fdiv_small(t, inv_nh), k = t - y * nh;
+      const int y = (NH ? t / nh : udiv_small(t, mag_nh)), k = t - y * nh;
       const C xk = s[y * row + k];
       const C xc = cconj(s[y * row + nh - k]);
       const C ev = cscale(cadd(xk, xc), (TC)0.5);
@@ -217,7 +220,7 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     __syncthreads();
     cur ^= 1;
   }
-  cur = fft_lines<C, true>(buf0, buf1, cur, e.px, ny, row, 1, twp<TC>(e, TW_H));
+  cur = fft_lines_n<C, true, NH>(buf0, buf1, cur, e.px, ny, row, 1, twp<TC>(e, TW_H));
   C* res = cur ? buf1 : buf0;
   const size_t plane_off = (size_t)j * e.ng + (size_t)z * e.nx * ny;
   if (MODE == XI_HAMILTONIAN) {
@@ -230,7 +233,8 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
         TC acc = 0;
         for (int q = e.s_ptr[s]; q < e.s_ptr[s + 1]; ++q) acc += (TC)e.s_gv[q] * (TC)cj[e.s_proj[q]];
         const int off = e.s_off[s];
-        const int y = off / e.nx, x = off - y * e.nx;
+        const int nx = 2 * nh;
+        const int y = off / nx, x = off - y * nx;
         rres[2 * (y * row) + x] += acc;
       }
       __syncthreads();
@@ -240,7 +244,7 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
     R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);
     const TC sg = (TC)e.sigma[0];  // 0 except in the shifted FP32 stage
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-      const int y = fdiv_small(t, inv_nh), k = t - y * nh;
+      const int y = (NH ? t / nh : udiv_small(t, mag_nh)), k = t - y * nh;
       const C kv = res[y * row + k];
       const R2 xv = xp[t];
       const R2 vv = vp[t];
@@ -249,7 +253,7 @@ __global__ void xy_inv_kernel(const ElemDev<real>* __restrict__ elems, BRef<real
   } else {
     R2* op = reinterpret_cast<R2*>(resolve(e, dst) + plane_off);
     for (int t = threadIdx.x; t < nh * ny; t += blockDim.x) {
-      const int y = fdiv_small(t, inv_nh), k = t - y * nh;
+      const int y = (NH ? t / nh : udiv_small(t, mag_nh)), k = t - y * nh;
       const C v = res[y * row + k];
       op[t] = cmake<R2>((real)v.x, (real)v.y);
     }
@@ -263,6 +267,48 @@ template <class T> size_t zcol_smem(const BatchShape& s) {
   return 2 * sizeof(cplx_t<T>) * (size_t)s.max_nz * ZROW;
 }
 
+// Pass launchers: on a batch whose elements share one grid of a supported
+// shape (the monolayer extended elements, 48 x 64 x 40 and 48 x 64 x 48) the
+// kernels specialised for those line lengths at compile time; otherwise the
+// kernels that follow each element's runtime plan.
+template <class real, class TC, class TZ>
+void launch_xy_fwd(const Batch<real>& b, BRef<real> src, int ncols, int filt, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int nc = ncols > 0 ? ncols : s.max_m;
+  const dim3 g(s.max_nz, nc, s.nel);
+  const size_t sm = plane_smem<TC>(s);
+  if (s.uni_nx == 48 && s.uni_ny == 64)
+    xy_fwd_kernel<real, TC, TZ, 24, 64><<<g, 256, sm, st>>>(b.d_elems, src, ncols, filt);
+  else
+    xy_fwd_kernel<real, TC, TZ><<<g, 256, sm, st>>>(b.d_elems, src, ncols, filt);
+}
+
+template <class real, class TZ, int MODE>
+void launch_z_mult(const Batch<real>& b, int ncols, const double* tkin_override, int filt, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int nc = ncols > 0 ? ncols : s.max_m;
+  const dim3 g((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel);
+  const size_t sm = zcol_smem<TZ>(s);
+  if (s.uni_nz == 40)
+    z_mult_kernel<real, TZ, MODE, 40><<<g, 256, sm, st>>>(b.d_elems, ncols, tkin_override, filt);
+  else if (s.uni_nz == 48)
+    z_mult_kernel<real, TZ, MODE, 48><<<g, 256, sm, st>>>(b.d_elems, ncols, tkin_override, filt);
+  else
+    z_mult_kernel<real, TZ, MODE><<<g, 256, sm, st>>>(b.d_elems, ncols, tkin_override, filt);
+}
+
+template <class real, class TZ, class TC, int MODE>
+void launch_xy_inv(const Batch<real>& b, BRef<real> dst, BRef<real> src, int ncols, int filt, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  const int nc = ncols > 0 ? ncols : s.max_m;
+  const dim3 g(s.max_nz, nc, s.nel);
+  const size_t sm = plane_smem<TC>(s);
+  if (s.uni_nx == 48 && s.uni_ny == 64)
+    xy_inv_kernel<real, TZ, TC, MODE, 24, 64><<<g, 256, sm, st>>>(b.d_elems, dst, src, ncols, filt);
+  else
+    xy_inv_kernel<real, TZ, TC, MODE><<<g, 256, sm, st>>>(b.d_elems, dst, src, ncols, filt);
+}
+
 }  // namespace
 
 template <class real, class F>
@@ -271,11 +317,10 @@ void apply_h_prec(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncol
   const int nc = ncols > 0 ? ncols : s.max_m;
   if (s.max_nproj > 0)
     proj_coef_kernel<real><<<dim3(s.max_nproj, 1, s.nel), 128, 0, st>>>(b.d_elems, src, ncols);
-  xy_fwd_kernel<real, F, F><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<F>(s), st>>>(b.d_elems, src, ncols, 0);
-  z_mult_kernel<real, F, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256, zcol_smem<F>(s),
-                                       st>>>(b.d_elems, ncols, nullptr, 0);
-  xy_inv_kernel<real, F, real, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<real>(s), st>>>(
-      b.d_elems, dst, src, ncols, 0);
+  (void)nc;
+  launch_xy_fwd<real, F, F>(b, src, ncols, 0, st);
+  launch_z_mult<real, F, ZM_KINETIC>(b, ncols, nullptr, 0, st);
+  launch_xy_inv<real, F, real, XI_HAMILTONIAN>(b, dst, src, ncols, 0, st);
 }
 
 // fwd64: run the forward transform (passes 1-2) in FP64 with an FP64
@@ -295,19 +340,27 @@ void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int nc
 template <class real>
 void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const double* tkin_override,
                   int ncols, cudaStream_t st, int only_teter_elems) {
-  const BatchShape& s = b.s;
-  const int nc = ncols > 0 ? ncols : s.max_m;
   const int f = only_teter_elems;
-  xy_fwd_kernel<real, real, real><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<real>(s), st>>>(b.d_elems, src,
-                                                                                               ncols, f);
-  z_mult_kernel<real, real, ZM_TETER><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256,
-                                        zcol_smem<real>(s), st>>>(b.d_elems, ncols, tkin_override, f);
-  xy_inv_kernel<real, real, real, XI_PLAIN><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<real>(s), st>>>(
-      b.d_elems, dst, src, ncols, f);
+  launch_xy_fwd<real, real, real>(b, src, ncols, f, st);
+  launch_z_mult<real, real, ZM_TETER>(b, ncols, tkin_override, f, st);
+  launch_xy_inv<real, real, real, XI_PLAIN>(b, dst, src, ncols, f, st);
 }
 
 // Allow the plane and column kernels the full opt-in shared memory once.
 template <class real> static void opt_in_smem_t() {
+  opt_in_dynamic_smem((const void*)xy_fwd_kernel<real, double, double, 24, 64>);
+  opt_in_dynamic_smem((const void*)xy_fwd_kernel<real, real, real, 24, 64>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<real, double, real, XI_HAMILTONIAN, 24, 64>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<real, real, real, XI_HAMILTONIAN, 24, 64>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<real, real, real, XI_PLAIN, 24, 64>);
+  for (int k = 0; k < 2; ++k) {
+    opt_in_dynamic_smem(k ? (const void*)z_mult_kernel<real, double, ZM_KINETIC, 48>
+                          : (const void*)z_mult_kernel<real, double, ZM_KINETIC, 40>);
+    opt_in_dynamic_smem(k ? (const void*)z_mult_kernel<real, real, ZM_KINETIC, 48>
+                          : (const void*)z_mult_kernel<real, real, ZM_KINETIC, 40>);
+    opt_in_dynamic_smem(k ? (const void*)z_mult_kernel<real, real, ZM_TETER, 48>
+                          : (const void*)z_mult_kernel<real, real, ZM_TETER, 40>);
+  }
   opt_in_dynamic_smem((const void*)xy_fwd_kernel<real, double, double>);
   opt_in_dynamic_smem((const void*)xy_fwd_kernel<real, real, real>);
   opt_in_dynamic_smem((const void*)xy_inv_kernel<real, double, real, XI_HAMILTONIAN>);
@@ -339,16 +392,12 @@ template <class real>
 void launch_h_pass(const Batch<real>& b, int pass, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st) {
   using F = real;
   using I = real;
-  const BatchShape& s = b.s;
-  const int nc = ncols > 0 ? ncols : s.max_m;
   if (pass == 0)
-    xy_fwd_kernel<real, F, F><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<F>(s), st>>>(b.d_elems, src, ncols, 0);
+    launch_xy_fwd<real, F, F>(b, src, ncols, 0, st);
   else if (pass == 1)
-    z_mult_kernel<real, F, ZM_KINETIC><<<dim3((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel), 256,
-                                         zcol_smem<F>(s), st>>>(b.d_elems, ncols, nullptr, 0);
+    launch_z_mult<real, F, ZM_KINETIC>(b, ncols, nullptr, 0, st);
   else
-    xy_inv_kernel<real, F, I, XI_HAMILTONIAN><<<dim3(s.max_nz, nc, s.nel), 256, plane_smem<I>(s), st>>>(
-        b.d_elems, dst, src, ncols, 0);
+    launch_xy_inv<real, F, I, XI_HAMILTONIAN>(b, dst, src, ncols, 0, st);
 }
 template void launch_h_pass<double>(const Batch<double>&, int, BRef<double>, BRef<double>, int, cudaStream_t);
 template void launch_h_pass<float>(const Batch<float>&, int, BRef<float>, BRef<float>, int, cudaStream_t);

@@ -31,6 +31,9 @@ struct BatchShape {
   int nel = 0;        // elements in the batch
   int max_nz = 0, max_ny = 0, max_nxh = 0, max_nplane = 0, max_m = 0, max_ng = 0;
   int max_nproj = 0, max_rows_e = 0;
+  // grid shared by every element (0 when the batch mixes grids): selects
+  // FFT kernels specialised for the line lengths at compile time
+  int uni_nx = 0, uni_ny = 0, uni_nz = 0;
 };
 
 template <class real> struct Batch {

@@ -313,6 +313,19 @@ template <class real> struct Wave {
       s.max_ng = std::max(s.max_ng, eh.ng());
       s.max_nproj = std::max(s.max_nproj, (int)eh.pgamma.size());
     }
+    {
+      const dgdft_element_desc& d0 = ctx->el[ids[0]].d;
+      bool uni = true;
+      for (int id : ids) {
+        const dgdft_element_desc& d = ctx->el[id].d;
+        uni = uni && d.nx == d0.nx && d.ny == d0.ny && d.nz == d0.nz;
+      }
+      if (uni) {
+        s.uni_nx = d0.nx;
+        s.uni_ny = d0.ny;
+        s.uni_nz = d0.nz;
+      }
+    }
     rnchunk = nchunk_rows(s.max_ng);
     const size_t tiles = ((s.max_m + 63) / 64) * ((s.max_m + 63) / 64);
     const size_t pcap = (size_t)nel * ((s.max_ng + 2047) / 2048) * 12 * tiles * 4096;
@@ -1269,6 +1282,9 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
     FftPlan p;
     if (d.nx < 4 || d.nx % 2 || !plan_length(d.nx / 2, p) || !plan_length(d.ny, p) || !plan_length(d.nz, p))
       return DGDFT_EINVAL;
+    // one FP64 half-spectrum plane (two buffers) and one z-column tile must
+    // fit a CTA's shared memory
+    if ((long long)(d.nx / 2 + 1) * d.ny > 7000 || d.nz > 400) return DGDFT_EINVAL;
     if (!(d.Lx > 0 && d.Ly > 0 && d.Lz > 0)) return DGDFT_EINVAL;
     if (d.n_keep <= 0 || d.n_keep > d.n_compute) return DGDFT_EINVAL;
     const long long ng = (long long)d.nx * d.ny * d.nz;
