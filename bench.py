@@ -159,10 +159,10 @@ STAGE_PER_ITER = {"xy_fwd": 3, "z_mult": 3, "xy_inv": 3, "gram": 1, "update": 3,
 # 2.07 GHz (the maximum SM clock)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes (read + write) of one element's share of the 12-pair FP32 Gram
-# launch, from the ncu capture summarised in profiles/gram48_config2.md
-# (None when the kernel changed after the capture)
-GRAM_TRAFFIC_PER_ELEMENT = 151.4e6
+# DRAM bytes (read + write) of one element's share of the FP32 stage's
+# tensor-core Gram launch, from the ncu capture summarised in
+# profiles/tcw_gram_config2.md (None when the kernel changed after it)
+GRAM_TRAFFIC_PER_ELEMENT = None
 
 
 def run_ours(args):
@@ -184,7 +184,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
-                    stream=stream.cuda_stream, tc_gram=args.tc_gram, h_fp64_forward=args.fwd64)
+                    stream=stream.cuda_stream, simt_gram=args.simt_gram, h_fp64_forward=args.fwd64)
     dev_x0 = []
     for k, e in enumerate(els):
         B.load_element(ctx, k, e)
@@ -236,15 +236,24 @@ def run_ours(args):
     share = {n: stages[n][0] * STAGE_PER_ITER[n] for n in stages}
     dom = max(share, key=share.get)
     dom_ms, nel, sbytes = stages[dom]
-    if dom == "gram":
-        # the FP32 Gram is bound by the FP32 FMA pipe (SIMT, compensated)
+    if dom == "gram" and args.simt_gram:
+        # the SIMT FP32 Gram is bound by the FP32 FMA pipe (compensated)
         flops = sum(12 * 2.0 * e.m * e.m * e.ng for e in els)
         achieved = flops / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_SIMT_TFLOPS,
-                "traffic": (GRAM_TRAFFIC_PER_ELEMENT * len(els)) if GRAM_TRAFFIC_PER_ELEMENT else None,
-                "kernel": "gram48 (12 Gram blocks of S^T S and (H S)^T S, FP32 stage)",
+                "frac": achieved / FP32_SIMT_TFLOPS, "traffic": None,
+                "kernel": "gram48 (12 Gram blocks of S^T S and (H S)^T S, FP32 stage, SIMT)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+    elif dom == "gram":
+        # the tensor-core Gram: 48 useful flop per byte of FP32 input, far
+        # below the bf16 ridge (~276 flop/B), so HBM bounds it
+        abytes = sum(stage_bytes("gram", e, sbytes) for e in els)
+        achieved = abytes / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": (GRAM_TRAFFIC_PER_ELEMENT * len(els)) if GRAM_TRAFFIC_PER_ELEMENT else None,
+                "kernel": "tcw_gram (tcgen05, 12 Gram blocks of S^T S and (H S)^T S, FP32 stage)",
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
     elif dom == "rayleigh_ritz":
         # FP64 ALU bound: lowest m of a 3m pencil, ~ (3m)^3 (1/3 + 1 + 2/3 + ...) flops
         n3 = (3 * els[0].m) ** 3
@@ -451,8 +460,8 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=3)
-    ap.add_argument("--tc-gram", action="store_true",
-                    help="tcgen05 split-BF16 Gram in the FP32 stage (default: compensated SIMT)")
+    ap.add_argument("--simt-gram", action="store_true",
+                    help="compensated SIMT Gram in the FP32 stage (default: tcgen05 tensor cores)")
     ap.add_argument("--fwd64", type=int, default=0, choices=[0, 1, 2],
                     help="FP64 forward FFT in the FP32 stage's H apply: 1 always, 2 for H X near convergence")
     args = ap.parse_args()

@@ -92,13 +92,12 @@ typedef struct {
   int device;             /* CUDA device ordinal; -1 = current device         */
   int keep_block;         /* 1: keep each converged N_g x m Ritz block on the
                              host after solve (for dgdft_alb_get_block)        */
-  int bulk_kernels;       /* Gram products of the FP32 stage.  0: SIMT FP32
-                             with compensated accumulation (~2e-7 relative);
-                             1: tcgen05 split-BF16 tensor-core kernel where
-                             the shapes allow (3m <= 256): faster per call,
-                             but its FP32 tensor-memory accumulation gives
-                             ~1e-5 relative, so the FP32 stage stalls higher
-                             and leaves more iterations to FP64           */
+  int bulk_kernels;       /* Gram products of the FP32 stage.  0: tcgen05
+                             tensor cores (bf16 hi/lo split, tensor-memory
+                             windows of 256 rows read out into compensated
+                             registers) where 3m <= 144 and N_g % 4 == 0,
+                             else SIMT; 1: SIMT FP32 with compensated
+                             accumulation everywhere                        */
   int h_fp64_forward;     /* FP64 forward FFT in the FP32 stage's H apply
                              (its rounding, amplified by |G|^2/2, sets the
                              stage's residual floor near 2e-6 Ha): 0 never;

@@ -132,7 +132,7 @@ class Context:
 
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
-                 precond_weights=None, tc_gram=False, h_fp64_forward=False):
+                 precond_weights=None, simt_gram=False, h_fp64_forward=False):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -142,7 +142,7 @@ class Context:
         cfg.maxit = maxit
         cfg.check_every = check_every
         cfg.keep_block = int(keep_block)
-        cfg.bulk_kernels = int(tc_gram)
+        cfg.bulk_kernels = int(simt_gram)
         cfg.h_fp64_forward = int(h_fp64_forward)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
         cfg.cuda_stream = stream

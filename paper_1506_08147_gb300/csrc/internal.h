@@ -34,6 +34,7 @@ struct BatchShape {
   // grid shared by every element (0 when the batch mixes grids): selects
   // FFT kernels specialised for the line lengths at compile time
   int uni_nx = 0, uni_ny = 0, uni_nz = 0;
+  bool ng_mult4 = true;  // every element's N_g is a multiple of 4 (16-byte columns)
 };
 
 template <class real> struct Batch {
@@ -153,8 +154,8 @@ std::string cuda_err_string(cudaError_t e);
 }  // namespace dgdft
 
 namespace dgdft {
-// tc_gram.cu: tcgen05 split-bf16 Gram products for the FP32 stage
-size_t tc_gram_smem_bytes(int n_cols);
+// tc_gram.cu: tcgen05 split-bf16 Gram products for the FP32 stage (3m <= 144,
+// N_g % 4 == 0)
 void init_tc_gram_kernel();
 void launch_tc_gram(const Batch<float>& b, int mode, double* partial, size_t partial_cap, cudaStream_t st);
 void launch_tc_gram_ptrs(const Batch<float>& b, const float* u, int p, const float* v, int q, int ng, double* c,

@@ -196,6 +196,13 @@ size_t elem_bytes(const ElemHost& h) {
 
 void default_x0(std::vector<double>& x, int elem);
 
+// The FP32 stage's Gram products run on the tensor cores (the windowed
+// tcgen05 kernel) when selected and the shapes allow: 3m <= 144 columns,
+// N_g a multiple of 4 (16-byte column starts); otherwise the SIMT kernel.
+inline bool tc_ok(const dgdft_alb_config& c, const BatchShape& s) {
+  return c.bulk_kernels == 0 && 3 * s.max_m <= 144 && s.ng_mult4;
+}
+
 template <class real> struct Wave {
   dgdft_alb_ctx* ctx = nullptr;
   std::vector<int> ids;
@@ -312,6 +319,7 @@ template <class real> struct Wave {
       s.max_m = std::max(s.max_m, eh.d.n_compute);
       s.max_ng = std::max(s.max_ng, eh.ng());
       s.max_nproj = std::max(s.max_nproj, (int)eh.pgamma.size());
+      s.ng_mult4 = s.ng_mult4 && (eh.ng() % 4 == 0);
     }
     {
       const dgdft_element_desc& d0 = ctx->el[ids[0]].d;
@@ -618,7 +626,7 @@ template <class real> struct Wave {
   // accumulator (3m <= 256); returns false when the SIMT kernel must run.
   bool tc_gram(int mode, cudaStream_t st) {
     if constexpr (std::is_same<real, float>::value) {
-      if (ctx->cfg.bulk_kernels == 1 && 3 * batch.s.max_m <= 256) {
+      if (tc_ok(ctx->cfg, batch.s)) {
         launch_tc_gram(batch, mode, partial, partial_cap, st);
         return true;
       }
@@ -1162,9 +1170,12 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
     if (mixed) {
       wp->w32.reset(new Wave<float>());
       // Cholesky condition limit of the FP32 stage's pencil: the compensated
-      // SIMT Gram is accurate to ~2e-7 relative and tolerates nearly dependent
-      // [X W P]; the tensor-core Gram (~1e-5) does not
-      const double cond32 = c.bulk_kernels == 1 ? 1e4 : 1e6;
+      // SIMT Gram (~2e-7 relative) tolerates nearly dependent [X W P] up to
+      // 1e6; the tensor-core Gram (bf16 split, a few 1e-8 on one-signed
+      // sums but coarser on cancelling ones) up to 1e5
+      bool tc = c.bulk_kernels == 0;
+      for (int id : ids) tc = tc && 3 * ctx->el[id].d.n_compute <= 144 && ctx->el[id].ng() % 4 == 0;
+      const double cond32 = tc ? 1e5 : 1e6;
       if ((s = wp->w32->build(ctx, ids, cond32)) != DGDFT_OK) return s;
     }
     wp->w64.reset(new Wave<double>());
@@ -1602,7 +1613,7 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
   int* dstate = nullptr;
   const size_t tiles = ((p + 63) / 64) * ((q + 63) / 64);
   bool use_tc = false;
-  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 1 && q <= 256;
+  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 0 && q <= 144 && ng % 4 == 0;
   const size_t pcap = use_tc ? ((size_t)(ng + 2047) / 2048) * ((p + 127) / 128) * 128 * 256
                              : ((size_t)(ng + 2047) / 2048) * tiles * 4096;
   CK(cudaMalloc(&du, sizeof(real) * (size_t)ng * p));

@@ -111,15 +111,15 @@ def test_teter(prec):
 GRAM_KINDS = [(B.DGDFT_PREC_FP64, False), (B.DGDFT_PREC_MIXED, False), (B.DGDFT_PREC_MIXED, True)]
 
 
-@pytest.mark.parametrize("prec,tc", GRAM_KINDS)
-@pytest.mark.parametrize("shape", [(1000, 7, 5), (122880, 48, 48), (70001, 130, 70)])
-def test_gram(prec, tc, shape):
+@pytest.mark.parametrize("prec,simt", GRAM_KINDS)
+@pytest.mark.parametrize("shape", [(1000, 7, 5), (122880, 48, 48), (70001, 130, 70), (4096, 288, 144)])
+def test_gram(prec, simt, shape):
     ng, p, q = shape
     gen = np.random.default_rng(3)
     u = gen.standard_normal((p, ng))
     v = gen.standard_normal((q, ng))
     el = small_kb_element()
-    c = ctx_for(el, prec, tc_gram=tc)
+    c = ctx_for(el, prec, simt_gram=simt)
     got = c.dgdft_alb_gram(u, v)
     ref = u @ v.T
     scale = np.sqrt(ng)  # typical |u_i| |v_j| / sqrt(ng) for random rows
@@ -129,23 +129,27 @@ def test_gram(prec, tc, shape):
     c.close()
 
 
-@pytest.mark.parametrize("tc", [False, True])
-def test_gram_accumulation_one_signed(tc):
+@pytest.mark.parametrize("simt", [False, True])
+@pytest.mark.parametrize("ng,q", [(122880, 48), (122880, 144), (70000, 70)])
+def test_gram_accumulation_one_signed(simt, ng, q):
     """Rows of one sign make every partial sum grow, the worst case for
     accumulation rounding.  Measured against the exact product of the
     FP32-rounded inputs, relative to sum_k |u_k| |v_k|: the compensated SIMT
-    kernel must stay within a few FP32 units over 122880 rows; the
-    tensor-core kernel's FP32 tensor-memory accumulation is bounded by 5e-5."""
-    ng, p = 122880, 48
+    kernel within a few FP32 units, the tensor-core kernel (bf16 split,
+    windowed tensor-memory accumulation; 70000 rows take the SIMT path as the
+    columns are not 16-byte aligned) within 2e-7."""
+    p = 48
     gen = np.random.default_rng(4)
     u = 1.0 + np.abs(gen.standard_normal((p, ng)))
+    v = 1.0 + np.abs(gen.standard_normal((q, ng)))
     u32 = u.astype(np.float32).astype(np.float64)
+    v32 = v.astype(np.float32).astype(np.float64)
     el = small_kb_element()
-    c = ctx_for(el, B.DGDFT_PREC_MIXED, tc_gram=tc)
-    got = c.dgdft_alb_gram(u, u)
-    ref = u32 @ u32.T
+    c = ctx_for(el, B.DGDFT_PREC_MIXED, simt_gram=simt)
+    got = c.dgdft_alb_gram(u, v)
+    ref = u32 @ v32.T
     err = np.max(np.abs(got - ref) / ref)
-    assert err < (5e-5 if tc else 2e-7), err
+    assert err < (2e-8 if simt else 2e-7), err
     c.close()
 
 
