@@ -184,7 +184,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
-                    stream=stream.cuda_stream, simt_gram=args.simt_gram, h_fp64_forward=args.fwd64)
+                    stream=stream.cuda_stream, tc_gram=args.tc_gram, h_fp64_forward=args.fwd64)
     dev_x0 = []
     for k, e in enumerate(els):
         B.load_element(ctx, k, e)
@@ -236,7 +236,7 @@ def run_ours(args):
     share = {n: stages[n][0] * STAGE_PER_ITER[n] for n in stages}
     dom = max(share, key=share.get)
     dom_ms, nel, sbytes = stages[dom]
-    if dom == "gram" and args.simt_gram:
+    if dom == "gram" and not args.tc_gram:
         # the SIMT FP32 Gram is bound by the FP32 FMA pipe (compensated)
         flops = sum(12 * 2.0 * e.m * e.m * e.ng for e in els)
         achieved = flops / (dom_ms / 1e3) / 1e12
@@ -348,6 +348,8 @@ def run_ours(args):
         "eigenpairs_per_step": pairs, "iterations_mean": mean_it,
         "iterations_fp32_mean": float(np.mean(iters32)),
         "elements_needing_fp64_iterations": int(sum(1 for a, b in zip(iters, iters32) if a > b)),
+        "fp64_iterations_max": int(max(a - b for a, b in zip(iters, iters32))),
+        "fp32_restarts": int(sum(r["restarts"] for r in reps)),
         "iterations_max": int(max(iters)) if iters else None,
         "roofline": roof, "stages": stage_report,
         "plain_fp64": plain,
@@ -460,8 +462,8 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=3)
-    ap.add_argument("--simt-gram", action="store_true",
-                    help="compensated SIMT Gram in the FP32 stage (default: tcgen05 tensor cores)")
+    ap.add_argument("--tc-gram", action="store_true",
+                    help="tcgen05 tensor-core Gram in the FP32 stage (default: compensated SIMT)")
     ap.add_argument("--fwd64", type=int, default=0, choices=[0, 1, 2],
                     help="FP64 forward FFT in the FP32 stage's H apply: 1 always, 2 for H X near convergence")
     args = ap.parse_args()

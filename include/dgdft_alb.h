@@ -92,12 +92,15 @@ typedef struct {
   int device;             /* CUDA device ordinal; -1 = current device         */
   int keep_block;         /* 1: keep each converged N_g x m Ritz block on the
                              host after solve (for dgdft_alb_get_block)        */
-  int bulk_kernels;       /* Gram products of the FP32 stage.  0: tcgen05
-                             tensor cores (bf16 hi/lo split, tensor-memory
-                             windows of 256 rows read out into compensated
-                             registers) where 3m <= 144 and N_g % 4 == 0,
-                             else SIMT; 1: SIMT FP32 with compensated
-                             accumulation everywhere                        */
+  int bulk_kernels;       /* Gram products of the FP32 stage.  0 (default):
+                             SIMT FP32 with compensated accumulation, pencil
+                             condition limit 1e6; 1: tcgen05 tensor cores
+                             (bf16 hi/lo split, tensor-memory windows of 256
+                             rows read out into compensated registers) where
+                             3m <= 144 and N_g % 4 == 0, else SIMT; limit
+                             1e5 (faster, but its ~2^-17 split error per
+                             product leaves some elements dropping P for
+                             hundreds of iterations)                       */
   int h_fp64_forward;     /* FP64 forward FFT in the FP32 stage's H apply
                              (its rounding, amplified by |G|^2/2, sets the
                              stage's residual floor near 2e-6 Ha): 0 never;
@@ -121,6 +124,9 @@ typedef struct {
                               graphs of this element's wave (both stages);
                               set-up, verify and orthonormalisation kernels
                               outside the graphs are not counted           */
+  int restarts;      /* FP32-stage restarts: every Rayleigh-Ritz level failed,
+                        so X was perturbed and P dropped (also counted in
+                        `fallbacks`)                                        */
 } dgdft_solve_report;
 
 /* Fill cfg with defaults: FP64, Teter, tol 1e-6, maxit 400, check_every 4. */

@@ -40,7 +40,8 @@ class dgdft_alb_config(C.Structure):
 class dgdft_solve_report(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("max_resid", C.c_double),
                 ("fallbacks", C.c_int), ("wave", C.c_int), ("seconds", C.c_double),
-                ("iterations_bulk", C.c_int), ("resid_bulk", C.c_double), ("graph_kernels", C.c_longlong)]
+                ("iterations_bulk", C.c_int), ("resid_bulk", C.c_double), ("graph_kernels", C.c_longlong),
+                ("restarts", C.c_int)]
 
 
 _P = C.c_void_p
@@ -132,7 +133,7 @@ class Context:
 
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
-                 precond_weights=None, simt_gram=False, h_fp64_forward=False):
+                 precond_weights=None, tc_gram=False, h_fp64_forward=False):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -142,7 +143,7 @@ class Context:
         cfg.maxit = maxit
         cfg.check_every = check_every
         cfg.keep_block = int(keep_block)
-        cfg.bulk_kernels = int(simt_gram)
+        cfg.bulk_kernels = int(tc_gram)
         cfg.h_fp64_forward = int(h_fp64_forward)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
         cfg.cuda_stream = stream
@@ -208,7 +209,7 @@ class Context:
         return st, [dict(status=r.status, iterations=r.iterations, max_resid=r.max_resid,
                          fallbacks=r.fallbacks, wave=r.wave, seconds=r.seconds,
                          iterations_bulk=r.iterations_bulk, resid_bulk=r.resid_bulk,
-                         graph_kernels=r.graph_kernels) for r in reps]
+                         graph_kernels=r.graph_kernels, restarts=r.restarts) for r in reps]
 
     def dgdft_alb_get_basis(self, elem, phi=None, eig=None, resid=None):
         d = self.descs[elem]

@@ -740,7 +740,43 @@ __global__ void iter_finish_kernel(const ElemDev<real>* __restrict__ elems, int 
   int* st = elems[i].state;
   if (!st[ST_ACTIVE]) return;
   st[ST_PARITY] ^= 1;
-  if (set_p) st[ST_HAS_P] = 1;
+  if (st[ST_RESTART]) {
+    // restarted this iteration: P' = 0, the next pencil is [X W]
+    st[ST_HAS_P] = 0;
+    st[ST_RESTART] = 0;
+  } else if (set_p) {
+    st[ST_HAS_P] = 1;
+  }
+}
+
+// Uniform in [-1, 1) from a 32-bit integer mix of (a, b).
+__device__ __forceinline__ float mix_unit(unsigned a, unsigned b) {
+  unsigned h = a * 0x9E3779B1u + b * 0x85EBCA77u;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+}
+
+// Restart of an element whose Rayleigh-Ritz found no usable pencil (X' = X
+// was written): add a seeded perturbation of relative size RESTART_AMP to
+// every column of X' (entries of a unit column are ~1/sqrt(N_g)), which
+// makes nearly dependent columns independent again; H X' is computed from
+// the perturbed block, and P is dropped for the next iteration.
+constexpr float RESTART_AMP = 0.03f;
+
+template <class real>
+__global__ void restart_kernel(const ElemDev<real>* __restrict__ elems) {
+  const ElemDev<real>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE] || !e.state[ST_RESTART]) return;
+  real* x = next_blk(e, BX);
+  const size_t n = (size_t)e.ng * e.m;
+  const float amp = RESTART_AMP * rsqrtf((float)e.ng);
+  const unsigned seed = 0x51EDu * (unsigned)(blockIdx.z + 1) + 0x2545F491u * (unsigned)e.state[ST_NRESTART];
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] += (real)(amp * mix_unit((unsigned)i, seed));
 }
 
 }  // namespace
@@ -820,6 +856,11 @@ void launch_theta(const Batch<real>& b, int nchunk, int mode, cudaStream_t st) {
 }
 
 template <class real>
+void launch_restart(const Batch<real>& b, cudaStream_t st) {
+  restart_kernel<real><<<dim3(64, 1, b.s.nel), 256, 0, st>>>(b.d_elems);
+}
+
+template <class real>
 void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st) {
   iter_finish_kernel<real><<<(b.s.nel + 127) / 128, 128, 0, st>>>(b.d_elems, b.s.nel, set_p);
 }
@@ -833,6 +874,7 @@ void init_blas_kernels() { opt_in_dynamic_smem((const void*)tsmm_rows_kernel); }
   template void launch_residual<real>(const Batch<real>&, int, cudaStream_t);                        \
   template void launch_post_residual<real>(const Batch<real>&, int, int, cudaStream_t);              \
   template void launch_iter_finish<real>(const Batch<real>&, int, cudaStream_t);                    \
+  template void launch_restart<real>(const Batch<real>&, cudaStream_t);                              \
   template void launch_theta<real>(const Batch<real>&, int, int, cudaStream_t);                     \
   template void launch_shift<real>(const Batch<real>&, cudaStream_t);
 DGDFT_INST(double)

@@ -46,7 +46,9 @@ enum {
   ST_CONVERGED = 5, // 1 once max residual <= tol
   ST_FALLBACK = 6,  // Rayleigh-Ritz retries without P
   ST_TETER = 7,     // 1: precondition with Teter (the learned network's fallback)
-  STATE_WORDS = 8
+  ST_RESTART = 8,   // 1: Rayleigh-Ritz found no usable pencil; X is perturbed and P dropped
+  ST_NRESTART = 9,  // restarts taken (bounded per solve)
+  STATE_WORDS = 10
 };
 enum { ERR_CHOL = 1, ERR_NONFINITE = 2, ERR_EIG = 4 };
 

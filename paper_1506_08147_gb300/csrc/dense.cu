@@ -335,7 +335,11 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
     // the last LOBPCG resort (X alone) takes any positive-definite B: its
     // Rayleigh-Ritz re-orthonormalises a block that has drifted
     const bool last_resort = T.mode == RR_LOBPCG && n == m;
-    if (!fail && !last_resort && (pmax / pmin) * (pmax / pmin) > T.cond_max) fail = true;
+    const double cond_lim = last_resort ? (T.restart_max > 0 ? 1e6 : 1e300) : T.cond_max;
+    if (!fail && (pmax / pmin) * (pmax / pmin) > cond_lim) fail = true;
+    // read before the barrier: thread 0 updates the count after it
+    const bool can_restart =
+        T.mode == RR_LOBPCG && T.restart_max > 0 && T.state && T.state[ST_NRESTART] < T.restart_max;
     __syncthreads();
     if (fail) {
       if (T.mode == RR_LOBPCG && n == 3 * m) {
@@ -352,6 +356,23 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict
         dropped = true;
         __syncthreads();
         continue;
+      }
+      if (can_restart) {
+        // no usable pencil, not even X alone: keep X (Y = [I; 0]) and let
+        // the restart step perturb it and drop P (Ritz values unchanged)
+        const int nr = 3 * m;
+        for (int idx = tid; idx < nr * m; idx += nt) {
+          const int r = idx % nr, c = idx / nr;
+          const double y = (r == c) ? 1.0 : 0.0;
+          T.Y[r + (size_t)c * T.ldy] = y;
+          if (T.Yf) T.Yf[r + (size_t)c * T.ldy] = (float)y;
+        }
+        if (tid == 0) {
+          T.state[ST_RESTART] = 1;
+          T.state[ST_NRESTART] += 1;
+          T.state[ST_FALLBACK] += 1;
+        }
+        return;
       }
       if (tid == 0 && T.state) {
         T.state[ST_ERROR] |= ERR_CHOL;
@@ -622,7 +643,11 @@ __global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __re
     // the last LOBPCG resort (X alone) takes any positive-definite B: its
     // Rayleigh-Ritz re-orthonormalises a block that has drifted
     const bool last_resort = T.mode == RR_LOBPCG && n == m;
-    if (!fail && !last_resort && (pmax / pmin) * (pmax / pmin) > T.cond_max) fail = true;
+    const double cond_lim = last_resort ? (T.restart_max > 0 ? 1e6 : 1e300) : T.cond_max;
+    if (!fail && (pmax / pmin) * (pmax / pmin) > cond_lim) fail = true;
+    // read before the barrier: thread 0 updates the count after it
+    const bool can_restart =
+        T.mode == RR_LOBPCG && T.restart_max > 0 && T.state && T.state[ST_NRESTART] < T.restart_max;
     __syncthreads();
     if (fail) {
       if (T.mode == RR_LOBPCG && n == 3 * m) {
@@ -639,6 +664,23 @@ __global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __re
         dropped = true;
         __syncthreads();
         continue;
+      }
+      if (can_restart) {
+        // no usable pencil, not even X alone: keep X (Y = [I; 0]) and let
+        // the restart step perturb it and drop P (Ritz values unchanged)
+        const int nr = 3 * m;
+        for (int idx = tid; idx < nr * m; idx += nt) {
+          const int r = idx % nr, c = idx / nr;
+          const double y = (r == c) ? 1.0 : 0.0;
+          T.Y[r + (size_t)c * T.ldy] = y;
+          if (T.Yf) T.Yf[r + (size_t)c * T.ldy] = (float)y;
+        }
+        if (tid == 0) {
+          T.state[ST_RESTART] = 1;
+          T.state[ST_NRESTART] += 1;
+          T.state[ST_FALLBACK] += 1;
+        }
+        return;
       }
       if (tid == 0 && T.state) {
         T.state[ST_ERROR] |= ERR_CHOL;

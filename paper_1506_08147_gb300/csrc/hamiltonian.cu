@@ -12,6 +12,8 @@
 //            the kinetic symbol |G|^2/2 (or the Teter factor), inverse FFT;
 //   xy_inv : inverse y, c2r along x, fused epilogue adding V_eff psi and the
 //            projector scatter for the points of plane z.
+#include <type_traits>
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -269,6 +271,7 @@ template <class T> size_t zcol_smem(const BatchShape& s) {
 
 // Pass launchers: on a batch whose elements share one grid of a supported
 // shape (the monolayer extended elements, 48 x 64 x 40 and 48 x 64 x 48) the
+// register-resident FP32 kernels of fft_mono.cu, or (FP64 arithmetic) these
 // kernels specialised for those line lengths at compile time; otherwise the
 // kernels that follow each element's runtime plan.
 template <class real, class TC, class TZ>
@@ -276,6 +279,9 @@ void launch_xy_fwd(const Batch<real>& b, BRef<real> src, int ncols, int filt, cu
   const BatchShape& s = b.s;
   const int nc = ncols > 0 ? ncols : s.max_m;
   const dim3 g(s.max_nz, nc, s.nel);
+  if constexpr (std::is_same_v<real, float> && std::is_same_v<TC, float> && std::is_same_v<TZ, float>) {
+    if (mono_grid(s)) return mono_xy_fwd(b, src, ncols, filt, st);
+  }
   const size_t sm = plane_smem<TC>(s);
   if (s.uni_nx == 48 && s.uni_ny == 64)
     xy_fwd_kernel<real, TC, TZ, 24, 64><<<g, 256, sm, st>>>(b.d_elems, src, ncols, filt);
@@ -287,6 +293,9 @@ template <class real, class TZ, int MODE>
 void launch_z_mult(const Batch<real>& b, int ncols, const double* tkin_override, int filt, cudaStream_t st) {
   const BatchShape& s = b.s;
   const int nc = ncols > 0 ? ncols : s.max_m;
+  if constexpr (std::is_same_v<real, float> && std::is_same_v<TZ, float>) {
+    if (mono_grid(s)) return mono_z(b, MODE, ncols, tkin_override, filt, st);
+  }
   const dim3 g((s.max_nplane + ZTILE - 1) / ZTILE, nc, s.nel);
   const size_t sm = zcol_smem<TZ>(s);
   if (s.uni_nz == 40)
@@ -302,6 +311,9 @@ void launch_xy_inv(const Batch<real>& b, BRef<real> dst, BRef<real> src, int nco
   const BatchShape& s = b.s;
   const int nc = ncols > 0 ? ncols : s.max_m;
   const dim3 g(s.max_nz, nc, s.nel);
+  if constexpr (std::is_same_v<real, float> && std::is_same_v<TZ, float> && std::is_same_v<TC, float>) {
+    if (mono_grid(s)) return mono_xy_inv(b, MODE, dst, src, ncols, filt, st);
+  }
   const size_t sm = plane_smem<TC>(s);
   if (s.uni_nx == 48 && s.uni_ny == 64)
     xy_inv_kernel<real, TZ, TC, MODE, 24, 64><<<g, 256, sm, st>>>(b.d_elems, dst, src, ncols, filt);
@@ -382,6 +394,7 @@ void opt_in_dynamic_smem(const void* kernel) {
 }
 
 void init_hamiltonian_kernels() {
+  init_mono_kernels();
   opt_in_smem_t<double>();
   opt_in_smem_t<float>();
 }

@@ -54,6 +54,16 @@ void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const do
                   int ncols, cudaStream_t st, int only_teter_elems = 0);
 
 void init_hamiltonian_kernels();
+
+// fft_mono.cu: the three H / Teter passes for FP32 batches on one monolayer
+// grid (48 x 64 x 40 or 48 x 64 x 48, mono_grid); all three run together
+// (their half spectrum is ordered [z][kx][y])
+bool mono_grid(const BatchShape& s);
+void mono_xy_fwd(const Batch<float>& b, BRef<float> src, int ncols, int filt, cudaStream_t st);
+void mono_z(const Batch<float>& b, int mode, int ncols, const double* tkin_override, int filt, cudaStream_t st);
+void mono_xy_inv(const Batch<float>& b, int mode, BRef<float> dst, BRef<float> xsrc, int ncols, int filt,
+                 cudaStream_t st);
+void init_mono_kernels();
 void opt_in_dynamic_smem(const void* kernel);
 template <class real>
 void launch_proj_coef(const Batch<real>& b, BRef<real> src, int ncols, cudaStream_t st);
@@ -115,6 +125,8 @@ template <class real>
 void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStream_t st);
 // End of an iteration: flip the X/P/HX/HP buffers, mark P valid.
 template <class real>
+void launch_restart(const Batch<real>& b, cudaStream_t st);
+template <class real>
 void launch_iter_finish(const Batch<real>& b, int set_p, cudaStream_t st);
 // FP32 stage: HX -= d X, HP -= d P for elements whose shift moved by d this
 // iteration (post_residual decides d).
@@ -140,6 +152,11 @@ struct RRTask {
   double* work;      // rr_work_doubles(n_max, m) doubles
   int* state;        // element state words, or nullptr
   double cond_max;   // Cholesky condition limit on the equilibrated B
+  // > 0 (LOBPCG tasks of the FP32 stage): when no pencil passes, not even X
+  // alone (condition limit 1e6 there), Y = [I; 0] keeps X and the element is
+  // marked for a restart (ST_RESTART) instead of failing, at most this many
+  // times; 0: such an element fails with ERR_CHOL
+  int restart_max;
 };
 size_t rr_work_doubles(int n_max, int m);
 // n_max, m_max bound the tasks' pencil sizes; pencils that fit use the

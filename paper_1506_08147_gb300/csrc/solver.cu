@@ -200,7 +200,7 @@ void default_x0(std::vector<double>& x, int elem);
 // tcgen05 kernel) when selected and the shapes allow: 3m <= 144 columns,
 // N_g a multiple of 4 (16-byte column starts); otherwise the SIMT kernel.
 inline bool tc_ok(const dgdft_alb_config& c, const BatchShape& s) {
-  return c.bulk_kernels == 0 && 3 * s.max_m <= 144 && s.ng_mult4;
+  return c.bulk_kernels == 1 && 3 * s.max_m <= 144 && s.ng_mult4;
 }
 
 template <class real> struct Wave {
@@ -304,7 +304,10 @@ template <class real> struct Wave {
     return DGDFT_OK;
   }
 
-  dgdft_status build(dgdft_alb_ctx* c, const std::vector<int>& elem_ids, double cond_max) {
+  int restart_max = 0;  // see RRTask::restart_max (FP32 waves)
+
+  dgdft_status build(dgdft_alb_ctx* c, const std::vector<int>& elem_ids, double cond_max, int restarts = 0) {
+    restart_max = restarts;
     ctx = c;
     ids = elem_ids;
     const int nel = (int)ids.size();
@@ -376,7 +379,9 @@ template <class real> struct Wave {
       t.work = E.rr_work;
       t.state = E.state;
       t.cond_max = cond_max;
+      t.restart_max = 0;
       rr_init[i] = t;
+      t.restart_max = restarts;
       t.mode = RR_LOBPCG;
       rr_lob[i] = t;
     }
@@ -752,6 +757,7 @@ template <class real> struct Wave {
         // whose rounding grows with |Y| |HW| once [X W P] is nearly dependent
         // and would leave HX inconsistent with X (the residual then stalls or
         // diverges near 1e-4 Ha)
+        if (restart_max > 0) launch_restart<real>(batch, st);
         launch_apply_h<real>(batch, bref<real>(BX, 1), bref<real>(BHX, 1), 0, st, fwd64() || hx64);
       }
       TsmmJob<real> u;
@@ -1105,7 +1111,8 @@ dgdft_status copy_block_to(Wave<real>& w, int i, Wave<double>& dst, int di, cuda
 
 dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, double seconds,
                          const std::vector<int>& extra_iters, const std::vector<int>& extra_fb,
-                         const std::vector<double>& bulk_res, long long graph_kernels) {
+                         const std::vector<double>& bulk_res, long long graph_kernels,
+                         const std::vector<int>& restarts) {
   for (size_t i = 0; i < w.ids.size(); ++i) {
     ElemHost& eh = ctx->el[w.ids[i]];
     const ElemDev<double>& E = w.h[i];
@@ -1141,6 +1148,7 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     eh.rep.wave = wave_idx;
     eh.rep.seconds = seconds;
     eh.rep.graph_kernels = graph_kernels;
+    eh.rep.restarts = restarts.empty() ? 0 : restarts[i];
     eh.rep.status = (sw[ST_ERROR] != 0 || s != DGDFT_OK) ? DGDFT_ENOTCONV
                                                          : (mx <= ctx->cfg.tol ? DGDFT_OK : DGDFT_ENOTCONV);
     eh.solved = true;
@@ -1173,10 +1181,12 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
       // SIMT Gram (~2e-7 relative) tolerates nearly dependent [X W P] up to
       // 1e6; the tensor-core Gram (bf16 split, a few 1e-8 on one-signed
       // sums but coarser on cancelling ones) up to 1e5
-      bool tc = c.bulk_kernels == 0;
+      bool tc = c.bulk_kernels == 1;
       for (int id : ids) tc = tc && 3 * ctx->el[id].d.n_compute <= 144 && ctx->el[id].ng() % 4 == 0;
       const double cond32 = tc ? 1e5 : 1e6;
-      if ((s = wp->w32->build(ctx, ids, cond32)) != DGDFT_OK) return s;
+      // an element whose pencil fails at every level is restarted (X
+      // perturbed, P dropped) up to 8 times before it is left to the FP64 stage
+      if ((s = wp->w32->build(ctx, ids, cond32, 8)) != DGDFT_OK) return s;
     }
     wp->w64.reset(new Wave<double>());
     if ((s = wp->w64->build(ctx, ids, 1e14)) != DGDFT_OK) return s;
@@ -1191,7 +1201,7 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
   Wave<double>& w64 = *wp->w64;
   w64.graph_kernels = 0;
   if (wp->w32) wp->w32->graph_kernels = 0;
-  std::vector<int> it32, fb32;
+  std::vector<int> it32, fb32, rs32;
   std::vector<double> res32;
   dgdft_status s;
   if (mixed) {
@@ -1224,14 +1234,15 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
       copy_block_to<float>(w32, (int)i, w64, (int)i, ctx->stream);
       it32.push_back(w32.h_state[i * STATE_WORDS + ST_ITER]);
       fb32.push_back(w32.h_state[i * STATE_WORDS + ST_FALLBACK]);
+      rs32.push_back(w32.h_state[i * STATE_WORDS + ST_NRESTART]);
     }
     CK(cudaStreamSynchronize(ctx->stream));
     if (std::getenv("DGDFT_TRACE")) {
       for (size_t i = 0; i < ids.size(); ++i) {
         const int* sw = &w32.h_state[i * STATE_WORDS];
-        if (sw[ST_ERROR] || sw[ST_ITER] < 50)
-          std::fprintf(stderr, "[dgdft] fp32 element %zu: iter %d err %d fallback %d converged %d\n", i, sw[ST_ITER],
-                       sw[ST_ERROR], sw[ST_FALLBACK], sw[ST_CONVERGED]);
+        if (sw[ST_ERROR] || sw[ST_ITER] < 50 || sw[ST_NRESTART])
+          std::fprintf(stderr, "[dgdft] fp32 element %zu: iter %d err %d fallback %d restarts %d converged %d\n", i,
+                       sw[ST_ITER], sw[ST_ERROR], sw[ST_FALLBACK], sw[ST_NRESTART], sw[ST_CONVERGED]);
       }
     }
     auto t1 = std::chrono::steady_clock::now();
@@ -1257,7 +1268,7 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const long long gk = w64.graph_kernels + (wp->w32 ? wp->w32->graph_kernels : 0);
-  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32, gk);
+  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32, gk, rs32);
 }
 
 }  // namespace
@@ -1613,7 +1624,7 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
   int* dstate = nullptr;
   const size_t tiles = ((p + 63) / 64) * ((q + 63) / 64);
   bool use_tc = false;
-  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 0 && q <= 144 && ng % 4 == 0;
+  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 1 && q <= 144 && ng % 4 == 0;
   const size_t pcap = use_tc ? ((size_t)(ng + 2047) / 2048) * ((p + 127) / 128) * 128 * 256
                              : ((size_t)(ng + 2047) / 2048) * tiles * 4096;
   CK(cudaMalloc(&du, sizeof(real) * (size_t)ng * p));

@@ -38,6 +38,17 @@ def cfg2_element(k=0):
     return synth.config2(elems=[k])[0]
 
 
+def element_of(which):
+    # small: general kernels (runtime plans); cfg2 / cfg5: the monolayer
+    # grids 48 x 64 x 40 and 48 x 64 x 48 (register-resident FP32 kernels in
+    # the mixed form, compile-time FP64 kernels otherwise)
+    if which == "small":
+        return small_kb_element()
+    if which == "cfg2":
+        return cfg2_element()
+    return synth.config5(elems=[100])[0]
+
+
 def ctx_for(el, prec, **kw):
     c = B.Context([B.element_dict(el)], precision=prec, **kw)
     B.load_element(c, 0, el)
@@ -51,9 +62,9 @@ def rel(a, b):
 # ------------------------------------------------------------ H apply
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("which", ["small", "cfg2"])
+@pytest.mark.parametrize("which", ["small", "cfg2", "cfg5"])
 def test_apply_h(prec, which):
-    el = small_kb_element() if which == "small" else cfg2_element()
+    el = element_of(which)
     gen = np.random.default_rng(1)
     k = 5 if which == "small" else 3
     x = gen.standard_normal((k, el.ng))
@@ -68,10 +79,12 @@ def test_apply_h(prec, which):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_apply_h_plane_wave_eigenvalue(prec):
+@pytest.mark.parametrize("grid,freq", [((16, 12, 10), (8, 2, 5)), ((48, 64, 40), (24, 7, 20)),
+                                       ((48, 64, 48), (5, 32, 24))])
+def test_apply_h_plane_wave_eigenvalue(prec, grid, freq):
     # a single plane wave cos(G.r) in a potential-free box: H x = |G|^2/2 x,
     # including the Nyquist frequency (|n/2|, the reading of the planewave set)
-    el = synth.random_element(9, 1, (16, 12, 10), 4, J=4, m=4)
+    el = synth.random_element(9, 1, grid, 4, J=4, m=4)
     el.veff[:] = 0.0
     el.proj_row_ptr = np.zeros(1, np.int64)
     el.proj_idx = np.zeros(0, np.int32)
@@ -79,7 +92,7 @@ def test_apply_h_plane_wave_eigenvalue(prec):
     el.proj_gamma = np.zeros(0)
     coords = [np.arange(n) * l / n for n, l in zip(el.n, el.L)]
     zz, yy, xx = np.meshgrid(coords[2], coords[1], coords[0], indexing="ij")
-    gx, gy, gz = (2 * np.pi * 8 / el.L[0], 2 * np.pi * 2 / el.L[1], 2 * np.pi * 5 / el.L[2])
+    gx, gy, gz = (2 * np.pi * f / l for f, l in zip(freq, el.L))
     x = np.cos(gx * xx + gy * yy + gz * zz).reshape(1, -1)
     c = ctx_for(el, prec)
     got = c.dgdft_alb_apply_h(0, x)
@@ -92,8 +105,9 @@ def test_apply_h_plane_wave_eigenvalue(prec):
 # ------------------------------------------------------------- Teter
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_teter(prec):
-    el = small_kb_element()
+@pytest.mark.parametrize("which", ["small", "cfg2", "cfg5"])
+def test_teter(prec, which):
+    el = element_of(which)
     gen = np.random.default_rng(2)
     x = gen.standard_normal((4, el.ng))
     r = gen.standard_normal((4, el.ng))
@@ -108,18 +122,18 @@ def test_teter(prec):
 
 # -------------------------------------------------------------- Gram
 
-GRAM_KINDS = [(B.DGDFT_PREC_FP64, False), (B.DGDFT_PREC_MIXED, False), (B.DGDFT_PREC_MIXED, True)]
+GRAM_KINDS = [(B.DGDFT_PREC_FP64, False), (B.DGDFT_PREC_MIXED, False), (B.DGDFT_PREC_MIXED, True)]  # (prec, tc)
 
 
-@pytest.mark.parametrize("prec,simt", GRAM_KINDS)
+@pytest.mark.parametrize("prec,tc", GRAM_KINDS)
 @pytest.mark.parametrize("shape", [(1000, 7, 5), (122880, 48, 48), (70001, 130, 70), (4096, 288, 144)])
-def test_gram(prec, simt, shape):
+def test_gram(prec, tc, shape):
     ng, p, q = shape
     gen = np.random.default_rng(3)
     u = gen.standard_normal((p, ng))
     v = gen.standard_normal((q, ng))
     el = small_kb_element()
-    c = ctx_for(el, prec, simt_gram=simt)
+    c = ctx_for(el, prec, tc_gram=tc)
     got = c.dgdft_alb_gram(u, v)
     ref = u @ v.T
     scale = np.sqrt(ng)  # typical |u_i| |v_j| / sqrt(ng) for random rows
@@ -129,9 +143,9 @@ def test_gram(prec, simt, shape):
     c.close()
 
 
-@pytest.mark.parametrize("simt", [False, True])
+@pytest.mark.parametrize("tc", [False, True])
 @pytest.mark.parametrize("ng,q", [(122880, 48), (122880, 144), (70000, 70)])
-def test_gram_accumulation_one_signed(simt, ng, q):
+def test_gram_accumulation_one_signed(tc, ng, q):
     """Rows of one sign make every partial sum grow, the worst case for
     accumulation rounding.  Measured against the exact product of the
     FP32-rounded inputs, relative to sum_k |u_k| |v_k|: the compensated SIMT
@@ -145,11 +159,11 @@ def test_gram_accumulation_one_signed(simt, ng, q):
     u32 = u.astype(np.float32).astype(np.float64)
     v32 = v.astype(np.float32).astype(np.float64)
     el = small_kb_element()
-    c = ctx_for(el, B.DGDFT_PREC_MIXED, simt_gram=simt)
+    c = ctx_for(el, B.DGDFT_PREC_MIXED, tc_gram=tc)
     got = c.dgdft_alb_gram(u, v)
     ref = u32 @ v32.T
     err = np.max(np.abs(got - ref) / ref)
-    assert err < (2e-8 if simt else 2e-7), err
+    assert err < (2e-7 if tc else 2e-8), err
     c.close()
 
 
