@@ -95,6 +95,10 @@ template <class real> struct ElemDev {
   const int* s_ptr;         // n_sup + 1 into (s_proj, s_gv)
   const int* s_proj;
   const real* s_gv;         // gamma_p * v_p(point)
+  // the same per point padded to 4 nonzeros (zero weight, projector 0), when
+  // no point has more than 4; nullptr otherwise
+  const int* s_proj4;
+  const real* s_gv4;
   real* Ccoef;              // n_proj x m projector coefficients (column j contiguous)
   // blocks
   real* blk[NBLK][2];       // [sel][buffer]; single-buffered blocks use [0]

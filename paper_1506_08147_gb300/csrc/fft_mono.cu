@@ -332,23 +332,80 @@ __global__ void __launch_bounds__(MTHREADS, 3)
   float4* out4 = reinterpret_cast<float4*>(resolve(e, dst) + off);
   if (MODE == XI_HAMILTONIAN) {
     if (e.n_sup > 0) {
-      // Kleinman-Bylander scatter: each support point of the 4 planes once
-      const float* cj = e.Ccoef + (size_t)j * e.n_proj;
-      const int sb = e.s_plane[z0], se = e.s_plane[z0 + MPL];
-      for (int s = sb + threadIdx.x; s < se; s += MTHREADS) {
-        float acc = 0.f;
-        for (int qq = e.s_ptr[s]; qq < e.s_ptr[s + 1]; ++qq) acc += e.s_gv[qq] * cj[e.s_proj[qq]];
-        int pz = 0;
-        while (pz + 1 < MPL && s >= e.s_plane[z0 + pz + 1]) ++pz;
-        const int o = e.s_off[s];
-        const int yy = o / MX, xx = o - yy * MX;
-        rows[(pz * MY + yy) * MROW + xx] += acc;
+      // Kleinman-Bylander scatter: each support point of the 4 planes once.
+      // The coefficients of column j go to the shared-memory tail past the
+      // rows (free once the spectrum is consumed); each thread takes SU
+      // points at a time and their nonzeros four at a time, so the loads of
+      // different points are in flight together.
+      constexpr int CTAIL = (int)(MSMEM / sizeof(float)) - MPL * MY * MROW;
+      constexpr int SU = 4;
+      float* ctail = rows + MPL * MY * MROW;
+      const float* cg = e.Ccoef + (size_t)j * e.n_proj;
+      const bool staged = e.n_proj <= CTAIL;
+      if (staged)
+        for (int q = threadIdx.x; q < e.n_proj; q += MTHREADS) ctail[q] = cg[q];
+      const float* cj = staged ? ctail : cg;
+      const int sb = e.s_plane[z0], b1 = e.s_plane[z0 + 1], b2 = e.s_plane[z0 + 2], b3 = e.s_plane[z0 + 3];
+      const int se = e.s_plane[z0 + MPL];
+      __syncthreads();
+      for (int s0 = sb + threadIdx.x; s0 < se; s0 += SU * MTHREADS) {
+        int qb[SU], qe[SU], o[SU];
+        float acc[SU];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          const int s = s0 + u * MTHREADS;
+          const bool in = s < se;
+          qb[u] = (in && !e.s_gv4) ? e.s_ptr[s] : 0;
+          qe[u] = (in && !e.s_gv4) ? e.s_ptr[s + 1] : 0;
+          o[u] = in ? e.s_off[s] : 0;
+          acc[u] = 0.f;
+        }
+        if (e.s_gv4) {
+          // at most 4 nonzeros per point, padded with zero weights
+#pragma unroll
+          for (int u = 0; u < SU; ++u) {
+            const int s = s0 + u * MTHREADS;
+            if (s < se) {
+              const float4 g = __ldg(reinterpret_cast<const float4*>(e.s_gv4) + s);
+              const int4 pj = __ldg(reinterpret_cast<const int4*>(e.s_proj4) + s);
+              float a = g.x * cj[pj.x];
+              a += g.y * cj[pj.y];
+              a += g.z * cj[pj.z];
+              a += g.w * cj[pj.w];
+              acc[u] = a;
+            }
+          }
+        } else {
+          for (int k0 = 0;; k0 += 4) {
+            bool more = false;
+#pragma unroll
+            for (int u = 0; u < SU; ++u) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const int q = qb[u] + k0 + k;
+                if (q < qe[u]) acc[u] += e.s_gv[q] * cj[e.s_proj[q]];
+              }
+              more |= qb[u] + k0 + 4 < qe[u];
+            }
+            if (!more) break;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          const int s = s0 + u * MTHREADS;
+          if (s < se) {
+            const int pz = (s >= b1) + (s >= b2) + (s >= b3);
+            const int yy = o[u] / MX, xx = o[u] - yy * MX;
+            rows[(pz * MY + yy) * MROW + xx] += acc[u];
+          }
+        }
       }
       __syncthreads();
     }
     const float4* x4 = reinterpret_cast<const float4*>(resolve(e, xsrc) + off);
     const float4* v4 = reinterpret_cast<const float4*>(e.V + (size_t)z0 * MPLANE);
     const float sg = (float)e.sigma[0];  // 0 except in the shifted FP32 stage
+#pragma unroll 4
     for (int t = threadIdx.x; t < MPL * MPLANE / 4; t += MTHREADS) {
       const int row = t / 12, q = t - row * 12;
       const float4 kv = *reinterpret_cast<const float4*>(rows + row * MROW + 4 * q);

@@ -183,6 +183,8 @@ size_t elem_bytes(const ElemHost& h) {
   s.add(sizeof(float) * (nxh + d.ny + d.nz + 3 * m * m) + 4 * ALIGN);
   s.add(sizeof(int) * (np + 1) + sizeof(int) * nnz + sizeof(real) * nnz + sizeof(double) * np);
   s.add(sizeof(int) * (d.nz + 1) + sizeof(int) * (3 * nnz + 1) + sizeof(real) * nnz);
+  s.add(sizeof(int) * 4 * nnz);   // padded per-point copy (at most 4 nnz per point,
+  s.add(sizeof(real) * 4 * nnz);  // so at most nnz points)
   s.add(sizeof(real) * np * m);
   for (int i = 0; i < 10; ++i) s.add(sizeof(real) * ng * m);
   s.add(sizeof(double2) * nspec * m);
@@ -520,6 +522,25 @@ template <class real> struct Wave {
       E.s_ptr = dsptr;
       E.s_proj = dspj;
       E.s_gv = dsg;
+      // fixed-width copy (4 per point) when every point has at most 4
+      int kmax = 0;
+      for (size_t p = 0; p + 1 < s_ptr.size(); ++p) kmax = std::max(kmax, s_ptr[p + 1] - s_ptr[p]);
+      E.s_proj4 = nullptr;
+      E.s_gv4 = nullptr;
+      if (kmax <= 4 && !s_off.empty()) {
+        std::vector<int> pj4(4 * s_off.size(), 0);
+        std::vector<real> gv4(4 * s_off.size(), (real)0);
+        for (size_t p = 0; p + 1 < s_ptr.size(); ++p)
+          for (int q = s_ptr[p]; q < s_ptr[p + 1]; ++q) {
+            pj4[4 * p + (q - s_ptr[p])] = s_proj[q];
+            gv4[4 * p + (q - s_ptr[p])] = s_gv[q];
+          }
+        int* d4p = take<int>(pj4.size());
+        real* d4g = take<real>(gv4.size());
+        if (put(d4p, pj4.data(), pj4.size()) || put(d4g, gv4.data(), gv4.size())) return DGDFT_ECUDA;
+        E.s_proj4 = d4p;
+        E.s_gv4 = d4g;
+      }
       E.Ccoef = take<real>((size_t)np * m);
     }
     for (int b = 0; b < NBLK; ++b) {
@@ -747,11 +768,9 @@ template <class real> struct Wave {
       launch_tsmm<real>(batch, t, st);
       t.from2 = -1;
       if (std::is_same<real, double>::value) {
-        t.in[0] = bref<real>(BHX);
-        t.in[1] = bref<real>(BHW);
-        t.in[2] = bref<real>(BHP);
-        t.out = bref<real>(BHX, 1);
-        launch_tsmm<real>(batch, t, st);
+        // FP64: H X' by the FFT (three FP64 passes cost less than the FP64
+        // block update [HX HW HP] Y on the FP64 pipe)
+        launch_apply_h<real>(batch, bref<real>(BX, 1), bref<real>(BHX, 1), 0, st, false);
       } else {
         // FP32: HX is recomputed as H X rather than updated as [HX HW HP] Y,
         // whose rounding grows with |Y| |HW| once [X W P] is nearly dependent
@@ -768,11 +787,16 @@ template <class real> struct Wave {
       u.yrow[1] = 2;
       u.needs_p[1] = 1;
       u.out = bref<real>(BP, 1);
-      if (!f32) launch_tsmm<real>(batch, u, st);
-      u.in[0] = bref<real>(BHW);
-      u.in[1] = bref<real>(BHP);
-      u.out = bref<real>(BHP, 1);
-      launch_tsmm<real>(batch, u, st);
+      if (!f32) {
+        launch_tsmm<real>(batch, u, st);
+        // H P' by the FFT, as H X'
+        launch_apply_h<real>(batch, bref<real>(BP, 1), bref<real>(BHP, 1), 0, st, false);
+      } else {
+        u.in[0] = bref<real>(BHW);
+        u.in[1] = bref<real>(BHP);
+        u.out = bref<real>(BHP, 1);
+        launch_tsmm<real>(batch, u, st);
+      }
     }
     launch_iter_finish<real>(batch, 1, st);
   }
@@ -871,6 +895,7 @@ template <class real> struct Wave {
     const int nel = (int)ids.size();
     const int every = std::max(1, ctx->cfg.check_every);
     std::vector<std::vector<double>> hist(nel);
+    std::vector<int> seen_restarts(nel, 0);
     std::vector<double> resbuf;
     int launched = 0;
     dgdft_status rs = DGDFT_OK;
@@ -908,6 +933,12 @@ template <class real> struct Wave {
         if (!sw[ST_ACTIVE]) continue;
         any = true;
         if (stall_window > 0) {
+          if (sw[ST_NRESTART] != seen_restarts[i]) {
+            // restarted since the last poll: the perturbed block climbs back
+            // from a higher residual, which is not a stall
+            seen_restarts[i] = sw[ST_NRESTART];
+            hist[i].clear();
+          }
           resbuf.resize(h[i].J);
           ce = ctx_copy(ctx, resbuf.data(), h[i].res, sizeof(double) * h[i].J, cudaMemcpyDeviceToHost);
           if (ce != cudaSuccess) break;
