@@ -15,6 +15,8 @@ whose FP64 residual is <= 1e-6 Ha.
             (set_potential/set_projectors/set_initial, solve, get_basis);
   plain   : the plain FP64 GPU solver on the same inputs (comparator);
   roofline: the dominant kernel, timed live by dgdft_alb_time_stage;
+  scf_step: SCF-mode steps (dgdft_alb_scf_step: 3 LOBPCG iterations from the
+            previous ALBs under an updated potential), device-timed;
   cpu_baseline: the FP64 CPU oracle on a bounded sample.
 
 --impl reference times the oracle alone (the reference arm).
@@ -159,9 +161,12 @@ STAGE_PER_ITER = {"xy_fwd": 3, "z_mult": 3, "xy_inv": 3, "gram": 1, "update": 3,
 # 2.07 GHz (the maximum SM clock)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes (read + write) of one element's share of the FP32 stage's
-# tensor-core Gram launch, from the ncu capture summarised in
-# profiles/tcw_gram_config2.md (None when the kernel changed after it)
+# DRAM bytes (read + write) of one element's share of the FP32 stage's Gram
+# launch (12 pairs), from the ncu captures summarised in profiles/: the
+# compensated SIMT kernel (gram48_config2.md, a 2-element launch scaled per
+# element: the blocks of every element are read once, so traffic grows with
+# the element count); the tensor-core kernel has no full-launch capture
+GRAM48_TRAFFIC_PER_ELEMENT = 151.4e6
 GRAM_TRAFFIC_PER_ELEMENT = None
 
 
@@ -241,7 +246,7 @@ def run_ours(args):
         flops = sum(12 * 2.0 * e.m * e.m * e.ng for e in els)
         achieved = flops / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_SIMT_TFLOPS, "traffic": None,
+                "frac": achieved / FP32_SIMT_TFLOPS, "traffic": GRAM48_TRAFFIC_PER_ELEMENT * len(els),
                 "kernel": "gram48 (12 Gram blocks of S^T S and (H S)^T S, FP32 stage, SIMT)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
     elif dom == "gram":
@@ -275,6 +280,43 @@ def run_ours(args):
                                            / (stages[n][0] / 1e3) / 1e9, 1)
                                      if stage_bytes(n, els[0], stages[n][2]) else None)}
                     for n in stages}
+
+    # SCF-mode steps (the paper's per-SCF-step workload): 3 LOBPCG iterations
+    # from the previous ALBs under an updated potential, all elements; the
+    # potential alternates between V_eff and V_eff + a smooth seeded field of
+    # 0.02 Ha (uploaded outside the timed region)
+    scf = None
+    if args.scf_steps > 0:
+        pots = []
+        for k, e in enumerate(els):
+            gen = np.random.default_rng([2, 9, k])
+            nx, ny, nz = e.n
+            z, y, x = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx, indexing="ij")
+            ph = gen.uniform(0, 2 * np.pi, size=3)
+            dv = 0.02 * (np.cos(2 * np.pi * x + ph[0]) * np.cos(2 * np.pi * y + ph[1]) +
+                         np.sin(2 * np.pi * z + ph[2]))
+            v0 = np.ascontiguousarray(e.veff.reshape(-1), np.float64)
+            pots.append((np.ascontiguousarray(v0 + dv.reshape(-1)), v0))
+        times, resmax = [], []
+        for step in range(args.scf_steps + 1):
+            for k in range(len(els)):
+                ctx.dgdft_alb_set_potential(k, pots[k][step % 2])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st_s, reps_s = ctx.dgdft_alb_scf_step(3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if step > 0:  # the first step is a warm-up
+                times.append(e0.elapsed_time(e1))
+                resmax.append(max(r["max_resid"] for r in reps_s))
+        t_scf = float(np.mean(times))
+        alb = sum(e.J for e in els)
+        scf = {"iterations_per_step": 3, "ms_per_step": round(t_scf, 2), "steps": len(times),
+               "alb_per_s": alb / (t_scf / 1e3), "alb_per_step": alb,
+               "max_resid_after_step": float(max(resmax)),
+               "potential_update": "alternating V_eff and V_eff + 0.02 Ha smooth field"}
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -351,7 +393,7 @@ def run_ours(args):
         "fp64_iterations_max": int(max(a - b for a, b in zip(iters, iters32))),
         "fp32_restarts": int(sum(r["restarts"] for r in reps)),
         "iterations_max": int(max(iters)) if iters else None,
-        "roofline": roof, "stages": stage_report,
+        "roofline": roof, "stages": stage_report, "scf_step": scf,
         "plain_fp64": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
         "cpu_baseline": cpu,
@@ -459,6 +501,7 @@ def main():
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--stage-reps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--scf-steps", type=int, default=4, help="timed SCF-mode steps (0: skip)")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=3)

@@ -168,6 +168,22 @@ dgdft_status dgdft_alb_set_initial(dgdft_alb_ctx* ctx, int elem, const double* x
  * element has no potential. */
 dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem);
 
+/* One SCF step of ALB generation (Sec. II.B: in each SCF iteration the ALBs
+ * are refined by a few LOBPCG iterations that start from those of the
+ * previous SCF step, under the updated V_eff set by dgdft_alb_set_potential).
+ * Every element runs exactly n_iter (>= 1) LOBPCG iterations, in the
+ * context's precision (FP32 storage and arithmetic with an FP64
+ * Rayleigh-Ritz in the mixed form), from the block given by
+ * dgdft_alb_set_initial since the last solve or step, else from its own
+ * Ritz block of the previous solve or step; then the FP64 residual check,
+ * restriction to E_K and orthonormalisation as in dgdft_alb_solve.  There is
+ * no tolerance: a report's status is DGDFT_OK unless the element failed, and
+ * max_resid is the FP64 residual after the step.  The workload must fit one
+ * memory-admission wave (it stays resident between steps; changing the
+ * projectors drops the resident blocks).  Returns DGDFT_ESTATE when an
+ * element has no block to start from, DGDFT_EINVAL for n_iter < 1. */
+dgdft_status dgdft_alb_scf_step(dgdft_alb_ctx* ctx, int n_iter, dgdft_solve_report* per_elem);
+
 /* Copy out element `elem`'s ALBs: phi is n_E x J column-major (n_E = product
  * of e_hi - e_lo, points ordered x fastest within E_K), eig the J lowest
  * eigenvalues (Ha), resid their residuals (Ha).  Any pointer may be NULL.

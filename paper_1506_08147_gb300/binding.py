@@ -53,6 +53,7 @@ _SIGS = {
     "dgdft_alb_set_projectors": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
     "dgdft_alb_set_initial": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "dgdft_alb_solve": (C.c_int, [_P, C.POINTER(dgdft_solve_report)]),
+    "dgdft_alb_scf_step": (C.c_int, [_P, C.c_int, C.POINTER(dgdft_solve_report)]),
     "dgdft_alb_get_basis": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_last_error": (C.c_char_p, [_P]),
     "dgdft_alb_destroy": (None, [_P]),
@@ -201,15 +202,26 @@ class Context:
         p, dev = _ptr(x0)
         self._check(self.lib.dgdft_alb_set_initial(self.h, elem, p, dev), "set_initial")
 
+    @staticmethod
+    def _reports(reps):
+        return [dict(status=r.status, iterations=r.iterations, max_resid=r.max_resid,
+                     fallbacks=r.fallbacks, wave=r.wave, seconds=r.seconds,
+                     iterations_bulk=r.iterations_bulk, resid_bulk=r.resid_bulk,
+                     graph_kernels=r.graph_kernels, restarts=r.restarts) for r in reps]
+
     def dgdft_alb_solve(self, check=False):
         reps = (dgdft_solve_report * self.n)()
         st = self.lib.dgdft_alb_solve(self.h, reps)
         if st not in (DGDFT_OK, DGDFT_ENOTCONV) or (check and st != DGDFT_OK):
             self._check(st, "solve")
-        return st, [dict(status=r.status, iterations=r.iterations, max_resid=r.max_resid,
-                         fallbacks=r.fallbacks, wave=r.wave, seconds=r.seconds,
-                         iterations_bulk=r.iterations_bulk, resid_bulk=r.resid_bulk,
-                         graph_kernels=r.graph_kernels, restarts=r.restarts) for r in reps]
+        return st, self._reports(reps)
+
+    def dgdft_alb_scf_step(self, n_iter=3):
+        reps = (dgdft_solve_report * self.n)()
+        st = self.lib.dgdft_alb_scf_step(self.h, int(n_iter), reps)
+        if st not in (DGDFT_OK, DGDFT_ENOTCONV):
+            self._check(st, "scf_step")
+        return st, self._reports(reps)
 
     def dgdft_alb_get_basis(self, elem, phi=None, eig=None, resid=None):
         d = self.descs[elem]

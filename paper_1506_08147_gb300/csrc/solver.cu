@@ -47,6 +47,7 @@ struct ElemHost {
   int proj_version = 0;
   double* d_x0 = nullptr;    // N_g x m
   bool has_x0 = false;
+  bool x0_fresh = false;     // set_initial since the last solve / SCF step
   // results, on the device after a solve
   double* d_phi = nullptr;   // n_E x J
   double* d_eig = nullptr;   // J
@@ -576,15 +577,19 @@ template <class real> struct Wave {
     return DGDFT_OK;
   }
 
-  // Working-precision copies of V_eff and X0 from the resident FP64 inputs.
-  dgdft_status load_inputs() {
+  // Working-precision copies of V_eff and X0 from the resident FP64 inputs;
+  // warm (SCF steps): an FP64 device block per element to start from instead.
+  dgdft_status load_inputs(const std::vector<const double*>* warm = nullptr) {
     dgdft_status ps = load_potential();
     if (ps != DGDFT_OK) return ps;
     for (size_t i = 0; i < ids.size(); ++i) {
       ElemHost& eh = ctx->el[ids[i]];
       ElemDev<real>& E = h[i];
       const size_t n = (size_t)E.ng * E.m;
-      if (eh.has_x0) {
+      if (warm) {
+        const double* src = (*warm)[i];
+        if ((const void*)src != (const void*)E.blk[BX][0]) launch_convert<double, real>(src, E.blk[BX][0], n, ctx->stream);
+      } else if (eh.has_x0) {
         launch_convert<double, real>(eh.d_x0, E.blk[BX][0], n, ctx->stream);
       } else {
         std::vector<double> x0(n);
@@ -1029,107 +1034,164 @@ void default_x0(std::vector<double>& x, int elem) {
   }
 }
 
-// FP64 restriction + orthonormalisation of one element's converged block.
-dgdft_status alb_orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, int i, const double* x, int J,
-                                double* phi_dev_out) {
-  ElemHost& eh = ctx->el[w.ids[i]];
-  const int ne = eh.ne();
+// FP64 restriction + orthonormalisation (Sec. II.A; Eq. orthonormal) of the
+// blocks xs[q] (first J[q] columns) of wave elements idx[q] into out[q]:
+// Phi~ = X restricted to E_K; G = Phi~^T Phi~; the pencil I y = th G y gives
+// Y1 with Y1^T G Y1 = I, U = Phi~ Y1 (the left singular vectors up to
+// rotation); one more pass on U restores orthonormality to rounding; scaled
+// by 1/sqrt(dV).  Everything is enqueued on the context's stream with one
+// scratch allocation and one synchronisation for all listed elements;
+// rank_ok[q] is false where the restricted block is rank deficient.
+dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vector<int>& idx,
+                            const std::vector<const double*>& xs, const std::vector<int>& Js,
+                            const std::vector<double*>& out, std::vector<char>& rank_ok) {
   cudaStream_t st = ctx->stream;
-  // scratch: phi_t, U (ne x J), G, G2, Aid, Adiag, Y1, Y2 (J x J), theta, rr work, task
-  const size_t jj = (size_t)J * J;
-  const size_t nbytes = sizeof(double) * (2 * (size_t)ne * J + 6 * jj + J + rr_work_doubles(J, J)) +
-                        2 * sizeof(RRTask) + 16 * ALIGN;
+  const size_t nq = idx.size();
+  rank_ok.assign(nq, 0);
+  if (nq == 0) return DGDFT_OK;
+  int Jmax = 1;
+  size_t nemax = 1;
+  for (size_t q = 0; q < nq; ++q) {
+    Jmax = std::max(Jmax, Js[q]);
+    nemax = std::max(nemax, (size_t)ctx->el[w.ids[idx[q]]].ne());
+  }
+  const size_t jj = (size_t)Jmax * Jmax;
+  // per element: phi_t, U (ne x J), G, G2, Y1, Y2, I, diag(1..J) (J x J),
+  // theta, Rayleigh-Ritz work; then the two task arrays and the checks, so
+  // that each Rayleigh-Ritz phase is one launch over all elements
+  const size_t per = 2 * nemax * Jmax + 6 * jj + Jmax + rr_work_doubles(Jmax, Jmax);
+  const size_t nbytes = sizeof(double) * (per * nq + nq) + 2 * nq * sizeof(RRTask) + (10 * nq + 16) * ALIGN;
   void* base = nullptr;
   CK(cudaMalloc(&base, nbytes));
   std::unique_ptr<void, decltype(&cudaFree)> guard(base, &cudaFree);
   Arena a;
   a.base = (char*)base;
   a.cap = nbytes;
-  double* phit = (double*)a.take(sizeof(double) * ne * J);
-  double* U = (double*)a.take(sizeof(double) * ne * J);
-  double* G = (double*)a.take(sizeof(double) * jj);
-  double* G2 = (double*)a.take(sizeof(double) * jj);
-  double* Aid = (double*)a.take(sizeof(double) * jj);
-  double* Adg = (double*)a.take(sizeof(double) * jj);
-  double* Y1 = (double*)a.take(sizeof(double) * jj);
-  double* Y2 = (double*)a.take(sizeof(double) * jj);
-  double* th = (double*)a.take(sizeof(double) * J);
-  double* work = (double*)a.take(sizeof(double) * rr_work_doubles(J, J));
-  RRTask* dt = (RRTask*)a.take(2 * sizeof(RRTask));
-  std::vector<double> id(jj, 0.0), dg(jj, 0.0);
-  for (int q = 0; q < J; ++q) {
-    id[q + (size_t)q * J] = 1.0;
-    dg[q + (size_t)q * J] = 1.0 + q;
+  struct Slot {
+    double *phit, *U, *G, *G2, *Y1, *Y2, *mats, *th, *work;
+  };
+  std::vector<Slot> sl(nq);
+  for (size_t q = 0; q < nq; ++q) {
+    Slot& z = sl[q];
+    z.phit = (double*)a.take(sizeof(double) * nemax * Jmax);
+    z.U = (double*)a.take(sizeof(double) * nemax * Jmax);
+    z.G = (double*)a.take(sizeof(double) * jj);
+    z.G2 = (double*)a.take(sizeof(double) * jj);
+    z.Y1 = (double*)a.take(sizeof(double) * jj);
+    z.Y2 = (double*)a.take(sizeof(double) * jj);
+    z.mats = (double*)a.take(sizeof(double) * 2 * jj);
+    z.th = (double*)a.take(sizeof(double) * Jmax);
+    z.work = (double*)a.take(sizeof(double) * rr_work_doubles(Jmax, Jmax));
   }
-  CK(ctx_copy(ctx, Aid, id.data(), sizeof(double) * jj, cudaMemcpyHostToDevice));
-  CK(ctx_copy(ctx, Adg, dg.data(), sizeof(double) * jj, cudaMemcpyHostToDevice));
-  RRTask t[2]{};
-  for (int q = 0; q < 2; ++q) {
-    t[q].A = q ? Adg : Aid;
-    t[q].B = q ? G2 : G;
-    t[q].ld = J;
-    t[q].mode = RR_FIXED;
-    t[q].n_fixed = J;
-    t[q].m = J;
-    t[q].Y = q ? Y2 : Y1;
-    t[q].ldy = J;
-    t[q].theta = th;
-    t[q].work = work;
-    t[q].state = nullptr;
-    t[q].cond_max = 1e30;
+  double* chk = (double*)a.take(sizeof(double) * nq);
+  RRTask* dt = (RRTask*)a.take(2 * nq * sizeof(RRTask));  // [0, nq): first pass, [nq, 2nq): second
+  if (!chk || !dt || !sl.back().work) return ctx->fail(DGDFT_ENOMEM, "orthonormalisation scratch");
+  std::vector<double> hm(2 * jj * nq, 0.0);
+  std::vector<RRTask> ht(2 * nq);
+  for (size_t q = 0; q < nq; ++q) {
+    const int J = Js[q];
+    double* id = hm.data() + 2 * jj * q;
+    double* dg = id + jj;
+    for (int c = 0; c < J; ++c) {
+      id[c + (size_t)c * J] = 1.0;
+      dg[c + (size_t)c * J] = 1.0 + c;
+    }
+    for (int k = 0; k < 2; ++k) {
+      RRTask& t = ht[k * nq + q];
+      t = RRTask{};
+      t.A = sl[q].mats + (k ? jj : 0);
+      t.B = k ? sl[q].G2 : sl[q].G;
+      t.ld = J;
+      t.mode = RR_FIXED;
+      t.n_fixed = J;
+      t.m = J;
+      t.Y = k ? sl[q].Y2 : sl[q].Y1;
+      t.ldy = J;
+      t.theta = sl[q].th;
+      t.work = sl[q].work;
+      t.state = nullptr;
+      t.cond_max = 1e30;
+    }
+    CK(cudaMemcpyAsync(sl[q].mats, id, sizeof(double) * 2 * jj, cudaMemcpyHostToDevice, st));
   }
-  CK(ctx_copy(ctx, dt, t, sizeof(t), cudaMemcpyHostToDevice));
-  // single-element view of the wave, element marked active for the step
-  Batch<double> one;
-  one.d_elems = w.d_elems + i;
-  one.s = w.batch.s;
-  one.s.nel = 1;
-  int act = 1;
-  CK(ctx_copy(ctx, w.h[i].state + ST_ACTIVE, &act, sizeof(int), cudaMemcpyHostToDevice));
-  const dgdft_element_desc& d = eh.d;
-  launch_restrict<double>(x, eh.ng(), d.nx, d.ny, d.e_lo, d.e_hi, J, phit, st);
-  GramJob<double> g;
-  g.npairs = 1;
-  g.a[0] = bptr<double>(phit);
-  g.b[0] = bptr<double>(phit);
-  g.needs_p[0] = 0;
-  g.out_id[0] = OUT_PTR;
-  g.brow[0] = g.bcol[0] = 0;
-  g.ncols_a = g.ncols_b = J;
-  g.rows = ne;
-  g.ld_in = ne;
-  g.ld_out = J;
-  g.out_ptr = G;
-  launch_gram<double>(one, g, w.partial, w.partial_cap, st);
-  launch_rr(dt, 1, st, J, J);
-  TsmmJob<double> u;
-  u.nin = 1;
-  u.in[0] = bptr<double>(phit);
-  u.y_id = Y_PTR;
-  u.y_ptr = Y1;
-  u.ldy = J;
-  u.ncols = J;
-  u.rows = ne;
-  u.ld_in = ne;
-  u.out = bptr<double>(U);
-  launch_tsmm<double>(one, u, st);
-  g.a[0] = bptr<double>(U);
-  g.b[0] = bptr<double>(U);
-  g.out_ptr = G2;
-  launch_gram<double>(one, g, w.partial, w.partial_cap, st);
-  launch_rr(dt + 1, 1, st, J, J);
-  u.in[0] = bptr<double>(U);
-  u.y_ptr = Y2;
-  u.out = bptr<double>(phi_dev_out);
-  launch_tsmm<double>(one, u, st);
-  launch_scale(phi_dev_out, (size_t)ne * J, 1.0 / std::sqrt(eh.dv()), st);
+  CK(cudaMemcpyAsync(dt, ht.data(), sizeof(RRTask) * ht.size(), cudaMemcpyHostToDevice, st));
+  // the single-element views below run only on active elements
+  const int one_word = 1, zero_word = 0;
+  for (size_t q = 0; q < nq; ++q)
+    CK(cudaMemcpyAsync(w.h[idx[q]].state + ST_ACTIVE, &one_word, sizeof(int), cudaMemcpyHostToDevice, st));
+  auto view = [&](size_t q) {
+    Batch<double> one;
+    one.d_elems = w.d_elems + idx[q];
+    one.s = w.batch.s;
+    one.s.nel = 1;
+    return one;
+  };
+  auto gram = [&](size_t q, const double* v, double* g_out) {
+    const int J = Js[q], ne = ctx->el[w.ids[idx[q]]].ne();
+    GramJob<double> g;
+    g.npairs = 1;
+    g.a[0] = bptr<double>(const_cast<double*>(v));
+    g.b[0] = bptr<double>(const_cast<double*>(v));
+    g.needs_p[0] = 0;
+    g.out_id[0] = OUT_PTR;
+    g.brow[0] = g.bcol[0] = 0;
+    g.ncols_a = g.ncols_b = J;
+    g.rows = ne;
+    g.ld_in = ne;
+    g.ld_out = J;
+    g.out_ptr = g_out;
+    launch_gram<double>(view(q), g, w.partial, w.partial_cap, st);
+  };
+  auto apply = [&](size_t q, const double* v, const double* y, double* dst) {
+    const int J = Js[q], ne = ctx->el[w.ids[idx[q]]].ne();
+    TsmmJob<double> u;
+    u.nin = 1;
+    u.in[0] = bptr<double>(const_cast<double*>(v));
+    u.y_id = Y_PTR;
+    u.y_ptr = const_cast<double*>(y);
+    u.ldy = J;
+    u.ncols = J;
+    u.rows = ne;
+    u.ld_in = ne;
+    u.out = bptr<double>(dst);
+    launch_tsmm<double>(view(q), u, st);
+  };
+  // Phi~ and G = Phi~^T Phi~ for every element, then one Rayleigh-Ritz launch
+  for (size_t q = 0; q < nq; ++q) {
+    const ElemHost& eh = ctx->el[w.ids[idx[q]]];
+    const dgdft_element_desc& d = eh.d;
+    launch_restrict<double>(xs[q], eh.ng(), d.nx, d.ny, d.e_lo, d.e_hi, Js[q], sl[q].phit, st);
+    gram(q, sl[q].phit, sl[q].G);
+  }
+  launch_rr(dt, (int)nq, st, Jmax, Jmax);
+  // U = Phi~ Y1 and its Gram, second Rayleigh-Ritz launch
+  for (size_t q = 0; q < nq; ++q) {
+    apply(q, sl[q].phit, sl[q].Y1, sl[q].U);
+    gram(q, sl[q].U, sl[q].G2);
+  }
+  launch_rr(dt + nq, (int)nq, st, Jmax, Jmax);
+  for (size_t q = 0; q < nq; ++q) {
+    const ElemHost& eh = ctx->el[w.ids[idx[q]]];
+    apply(q, sl[q].U, sl[q].Y2, out[q]);
+    launch_scale(out[q], (size_t)eh.ne() * Js[q], 1.0 / std::sqrt(eh.dv()), st);
+    CK(cudaMemcpyAsync(chk + q, sl[q].th, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  for (size_t q = 0; q < nq; ++q)
+    CK(cudaMemcpyAsync(w.h[idx[q]].state + ST_ACTIVE, &zero_word, sizeof(int), cudaMemcpyHostToDevice, st));
+  std::vector<double> hchk(nq);
+  CK(cudaMemcpyAsync(hchk.data(), chk, sizeof(double) * nq, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
-  double chk = 0.0;
-  CK(ctx_copy(ctx, &chk, th, sizeof(double), cudaMemcpyDeviceToHost));
-  act = 0;
-  CK(ctx_copy(ctx, w.h[i].state + ST_ACTIVE, &act, sizeof(int), cudaMemcpyHostToDevice));
-  if (!std::isfinite(chk)) return ctx->fail(DGDFT_ENOTCONV, "orthonormalisation: restricted block is rank deficient");
+  for (size_t q = 0; q < nq; ++q) rank_ok[q] = std::isfinite(hchk[q]) ? 1 : 0;
+  return DGDFT_OK;
+}
+
+dgdft_status alb_orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, int i, const double* x, int J,
+                                double* phi_dev_out) {
+  std::vector<char> ok;
+  dgdft_status s = orthonormalise(ctx, w, {i}, {x}, {J}, {phi_dev_out}, ok);
+  if (s != DGDFT_OK) return s;
+  if (!ok[0]) return ctx->fail(DGDFT_ENOTCONV, "orthonormalisation: restricted block is rank deficient");
   return DGDFT_OK;
 }
 
@@ -1143,22 +1205,38 @@ dgdft_status copy_block_to(Wave<real>& w, int i, Wave<double>& dst, int di, cuda
 dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, double seconds,
                          const std::vector<int>& extra_iters, const std::vector<int>& extra_fb,
                          const std::vector<double>& bulk_res, long long graph_kernels,
-                         const std::vector<int>& restarts) {
-  for (size_t i = 0; i < w.ids.size(); ++i) {
+                         const std::vector<int>& restarts, bool scf = false) {
+  const size_t nel = w.ids.size();
+  std::vector<int> idx(nel), Js(nel);
+  std::vector<const double*> xs(nel);
+  std::vector<double*> outs(nel);
+  for (size_t i = 0; i < nel; ++i) {
     ElemHost& eh = ctx->el[w.ids[i]];
-    const ElemDev<double>& E = w.h[i];
-    const int* sw = &w.h_state[i * STATE_WORDS];
-    const int J = E.J, m = E.m, ne = eh.ne();
+    const int J = w.h[i].J, ne = eh.ne();
     if (!eh.d_phi) {
       CK(cudaMalloc(&eh.d_phi, sizeof(double) * (size_t)ne * J));
       CK(cudaMalloc(&eh.d_eig, sizeof(double) * J));
       CK(cudaMalloc(&eh.d_res, sizeof(double) * J));
     }
-    const double* x = w.current_x((int)i);
-    dgdft_status s = alb_orthonormalise(ctx, w, (int)i, x, J, eh.d_phi);
-    if (s != DGDFT_OK && s != DGDFT_ENOTCONV) return s;
-    CK(cudaMemcpyAsync(eh.d_eig, E.theta, sizeof(double) * J, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(eh.d_res, E.res, sizeof(double) * J, cudaMemcpyDeviceToDevice, ctx->stream));
+    idx[i] = (int)i;
+    Js[i] = J;
+    xs[i] = w.current_x((int)i);
+    outs[i] = eh.d_phi;
+    CK(cudaMemcpyAsync(eh.d_eig, w.h[i].theta, sizeof(double) * J, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(eh.d_res, w.h[i].res, sizeof(double) * J, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  std::vector<char> rank_ok;
+  {
+    dgdft_status so = orthonormalise(ctx, w, idx, xs, Js, outs, rank_ok);
+    if (so != DGDFT_OK) return so;
+  }
+  for (size_t i = 0; i < nel; ++i) {
+    ElemHost& eh = ctx->el[w.ids[i]];
+    const ElemDev<double>& E = w.h[i];
+    const int* sw = &w.h_state[i * STATE_WORDS];
+    const int J = E.J, m = E.m;
+    const double* x = xs[i];
+    const dgdft_status s = rank_ok[i] ? DGDFT_OK : DGDFT_ENOTCONV;
     eh.eig.resize(J);
     eh.resid.resize(J);
     CK(ctx_copy(ctx, eh.eig.data(), E.theta, sizeof(double) * J, cudaMemcpyDeviceToHost));
@@ -1171,7 +1249,10 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     }
     double mx = 0.0;
     for (double r : eh.resid) mx = std::max(mx, r);
-    eh.rep.iterations = sw[ST_ITER] + (extra_iters.empty() ? 0 : extra_iters[i]);
+    // (an SCF step's FP64 stage is only the residual check, whose pass counts
+    // as one in the FP64 wave's iteration word)
+    eh.rep.iterations = (scf && !extra_iters.empty()) ? extra_iters[i]
+                                                      : sw[ST_ITER] + (extra_iters.empty() ? 0 : extra_iters[i]);
     eh.rep.fallbacks = sw[ST_FALLBACK] + (extra_fb.empty() ? 0 : extra_fb[i]);
     eh.rep.iterations_bulk = extra_iters.empty() ? 0 : extra_iters[i];
     eh.rep.resid_bulk = bulk_res.empty() ? 0.0 : bulk_res[i];
@@ -1180,8 +1261,10 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     eh.rep.seconds = seconds;
     eh.rep.graph_kernels = graph_kernels;
     eh.rep.restarts = restarts.empty() ? 0 : restarts[i];
+    // an SCF step has no tolerance: OK unless the element failed
     eh.rep.status = (sw[ST_ERROR] != 0 || s != DGDFT_OK) ? DGDFT_ENOTCONV
-                                                         : (mx <= ctx->cfg.tol ? DGDFT_OK : DGDFT_ENOTCONV);
+                    : (scf || mx <= ctx->cfg.tol)     ? DGDFT_OK
+                                                      : DGDFT_ENOTCONV;
     eh.solved = true;
   }
   return DGDFT_OK;
@@ -1194,12 +1277,12 @@ struct WavePair {
 };
 void free_wave_pair(void* p) { delete static_cast<WavePair*>(p); }
 
-dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wave_idx, bool keep) {
-  auto t0 = std::chrono::steady_clock::now();
+// The FP32 and FP64 waves of `ids`: the resident pair when keep and one is
+// cached, else a new pair (cached when keep).
+dgdft_status get_waves(dgdft_alb_ctx* ctx, const std::vector<int>& ids, bool keep, WavePair*& wp,
+                       std::unique_ptr<WavePair>& owned) {
   const dgdft_alb_config& c = ctx->cfg;
   const bool mixed = c.precision == DGDFT_PREC_MIXED;
-  WavePair* wp = nullptr;
-  std::unique_ptr<WavePair> owned;
   if (keep && ctx->cache) {
     wp = static_cast<WavePair*>(ctx->cache);
   } else {
@@ -1228,6 +1311,19 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
       ctx->cache_proj_version.clear();
       for (const ElemHost& eh : ctx->el) ctx->cache_proj_version.push_back(eh.proj_version);
     }
+  }
+  return DGDFT_OK;
+}
+
+dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wave_idx, bool keep) {
+  auto t0 = std::chrono::steady_clock::now();
+  const dgdft_alb_config& c = ctx->cfg;
+  const bool mixed = c.precision == DGDFT_PREC_MIXED;
+  WavePair* wp = nullptr;
+  std::unique_ptr<WavePair> owned;
+  {
+    dgdft_status s = get_waves(ctx, ids, keep, wp, owned);
+    if (s != DGDFT_OK) return s;
   }
   Wave<double>& w64 = *wp->w64;
   w64.graph_kernels = 0;
@@ -1300,6 +1396,99 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const long long gk = w64.graph_kernels + (wp->w32 ? wp->w32->graph_kernels : 0);
   return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32, gk, rs32);
+}
+
+// One SCF step for a resident single-wave workload (Sec. II.B: in every SCF
+// iteration the ALBs are refined by a few LOBPCG iterations that start from
+// those of the previous SCF step, under the updated potential).  Each element
+// starts from the block given by set_initial since the last solve or step,
+// else from its resident block of the previous solve or step; exactly n_iter
+// iterations run in the context's precision (FP32 in the mixed form), with no
+// tolerance, then the FP64 residual check, restriction and orthonormalisation.
+dgdft_status scf_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int n_iter) {
+  auto t0 = std::chrono::steady_clock::now();
+  const bool mixed = ctx->cfg.precision == DGDFT_PREC_MIXED;
+  WavePair* resident = static_cast<WavePair*>(ctx->cache);
+  std::vector<const double*> warm(ids.size(), nullptr);
+  for (size_t i = 0; i < ids.size(); ++i) {
+    const ElemHost& eh = ctx->el[ids[i]];
+    // a resident wave pair was made by a solve or step over every element
+    if (eh.x0_fresh) warm[i] = eh.d_x0;
+    else if (resident) warm[i] = resident->w64->current_x((int)i);
+    else return ctx->fail(DGDFT_ESTATE, "SCF step: no block to start from (solve first, or set_initial)");
+  }
+  WavePair* wp = nullptr;
+  std::unique_ptr<WavePair> owned;
+  dgdft_status s = get_waves(ctx, ids, true, wp, owned);
+  if (s != DGDFT_OK) return s;
+  Wave<double>& w64 = *wp->w64;
+  w64.graph_kernels = 0;
+  std::vector<int> it32, fb32, rs32;
+  std::vector<double> res32;
+  if (mixed) {
+    Wave<float>& w32 = *wp->w32;
+    w32.graph_kernels = 0;
+    if ((s = w32.load_inputs(&warm)) != DGDFT_OK) return s;
+    std::vector<double> r32;
+    if ((s = w32.run(0.0, n_iter, 0, &r32)) != DGDFT_OK) return s;
+    size_t off = 0;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      ElemHost& eh = ctx->el[ids[i]];
+      const int m = w32.h[i].m, J = w32.h[i].J;
+      res32.push_back(*std::max_element(r32.begin() + off, r32.begin() + off + J));
+      off += m;
+      launch_convert<double, double>(eh.d_veff, const_cast<double*>(w64.h[i].V), (size_t)eh.ng(), ctx->stream);
+      copy_block_to<float>(w32, (int)i, w64, (int)i, ctx->stream);
+      it32.push_back(w32.h_state[i * STATE_WORDS + ST_ITER]);
+      fb32.push_back(w32.h_state[i * STATE_WORDS + ST_FALLBACK]);
+      rs32.push_back(w32.h_state[i * STATE_WORDS + ST_NRESTART]);
+    }
+    if ((s = w64.verify(ctx->cfg.tol)) != DGDFT_OK) return s;
+  } else {
+    if ((s = w64.load_inputs(&warm)) != DGDFT_OK) return s;
+    if ((s = w64.run(0.0, n_iter, 0, nullptr)) != DGDFT_OK) return s;
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  const long long gk = w64.graph_kernels + (wp->w32 ? wp->w32->graph_kernels : 0);
+  return finish_wave(ctx, w64, 0, secs, it32, fb32, res32, gk, rs32, true);
+}
+
+// Device-memory admission: elements in order, greedily into waves that fit
+// the budget (each element with its share of the wave-level buffers).
+dgdft_status plan_waves(dgdft_alb_ctx* ctx, std::vector<std::vector<int>>& waves) {
+  size_t cap = ctx->cfg.hbm_cap_bytes;
+  if (cap == 0) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    cap = (size_t)(0.9 * (double)fr);
+  }
+  size_t acc = 0;
+  for (int id = 0; id < (int)ctx->el.size(); ++id) {
+    const ElemHost& eh = ctx->el[id];
+    if (!eh.has_v) return ctx->fail(DGDFT_ESTATE, "element without potential");
+    // plus the element's share of the wave-level buffers (Gram partials and
+    // residual partial sums, sized here by the element itself)
+    const size_t m = (size_t)eh.d.n_compute, ng = (size_t)eh.ng();
+    const size_t shared = sizeof(double) * (((ng + 2047) / 2048) * 12 * ((m + 63) / 64) * ((m + 63) / 64) * 4096 +
+                                            m * (size_t)nchunk_rows((int)ng) * 4);
+    size_t b = elem_bytes<double>(eh) + shared;
+    if (ctx->cfg.precision == DGDFT_PREC_MIXED) b += elem_bytes<float>(eh) + shared;
+    if (b > cap) return ctx->fail(DGDFT_ENOMEM, "one element exceeds the device-memory budget");
+    if (waves.empty() || acc + b > cap) {
+      waves.emplace_back();
+      acc = 0;
+    }
+    waves.back().push_back(id);
+    acc += b;
+  }
+  // a single wave stays resident for later solves unless projectors changed
+  if (waves.size() != 1) ctx->drop_cache();
+  if (waves.size() == 1 && ctx->cache) {
+    bool same = ctx->cache_proj_version.size() == ctx->el.size();
+    for (size_t i = 0; same && i < ctx->el.size(); ++i) same = ctx->cache_proj_version[i] == ctx->el[i].proj_version;
+    if (!same) ctx->drop_cache();
+  }
+  return DGDFT_OK;
 }
 
 }  // namespace
@@ -1474,55 +1663,41 @@ dgdft_status dgdft_alb_set_initial(dgdft_alb_ctx* ctx, int elem, const double* x
   ElemHost& eh = ctx->el[elem];
   dgdft_status s = copy_resident(ctx, eh.d_x0, x0, (size_t)eh.ng() * eh.d.n_compute, on_device);
   eh.has_x0 = (s == DGDFT_OK);
+  eh.x0_fresh = eh.has_x0;
   return s;
+}
+
+dgdft_status dgdft_alb_scf_step(dgdft_alb_ctx* ctx, int n_iter, dgdft_solve_report* per_elem) {
+  if (!ctx || n_iter < 1) return DGDFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<std::vector<int>> waves;
+  dgdft_status s = plan_waves(ctx, waves);
+  if (s != DGDFT_OK) return s;
+  if (waves.size() != 1) return ctx->fail(DGDFT_ESTATE, "SCF steps need the workload resident in one wave");
+  if ((s = scf_wave(ctx, waves[0], n_iter)) != DGDFT_OK) return s;
+  for (ElemHost& eh : ctx->el) eh.x0_fresh = false;
+  ctx->solved_any = true;
+  dgdft_status out = DGDFT_OK;
+  for (int i = 0; i < (int)ctx->el.size(); ++i) {
+    if (per_elem) per_elem[i] = ctx->el[i].rep;
+    if (ctx->el[i].rep.status != DGDFT_OK) out = DGDFT_ENOTCONV;
+  }
+  if (out != DGDFT_OK) ctx->err = "some elements failed in the SCF step";
+  return out;
 }
 
 dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem) {
   if (!ctx) return DGDFT_EINVAL;
   CK(cudaSetDevice(ctx->device));
-  std::vector<int> todo;
-  for (int i = 0; i < (int)ctx->el.size(); ++i) {
-    if (!ctx->el[i].has_v) return ctx->fail(DGDFT_ESTATE, "element without potential");
-    todo.push_back(i);
-  }
-  size_t cap = ctx->cfg.hbm_cap_bytes;
-  if (cap == 0) {
-    size_t fr = 0, tot = 0;
-    CK(cudaMemGetInfo(&fr, &tot));
-    cap = (size_t)(0.9 * (double)fr);
-  }
-  // waves admitted by device-memory footprint (greedy, in element order)
   std::vector<std::vector<int>> waves;
-  size_t acc = 0;
-  for (int id : todo) {
-    const ElemHost& eh = ctx->el[id];
-    // plus the element's share of the wave-level buffers (Gram partials and
-    // residual partial sums, sized here by the element itself)
-    const size_t m = (size_t)eh.d.n_compute, ng = (size_t)eh.ng();
-    const size_t shared = sizeof(double) * (((ng + 2047) / 2048) * 12 * ((m + 63) / 64) * ((m + 63) / 64) * 4096 +
-                                            m * (size_t)nchunk_rows((int)ng) * 4);
-    size_t b = elem_bytes<double>(eh) + shared;
-    if (ctx->cfg.precision == DGDFT_PREC_MIXED) b += elem_bytes<float>(eh) + shared;
-    if (b > cap) return ctx->fail(DGDFT_ENOMEM, "one element exceeds the device-memory budget");
-    if (waves.empty() || acc + b > cap) {
-      waves.emplace_back();
-      acc = 0;
-    }
-    waves.back().push_back(id);
-    acc += b;
-  }
-  // one wave: keep it resident for later solves unless projectors changed
+  dgdft_status ps = plan_waves(ctx, waves);
+  if (ps != DGDFT_OK) return ps;
   const bool keep = waves.size() == 1;
-  if (!keep) ctx->drop_cache();
-  if (keep && ctx->cache) {
-    bool same = ctx->cache_proj_version.size() == ctx->el.size();
-    for (size_t i = 0; same && i < ctx->el.size(); ++i) same = ctx->cache_proj_version[i] == ctx->el[i].proj_version;
-    if (!same) ctx->drop_cache();
-  }
   for (size_t w = 0; w < waves.size(); ++w) {
     dgdft_status s = solve_wave(ctx, waves[w], (int)w, keep);
     if (s != DGDFT_OK) return s;
   }
+  for (ElemHost& eh : ctx->el) eh.x0_fresh = false;
   ctx->solved_any = true;
   dgdft_status out = DGDFT_OK;
   for (int i = 0; i < (int)ctx->el.size(); ++i) {

@@ -128,9 +128,9 @@ __device__ __forceinline__ const float* side_col(const ElemDev<float>& e, const 
 }
 
 // ---------------------------------------------------------------------------
-// Windowed tensor-core Gram.  The accuracy limit of the kernel above is the
-// FP32 accumulation in tensor memory over a whole chunk (its error grows with
-// the number of accumulations, ~1e-5 relative over 2048 rows).  Here the
+// Windowed tensor-core Gram.  Accumulating a whole chunk in tensor memory
+// (FP32) would limit the accuracy: the error grows with the number of
+// accumulations, ~1e-5 relative over 2048 rows.  Here the
 // dominant product hi*hi accumulates in tensor memory for a window of four
 // 64-row steps (16 accumulations); after each window epilogue warps read it out with
 // tcgen05.ld and add it to two-sum compensated registers, while the next
