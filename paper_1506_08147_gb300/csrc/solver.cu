@@ -952,17 +952,32 @@ template <class real> struct Wave {
           active_res.push_back(mx);
           const size_t L = hist[i].size();
           // stalled: the best residual of the last `stall_window` polls is not
-          // 5% below the best one before them (the FP32 floor has been
-          // reached).  Only near the floor: early plateaus (a random start
-          // still sorting its subspace) are not stalls.
-          bool stalled = false, near_floor = false;
+          // stall_gain below the best one before them (the FP32 floor has
+          // been reached).  Only near the floor (below max(10 tol, 1e-5)):
+          // above it, up to max(100 tol, 1e-4), a plateau has to last four
+          // times as long, since an element that leaves early at 2e-5 costs
+          // ~10 more FP64 iterations while its FP32 iterations are free as
+          // long as other elements still iterate; early plateaus of a random
+          // start are never stalls.
+          bool stalled = false, near_floor = false, stalled_any = false;
+          auto stall_over = [&](size_t win) {
+            if (hist[i].size() <= win) return false;
+            const double before = *std::min_element(hist[i].begin(), hist[i].end() - win);
+            const double recent = *std::min_element(hist[i].end() - win, hist[i].end());
+            return recent > stall_gain * before;
+          };
           if (L > (size_t)stall_window) {
-            const double before = *std::min_element(hist[i].begin(), hist[i].end() - stall_window);
             const double recent = *std::min_element(hist[i].end() - stall_window, hist[i].end());
-            stalled = recent > stall_gain * before;
-            near_floor = recent < std::max(100.0 * tol, 1e-5);
+            stalled_any = stall_over((size_t)stall_window);  // the learned network's fallback
+            if (recent < std::max(10.0 * tol, 1e-5)) {
+              stalled = stall_over((size_t)stall_window);
+              near_floor = true;
+            } else if (recent < std::max(100.0 * tol, 1e-4)) {
+              stalled = stall_over(4 * (size_t)stall_window);
+              near_floor = true;
+            }
           }
-          if (stalled && learned && !sw[ST_TETER]) {
+          if (stalled_any && learned && !sw[ST_TETER]) {
             // the learned preconditioner stalled: fall back to Teter
             int one = 1;
             ce = ctx_copy(ctx, h[i].state + ST_TETER, &one, sizeof(int), cudaMemcpyHostToDevice);
