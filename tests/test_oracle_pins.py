@@ -9,7 +9,8 @@ Each test ties an oracle function to something other than itself:
   * separable potential: product spectrum from 1-D dense eigensolves;
   * full H (local + Kleinman-Bylander): explicit Kronecker-sum assembly;
   * LOBPCG: dense diagonalisation, Ritz monotonicity, Cauchy interlacing,
-    orthonormality, Hermiticity;
+    orthonormality, Hermiticity; the warm-started fixed-iteration run (the
+    SCF-mode reference) against the dense Rayleigh-Ritz of its start block;
   * Teter: limits of the rational function and plane-wave eigenfunctions;
   * restriction/SVD: orthonormality, span equality, E_K = Q_K.
 """
@@ -226,6 +227,34 @@ def test_lobpcg_matches_dense_small_with_projectors():
     assert np.all(th >= exact[0][None, :12] - 1e-12)
     # orthonormality of the Ritz block
     np.testing.assert_allclose(out["X"] @ out["X"].T, np.eye(12), atol=1e-12)
+
+
+def test_lobpcg_fixed_iterations_from_warm_block():
+    # the SCF-mode reference: a block converged for V0, three iterations under
+    # V1 = V0 + a smooth field.  Pinned to dense diagonalisation of the
+    # explicitly assembled H1: the first Ritz values are the Rayleigh-Ritz of
+    # the warm block under H1, Ritz values never increase, never fall below
+    # H1's eigenvalues, and move toward them
+    gen = np.random.default_rng(23)
+    n, L_ = (8, 8, 8), (6.0, 6.0, 6.0)
+    v0 = gen.uniform(-4, 0, size=(8, 8, 8))
+    proj = random_projectors(n, L_, 6, gen)
+    el0 = make_element(n, L_, v0, proj, m=10, J=8, tol=1e-11)
+    x0 = L.lobpcg(el0, gen.standard_normal((10, el0.ng)))["X"]
+    z, y, x = np.meshgrid(*(np.arange(8) / 8.0,) * 3, indexing="ij")
+    v1 = v0 + 0.3 * np.cos(2 * np.pi * x) * np.sin(2 * np.pi * (y + z))
+    el1 = make_element(n, L_, v1, proj, m=10, J=8, tol=1e-11)
+    nl = H.nonlocal_matrix(el1)
+    h1 = kron_kinetic(n, L_) + np.diag(v1.reshape(-1)) + nl.T @ np.diag(el1.proj_gamma) @ nl
+    exact = np.linalg.eigvalsh(h1)[:10]
+    out = L.lobpcg(el1, x0, tol=0.0, maxit=3)
+    th = np.array(out["history"]["theta"])
+    assert out["iterations"] == 3 and th.shape == (4, 10)
+    q, _ = np.linalg.qr(x0.T)
+    np.testing.assert_allclose(th[0], np.linalg.eigvalsh(q.T @ h1 @ q), atol=1e-10)
+    assert np.all(np.diff(th, axis=0) <= 1e-12)
+    assert np.all(th >= exact[None, :] - 1e-12)
+    assert np.sum(th[-1] - exact) < 0.1 * np.sum(th[0] - exact)
 
 
 def test_config1_golden_eigenvalues():
