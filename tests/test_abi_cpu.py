@@ -88,3 +88,11 @@ def test_no_cpu_fallback_without_device(lib):
     h = C.c_void_p()
     assert lib.dgdft_alb_create(C.byref(cfg), 1, arr, C.byref(h)) == B.DGDFT_ECUDA
     assert not h.value
+
+
+def test_null_context_rejected(lib):
+    # entry points validate their arguments before touching a device
+    assert lib.dgdft_alb_solve(None, None) == B.DGDFT_EINVAL
+    assert lib.dgdft_alb_scf_step(None, 3, None) == B.DGDFT_EINVAL
+    assert lib.dgdft_alb_set_initial(None, 0, None, 0) == B.DGDFT_EINVAL
+    assert lib.dgdft_alb_get_basis(None, 0, None, None, None, 0) == B.DGDFT_EINVAL
