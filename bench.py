@@ -312,10 +312,19 @@ def run_ours(args):
                 times.append(e0.elapsed_time(e1))
                 resmax.append(max(r["max_resid"] for r in reps_s))
         t_scf = float(np.mean(times))
-        alb = sum(e.J for e in els)
+        alb = float(sum(e.J for e in els))
+        rmax = float(max(resmax))
+        if dist:
+            # whole job: the slowest rank's step time, every rank's ALBs
+            t = torch.tensor([t_scf, rmax], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_scf, rmax = float(t[0].item()), float(t[1].item())
+            a = torch.tensor([alb], device="cuda", dtype=torch.float64)
+            dist.all_reduce(a)
+            alb = float(a.item())
         scf = {"iterations_per_step": 3, "ms_per_step": round(t_scf, 2), "steps": len(times),
-               "alb_per_s": alb / (t_scf / 1e3), "alb_per_step": alb,
-               "max_resid_after_step": float(max(resmax)),
+               "alb_per_s": alb / (t_scf / 1e3), "alb_per_step": int(alb),
+               "max_resid_after_step": rmax,
                "potential_update": "alternating V_eff and V_eff + 0.02 Ha smooth field"}
 
     # end to end through the public API from pinned host buffers
