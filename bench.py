@@ -163,9 +163,9 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) of one element's share of the FP32 stage's Gram
 # launch (12 pairs), from the ncu captures summarised in profiles/: the
-# compensated SIMT kernel (gram48_config2.md, a 2-element launch scaled per
-# element: the blocks of every element are read once, so traffic grows with
-# the element count); the tensor-core kernel has no full-launch capture
+# compensated SIMT kernel (a 2-element launch scaled per element: the blocks
+# of every element are read once, so traffic grows with the element count);
+# the tensor-core kernel has no full-launch capture
 GRAM48_TRAFFIC_PER_ELEMENT = 151.4e6
 GRAM_TRAFFIC_PER_ELEMENT = None
 
@@ -297,10 +297,13 @@ def run_ours(args):
                          np.sin(2 * np.pi * z + ph[2]))
             v0 = np.ascontiguousarray(e.veff.reshape(-1), np.float64)
             pots.append((np.ascontiguousarray(v0 + dv.reshape(-1)), v0))
-        times, resmax = [], []
+        times, resmax, res0max, worst_ratio, restarts = [], [], [], [], 0
         for step in range(args.scf_steps + 1):
             for k in range(len(els)):
                 ctx.dgdft_alb_set_potential(k, pots[k][step % 2])
+            # untimed: the FP64 residuals of the starting block's Ritz pairs
+            # under the new potential (no iteration)
+            _, reps_0 = ctx.dgdft_alb_scf_step(0)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -311,21 +314,26 @@ def run_ours(args):
             if step > 0:  # the first step is a warm-up
                 times.append(e0.elapsed_time(e1))
                 resmax.append(max(r["max_resid"] for r in reps_s))
+                res0max.append(max(r["max_resid"] for r in reps_0))
+                worst_ratio.append(max(a["max_resid"] / b["max_resid"] for a, b in zip(reps_s, reps_0)))
+                restarts += sum(r["restarts"] for r in reps_s)
         t_scf = float(np.mean(times))
         alb = float(sum(e.J for e in els))
-        rmax = float(max(resmax))
+        rmax, r0max, wr = float(max(resmax)), float(max(res0max)), float(max(worst_ratio))
         if dist:
             # whole job: the slowest rank's step time, every rank's ALBs
-            t = torch.tensor([t_scf, rmax], device="cuda", dtype=torch.float64)
+            t = torch.tensor([t_scf, rmax, r0max, wr], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_scf, rmax = float(t[0].item()), float(t[1].item())
+            t_scf, rmax, r0max, wr = (float(v) for v in t.tolist())
             a = torch.tensor([alb], device="cuda", dtype=torch.float64)
             dist.all_reduce(a)
             alb = float(a.item())
         scf = {"iterations_per_step": 3, "ms_per_step": round(t_scf, 2), "steps": len(times),
                "alb_per_s": alb / (t_scf / 1e3), "alb_per_step": int(alb),
-               "max_resid_after_step": rmax,
-               "potential_update": "alternating V_eff and V_eff + 0.02 Ha smooth field"}
+               "max_resid_before_step": r0max, "max_resid_after_step": rmax,
+               "worst_element_resid_ratio": wr, "restarts": restarts,
+               "potential_update": "alternating V_eff and V_eff + 0.02 Ha smooth field; "
+                                   "before = FP64 residual of the starting block's Ritz pairs"}
 
     # end to end through the public API from pinned host buffers
     e2e = None

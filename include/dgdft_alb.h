@@ -61,9 +61,10 @@ typedef enum {
  * eigensolve and the final orthonormalisation are FP64 in every mode.      */
 enum {
   DGDFT_PREC_FP64 = 0,  /* plain: FP64 everywhere                             */
-  DGDFT_PREC_MIXED = 1  /* chosen form: FP32 storage/FFTs, tensor-core split-BF16
-                           Gram and update products with FP32 accumulation,
-                           then FP64 refinement to the requested tolerance     */
+  DGDFT_PREC_MIXED = 1  /* chosen form: FP32 storage, FFTs and block updates,
+                           Gram products with compensated FP32 accumulation
+                           (see bulk_kernels), FP64 Rayleigh-Ritz; then the
+                           FP64 check and FP64 iterations to the tolerance     */
 };
 
 enum {
@@ -171,7 +172,7 @@ dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem);
 /* One SCF step of ALB generation (Sec. II.B: in each SCF iteration the ALBs
  * are refined by a few LOBPCG iterations that start from those of the
  * previous SCF step, under the updated V_eff set by dgdft_alb_set_potential).
- * Every element runs exactly n_iter (>= 1) LOBPCG iterations, in the
+ * Every element runs exactly n_iter (>= 0) LOBPCG iterations, in the
  * context's precision (FP32 storage and arithmetic with an FP64
  * Rayleigh-Ritz in the mixed form), from the block given by
  * dgdft_alb_set_initial since the last solve or step, else from its own
@@ -180,8 +181,12 @@ dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem);
  * no tolerance: a report's status is DGDFT_OK unless the element failed, and
  * max_resid is the FP64 residual after the step.  The workload must fit one
  * memory-admission wave (it stays resident between steps; changing the
- * projectors drops the resident blocks).  Returns DGDFT_ESTATE when an
- * element has no block to start from, DGDFT_EINVAL for n_iter < 1. */
+ * projectors drops the resident blocks).  n_iter = 0 runs no iteration: the
+ * starting block is rotated to its Ritz vectors under the current potential
+ * (FP64 Rayleigh-Ritz) and their FP64 residuals are reported, which tells a
+ * caller how far the previous ALBs are from the new problem.  Returns
+ * DGDFT_ESTATE when an element has no block to start from, DGDFT_EINVAL for
+ * n_iter < 0. */
 dgdft_status dgdft_alb_scf_step(dgdft_alb_ctx* ctx, int n_iter, dgdft_solve_report* per_elem);
 
 /* Copy out element `elem`'s ALBs: phi is n_E x J column-major (n_E = product

@@ -158,9 +158,15 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
 // step the cluster's vectors are orthogonalised by modified Gram-Schmidt
 // (inverse iteration alone cannot separate them).  Isolated vectors take
 // the Rayleigh quotient as the shift after the first step (cubic
-// convergence from a rough start).  On return the columns are orthonormal
-// and lam[] holds their Rayleigh quotients.  shift, dots: m doubles; tri:
-// 5 n doubles per vector; cstart: m ints.  Every thread of the block calls.
+// convergence from a rough start).  The estimates come from bisection whose
+// location error can approach ortol, so two close eigenvalues taken as
+// isolated may both converge to one eigenvector; the vectors are therefore
+// checked against their next few neighbours, and if any two overlap the
+// inverse iteration is redone with all m vectors in one orthogonalised
+// cluster (rare, and then ~m^2 n more work).  On return the columns are
+// orthonormal and lam[] holds their Rayleigh quotients.  shift, dots: m
+// doubles; tri: 5 n doubles per vector; cstart: m ints.  Every thread of the
+// block calls.
 __device__ void tri_eigvecs(const double* d, const double* e, int n, int m, double* lam, double* Z, int ldz,
                             int* cstart, double* shift, double* dots, double* tri, double ortol, double gnorm,
                             double* red, unsigned seed) {
@@ -168,7 +174,7 @@ __device__ void tri_eigvecs(const double* d, const double* e, int n, int m, doub
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const double eps = DBL_EPSILON;
   const double sep = 10.0 * eps * fmax(gnorm, 1e-300);
-  __shared__ int any_cluster;
+  __shared__ int any_cluster, overlap;
   if (tid == 0) {
     any_cluster = 0;
     for (int i = 0; i < m; ++i) {
@@ -179,6 +185,7 @@ __device__ void tri_eigvecs(const double* d, const double* e, int n, int m, doub
     }
   }
   __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
   for (int it = 0; it < 3; ++it) {
     for (int q = tid; q < m; q += nt) {
       double* b = Z + (size_t)q * ldz;
@@ -231,6 +238,33 @@ __device__ void tri_eigvecs(const double* d, const double* e, int n, int m, doub
       }
       __syncthreads();
     }
+  }
+  if (pass == 1) break;
+  // overlap check: unit vectors of distinct eigenvalues are orthogonal to
+  // rounding; a large product means two of them found the same eigenvector
+  constexpr int REACH = 4;
+  if (tid == 0) overlap = 0;
+  __syncthreads();
+  for (int t = warp; t < m * REACH; t += nw) {
+    const int j = t / REACH, k = j + 1 + (t - j * REACH);
+    if (k >= m) continue;
+    const double* zj = Z + (size_t)j * ldz;
+    const double* zk = Z + (size_t)k * ldz;
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) s2 += zj[i] * zk[i];
+    s2 = warp_sum(s2);
+    if (lane == 0 && fabs(s2) > 1e-3) overlap = 1;
+  }
+  __syncthreads();
+  if (!overlap) break;
+  if (tid == 0) {
+    any_cluster = 1;
+    for (int i = 1; i < m; ++i) {
+      cstart[i] = 0;
+      shift[i] = fmax(shift[i], shift[i - 1] + sep);
+    }
+  }
+  __syncthreads();
   }
   // eigenvalues as FP64 Rayleigh quotients z^T T z of the unit vectors
   for (int j = warp; j < m; j += nw) {

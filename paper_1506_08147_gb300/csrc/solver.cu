@@ -832,10 +832,17 @@ template <class real> struct Wave {
   dgdft_status run(double tol, int maxit, int stall_window, std::vector<double>* res_out, int refresh_every = 0,
                    bool resume = false, double precise_below = 0.0, double stall_gain = 0.95) {
     cudaStream_t st = ctx->stream;
+    const auto tr0 = std::chrono::steady_clock::now();
+    auto trace_ms = [&]() { return 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - tr0).count(); };
     dgdft_status s = reset_states(tol, resume);
     if (s != DGDFT_OK) return s;
+    if (trace_) std::fprintf(stderr, "[dgdft] run: states reset at %.2f ms\n", trace_ms());
     enqueue_initial(st);
     CK(cudaGetLastError());
+    if (trace_) {
+      cudaStreamSynchronize(st);
+      std::fprintf(stderr, "[dgdft] run: initial Rayleigh-Ritz done at %.2f ms\n", trace_ms());
+    }
     cudaGraphExec_t exec = nullptr, exec2 = nullptr;
     long long nodes1 = 0, nodes2 = 0;
     cudaError_t ce = cudaSuccess;
@@ -886,6 +893,11 @@ template <class real> struct Wave {
       hx64 = false;
     }
     bool precise = false;
+    if (trace_) {
+      cudaStreamSynchronize(st);
+      if (split) cudaStreamSynchronize(st2);
+      std::fprintf(stderr, "[dgdft] run: graphs captured at %.2f ms\n", trace_ms());
+    }
     if (ce != cudaSuccess) {
       if (exec) cudaGraphExecDestroy(exec);
       if (exec2) cudaGraphExecDestroy(exec2);
@@ -1072,10 +1084,12 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
   }
   const size_t jj = (size_t)Jmax * Jmax;
   // per element: phi_t, U (ne x J), G, G2, Y1, Y2, I, diag(1..J) (J x J),
-  // theta, Rayleigh-Ritz work; then the two task arrays and the checks, so
-  // that each Rayleigh-Ritz phase is one launch over all elements
+  // theta, Rayleigh-Ritz work; then the task arrays, the Gram partials and
+  // the checks, so that each phase is one launch over all elements
   const size_t per = 2 * nemax * Jmax + 6 * jj + Jmax + rr_work_doubles(Jmax, Jmax);
-  const size_t nbytes = sizeof(double) * (per * nq + nq) + 2 * nq * sizeof(RRTask) + (10 * nq + 16) * ALIGN;
+  const size_t npart = ortho_partial_doubles((int)nq, (int)nemax, Jmax);
+  const size_t nbytes = sizeof(double) * (per * nq + nq + npart) + 2 * nq * sizeof(RRTask) +
+                        4 * nq * sizeof(OrthoTask) + (10 * nq + 32) * ALIGN;
   void* base = nullptr;
   CK(cudaMalloc(&base, nbytes));
   std::unique_ptr<void, decltype(&cudaFree)> guard(base, &cudaFree);
@@ -1099,12 +1113,16 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
     z.work = (double*)a.take(sizeof(double) * rr_work_doubles(Jmax, Jmax));
   }
   double* chk = (double*)a.take(sizeof(double) * nq);
+  double* part = (double*)a.take(sizeof(double) * npart);
   RRTask* dt = (RRTask*)a.take(2 * nq * sizeof(RRTask));  // [0, nq): first pass, [nq, 2nq): second
-  if (!chk || !dt || !sl.back().work) return ctx->fail(DGDFT_ENOMEM, "orthonormalisation scratch");
+  // [0, nq): Gram of Phi~, then U = Phi~ Y1, Gram of U, out = U Y2
+  OrthoTask* ot = (OrthoTask*)a.take(4 * nq * sizeof(OrthoTask));
+  if (!chk || !dt || !ot || !part || !sl.back().work) return ctx->fail(DGDFT_ENOMEM, "orthonormalisation scratch");
   std::vector<double> hm(2 * jj * nq, 0.0);
   std::vector<RRTask> ht(2 * nq);
+  std::vector<OrthoTask> hot(4 * nq);
   for (size_t q = 0; q < nq; ++q) {
-    const int J = Js[q];
+    const int J = Js[q], ne = ctx->el[w.ids[idx[q]]].ne();
     double* id = hm.data() + 2 * jj * q;
     double* dg = id + jj;
     for (int c = 0; c < J; ++c) {
@@ -1127,72 +1145,33 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
       t.state = nullptr;
       t.cond_max = 1e30;
     }
+    hot[q] = OrthoTask{sl[q].phit, nullptr, sl[q].G, ne, J};
+    hot[nq + q] = OrthoTask{sl[q].phit, sl[q].Y1, sl[q].U, ne, J};
+    hot[2 * nq + q] = OrthoTask{sl[q].U, nullptr, sl[q].G2, ne, J};
+    hot[3 * nq + q] = OrthoTask{sl[q].U, sl[q].Y2, out[q], ne, J};
     CK(cudaMemcpyAsync(sl[q].mats, id, sizeof(double) * 2 * jj, cudaMemcpyHostToDevice, st));
   }
   CK(cudaMemcpyAsync(dt, ht.data(), sizeof(RRTask) * ht.size(), cudaMemcpyHostToDevice, st));
-  // the single-element views below run only on active elements
-  const int one_word = 1, zero_word = 0;
-  for (size_t q = 0; q < nq; ++q)
-    CK(cudaMemcpyAsync(w.h[idx[q]].state + ST_ACTIVE, &one_word, sizeof(int), cudaMemcpyHostToDevice, st));
-  auto view = [&](size_t q) {
-    Batch<double> one;
-    one.d_elems = w.d_elems + idx[q];
-    one.s = w.batch.s;
-    one.s.nel = 1;
-    return one;
-  };
-  auto gram = [&](size_t q, const double* v, double* g_out) {
-    const int J = Js[q], ne = ctx->el[w.ids[idx[q]]].ne();
-    GramJob<double> g;
-    g.npairs = 1;
-    g.a[0] = bptr<double>(const_cast<double*>(v));
-    g.b[0] = bptr<double>(const_cast<double*>(v));
-    g.needs_p[0] = 0;
-    g.out_id[0] = OUT_PTR;
-    g.brow[0] = g.bcol[0] = 0;
-    g.ncols_a = g.ncols_b = J;
-    g.rows = ne;
-    g.ld_in = ne;
-    g.ld_out = J;
-    g.out_ptr = g_out;
-    launch_gram<double>(view(q), g, w.partial, w.partial_cap, st);
-  };
-  auto apply = [&](size_t q, const double* v, const double* y, double* dst) {
-    const int J = Js[q], ne = ctx->el[w.ids[idx[q]]].ne();
-    TsmmJob<double> u;
-    u.nin = 1;
-    u.in[0] = bptr<double>(const_cast<double*>(v));
-    u.y_id = Y_PTR;
-    u.y_ptr = const_cast<double*>(y);
-    u.ldy = J;
-    u.ncols = J;
-    u.rows = ne;
-    u.ld_in = ne;
-    u.out = bptr<double>(dst);
-    launch_tsmm<double>(view(q), u, st);
-  };
+  CK(cudaMemcpyAsync(ot, hot.data(), sizeof(OrthoTask) * hot.size(), cudaMemcpyHostToDevice, st));
+  const int nqi = (int)nq, nem = (int)nemax;
   // Phi~ and G = Phi~^T Phi~ for every element, then one Rayleigh-Ritz launch
   for (size_t q = 0; q < nq; ++q) {
     const ElemHost& eh = ctx->el[w.ids[idx[q]]];
     const dgdft_element_desc& d = eh.d;
     launch_restrict<double>(xs[q], eh.ng(), d.nx, d.ny, d.e_lo, d.e_hi, Js[q], sl[q].phit, st);
-    gram(q, sl[q].phit, sl[q].G);
   }
-  launch_rr(dt, (int)nq, st, Jmax, Jmax);
+  launch_ortho_gram(ot, nqi, nem, Jmax, part, st);
+  launch_rr(dt, nqi, st, Jmax, Jmax);
   // U = Phi~ Y1 and its Gram, second Rayleigh-Ritz launch
-  for (size_t q = 0; q < nq; ++q) {
-    apply(q, sl[q].phit, sl[q].Y1, sl[q].U);
-    gram(q, sl[q].U, sl[q].G2);
-  }
-  launch_rr(dt + nq, (int)nq, st, Jmax, Jmax);
+  launch_ortho_apply(ot + nq, nqi, nem, Jmax, st);
+  launch_ortho_gram(ot + 2 * nq, nqi, nem, Jmax, part, st);
+  launch_rr(dt + nq, nqi, st, Jmax, Jmax);
+  launch_ortho_apply(ot + 3 * nq, nqi, nem, Jmax, st);
   for (size_t q = 0; q < nq; ++q) {
     const ElemHost& eh = ctx->el[w.ids[idx[q]]];
-    apply(q, sl[q].U, sl[q].Y2, out[q]);
     launch_scale(out[q], (size_t)eh.ne() * Js[q], 1.0 / std::sqrt(eh.dv()), st);
     CK(cudaMemcpyAsync(chk + q, sl[q].th, sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
-  for (size_t q = 0; q < nq; ++q)
-    CK(cudaMemcpyAsync(w.h[idx[q]].state + ST_ACTIVE, &zero_word, sizeof(int), cudaMemcpyHostToDevice, st));
   std::vector<double> hchk(nq);
   CK(cudaMemcpyAsync(hchk.data(), chk, sizeof(double) * nq, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1440,12 +1419,27 @@ dgdft_status scf_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int n_ite
   w64.graph_kernels = 0;
   std::vector<int> it32, fb32, rs32;
   std::vector<double> res32;
-  if (mixed) {
+  const bool trace = std::getenv("DGDFT_TRACE") != nullptr;
+  auto stamp = [&](const char* what) {
+    if (!trace) return;
+    cudaStreamSynchronize(ctx->stream);
+    std::fprintf(stderr, "[dgdft] scf step: %s at %.2f ms\n", what,
+                 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+  };
+  stamp("waves ready");
+  if (n_iter == 0) {
+    // no iteration: Rayleigh-Ritz of the starting block and its FP64
+    // residuals under the current potential
+    if ((s = w64.load_inputs(&warm)) != DGDFT_OK) return s;
+    if ((s = w64.run(0.0, 0, 0, nullptr)) != DGDFT_OK) return s;
+  } else if (mixed) {
     Wave<float>& w32 = *wp->w32;
     w32.graph_kernels = 0;
     if ((s = w32.load_inputs(&warm)) != DGDFT_OK) return s;
+    stamp("inputs converted");
     std::vector<double> r32;
     if ((s = w32.run(0.0, n_iter, 0, &r32)) != DGDFT_OK) return s;
+    stamp("FP32 iterations done");
     size_t off = 0;
     for (size_t i = 0; i < ids.size(); ++i) {
       ElemHost& eh = ctx->el[ids[i]];
@@ -1459,13 +1453,16 @@ dgdft_status scf_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int n_ite
       rs32.push_back(w32.h_state[i * STATE_WORDS + ST_NRESTART]);
     }
     if ((s = w64.verify(ctx->cfg.tol)) != DGDFT_OK) return s;
+    stamp("FP64 check done");
   } else {
     if ((s = w64.load_inputs(&warm)) != DGDFT_OK) return s;
     if ((s = w64.run(0.0, n_iter, 0, nullptr)) != DGDFT_OK) return s;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const long long gk = w64.graph_kernels + (wp->w32 ? wp->w32->graph_kernels : 0);
-  return finish_wave(ctx, w64, 0, secs, it32, fb32, res32, gk, rs32, true);
+  s = finish_wave(ctx, w64, 0, secs, it32, fb32, res32, gk, rs32, true);
+  stamp("restriction and orthonormalisation done");
+  return s;
 }
 
 // Device-memory admission: elements in order, greedily into waves that fit
@@ -1683,7 +1680,7 @@ dgdft_status dgdft_alb_set_initial(dgdft_alb_ctx* ctx, int elem, const double* x
 }
 
 dgdft_status dgdft_alb_scf_step(dgdft_alb_ctx* ctx, int n_iter, dgdft_solve_report* per_elem) {
-  if (!ctx || n_iter < 1) return DGDFT_EINVAL;
+  if (!ctx || n_iter < 0) return DGDFT_EINVAL;
   CK(cudaSetDevice(ctx->device));
   std::vector<std::vector<int>> waves;
   dgdft_status s = plan_waves(ctx, waves);

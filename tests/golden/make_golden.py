@@ -1,7 +1,14 @@
 """Write the stored expected values under tests/golden/ from the oracle alone.
 
-Run from the repository root:  python tests/golden/make_golden.py [--config2]
+Run from the repository root:
+    python tests/golden/make_golden.py [--skip-config1] [--config2] [--ritz]
 Calls only oracle/ and synth/ (no GPU code).
+
+--ritz writes, for the elements the GPU parity tests solve (monolayer
+elements 0 and 7, six elements of the uneven batch, element 100 of the large
+monolayer), the oracle's lowest Ritz values and their residuals, converged to
+1e-9 Ha for the kept J plus four more (so the spectral gap at the J cut is
+known): tests/golden/<name>_ritz.txt, two columns (eigenvalue, residual).
 """
 
 import os
@@ -45,8 +52,44 @@ def config2(elems):
                           "(Eq. localproblem; Sec. II.B).")
 
 
+# Elements whose full solves the GPU tests compare with these values.
+CONFIG3_PICK = [2, 11, 3, 25, 0, 7]
+
+
+def ritz_targets():
+    out = [(f"config2_elem{k}", (lambda k=k: synth.config2(elems=[k])[0])) for k in (0, 7)]
+    out += [(f"config3_elem{k}", (lambda k=k: synth.config3(elems=[k])[0])) for k in CONFIG3_PICK]
+    out += [("config5_elem100", lambda: synth.config5(elems=[100])[0])]
+    return out
+
+
+def ritz(names=None, tol=1e-9):
+    """Oracle LOBPCG (Sec. II.B) run until the lowest J + 4 Ritz pairs have
+    residual <= tol.  The block is the seeded m-block plus max(8, m/4) more
+    seeded rows, so that the last kept pair is well inside the block."""
+    for name, make in ritz_targets():
+        if names and name not in names:
+            continue
+        el = make()
+        keep = min(el.m, el.J + 4)
+        extra = np.random.default_rng([*el.seed_key, 101]).standard_normal((max(8, el.m // 4), el.ng))
+        x0 = np.vstack([synth.initial_block(el), extra])
+        out = lobpcg.lobpcg(el, x0, tol=tol, maxit=4000, keep=keep)
+        assert out["converged"], name
+        data = np.column_stack([out["theta"][:keep], out["res"][:keep]])
+        np.savetxt(os.path.join(HERE, f"{name}_ritz.txt"), data, fmt="%.15e",
+                   header=f"{name}: grid {el.n}, m = {el.m}, J = {el.J}.  Lowest {keep} Ritz values (Ha)\n"
+                          f"and residuals |H x - theta x| / |x| (Ha) of the oracle LOBPCG run to residual\n"
+                          f"{tol:g} on all {keep} (Eq. localproblem; Sec. II.B); "
+                          f"{out['iterations']} iterations from a seeded random block of {x0.shape[0]}.")
+        print(name, "iterations", out["iterations"], flush=True)
+
+
 if __name__ == "__main__":
     if "--skip-config1" not in sys.argv:
         config1()
     if "--config2" in sys.argv:
         config2([0, 7])
+    if "--ritz" in sys.argv:
+        only = [a.split("=", 1)[1] for a in sys.argv if a.startswith("--only=")]
+        ritz(only[0].split(",") if only else None)

@@ -206,6 +206,33 @@ def test_rayleigh_ritz_degenerate_shells():
     c.close()
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_rayleigh_ritz_close_pairs(seed):
+    """Pencils shaped like the FP32 stage's: the lowest 48 of 144 eigenvalues
+    near zero in close pairs (gaps 1e-7 to 1e-3 of the norm), the rest spread
+    up to ~30.  Eigenvalue estimates from bisection are good to roughly the
+    cluster threshold here, so two close eigenvalues can be taken as
+    isolated; the eigenvectors must still come out B-orthonormal (two copies
+    of one eigenvector would make the next LOBPCG block rank deficient)."""
+    gen = np.random.default_rng(100 + seed)
+    n, m = 144, 48
+    low = np.sort(gen.uniform(-0.4, 0.4, m // 2))
+    gaps = 30.0 * 10.0 ** gen.uniform(-7, -3, m // 2)
+    ev = np.sort(np.r_[low, low + gaps, gen.uniform(1.0, 30.0, n - m)])
+    q, _ = np.linalg.qr(gen.standard_normal((n, n)))
+    b = spd(n, gen, cond=1e2) if seed % 2 else np.eye(n)
+    lb = np.linalg.cholesky(b)
+    a = lb @ (q * ev) @ q.T @ lb.T
+    a = 0.5 * (a + a.T)
+    el = small_kb_element()
+    c = ctx_for(el, B.DGDFT_PREC_FP64)
+    theta, y = c.dgdft_alb_rayleigh_ritz(a, b, m)
+    c.close()
+    np.testing.assert_allclose(theta, ev[:m], atol=1e-10 * 30.0)
+    np.testing.assert_allclose(y.T @ b @ y, np.eye(m), atol=1e-9)
+    assert np.max(np.abs(a @ y - b @ y * theta)) < 1e-8 * 30.0
+
+
 def test_rayleigh_ritz_rejects_indefinite_b():
     n = 10
     a = np.eye(n)

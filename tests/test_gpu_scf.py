@@ -121,33 +121,104 @@ def test_scf_step_warm_from_previous_solve(warm_case):
     c.close()
 
 
-def start_ritz_values(x, el):
-    """Ritz values of the block x (rows) under el's H."""
+def start_ritz(x, el, J):
+    """Ritz values of the block x (rows) under el's H, and the largest
+    residual |H y - theta y| of its lowest J Ritz vectors y."""
     q, _ = np.linalg.qr(x.T)
     hq = H.apply_h(q.T, el)
-    return np.linalg.eigvalsh(0.5 * (hq @ q + (hq @ q).T))
+    th, z = np.linalg.eigh(0.5 * (hq @ q + (hq @ q).T))
+    y = z[:, :J].T @ q.T
+    r = z[:, :J].T @ hq - th[:J, None] * y
+    return th, float(np.max(np.linalg.norm(r, axis=1)))
 
 
 def test_scf_step_monolayer_mixed():
-    # one monolayer element: mixed-form solve, potential update, SCF step
-    # (FP32 iterations).  The returned block's residuals are recomputed with
-    # the oracle's H; each kept Ritz value is at or below the same-index Ritz
+    # monolayer elements: mixed-form solve, potential update, SCF step (FP32
+    # iterations).  The returned block's residuals are recomputed with the
+    # oracle's H; each kept Ritz value is at or below the same-index Ritz
     # value of the starting block under the new H (the step's subspace
-    # contains the starting block), up to the FP32 rounding of the iterations,
-    # and their sum drops
-    el0 = synth.config2(elems=[0])[0]
-    el1 = perturbed(el0, amp=0.02)
-    c = B.Context([B.element_dict(el0)], precision=B.DGDFT_PREC_MIXED, keep_block=True)
-    B.load_element(c, 0, el0, synth.initial_block(el0))
+    # contains the starting block), up to the FP32 rounding of the
+    # iterations, and their sum drops.  The oracle runs the same three
+    # iterations from the same block: Ritz values agree to FP32 rounding and
+    # the residuals are no worse than the oracle's (a residual may grow over
+    # a step: a state from outside the starting block can enter the kept J).
+    # Two elements, so that the two half batches of the FP32 stage both run.
+    els0 = synth.config2(elems=[0, 32])
+    els1 = [perturbed(e, amp=0.02) for e in els0]
+    c = B.Context([B.element_dict(e) for e in els0], precision=B.DGDFT_PREC_MIXED, keep_block=True)
+    for k, e in enumerate(els0):
+        B.load_element(c, k, e, synth.initial_block(e))
     st, _ = c.dgdft_alb_solve()
     assert st == B.DGDFT_OK
-    th0 = start_ritz_values(c.dgdft_alb_get_block(0), el1)[:el1.J]
-    c.dgdft_alb_set_potential(0, np.ascontiguousarray(el1.veff.reshape(-1)))
+    blocks = [c.dgdft_alb_get_block(k) for k in range(len(els0))]
+    for k, e in enumerate(els1):
+        c.dgdft_alb_set_potential(k, np.ascontiguousarray(e.veff.reshape(-1)))
     st, reps = c.dgdft_alb_scf_step(N_ITER)
     assert st == B.DGDFT_OK
-    eig, _ = check_block(c, el1, reps[0])
-    assert np.all(eig <= th0 + 1e-6)
-    assert np.sum(th0 - eig) > 1e-4
+    for k, e in enumerate(els1):
+        th0, r0 = start_ritz(blocks[k], e, e.J)
+        ref = OL.lobpcg(e, blocks[k], tol=0.0, maxit=N_ITER)
+        phi, eig, res = c.dgdft_alb_get_basis(k)
+        x = c.dgdft_alb_get_block(k)
+        assert reps[k]["status"] == B.DGDFT_OK and reps[k]["iterations"] == N_ITER
+        assert reps[k]["restarts"] == 0
+        r = H.apply_h(x[:e.J], e) - eig[:, None] * x[:e.J]
+        got = np.linalg.norm(r, axis=1) / np.linalg.norm(x[:e.J], axis=1)
+        np.testing.assert_allclose(res, got, rtol=1e-3, atol=1e-12)
+        np.testing.assert_allclose(phi @ phi.T * e.dv, np.eye(e.J), atol=1e-12)
+        assert np.all(eig <= th0[:e.J] + 1e-6)
+        assert np.sum(th0[:e.J] - eig) > 1e-4
+        np.testing.assert_allclose(eig, ref["theta"][:e.J], rtol=0, atol=1e-5)
+        print(f"SCF step, element {[0, 32][k]}: max residual of the starting Ritz pairs {r0:.3e}, "
+              f"after {np.max(got):.3e} (oracle {np.max(ref['res'][:e.J]):.3e})")
+        assert np.max(got) <= max(1.5 * np.max(ref["res"][:e.J]), 5e-6)
+    c.close()
+
+
+def test_scf_steps_monolayer_workload():
+    """The 36-element monolayer in the launch configuration of the benchmark
+    (mixed form, both half batches): a solve, then SCF steps under a
+    potential that alternates between V_eff + a smooth 0.02 Ha field and
+    V_eff.  n_iter = 0 first gives the FP64 residuals of the starting block's
+    Ritz pairs under the new potential.  No element may restart (a restart
+    perturbs the block by 3 % and leaves residuals near 0.3 Ha after three
+    iterations); the worst element of the last step and element 32 are
+    checked against the oracle's three iterations from the same block.  The
+    largest kept residual is not required to drop over a step: from a warm
+    start under a 0.02 Ha change the vectors near the J cut mix with states
+    from the guard set, and the oracle's own three iterations leave it 2-4x
+    above the starting Ritz residual on these elements."""
+    els = synth.config2()
+    c = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_MIXED, keep_block=True)
+    for k, e in enumerate(els):
+        B.load_element(c, k, e, synth.initial_block(e))
+    st, _ = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK
+    pert = [perturbed(e, amp=0.02, seed=20 + k) for k, e in enumerate(els)]
+    for step in range(3):
+        cur = pert if step % 2 == 0 else els
+        for k, e in enumerate(cur):
+            c.dgdft_alb_set_potential(k, np.ascontiguousarray(e.veff.reshape(-1)))
+        st, before = c.dgdft_alb_scf_step(0)
+        assert st == B.DGDFT_OK
+        assert all(r["iterations"] == 0 for r in before)
+        start = {k: c.dgdft_alb_get_block(k) for k in range(len(els))}
+        st, after = c.dgdft_alb_scf_step(N_ITER)
+        assert st == B.DGDFT_OK
+        r0 = np.array([r["max_resid"] for r in before])
+        r1 = np.array([r["max_resid"] for r in after])
+        print(f"step {step}: max residual before {r0.max():.3e}, after {r1.max():.3e}")
+        assert all(r["restarts"] == 0 for r in after)
+    for k in sorted({32, int(np.argmax(r1))}):
+        e = cur[k]
+        ref = OL.lobpcg(e, start[k], tol=0.0, maxit=N_ITER)
+        _, eig, res = c.dgdft_alb_get_basis(k)
+        x = c.dgdft_alb_get_block(k)
+        r = H.apply_h(x[:e.J], e) - eig[:, None] * x[:e.J]
+        got = np.linalg.norm(r, axis=1)
+        np.testing.assert_allclose(res, got, rtol=1e-3, atol=1e-12)
+        np.testing.assert_allclose(eig, ref["theta"][:e.J], rtol=0, atol=1e-5)
+        assert np.max(got) <= max(1.5 * np.max(ref["res"][:e.J]), 5e-6)
     c.close()
 
 
@@ -158,5 +229,5 @@ def test_scf_step_errors():
     # no previous solve and no set_initial: nothing to start from
     st = c.lib.dgdft_alb_scf_step(c.h, N_ITER, None)
     assert st == B.DGDFT_ESTATE
-    assert c.lib.dgdft_alb_scf_step(c.h, 0, None) == B.DGDFT_EINVAL
+    assert c.lib.dgdft_alb_scf_step(c.h, -1, None) == B.DGDFT_EINVAL
     c.close()
