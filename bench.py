@@ -157,10 +157,6 @@ def stage_bytes(name, e, s):
 STAGE_PER_ITER = {"xy_fwd": 3, "z_mult": 3, "xy_inv": 3, "gram": 1, "update": 3, "rayleigh_ritz": 1,
                   "residual": 1}
 
-# FP32 peak of the SIMT pipe: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x
-# 2.07 GHz (the maximum SM clock)
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-
 # DRAM bytes (read + write) of one element's share of the FP32 stage's Gram
 # launch (12 pairs), from the ncu captures summarised in profiles/: the
 # compensated SIMT kernel (a 2-element launch scaled per element: the blocks
@@ -189,7 +185,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
-                    stream=stream.cuda_stream, tc_gram=args.tc_gram, h_fp64_forward=args.fwd64)
+                    stream=stream.cuda_stream, simt_gram=args.simt_gram, h_fp64_forward=args.fwd64)
     dev_x0 = []
     for k, e in enumerate(els):
         B.load_element(ctx, k, e)
@@ -233,6 +229,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel (stage timed live on the same stream)
     hbm, bf16, peak_kind = peaks()
+    peak_src = ("measured hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s")
     stages = {}
     for name, sid in B.STAGES.items():
         t_ms, nel, sbytes = ctx.dgdft_alb_time_stage(sid, reps=args.stage_reps)
@@ -241,25 +239,7 @@ def run_ours(args):
     share = {n: stages[n][0] * STAGE_PER_ITER[n] for n in stages}
     dom = max(share, key=share.get)
     dom_ms, nel, sbytes = stages[dom]
-    if dom == "gram" and not args.tc_gram:
-        # the SIMT FP32 Gram is bound by the FP32 FMA pipe (compensated)
-        flops = sum(12 * 2.0 * e.m * e.m * e.ng for e in els)
-        achieved = flops / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_SIMT_TFLOPS, "traffic": GRAM48_TRAFFIC_PER_ELEMENT * len(els),
-                "kernel": "gram48 (12 Gram blocks of S^T S and (H S)^T S, FP32 stage, SIMT)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
-    elif dom == "gram":
-        # the tensor-core Gram: 48 useful flop per byte of FP32 input, far
-        # below the bf16 ridge (~276 flop/B), so HBM bounds it
-        abytes = sum(stage_bytes("gram", e, sbytes) for e in els)
-        achieved = abytes / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": (GRAM_TRAFFIC_PER_ELEMENT * len(els)) if GRAM_TRAFFIC_PER_ELEMENT else None,
-                "kernel": "tcw_gram (tcgen05, 12 Gram blocks of S^T S and (H S)^T S, FP32 stage)",
-                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s"}
-    elif dom == "rayleigh_ritz":
+    if dom == "rayleigh_ritz":
         # FP64 ALU bound: lowest m of a 3m pencil, ~ (3m)^3 (1/3 + 1 + 2/3 + ...) flops
         n3 = (3 * els[0].m) ** 3
         flops = nel * 2.5 * 2 * n3
@@ -269,12 +249,28 @@ def run_ours(args):
                 "frac": achieved / fp64_peak, "traffic": None, "kernel": dom,
                 "peak_source": "FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz (derived)"}
     else:
+        # HBM bound (the Gram too: 3m/2 flop per byte at FP32, far below the
+        # tensor ridge): algorithmic bytes of the stage over its launch time
         abytes = sum(stage_bytes(dom, e, sbytes) for e in els)
         achieved = abytes / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": dom,
-                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s"}
+                "frac": achieved / hbm, "traffic": None, "kernel": dom, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": abytes}
+        if dom == "gram":
+            roof["kernel"] = ("tf32_gram (tcgen05 TF32 split, TMA; 12 Gram blocks of S^T S and (H S)^T S, "
+                              "FP32 stage)" if not args.simt_gram else "gram48 (compensated SIMT, FP32 stage)")
+            per_el = GRAM_TRAFFIC_PER_ELEMENT if not args.simt_gram else GRAM48_TRAFFIC_PER_ELEMENT
+            roof["traffic"] = per_el * len(els) if per_el else None
+            # secondary: useful flops of the 12 blocks (symmetric halves)
+            roof["useful_tflops"] = sum(2.0 * e.ng * (3 * e.m) ** 2 for e in els) / (dom_ms / 1e3) / 1e12
+    # whole solve on the same basis: 20 N_g m s algorithmic bytes per
+    # element-iteration (H W, Teter, Gram, updates, residual), over the
+    # measured step time at the measured iteration counts
+    step_bytes = sum(20.0 * e.ng * e.m * sbytes * r["iterations"] for e, r in zip(els, reps))
+    step_roof = {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes,
+                 "achieved": step_bytes / (ms_step / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                 "frac": step_bytes / (ms_step / 1e3) / 1e9 / hbm,
+                 "basis": "20 N_g m s bytes per element-iteration, s = 4 (FP32 stage) for every iteration"}
     stage_report = {n: {"ms_per_launch": round(stages[n][0], 4), "launches_per_iter": STAGE_PER_ITER[n],
                         "alg_GBps": (round(sum(stage_bytes(n, e, stages[n][2]) for e in els)
                                            / (stages[n][0] / 1e3) / 1e9, 1)
@@ -410,7 +406,7 @@ def run_ours(args):
         "fp64_iterations_max": int(max(a - b for a, b in zip(iters, iters32))),
         "fp32_restarts": int(sum(r["restarts"] for r in reps)),
         "iterations_max": int(max(iters)) if iters else None,
-        "roofline": roof, "stages": stage_report, "scf_step": scf,
+        "roofline": roof, "step_roofline": step_roof, "stages": stage_report, "scf_step": scf,
         "plain_fp64": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
         "cpu_baseline": cpu,
@@ -522,8 +518,8 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=3)
-    ap.add_argument("--tc-gram", action="store_true",
-                    help="tcgen05 tensor-core Gram in the FP32 stage (default: compensated SIMT)")
+    ap.add_argument("--simt-gram", action="store_true",
+                    help="compensated SIMT Gram in the FP32 stage (default: tcgen05 TF32-split tensor cores)")
     ap.add_argument("--fwd64", type=int, default=0, choices=[0, 1, 2],
                     help="FP64 forward FFT in the FP32 stage's H apply: 1 always, 2 for H X near convergence")
     args = ap.parse_args()

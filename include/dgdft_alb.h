@@ -94,14 +94,14 @@ typedef struct {
   int keep_block;         /* 1: keep each converged N_g x m Ritz block on the
                              host after solve (for dgdft_alb_get_block)        */
   int bulk_kernels;       /* Gram products of the FP32 stage.  0 (default):
-                             SIMT FP32 with compensated accumulation, pencil
-                             condition limit 1e6; 1: tcgen05 tensor cores
-                             (bf16 hi/lo split, tensor-memory windows of 256
-                             rows read out into compensated registers) where
-                             3m <= 144 and N_g % 4 == 0, else SIMT; limit
-                             1e5 (faster, but its ~2^-17 split error per
-                             product leaves some elements dropping P for
-                             hundreds of iterations)                       */
+                             tcgen05 tensor cores where every element of a
+                             wave has m <= 48 and N_g % 4 == 0 (TMA copies of
+                             the blocks, each FP32 value split into two TF32
+                             parts, ~2^-22 relative per product, FP32
+                             accumulation in tensor memory over 256 rows,
+                             then compensated), else the SIMT kernel; 1: the
+                             SIMT FP32 kernel with compensated accumulation
+                             everywhere.  Other values give DGDFT_EINVAL.  */
   int h_fp64_forward;     /* FP64 forward FFT in the FP32 stage's H apply
                              (its rounding, amplified by |G|^2/2, sets the
                              stage's residual floor near 2e-6 Ha): 0 never;
@@ -109,11 +109,20 @@ typedef struct {
                              once the median residual is below 1e-5        */
   const char* autotune_cache;   /* optional JSON path; NULL = none            */
   const char* precond_weights;  /* learned preconditioner weights; NULL = none */
+  int device_wait_polls;  /* bound on every device-side wait of the tensor-core
+                             kernels, in polls: 0 (default) about a second;
+                             a small value makes the waits run out, which is
+                             how failure handling is tested: the element's
+                             report (and the call) then return
+                             DGDFT_ETIMEOUT.  Negative gives DGDFT_EINVAL. */
 } dgdft_alb_config;
 
 /* Per-element outcome of dgdft_alb_solve. */
 typedef struct {
-  int status;        /* DGDFT_OK or DGDFT_ENOTCONV (or another error)         */
+  int status;        /* DGDFT_OK, DGDFT_ENOTCONV, or DGDFT_ETIMEOUT when a
+                        bounded device wait ran out for the element (its
+                        FP32-stage products were then abandoned; the FP64
+                        stage may still have converged it: see max_resid) */
   int iterations;    /* LOBPCG iterations taken (all precision stages)        */
   double max_resid;  /* max_{j<J} residual (Ha) at exit, FP64-checked         */
   int fallbacks;     /* Rayleigh-Ritz retries without P / preconditioner falls */
@@ -165,8 +174,9 @@ dgdft_status dgdft_alb_set_initial(dgdft_alb_ctx* ctx, int elem, const double* x
 
 /* Run ALB generation for every element with a potential.  Writes n_elem
  * reports when per_elem is non-NULL.  Returns DGDFT_ENOTCONV when some
- * element missed tol (its basis is still available), DGDFT_ESTATE when an
- * element has no potential. */
+ * element missed tol (its basis is still available), DGDFT_ETIMEOUT when a
+ * bounded device wait ran out for some element (this takes precedence),
+ * DGDFT_ESTATE when an element has no potential. */
 dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem);
 
 /* One SCF step of ALB generation (Sec. II.B: in each SCF iteration the ALBs

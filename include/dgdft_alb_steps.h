@@ -34,10 +34,28 @@ dgdft_status dgdft_alb_apply_teter(dgdft_alb_ctx* ctx, int elem, int k, const do
 
 /* Gram product C = U^T V (Sec. II.B, operation 2) over ng rows:
  * U is ng x p, V is ng x q (column-major), C is p x q column-major (host,
- * FP64).  Computed by the same split-K kernels as the solver, in the
- * context's precision.  p, q <= 3 * max n_compute of the context. */
+ * FP64).  Computed by the solver's split-K SIMT kernels in the context's
+ * precision (FP32 with compensated accumulation in DGDFT_PREC_MIXED,
+ * FP64 otherwise); the solver's tensor-core Gram is exercised through
+ * dgdft_alb_lobpcg_gram. */
 dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u,
                             const double* v, double* c, int on_device);
+
+/* The Gram products of one LOBPCG iteration (Sec. II.B, operation 2: the 12
+ * products Phi^T Psi), computed on caller blocks by the same kernels and
+ * with the same precision choices as the solver for element `elem`
+ * (tensor cores in the FP32 stage unless bulk_kernels = 1).  blocks holds
+ * six N_g x m column-major blocks one after another: X, W, P, H X, H W, H P
+ * (m = n_compute; P and H P are ignored when has_p = 0).  With S = [X W P]:
+ * a = (H S)^T S and b = S^T S, each 3m x 3m column-major, are returned in
+ * their upper block triangle (the diagonal blocks included), which is all
+ * the Rayleigh-Ritz step reads; the rest is zero, and so is every P row and
+ * column when has_p = 0.  In the upper triangle the H-image is on the
+ * earlier block: a(i, j) = (H s_i)^T s_j for block(i) <= block(j).  xtw =
+ * X^T W (m x m).  a, b, xtw are host arrays; blocks is on the device when
+ * on_device = 1.  DGDFT_ETIMEOUT when a bounded device wait ran out. */
+dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int has_p, const double* blocks, double* a,
+                                   double* b, double* xtw, int on_device);
 
 /* Rayleigh-Ritz on a symmetric pencil (Sec. II.B, operation 4), FP64 on the
  * GPU: the lowest m eigenpairs of A y = theta B y with B positive definite.

@@ -34,7 +34,8 @@ class dgdft_alb_config(C.Structure):
                 ("maxit", C.c_int), ("check_every", C.c_int), ("hbm_cap_bytes", C.c_size_t),
                 ("cuda_stream", C.c_void_p), ("device", C.c_int), ("keep_block", C.c_int),
                 ("bulk_kernels", C.c_int), ("h_fp64_forward", C.c_int),
-                ("autotune_cache", C.c_char_p), ("precond_weights", C.c_char_p)]
+                ("autotune_cache", C.c_char_p), ("precond_weights", C.c_char_p),
+                ("device_wait_polls", C.c_int)]
 
 
 class dgdft_solve_report(C.Structure):
@@ -61,6 +62,7 @@ _SIGS = {
     "dgdft_alb_apply_teter": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "dgdft_alb_lobpcg_gram": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P, C.c_int]),
     "dgdft_alb_restrict_orthonormalise": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P,
                                                     C.c_int]),
     "dgdft_alb_get_block": (C.c_int, [_P, C.c_int, _P, C.c_int]),
@@ -134,7 +136,7 @@ class Context:
 
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
-                 precond_weights=None, tc_gram=False, h_fp64_forward=False):
+                 precond_weights=None, simt_gram=False, h_fp64_forward=False, device_wait_polls=0):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -144,7 +146,8 @@ class Context:
         cfg.maxit = maxit
         cfg.check_every = check_every
         cfg.keep_block = int(keep_block)
-        cfg.bulk_kernels = int(tc_gram)
+        cfg.bulk_kernels = int(simt_gram)
+        cfg.device_wait_polls = int(device_wait_polls)
         cfg.h_fp64_forward = int(h_fp64_forward)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
         cfg.cuda_stream = stream
@@ -212,14 +215,14 @@ class Context:
     def dgdft_alb_solve(self, check=False):
         reps = (dgdft_solve_report * self.n)()
         st = self.lib.dgdft_alb_solve(self.h, reps)
-        if st not in (DGDFT_OK, DGDFT_ENOTCONV) or (check and st != DGDFT_OK):
+        if st not in (DGDFT_OK, DGDFT_ENOTCONV, DGDFT_ETIMEOUT) or (check and st != DGDFT_OK):
             self._check(st, "solve")
         return st, self._reports(reps)
 
     def dgdft_alb_scf_step(self, n_iter=3):
         reps = (dgdft_solve_report * self.n)()
         st = self.lib.dgdft_alb_scf_step(self.h, int(n_iter), reps)
-        if st not in (DGDFT_OK, DGDFT_ENOTCONV):
+        if st not in (DGDFT_OK, DGDFT_ENOTCONV, DGDFT_ETIMEOUT):
             self._check(st, "scf_step")
         return st, self._reports(reps)
 
@@ -346,6 +349,20 @@ class Context:
         self._check(self.lib.dgdft_alb_gram(self.h, ng, p, q, _ptr(u)[0], _ptr(v)[0], _ptr(c)[0], 0),
                     "gram")
         return c.T.copy()
+
+    def dgdft_alb_lobpcg_gram(self, elem, blocks, has_p=True):
+        """blocks: (6, m, N_g) rows X, W, P, HX, HW, HP.  Returns (a, b, xtw)
+        with a, b the 3m x 3m pencil blocks (upper block triangle) and xtw =
+        X^T W, as row-major NumPy arrays of the matrices."""
+        blk = np.ascontiguousarray(blocks, np.float64)
+        m = blk.shape[1]
+        a = np.zeros((3 * m, 3 * m))
+        b = np.zeros((3 * m, 3 * m))
+        xtw = np.zeros((m, m))
+        self._check(self.lib.dgdft_alb_lobpcg_gram(self.h, elem, int(bool(has_p)), _ptr(blk)[0], _ptr(a)[0],
+                                                   _ptr(b)[0], _ptr(xtw)[0], 0), "lobpcg_gram")
+        # column-major out -> matrices
+        return a.T.copy(), b.T.copy(), xtw.T.copy()
 
     def dgdft_alb_rayleigh_ritz(self, a, b, m):
         n = a.shape[0]

@@ -50,7 +50,7 @@ enum {
   ST_NRESTART = 9,  // restarts taken (bounded per solve)
   STATE_WORDS = 10
 };
-enum { ERR_CHOL = 1, ERR_NONFINITE = 2, ERR_EIG = 4 };
+enum { ERR_CHOL = 1, ERR_NONFINITE = 2, ERR_EIG = 4, ERR_TIMEOUT = 8 };  // ERR_TIMEOUT: a bounded device wait ran out
 
 constexpr int MAX_STAGES = 8;
 enum { TW_H = 0, TW_X = 1, TW_Y = 2, TW_Z = 3 };

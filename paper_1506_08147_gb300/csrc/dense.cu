@@ -285,6 +285,11 @@ __device__ void tri_eigvecs(const double* d, const double* e, int n, int m, doub
 __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const RRTask* __restrict__ tasks) {
   const RRTask T = tasks[blockIdx.x];
   if (T.state && !T.state[ST_ACTIVE]) return;
+  if (T.state && (T.state[ST_ERROR] & ERR_TIMEOUT)) {
+    // a wait in this iteration's Gram launch ran out: its products are stale
+    if (threadIdx.x == 0) T.state[ST_ACTIVE] = 0;
+    return;
+  }
   __shared__ double red[32];
   __shared__ int sflag;
   __shared__ double sval[4];
@@ -594,6 +599,11 @@ constexpr int RRS_THREADS = 512;
 __global__ void __launch_bounds__(RRS_THREADS) rr_smem_kernel(const RRTask* __restrict__ tasks) {
   const RRTask T = tasks[blockIdx.x];
   if (T.state && !T.state[ST_ACTIVE]) return;
+  if (T.state && (T.state[ST_ERROR] & ERR_TIMEOUT)) {
+    // a wait in this iteration's Gram launch ran out: its products are stale
+    if (threadIdx.x == 0) T.state[ST_ACTIVE] = 0;
+    return;
+  }
   extern __shared__ __align__(16) double smd[];
   __shared__ double red[32];
   __shared__ int sflag;

@@ -171,12 +171,18 @@ std::string cuda_err_string(cudaError_t e);
 }  // namespace dgdft
 
 namespace dgdft {
-// tc_gram.cu: tcgen05 split-bf16 Gram products for the FP32 stage (3m <= 144,
-// N_g % 4 == 0)
-void init_tc_gram_kernel();
-void launch_tc_gram(const Batch<float>& b, int mode, double* partial, size_t partial_cap, cudaStream_t st);
-void launch_tc_gram_ptrs(const Batch<float>& b, const float* u, int p, const float* v, int q, int ng, double* c,
-                         double* partial, size_t partial_cap, cudaStream_t st);
+// tf32_gram.cu: tcgen05 TF32-split Gram products of the FP32 stage, operands
+// loaded by TMA (m <= 48, N_g % 4 == 0)
+bool tf32_gram_eligible(const BatchShape& s);
+// encodes the 10 block tensor maps of each element (128 bytes each) into
+// host_out; returns "" or the reason it could not
+std::string encode_tf32_gram_maps(const ElemDev<float>* h, int nel, void* host_out);
+void init_tf32_gram_kernel();
+// mode 0: the 12 LOBPCG Gram blocks into gram (A, B); mode 1: X^T W into gxw.
+// polls: bound of every device wait (0: the default, about a second).
+// Returns false (nothing launched) when the partial buffer is too small.
+bool launch_tf32_gram(const Batch<float>& b, const void* d_maps, int mode, double* partial, size_t partial_cap,
+                      uint32_t polls, cudaStream_t st);
 
 // alb.cu
 // One product of the FP64 orthonormalisation for one element: the Gram

@@ -137,6 +137,7 @@ struct dgdft_alb_ctx {
   void (*cache_free)(void*) = nullptr;
   std::vector<int> cache_proj_version;
   ConvNet* net = nullptr;  // learned preconditioner, created on first use
+  int wait_polls = 0;      // bounded device waits: polls before giving up (0: default)
   void drop_cache() {
     if (cache && cache_free) cache_free(cache);
     cache = nullptr;
@@ -199,11 +200,11 @@ size_t elem_bytes(const ElemHost& h) {
 
 void default_x0(std::vector<double>& x, int elem);
 
-// The FP32 stage's Gram products run on the tensor cores (the windowed
-// tcgen05 kernel) when selected and the shapes allow: 3m <= 144 columns,
-// N_g a multiple of 4 (16-byte column starts); otherwise the SIMT kernel.
-inline bool tc_ok(const dgdft_alb_config& c, const BatchShape& s) {
-  return c.bulk_kernels == 1 && 3 * s.max_m <= 144 && s.ng_mult4;
+// The FP32 stage's Gram products run on the tensor cores (TF32 split, TMA)
+// unless the SIMT kernels are selected, when every element has m <= 48 and
+// N_g a multiple of 4 (16-byte column starts for the copies).
+inline bool tf32_selected(const dgdft_alb_config& c, const BatchShape& s) {
+  return c.bulk_kernels == 0 && tf32_gram_eligible(s);
 }
 
 template <class real> struct Wave {
@@ -232,7 +233,12 @@ template <class real> struct Wave {
     RRTask *rr_init = nullptr, *rr_lob = nullptr;
     double* partial = nullptr;
     size_t partial_cap = 0;
+    const unsigned char* maps = nullptr;
   };
+  // TMA tensor maps of every element's blocks (FP32 waves on the tensor-core
+  // Gram), 10 x 128 bytes per element; nullptr when the SIMT Gram runs
+  unsigned char* d_maps = nullptr;
+  const unsigned char* maps = nullptr;  // of the current view
   SubView full, sub[2];
   bool split = false;
   bool hx64 = false;            // capture H X' with the FP64 forward transform
@@ -255,6 +261,7 @@ template <class real> struct Wave {
     d_rr_lob = v.rr_lob;
     partial = v.partial;
     partial_cap = v.partial_cap;
+    maps = v.maps;
   }
 
   // Half-batch views; split only FP32 waves of >= 2 elements without the
@@ -265,6 +272,8 @@ template <class real> struct Wave {
     full.rr_lob = d_rr_lob;
     full.partial = partial;
     full.partial_cap = partial_cap;
+    full.maps = d_maps;
+    maps = d_maps;
     const int nel = batch.s.nel;
     if (!std::is_same<real, float>::value || learned || nel < 2) return DGDFT_OK;
     const int h0 = nel / 2;
@@ -279,6 +288,7 @@ template <class real> struct Wave {
       v.rr_lob = d_rr_lob + off;
       v.partial = partial + per * off;
       v.partial_cap = per * cnt;
+      v.maps = d_maps ? d_maps + (size_t)off * 10 * 128 : nullptr;
     }
     CK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
@@ -350,6 +360,8 @@ template <class real> struct Wave {
     }
     total += sizeof(double) * pcap + ALIGN;
     total += (sizeof(ElemDev<real>) + 2 * sizeof(RRTask)) * nel + 4 * ALIGN;
+    const bool want_maps = std::is_same<real, float>::value && tf32_selected(ctx->cfg, s);
+    if (want_maps) total += (size_t)nel * 10 * 128 + ALIGN;
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, total);
     if (e != cudaSuccess) return ctx->fail(DGDFT_ENOMEM, "device allocation of a wave failed: " + cuda_err_string(e));
@@ -387,6 +399,17 @@ template <class real> struct Wave {
       t.restart_max = restarts;
       t.mode = RR_LOBPCG;
       rr_lob[i] = t;
+    }
+    if (want_maps) {
+      // tensor maps need the blocks' device addresses: encoded here, once
+      std::vector<unsigned char> hm((size_t)nel * 10 * 128);
+      std::string err;
+      if constexpr (std::is_same<real, float>::value) err = encode_tf32_gram_maps(h.data(), nel, hm.data());
+      unsigned char* dm = (unsigned char*)arena.take(hm.size());
+      if (err.empty() && dm) {
+        CK(ctx_copy(ctx, dm, hm.data(), hm.size(), cudaMemcpyHostToDevice));
+        d_maps = dm;
+      }
     }
     CK(ctx_copy(ctx, d_elems, h.data(), sizeof(ElemDev<real>) * nel, cudaMemcpyHostToDevice));
     CK(ctx_copy(ctx, d_rr_init, rr_init.data(), sizeof(RRTask) * nel, cudaMemcpyHostToDevice));
@@ -653,14 +676,11 @@ template <class real> struct Wave {
   }
   const bool trace_ = std::getenv("DGDFT_TRACE") != nullptr;
 
-  // Tensor-core Gram for the FP32 stage when the pencil fits one TMEM
-  // accumulator (3m <= 256); returns false when the SIMT kernel must run.
+  // Tensor-core Gram of the FP32 stage (mode 0: the 12 LOBPCG blocks, mode
+  // 1: X^T W); returns false when the SIMT kernel must run.
   bool tc_gram(int mode, cudaStream_t st) {
     if constexpr (std::is_same<real, float>::value) {
-      if (tc_ok(ctx->cfg, batch.s)) {
-        launch_tc_gram(batch, mode, partial, partial_cap, st);
-        return true;
-      }
+      if (maps) return launch_tf32_gram(batch, maps, mode, partial, partial_cap, (uint32_t)ctx->wait_polls, st);
     }
     (void)mode;
     (void)st;
@@ -690,6 +710,23 @@ template <class real> struct Wave {
       }
     }
     return g;
+  }
+
+  // X^T W (into gxw) and the 12 pencil blocks (into gram): tensor cores in
+  // the FP32 stage when selected, else the split-K SIMT kernels
+  void gram_xtw(cudaStream_t st) {
+    if (tc_gram(1, st)) return;
+    GramJob<real> g;
+    g.npairs = 1;
+    g.a[0] = bref<real>(BX);
+    g.b[0] = bref<real>(BW);
+    g.needs_p[0] = 0;
+    g.out_id[0] = OUT_GXW;
+    g.brow[0] = g.bcol[0] = 0;
+    launch_gram<real>(batch, g, partial, partial_cap, st);
+  }
+  void gram_pencil(cudaStream_t st) {
+    if (!tc_gram(0, st)) launch_gram<real>(batch, gram12(), partial, partial_cap, st);
   }
 
   void enqueue_initial(cudaStream_t st) {
@@ -729,14 +766,7 @@ template <class real> struct Wave {
     if (std::is_same<real, float>::value) launch_shift<real>(batch, st);
     precondition(st);
     {
-      GramJob<real> g;
-      g.npairs = 1;
-      g.a[0] = bref<real>(BX);
-      g.b[0] = bref<real>(BW);
-      g.needs_p[0] = 0;
-      g.out_id[0] = OUT_GXW;
-      g.brow[0] = g.bcol[0] = 0;
-      if (!tc_gram(1, st)) launch_gram<real>(batch, g, partial, partial_cap, st);
+      gram_xtw(st);
       TsmmJob<real> t;
       t.nin = 1;
       t.in[0] = bref<real>(BX);
@@ -747,7 +777,7 @@ template <class real> struct Wave {
       launch_tsmm<real>(batch, t, st);
     }
     launch_apply_h<real>(batch, bref<real>(BW), bref<real>(BHW), 0, st, fwd64());
-    if (!tc_gram(0, st)) launch_gram<real>(batch, gram12(), partial, partial_cap, st);
+    gram_pencil(st);
   }
 
   // Rayleigh-Ritz and the block updates (operations 3, 4; H X for FP32).
@@ -1199,7 +1229,8 @@ dgdft_status copy_block_to(Wave<real>& w, int i, Wave<double>& dst, int di, cuda
 dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, double seconds,
                          const std::vector<int>& extra_iters, const std::vector<int>& extra_fb,
                          const std::vector<double>& bulk_res, long long graph_kernels,
-                         const std::vector<int>& restarts, bool scf = false) {
+                         const std::vector<int>& restarts, bool scf = false,
+                         const std::vector<int>& bulk_err = std::vector<int>()) {
   const size_t nel = w.ids.size();
   std::vector<int> idx(nel), Js(nel);
   std::vector<const double*> xs(nel);
@@ -1255,10 +1286,14 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     eh.rep.seconds = seconds;
     eh.rep.graph_kernels = graph_kernels;
     eh.rep.restarts = restarts.empty() ? 0 : restarts[i];
-    // an SCF step has no tolerance: OK unless the element failed
-    eh.rep.status = (sw[ST_ERROR] != 0 || s != DGDFT_OK) ? DGDFT_ENOTCONV
-                    : (scf || mx <= ctx->cfg.tol)     ? DGDFT_OK
-                                                      : DGDFT_ENOTCONV;
+    // an SCF step has no tolerance: OK unless the element failed.  A
+    // bounded device wait that ran out (in either stage) is reported as such
+    // even when the FP64 stage went on to converge the element.
+    const int err = sw[ST_ERROR] | (bulk_err.empty() ? 0 : bulk_err[i]);
+    eh.rep.status = (err & ERR_TIMEOUT)                   ? DGDFT_ETIMEOUT
+                    : (sw[ST_ERROR] != 0 || s != DGDFT_OK) ? DGDFT_ENOTCONV
+                    : (scf || mx <= ctx->cfg.tol)          ? DGDFT_OK
+                                                           : DGDFT_ENOTCONV;
     eh.solved = true;
   }
   return DGDFT_OK;
@@ -1285,13 +1320,10 @@ dgdft_status get_waves(dgdft_alb_ctx* ctx, const std::vector<int>& ids, bool kee
     dgdft_status s;
     if (mixed) {
       wp->w32.reset(new Wave<float>());
-      // Cholesky condition limit of the FP32 stage's pencil: the compensated
-      // SIMT Gram (~2e-7 relative) tolerates nearly dependent [X W P] up to
-      // 1e6; the tensor-core Gram (bf16 split, a few 1e-8 on one-signed
-      // sums but coarser on cancelling ones) up to 1e5
-      bool tc = c.bulk_kernels == 1;
-      for (int id : ids) tc = tc && 3 * ctx->el[id].d.n_compute <= 144 && ctx->el[id].ng() % 4 == 0;
-      const double cond32 = tc ? 1e5 : 1e6;
+      // Cholesky condition limit of the FP32 stage's pencil: the Gram
+      // products (compensated SIMT ~2e-7 relative; TF32 split ~2^-22 per
+      // product) tolerate nearly dependent [X W P] up to 1e6
+      const double cond32 = 1e6;
       // an element whose pencil fails at every level is restarted (X
       // perturbed, P dropped) up to 8 times before it is left to the FP64 stage
       if ((s = wp->w32->build(ctx, ids, cond32, 8)) != DGDFT_OK) return s;
@@ -1322,7 +1354,7 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
   Wave<double>& w64 = *wp->w64;
   w64.graph_kernels = 0;
   if (wp->w32) wp->w32->graph_kernels = 0;
-  std::vector<int> it32, fb32, rs32;
+  std::vector<int> it32, fb32, rs32, er32;
   std::vector<double> res32;
   dgdft_status s;
   if (mixed) {
@@ -1356,6 +1388,7 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
       it32.push_back(w32.h_state[i * STATE_WORDS + ST_ITER]);
       fb32.push_back(w32.h_state[i * STATE_WORDS + ST_FALLBACK]);
       rs32.push_back(w32.h_state[i * STATE_WORDS + ST_NRESTART]);
+      er32.push_back(w32.h_state[i * STATE_WORDS + ST_ERROR]);
     }
     CK(cudaStreamSynchronize(ctx->stream));
     if (std::getenv("DGDFT_TRACE")) {
@@ -1389,7 +1422,7 @@ dgdft_status solve_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int wav
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const long long gk = w64.graph_kernels + (wp->w32 ? wp->w32->graph_kernels : 0);
-  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32, gk, rs32);
+  return finish_wave(ctx, w64, wave_idx, secs, it32, fb32, res32, gk, rs32, false, er32);
 }
 
 // One SCF step for a resident single-wave workload (Sec. II.B: in every SCF
@@ -1417,7 +1450,7 @@ dgdft_status scf_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int n_ite
   if (s != DGDFT_OK) return s;
   Wave<double>& w64 = *wp->w64;
   w64.graph_kernels = 0;
-  std::vector<int> it32, fb32, rs32;
+  std::vector<int> it32, fb32, rs32, er32;
   std::vector<double> res32;
   const bool trace = std::getenv("DGDFT_TRACE") != nullptr;
   auto stamp = [&](const char* what) {
@@ -1451,6 +1484,7 @@ dgdft_status scf_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int n_ite
       it32.push_back(w32.h_state[i * STATE_WORDS + ST_ITER]);
       fb32.push_back(w32.h_state[i * STATE_WORDS + ST_FALLBACK]);
       rs32.push_back(w32.h_state[i * STATE_WORDS + ST_NRESTART]);
+      er32.push_back(w32.h_state[i * STATE_WORDS + ST_ERROR]);
     }
     if ((s = w64.verify(ctx->cfg.tol)) != DGDFT_OK) return s;
     stamp("FP64 check done");
@@ -1460,7 +1494,7 @@ dgdft_status scf_wave(dgdft_alb_ctx* ctx, const std::vector<int>& ids, int n_ite
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const long long gk = w64.graph_kernels + (wp->w32 ? wp->w32->graph_kernels : 0);
-  s = finish_wave(ctx, w64, 0, secs, it32, fb32, res32, gk, rs32, true);
+  s = finish_wave(ctx, w64, 0, secs, it32, fb32, res32, gk, rs32, true, er32);
   stamp("restriction and orthonormalisation done");
   return s;
 }
@@ -1531,6 +1565,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   if (cfg->precision != DGDFT_PREC_FP64 && cfg->precision != DGDFT_PREC_MIXED) return DGDFT_EINVAL;
   if (cfg->precond != DGDFT_PRECOND_TETER && cfg->precond != DGDFT_PRECOND_LEARNED) return DGDFT_EINVAL;
   if (!(cfg->tol > 0.0) || cfg->maxit <= 0) return DGDFT_EINVAL;
+  if (cfg->bulk_kernels != 0 && cfg->bulk_kernels != 1) return DGDFT_EINVAL;
   for (int i = 0; i < n_elem; ++i) {
     const dgdft_element_desc& d = elems[i];
     FftPlan p;
@@ -1554,6 +1589,8 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   std::unique_ptr<dgdft_alb_ctx> ctx(new dgdft_alb_ctx());
   ctx->cfg = *cfg;
   if (ctx->cfg.check_every < 1) ctx->cfg.check_every = 1;
+  if (cfg->device_wait_polls < 0) return DGDFT_EINVAL;
+  ctx->wait_polls = cfg->device_wait_polls;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DGDFT_ECUDA;
   int dev = cfg->device;
@@ -1570,7 +1607,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
     ctx->own_stream = true;
   }
   init_hamiltonian_kernels();
-  init_tc_gram_kernel();
+  init_tf32_gram_kernel();
   init_rr_kernels();
   init_blas_kernels();
   cudaGetLastError();  // attribute queries above must not leave an error behind
@@ -1692,9 +1729,11 @@ dgdft_status dgdft_alb_scf_step(dgdft_alb_ctx* ctx, int n_iter, dgdft_solve_repo
   dgdft_status out = DGDFT_OK;
   for (int i = 0; i < (int)ctx->el.size(); ++i) {
     if (per_elem) per_elem[i] = ctx->el[i].rep;
-    if (ctx->el[i].rep.status != DGDFT_OK) out = DGDFT_ENOTCONV;
+    if (ctx->el[i].rep.status == DGDFT_ETIMEOUT) out = DGDFT_ETIMEOUT;
+    else if (ctx->el[i].rep.status != DGDFT_OK && out == DGDFT_OK) out = DGDFT_ENOTCONV;
   }
-  if (out != DGDFT_OK) ctx->err = "some elements failed in the SCF step";
+  if (out == DGDFT_ETIMEOUT) ctx->err = "a bounded device wait ran out";
+  else if (out != DGDFT_OK) ctx->err = "some elements failed in the SCF step";
   return out;
 }
 
@@ -1714,9 +1753,11 @@ dgdft_status dgdft_alb_solve(dgdft_alb_ctx* ctx, dgdft_solve_report* per_elem) {
   dgdft_status out = DGDFT_OK;
   for (int i = 0; i < (int)ctx->el.size(); ++i) {
     if (per_elem) per_elem[i] = ctx->el[i].rep;
-    if (ctx->el[i].rep.status != DGDFT_OK) out = DGDFT_ENOTCONV;
+    if (ctx->el[i].rep.status == DGDFT_ETIMEOUT) out = DGDFT_ETIMEOUT;
+    else if (ctx->el[i].rep.status != DGDFT_OK && out == DGDFT_OK) out = DGDFT_ENOTCONV;
   }
-  if (out != DGDFT_OK) ctx->err = "some elements did not reach the tolerance";
+  if (out == DGDFT_ETIMEOUT) ctx->err = "a bounded device wait ran out";
+  else if (out != DGDFT_OK) ctx->err = "some elements did not reach the tolerance";
   return out;
 }
 
@@ -1841,10 +1882,7 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
   ElemDev<real>* de = nullptr;
   int* dstate = nullptr;
   const size_t tiles = ((p + 63) / 64) * ((q + 63) / 64);
-  bool use_tc = false;
-  if constexpr (std::is_same<real, float>::value) use_tc = ctx->cfg.bulk_kernels == 1 && q <= 144 && ng % 4 == 0;
-  const size_t pcap = use_tc ? ((size_t)(ng + 2047) / 2048) * ((p + 127) / 128) * 128 * 256
-                             : ((size_t)(ng + 2047) / 2048) * tiles * 4096;
+  const size_t pcap = ((size_t)(ng + 2047) / 2048) * tiles * 4096;
   CK(cudaMalloc(&du, sizeof(real) * (size_t)ng * p));
   CK(cudaMalloc(&dv, sizeof(real) * (size_t)ng * q));
   CK(cudaMalloc(&dc, sizeof(double) * (size_t)p * q));
@@ -1881,14 +1919,7 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
     g.ld_in = ng;
     g.ld_out = p;
     g.out_ptr = dc;
-    if constexpr (std::is_same<real, float>::value) {
-      if (use_tc)
-        launch_tc_gram_ptrs(b, du, p, dv, q, ng, dc, part, pcap, ctx->stream);
-      else
-        launch_gram<real>(b, g, part, pcap, ctx->stream);
-    } else {
-      launch_gram<real>(b, g, part, pcap, ctx->stream);
-    }
+    launch_gram<real>(b, g, part, pcap, ctx->stream);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = ctx_copy(ctx, c, dc, sizeof(double) * (size_t)p * q, cudaMemcpyDeviceToHost);
@@ -1901,6 +1932,47 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
   cudaFree(de);
   cudaFree(dstate);
   return s;
+}
+
+// The Gram products of one LOBPCG iteration on caller blocks, through the
+// wave's own kernels (see dgdft_alb_lobpcg_gram).
+template <class real>
+dgdft_status lobpcg_gram_t(dgdft_alb_ctx* ctx, int elem, int has_p, const double* blocks, double* a, double* b,
+                           double* xtw, int on_device) {
+  Wave<real> w;
+  dgdft_status s = with_step_wave<real>(ctx, elem, w);
+  if (s != DGDFT_OK) return s;
+  ElemDev<real>& E = w.h[0];
+  const int m = E.m;
+  const size_t n = (size_t)E.ng * m;
+  const int order[6] = {BX, BW, BP, BHX, BHW, BHP};
+  for (int q = 0; q < 6; ++q)
+    if ((s = step_in<real>(ctx, E.blk[order[q]][0], blocks + q * n, n, on_device)) != DGDFT_OK) return s;
+  const int hp = has_p ? 1 : 0;
+  CK(ctx_copy(ctx, E.state + ST_HAS_P, &hp, sizeof(int), cudaMemcpyHostToDevice));
+  const size_t nn = (size_t)9 * m * m;
+  CK(cudaMemsetAsync(E.gram, 0, sizeof(double) * 2 * nn, ctx->stream));
+  CK(cudaMemsetAsync(E.gxw, 0, sizeof(double) * m * m, ctx->stream));
+  w.gram_xtw(ctx->stream);
+  w.gram_pencil(ctx->stream);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  int err = 0;
+  CK(ctx_copy(ctx, &err, E.state + ST_ERROR, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err & ERR_TIMEOUT) return ctx->fail(DGDFT_ETIMEOUT, "lobpcg_gram: a bounded device wait ran out");
+  std::vector<double> g(2 * nn);
+  CK(ctx_copy(ctx, g.data(), E.gram, sizeof(double) * 2 * nn, cudaMemcpyDeviceToHost));
+  // upper block triangle (with the diagonal blocks) as computed, zeros below
+  const int ld = 3 * m;
+  for (int c = 0; c < ld; ++c)
+    for (int r = 0; r < ld; ++r) {
+      const bool upper = r / m <= c / m;
+      const bool p_part = !has_p && (r >= 2 * m || c >= 2 * m);
+      a[r + (size_t)c * ld] = (upper && !p_part) ? g[r + (size_t)c * ld] : 0.0;
+      b[r + (size_t)c * ld] = (upper && !p_part) ? g[nn + r + (size_t)c * ld] : 0.0;
+    }
+  CK(ctx_copy(ctx, xtw, E.gxw, sizeof(double) * m * m, cudaMemcpyDeviceToHost));
+  return DGDFT_OK;
 }
 
 template <class real>
@@ -1919,9 +1991,7 @@ dgdft_status time_stage_t(dgdft_alb_ctx* ctx, Wave<real>& w, int stage, int reps
       case DGDFT_STAGE_XY_FWD: launch_h_pass<real>(w.batch, 0, bref<real>(BW), bref<real>(BHW), 0, st); break;
       case DGDFT_STAGE_Z_MULT: launch_h_pass<real>(w.batch, 1, bref<real>(BW), bref<real>(BHW), 0, st); break;
       case DGDFT_STAGE_XY_INV: launch_h_pass<real>(w.batch, 2, bref<real>(BW), bref<real>(BHW), 0, st); break;
-      case DGDFT_STAGE_GRAM:
-        if (!w.tc_gram(0, st)) launch_gram<real>(w.batch, w.gram12(), w.partial, w.partial_cap, st);
-        break;
+      case DGDFT_STAGE_GRAM: w.gram_pencil(st); break;
       case DGDFT_STAGE_UPDATE: {
         TsmmJob<real> t;
         t.nin = 3;
@@ -2001,6 +2071,15 @@ dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const doub
   CK(cudaSetDevice(ctx->device));
   return ctx->cfg.precision == DGDFT_PREC_FP64 ? gram_t<double>(ctx, ng, p, q, u, v, c, on_device)
                                                 : gram_t<float>(ctx, ng, p, q, u, v, c, on_device);
+}
+
+dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int has_p, const double* blocks, double* a,
+                                   double* b, double* xtw, int on_device) {
+  if (!ctx || !blocks || !a || !b || !xtw || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  return ctx->cfg.precision == DGDFT_PREC_FP64
+             ? lobpcg_gram_t<double>(ctx, elem, has_p, blocks, a, b, xtw, on_device)
+             : lobpcg_gram_t<float>(ctx, elem, has_p, blocks, a, b, xtw, on_device);
 }
 
 dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int n, int m, const double* a, const double* b,

@@ -122,18 +122,18 @@ def test_teter(prec, which):
 
 # -------------------------------------------------------------- Gram
 
-GRAM_KINDS = [(B.DGDFT_PREC_FP64, False), (B.DGDFT_PREC_MIXED, False), (B.DGDFT_PREC_MIXED, True)]  # (prec, tc)
+GRAM_KINDS = [B.DGDFT_PREC_FP64, B.DGDFT_PREC_MIXED]
 
 
-@pytest.mark.parametrize("prec,tc", GRAM_KINDS)
+@pytest.mark.parametrize("prec", GRAM_KINDS)
 @pytest.mark.parametrize("shape", [(1000, 7, 5), (122880, 48, 48), (70001, 130, 70), (4096, 288, 144)])
-def test_gram(prec, tc, shape):
+def test_gram(prec, shape):
     ng, p, q = shape
     gen = np.random.default_rng(3)
     u = gen.standard_normal((p, ng))
     v = gen.standard_normal((q, ng))
     el = small_kb_element()
-    c = ctx_for(el, prec, tc_gram=tc)
+    c = ctx_for(el, prec)
     got = c.dgdft_alb_gram(u, v)
     ref = u @ v.T
     scale = np.sqrt(ng)  # typical |u_i| |v_j| / sqrt(ng) for random rows
@@ -143,15 +143,12 @@ def test_gram(prec, tc, shape):
     c.close()
 
 
-@pytest.mark.parametrize("tc", [False, True])
 @pytest.mark.parametrize("ng,q", [(122880, 48), (122880, 144), (70000, 70)])
-def test_gram_accumulation_one_signed(tc, ng, q):
+def test_gram_accumulation_one_signed(ng, q):
     """Rows of one sign make every partial sum grow, the worst case for
     accumulation rounding.  Measured against the exact product of the
     FP32-rounded inputs, relative to sum_k |u_k| |v_k|: the compensated SIMT
-    kernel within a few FP32 units, the tensor-core kernel (bf16 split,
-    windowed tensor-memory accumulation; 70000 rows take the SIMT path as the
-    columns are not 16-byte aligned) within 2e-7."""
+    kernel within a few FP32 units."""
     p = 48
     gen = np.random.default_rng(4)
     u = 1.0 + np.abs(gen.standard_normal((p, ng)))
@@ -159,12 +156,93 @@ def test_gram_accumulation_one_signed(tc, ng, q):
     u32 = u.astype(np.float32).astype(np.float64)
     v32 = v.astype(np.float32).astype(np.float64)
     el = small_kb_element()
-    c = ctx_for(el, B.DGDFT_PREC_MIXED, tc_gram=tc)
+    c = ctx_for(el, B.DGDFT_PREC_MIXED)
     got = c.dgdft_alb_gram(u, v)
     ref = u32 @ v32.T
     err = np.max(np.abs(got - ref) / ref)
-    assert err < (2e-7 if tc else 2e-8), err
+    assert err < 2e-8, err
     c.close()
+
+
+def ragged_element():
+    # N_g = 20 * 15 * 9 = 2700: a multiple of 4 (16-byte columns) but not of
+    # the tensor-core kernel's 32-row stage; m = 40 < 48 leaves zero-filled
+    # columns in every 48-column slot
+    return synth.random_element(9, 2, (20, 15, 9), 5, J=30, m=40)
+
+
+def lobpcg_blocks(el, gen, kind):
+    """Six (m, N_g) blocks X, W, P, HX, HW, HP.  kind 'random': independent
+    normal rows; 'ortho': X orthonormal and W, P orthogonal to X, so X^T W
+    and X^T P are zero up to rounding (sums that cancel), with H-images that
+    are near multiples of their blocks as in a converging LOBPCG."""
+    m, ng = el.m, el.ng
+    if kind == "random":
+        return gen.standard_normal((6, m, ng))
+    q, _ = np.linalg.qr(gen.standard_normal((ng, 3 * m)))
+    x, w, p = q[:, :m].T, q[:, m:2 * m].T, q[:, 2 * m:].T * 1e-3
+    th = np.sort(gen.uniform(-6.0, -4.0, m))
+    hx = th[:, None] * x + 1e-4 * gen.standard_normal((m, ng)) / np.sqrt(ng)
+    hw = 5.0 * w + gen.standard_normal((m, ng)) / np.sqrt(ng)
+    hp = -5.0 * p + 1e-3 * gen.standard_normal((m, ng)) / np.sqrt(ng)
+    return np.stack([x, w, p, hx, hw, hp])
+
+
+# (precision, SIMT Gram): the FP64 kernels, the compensated FP32 SIMT
+# kernel, the tensor-core TF32-split kernel (default of the mixed form)
+LOBPCG_GRAM_KINDS = [(B.DGDFT_PREC_FP64, False), (B.DGDFT_PREC_MIXED, True), (B.DGDFT_PREC_MIXED, False)]
+
+
+@pytest.mark.parametrize("prec,simt", LOBPCG_GRAM_KINDS)
+@pytest.mark.parametrize("which", ["small", "ragged", "cfg2"])
+@pytest.mark.parametrize("has_p", [True, False])
+@pytest.mark.parametrize("kind", ["random", "ortho"])
+def test_lobpcg_gram(prec, simt, which, has_p, kind):
+    """The Gram products of one LOBPCG iteration through the solver's own
+    kernels, against NumPy FP64 products of the same (working-precision)
+    inputs, entry by entry relative to sum_k |a_k| |b_k| (the scale of the
+    rounding of any summation order): FP64 to 1e-13, the compensated SIMT
+    kernel to 2e-7, the TF32-split tensor-core kernel to 2^-20 (two TF32
+    parts carry ~2^-22 of each value) except on one-signed sums (the
+    diagonals of the diagonal blocks, x^T x and x^T (H x) of a near
+    eigenvector): there the tensor core's FP32 accumulation, which does not
+    round to nearest, loses ~1/2 unit of the running sum per MMA and leaves
+    a bias below 4e-6."""
+    el = {"small": small_kb_element, "ragged": ragged_element, "cfg2": cfg2_element}[which]()
+    gen = np.random.default_rng(31)
+    blk = lobpcg_blocks(el, gen, kind)
+    c = ctx_for(el, prec, simt_gram=simt)
+    a, b, xtw = c.dgdft_alb_lobpcg_gram(0, blk, has_p)
+    c.close()
+    if prec == B.DGDFT_PREC_MIXED:
+        blk = blk.astype(np.float32).astype(np.float64)
+    x, w, p, hx, hw, hp = blk
+    m = el.m
+    s_ = np.vstack([x, w, p])
+    hs = np.vstack([hx, hw, hp])
+    ref_a, ref_b = hs @ s_.T, s_ @ s_.T
+    sc_a, sc_b = np.abs(hs) @ np.abs(s_).T, np.abs(s_) @ np.abs(s_).T
+    nb = 3 if has_p else 2
+    tol = {B.DGDFT_PREC_FP64: 1e-13}.get(prec, 2e-7 if simt else 2.0 ** -20)
+    worst = worst_diag = 0.0
+    for bi in range(3):
+        for bj in range(3):
+            rs, cs = slice(bi * m, bi * m + m), slice(bj * m, bj * m + m)
+            if bi > bj or bi >= nb or bj >= nb:
+                assert np.all(a[rs, cs] == 0.0) and np.all(b[rs, cs] == 0.0)
+                continue
+            for got, ref, sc in ((a, ref_a, sc_a), (b, ref_b, sc_b)):
+                e = np.abs(got[rs, cs] - ref[rs, cs]) / sc[rs, cs]
+                if bi == bj and prec == B.DGDFT_PREC_MIXED and not simt:
+                    diag = float(np.max(np.diag(e)))
+                    worst_diag = max(worst_diag, diag)
+                    assert diag < 4e-6
+                    e = e - np.diag(np.diag(e))
+                worst = max(worst, float(np.max(e)))
+    e_xtw = float(np.max(np.abs(xtw - x @ w.T) / (np.abs(x) @ np.abs(w).T)))
+    print(f"{which} {kind} has_p={has_p} prec={prec} simt={simt}: pencil {worst:.2e} "
+          f"(one-signed diagonals {worst_diag:.2e}), X^T W {e_xtw:.2e}")
+    assert worst < tol and e_xtw < tol
 
 
 # ---------------------------------------------------- Rayleigh-Ritz
@@ -294,11 +372,12 @@ def test_solve_config1(prec):
     assert alb.sin_max_angle(v[:, :16].T, phi) <= max(bound, 1e-12) * 1.5
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_solve_config2_elements(prec):
+@pytest.mark.parametrize("prec,simt", [(B.DGDFT_PREC_FP64, False), (B.DGDFT_PREC_MIXED, False),
+                                       (B.DGDFT_PREC_MIXED, True)])
+def test_solve_config2_elements(prec, simt):
     els = synth.config2(elems=[0, 7])
     c = B.Context([B.element_dict(e) for e in els], precision=prec, tol=1e-6, maxit=600,
-                  keep_block=True)
+                  keep_block=True, simt_gram=simt)
     for k, e in enumerate(els):
         B.load_element(c, k, e, synth.initial_block(e))
     st, rep = c.dgdft_alb_solve()
