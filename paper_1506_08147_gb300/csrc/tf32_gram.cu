@@ -66,7 +66,7 @@ constexpr int THREADS = 32 * (4 + NEPI);         // 512
 constexpr int PART = MT * NACC;                  // (hi, lo) pairs per partial (one item)
 constexpr int MAX_SCHED_EL = 1024;               // elements a launch can schedule
 constexpr size_t DYN_SMEM = 2 * (size_t)NST * STAGE_BYTES + 1024;
-constexpr uint32_t DEFAULT_POLLS = 1u << 22;     // ~1 s of polling with backoff
+constexpr uint32_t DEFAULT_POLLS = 1u << 22;     // blocking tests: 0.1 s to a few s
 
 struct MmaOp {
   int a_row, b_row, n, d_col;
@@ -125,14 +125,33 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: at most `polls` tests, sleeping between them.
+// One potentially blocking test: the thread may be suspended in the barrier
+// (for at most about a microsecond) and resumes when the phase completes.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: at most `polls` tests.  Budgets below SHORT_POLLS (tests of
+// the timeout path) use non-blocking tests, so that a wait runs out in a
+// known number of tries.
+constexpr uint32_t SHORT_POLLS = 64;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t polls) {
-  unsigned ns = 16;
-  for (uint32_t i = 0; i < polls; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    __nanosleep(ns);
-    if (ns < 256) ns <<= 1;
+  if (polls < SHORT_POLLS) {
+    for (uint32_t i = 0; i < polls; ++i)
+      if (mbar_test(bar, parity)) return true;
+    return false;
   }
+  for (uint32_t i = 0; i < polls; ++i)
+    if (mbar_try(bar, parity)) return true;
   return false;
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -199,10 +218,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Nearest TF32 value (ties away from zero): add half a unit of the 10-bit
+// mantissa to the magnitude bits and clear the 13 dropped bits.
 __device__ __forceinline__ float rn_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 struct Sched {
