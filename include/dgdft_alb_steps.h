@@ -43,8 +43,12 @@ dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const doub
 
 /* The Gram products of one LOBPCG iteration (Sec. II.B, operation 2: the 12
  * products Phi^T Psi), computed on caller blocks by the same kernels and
- * with the same precision choices as the solver for element `elem`
- * (tensor cores in the FP32 stage unless bulk_kernels = 1).  blocks holds
+ * with the same precision choices as the solver for element `elem`, in the
+ * stage `stage` selects: 0 the bulk stage (in DGDFT_PREC_MIXED the FP32
+ * stage: tensor cores unless bulk_kernels = 1), 1 the FP64 stage (in
+ * DGDFT_PREC_MIXED double-float products, FP32 pairs with exact products
+ * and two-sum accumulation, ~2^-44 relative; plain FP64 in
+ * DGDFT_PREC_FP64, where both stages are the same).  blocks holds
  * six N_g x m column-major blocks one after another: X, W, P, H X, H W, H P
  * (m = n_compute; P and H P are ignored when has_p = 0).  With S = [X W P]:
  * a = (H S)^T S and b = S^T S, each 3m x 3m column-major, are returned in
@@ -54,8 +58,8 @@ dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const doub
  * earlier block: a(i, j) = (H s_i)^T s_j for block(i) <= block(j).  xtw =
  * X^T W (m x m).  a, b, xtw are host arrays; blocks is on the device when
  * on_device = 1.  DGDFT_ETIMEOUT when a bounded device wait ran out. */
-dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int has_p, const double* blocks, double* a,
-                                   double* b, double* xtw, int on_device);
+dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int stage, int has_p, const double* blocks,
+                                   double* a, double* b, double* xtw, int on_device);
 
 /* Rayleigh-Ritz on a symmetric pencil (Sec. II.B, operation 4), FP64 on the
  * GPU: the lowest m eigenpairs of A y = theta B y with B positive definite.
@@ -80,9 +84,9 @@ dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on
 
 /* Gram product C = U^T V in FP64 that allocates nothing.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory while
- * they run (a custom pool that must not fragment, allocator-free real-time
- * loops, frameworks that forbid allocation during graph recording).  It
- * needs no context.  u is ng x p, v is ng x q, c is p x q, all column-major
+ * they run (code inside a custom memory pool that must not fragment, or
+ * allocator-free real-time loops whose latency must not include an
+ * allocation).  It needs no context.  u is ng x p, v is ng x q, c is p x q, all column-major
  * FP64 *device* pointers on the current device, owned by the caller; the
  * work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
  * stream) and the call returns without waiting for it.
@@ -91,7 +95,10 @@ dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on
  * device array inside the library, held by every GPU that loads it until
  * the process exits.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress), so make the first call on each
- * device outside any stream capture.  Every call reuses the same array:
+ * device outside any stream capture.  That address is cached per device
+ * for the life of the process: do not use this entry point across a device
+ * reset (cudaDeviceReset, or a reset of the primary context), after which
+ * the cached address is stale.  Every call reuses the same array:
  * calls that can overlap on the GPU (different streams, or the same
  * stream from different host threads without ordering) race and corrupt
  * each other's results; serialise them.  Returns DGDFT_ECUDA if the launch

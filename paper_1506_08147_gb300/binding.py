@@ -62,7 +62,7 @@ _SIGS = {
     "dgdft_alb_apply_teter": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
-    "dgdft_alb_lobpcg_gram": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P, C.c_int]),
+    "dgdft_alb_lobpcg_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, C.c_int]),
     "dgdft_alb_restrict_orthonormalise": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P,
                                                     C.c_int]),
     "dgdft_alb_get_block": (C.c_int, [_P, C.c_int, _P, C.c_int]),
@@ -350,17 +350,18 @@ class Context:
                     "gram")
         return c.T.copy()
 
-    def dgdft_alb_lobpcg_gram(self, elem, blocks, has_p=True):
+    def dgdft_alb_lobpcg_gram(self, elem, blocks, has_p=True, stage=0):
         """blocks: (6, m, N_g) rows X, W, P, HX, HW, HP.  Returns (a, b, xtw)
         with a, b the 3m x 3m pencil blocks (upper block triangle) and xtw =
-        X^T W, as row-major NumPy arrays of the matrices."""
+        X^T W, as row-major NumPy arrays of the matrices.  stage 0: the bulk
+        stage's kernels, 1: the FP64 stage's."""
         blk = np.ascontiguousarray(blocks, np.float64)
         m = blk.shape[1]
         a = np.zeros((3 * m, 3 * m))
         b = np.zeros((3 * m, 3 * m))
         xtw = np.zeros((m, m))
-        self._check(self.lib.dgdft_alb_lobpcg_gram(self.h, elem, int(bool(has_p)), _ptr(blk)[0], _ptr(a)[0],
-                                                   _ptr(b)[0], _ptr(xtw)[0], 0), "lobpcg_gram")
+        self._check(self.lib.dgdft_alb_lobpcg_gram(self.h, elem, int(stage), int(bool(has_p)), _ptr(blk)[0],
+                                                   _ptr(a)[0], _ptr(b)[0], _ptr(xtw)[0], 0), "lobpcg_gram")
         # column-major out -> matrices
         return a.T.copy(), b.T.copy(), xtw.T.copy()
 

@@ -315,6 +315,131 @@ __global__ void __launch_bounds__(144) gram48d_kernel(const ElemDev<double>* __r
     for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * TILE + tx * 4 + j] = acc[i][j];
 }
 
+// FP64 Gram products in double-float arithmetic (the FP64 stage at m <= 48).
+// GB300 runs FP64 at 1/64 of the FP32 rate, and gram48d_kernel is bound by
+// it.  Here each staged FP64 value x is split once into FP32 parts
+// x = xh + xl (|xl| <= 2^-24 |xh|, the pair carries ~2^-48 of x); a product
+// is formed as xh*yh exactly (its rounding error recovered by an FMA) plus
+// the cross terms xh*yl + xl*yh, and accumulated into a (hi, lo) FP32 pair
+// by a two-sum per product: ~2^-44 relative, at FP32-pipe rates.  The FP64
+// stage only needs its pencil far more accurately than the FP32 stage's,
+// not to FP64 rounding.  Layout and staging as gram48d_kernel (FP64 blocks
+// staged by cp.async), then a conversion pass writes the parts row-major
+// ([row][column], 48 floats a row) so a thread reads its four columns as
+// one float4.  grid: (npairs, nchunk, nel); block 144.
+__global__ void __launch_bounds__(144) gram48df_kernel(const ElemDev<double>* __restrict__ elems,
+                                                        GramJob<double> job, double* __restrict__ partial,
+                                                        size_t pstride, int kchunk) {
+  __shared__ __align__(16) double As[2][G48 * GKD];
+  __shared__ __align__(16) double Bs[2][G48 * GKD];
+  __shared__ __align__(16) float Ah[GKD][G48], Al[GKD][G48], Bh[GKD][G48], Bl[GKD][G48];
+  const ElemDev<double>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int pair = blockIdx.x;
+  if (job.needs_p[pair] && !e.state[ST_HAS_P]) return;
+  const int ca = job.ncols_a > 0 ? job.ncols_a : e.m;
+  const int cb = job.ncols_b > 0 ? job.ncols_b : e.m;
+  const int rows = job.rows > 0 ? job.rows : e.ng;
+  const double* A = resolve(e, job.a[pair]);
+  const double* B = resolve(e, job.b[pair]);
+  const int lda = ld_of(e, job.a[pair], job.ld_in, rows);
+  const int ldb = ld_of(e, job.b[pair], job.ld_in, rows);
+  const int tx = threadIdx.x % 12, ty = threadIdx.x / 12;
+  const int k_beg = blockIdx.y * kchunk;
+  const int k_end = min(rows, k_beg + kchunk);
+  const bool vec = ((lda | ldb | k_beg) & 1) == 0 && ((((uintptr_t)A) | ((uintptr_t)B)) & 15) == 0;
+  auto load_stage = [&](int buf, int k0) {
+    for (int t = threadIdx.x; t < 2 * G48 * (GKD / 2); t += blockDim.x) {
+      const int op = t / (G48 * (GKD / 2));
+      const int rem = t - op * (G48 * (GKD / 2));
+      const int c = rem / (GKD / 2), q = rem - c * (GKD / 2);
+      const double* src = op ? B : A;
+      const int ld = op ? ldb : lda;
+      const int cc = op ? cb : ca;
+      double* dst = (op ? Bs[buf] : As[buf]) + g48d_off(c, 2 * q);
+      const int k = k0 + 2 * q;
+      const int nv = (c < cc) ? max(0, min(2, k_end - k)) : 0;
+      const double* g = nv ? src + (size_t)c * ld + k : src;
+      if (vec) {
+        cp_async16(dst, g, 8 * nv);
+      } else {
+        const float* gf = reinterpret_cast<const float*>(g);
+        const float* sf = reinterpret_cast<const float*>(src);
+        float* df = reinterpret_cast<float*>(dst);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cp_async4(df + u, u < 2 * nv ? gf + u : sf, u < 2 * nv ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+  const int nst = (k_end > k_beg) ? (k_end - k_beg + GKD - 1) / GKD : 0;
+  if (nst > 0) load_stage(0, k_beg);
+  for (int st = 0; st < nst; ++st) {
+    if (st + 1 < nst) {
+      load_stage((st + 1) & 1, k_beg + (st + 1) * GKD);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // split the stage into FP32 parts, transposed to [row][column]
+    for (int t = threadIdx.x; t < 2 * G48 * GKD; t += blockDim.x) {
+      const int op = t / (G48 * GKD);
+      const int rem = t - op * (G48 * GKD);
+      const int c = rem / GKD, r = rem - c * GKD;
+      const double x = (op ? Bs[st & 1] : As[st & 1])[g48d_off(c, r)];
+      const float h = __double2float_rn(x);
+      const float l = __double2float_rn(x - (double)h);
+      (op ? Bh : Ah)[r][c] = h;
+      (op ? Bl : Al)[r][c] = l;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int r = 0; r < GKD; ++r) {
+      const float4 ah = *reinterpret_cast<const float4*>(&Ah[r][ty * 4]);
+      const float4 al = *reinterpret_cast<const float4*>(&Al[r][ty * 4]);
+      const float4 bh = *reinterpret_cast<const float4*>(&Bh[r][tx * 4]);
+      const float4 bl = *reinterpret_cast<const float4*>(&Bl[r][tx * 4]);
+      const float a_h[4] = {ah.x, ah.y, ah.z, ah.w}, a_l[4] = {al.x, al.y, al.z, al.w};
+      const float b_h[4] = {bh.x, bh.y, bh.z, bh.w}, b_l[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float p = a_h[i] * b_h[j];
+          const float pe = fmaf(a_h[i], b_h[j], -p);           // exact: p + pe = a_h b_h
+          const float cr = fmaf(a_h[i], b_l[j], a_l[i] * b_h[j]);
+          const float s = sh[i][j] + p;                          // two-sum of sh and p
+          const float bp = s - sh[i][j];
+          const float err = (sh[i][j] - (s - bp)) + (p - bp);
+          sh[i][j] = s;
+          sl[i][j] += err + (pe + cr);
+        }
+    }
+    // renormalise the pairs: the low part stays within a few units of the
+    // high part's last place, so its own rounding stays at ~2^-48 of it
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float t = sh[i][j] + sl[i][j];
+        sl[i][j] -= t - sh[i][j];
+        sh[i][j] = t;
+      }
+    __syncthreads();
+  }
+  double* out = partial + blockIdx.z * pstride + ((size_t)blockIdx.y * gridDim.x + pair) * (TILE * TILE);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * TILE + tx * 4 + j] = (double)sh[i][j] + (double)sl[i][j];
+}
+
 template <class real>
 __global__ void gram_reduce_kernel(const ElemDev<real>* __restrict__ elems, GramJob<real> job,
                                    const double* __restrict__ partial, size_t pstride, int nchunk,
@@ -419,6 +544,110 @@ __global__ void __launch_bounds__(256) tsmm_kernel(const ElemDev<real>* __restri
       real* o = O + (size_t)col * ldo + row;
       real v = (real)job.alpha * acc[i][j];
       if (job.beta != 0.0) v += (real)job.beta * *o;
+      *o = v;
+    }
+  }
+}
+
+// FP64 block update in double-float arithmetic (the mixed form's FP64 stage):
+// the tiling of tsmm_kernel, with every staged block and coefficient value
+// split into FP32 parts (x = xh + xl) and each output accumulated as a
+// (hi, lo) FP32 pair: exact leading products by FMA, cross terms, a two-sum
+// per product (~2^-44 relative, at FP32-pipe rates).  alpha and beta are
+// applied in FP64 to the pair's sum.
+__global__ void __launch_bounds__(256) tsmm_df_kernel(const ElemDev<double>* __restrict__ elems,
+                                                       TsmmJob<double> job) {
+  __shared__ float Sh[KU][TILE + 4], Sl[KU][TILE + 4];
+  __shared__ float Yh[KU][TILE + 4], Yl[KU][TILE + 4];
+  const ElemDev<double>& e = elems[blockIdx.z];
+  if (!e.state[ST_ACTIVE]) return;
+  const int nc = job.ncols > 0 ? job.ncols : e.m;
+  const int rows = job.rows > 0 ? job.rows : e.ng;
+  const int r0 = blockIdx.x * TILE, c0 = blockIdx.y * TILE;
+  if (r0 >= rows || c0 >= nc) return;
+  const double* Y;
+  int ldy;
+  switch (job.y_id) {
+    case Y_RR: Y = e.Y; ldy = job.ldy > 0 ? job.ldy : 3 * e.m; break;
+    case Y_GXW: Y = e.gxw; ldy = job.ldy > 0 ? job.ldy : e.m; break;
+    default: Y = job.y_ptr; ldy = job.ldy; break;
+  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float ah[4][4], al[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ah[i][j] = al[i][j] = 0.f;
+  const int ycol0 = job.ycol * nc + c0;
+  for (int in = 0; in < job.nin; ++in) {
+    if (job.needs_p[in] && !e.state[ST_HAS_P]) continue;
+    const double* S = resolve(e, job.in[in]);
+    const int lds = ld_of(e, job.in[in], job.ld_in, rows);
+    const int yrow0 = job.yrow[in] * nc;
+    for (int k0 = 0; k0 < nc; k0 += KU) {
+      for (int i = threadIdx.x; i < KU * TILE; i += blockDim.x) {
+        const int kk = i / TILE, r = i - kk * TILE;
+        const bool kin = k0 + kk < nc;
+        const double sv = (kin && r0 + r < rows) ? S[(size_t)(k0 + kk) * lds + r0 + r] : 0.0;
+        const double yv = (kin && c0 + r < nc) ? Y[(yrow0 + k0 + kk) + (size_t)(ycol0 + r) * ldy] : 0.0;
+        const float svh = __double2float_rn(sv), yvh = __double2float_rn(yv);
+        Sh[kk][r] = svh;
+        Sl[kk][r] = __double2float_rn(sv - (double)svh);
+        Yh[kk][r] = yvh;
+        Yl[kk][r] = __double2float_rn(yv - (double)yvh);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < KU; ++kk) {
+        float sh[4], sl[4], yh[4], yl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          sh[i] = Sh[kk][tx + 16 * i];
+          sl[i] = Sl[kk][tx + 16 * i];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          yh[j] = Yh[kk][ty * 4 + j];
+          yl[j] = Yl[kk][ty * 4 + j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float p = sh[i] * yh[j];
+            const float pe = fmaf(sh[i], yh[j], -p);
+            const float cr = fmaf(sh[i], yl[j], sl[i] * yh[j]);
+            const float t = ah[i][j] + p;
+            const float bp = t - ah[i][j];
+            const float err = (ah[i][j] - (t - bp)) + (p - bp);
+            ah[i][j] = t;
+            al[i][j] += err + (pe + cr);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float t = ah[i][j] + al[i][j];
+          al[i][j] -= t - ah[i][j];
+          ah[i][j] = t;
+        }
+      __syncthreads();
+    }
+  }
+  double* O = resolve(e, job.out);
+  const int ldo = ld_of(e, job.out, job.ld_in, rows);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int col = c0 + ty * 4 + j;
+    if (col >= nc) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = r0 + tx + 16 * i;
+      if (row >= rows) continue;
+      double* o = O + (size_t)col * ldo + row;
+      double v = job.alpha * ((double)ah[i][j] + (double)al[i][j]);
+      if (job.beta != 0.0) v += job.beta * *o;
       *o = v;
     }
   }
@@ -802,6 +1031,10 @@ void launch_gram(const Batch<real>& b, const GramJob<real>& job, double* partial
     gram48_kernel<<<dim3(ny, nchunk, s.nel), 144, 0, st>>>(
         reinterpret_cast<const ElemDev<float>*>(b.d_elems), *reinterpret_cast<const GramJob<float>*>(&job), partial,
         pstride, kchunk);
+  } else if (std::is_same<real, double>::value && ca <= G48 && cb <= G48 && s.dfloat) {
+    gram48df_kernel<<<dim3(ny, nchunk, s.nel), 144, 0, st>>>(
+        reinterpret_cast<const ElemDev<double>*>(b.d_elems), *reinterpret_cast<const GramJob<double>*>(&job),
+        partial, pstride, kchunk);
   } else if (std::is_same<real, double>::value && ca <= G48 && cb <= G48) {
     gram48d_kernel<<<dim3(ny, nchunk, s.nel), 144, 0, st>>>(
         reinterpret_cast<const ElemDev<double>*>(b.d_elems), *reinterpret_cast<const GramJob<double>*>(&job),
@@ -831,6 +1064,13 @@ void launch_tsmm(const Batch<real>& b, const TsmmJob<real>& job, cudaStream_t st
     }
   }
   const int rows = job.rows > 0 ? job.rows : s.max_ng;
+  if constexpr (std::is_same<real, double>::value) {
+    if (s.dfloat) {
+      tsmm_df_kernel<<<dim3((rows + TILE - 1) / TILE, (nc + TILE - 1) / TILE, s.nel), 256, 0, st>>>(b.d_elems,
+                                                                                                  job);
+      return;
+    }
+  }
   tsmm_kernel<real><<<dim3((rows + TILE - 1) / TILE, (nc + TILE - 1) / TILE, s.nel), 256, 0, st>>>(
       b.d_elems, job);
 }

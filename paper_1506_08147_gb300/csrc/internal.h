@@ -35,6 +35,9 @@ struct BatchShape {
   // FFT kernels specialised for the line lengths at compile time
   int uni_nx = 0, uni_ny = 0, uni_nz = 0;
   bool ng_mult4 = true;  // every element's N_g is a multiple of 4 (16-byte columns)
+  // FP64 wave of the mixed form: Gram products in double-float arithmetic
+  // (FP32 pairs) instead of on the FP64 pipe
+  bool dfloat = false;
 };
 
 template <class real> struct Batch {

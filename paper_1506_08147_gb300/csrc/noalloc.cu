@@ -1,9 +1,9 @@
 // Gram product C = U^T V with no device allocation at all.
 //
 // Some callers cannot call cudaMalloc while they run: code inside a custom
-// memory pool that must not fragment, allocator-free real-time loops, and
-// frameworks that forbid allocation during CUDA graph recording.  This entry
-// point serves them: the caller passes device inputs and the device output,
+// memory pool that must not fragment, and allocator-free real-time loops
+// whose latency must not include an allocation.  This entry point serves
+// them: the caller passes device inputs and the device output,
 // and the split-K partial sums of the FP64 Gram kernel live in a fixed
 // file-scope device array instead of an allocated buffer.  Every GPU that
 // loads the library holds that array (8 MiB) until the process exits.
@@ -24,7 +24,8 @@ constexpr int NOALLOC_MAX_COLS = 256;
 // The scratch shared by every call of dgdft_alb_gram_noalloc on a device.
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
-// Per-device address of g_noalloc_scratch, looked up once per device.
+// Per-device address of g_noalloc_scratch, looked up once per device and
+// kept for the life of the process (stale after a device reset).
 std::mutex g_addr_mu;
 double* g_addr[64] = {nullptr};
 

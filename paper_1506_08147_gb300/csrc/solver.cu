@@ -350,6 +350,9 @@ template <class real> struct Wave {
         s.uni_nz = d0.nz;
       }
     }
+    // the refinement (FP64) stage of the mixed form takes its Gram products
+    // in double-float arithmetic; the plain FP64 solver stays on the FP64 pipe
+    s.dfloat = std::is_same<real, double>::value && ctx->cfg.precision == DGDFT_PREC_MIXED;
     rnchunk = nchunk_rows(s.max_ng);
     const size_t tiles = ((s.max_m + 63) / 64) * ((s.max_m + 63) / 64);
     const size_t pcap = (size_t)nel * ((s.max_ng + 2047) / 2048) * 12 * tiles * 4096;
@@ -1939,6 +1942,7 @@ dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, c
 template <class real>
 dgdft_status lobpcg_gram_t(dgdft_alb_ctx* ctx, int elem, int has_p, const double* blocks, double* a, double* b,
                            double* xtw, int on_device) {
+  // (a Wave<double> of a mixed context is its refinement stage: double-float)
   Wave<real> w;
   dgdft_status s = with_step_wave<real>(ctx, elem, w);
   if (s != DGDFT_OK) return s;
@@ -2073,11 +2077,12 @@ dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const doub
                                                 : gram_t<float>(ctx, ng, p, q, u, v, c, on_device);
 }
 
-dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int has_p, const double* blocks, double* a,
-                                   double* b, double* xtw, int on_device) {
+dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int stage, int has_p, const double* blocks,
+                                   double* a, double* b, double* xtw, int on_device) {
   if (!ctx || !blocks || !a || !b || !xtw || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  if (stage != 0 && stage != 1) return DGDFT_EINVAL;
   CK(cudaSetDevice(ctx->device));
-  return ctx->cfg.precision == DGDFT_PREC_FP64
+  return (ctx->cfg.precision == DGDFT_PREC_FP64 || stage == 1)
              ? lobpcg_gram_t<double>(ctx, elem, has_p, blocks, a, b, xtw, on_device)
              : lobpcg_gram_t<float>(ctx, elem, has_p, blocks, a, b, xtw, on_device);
 }

@@ -1,7 +1,9 @@
 """Write the stored expected values under tests/golden/ from the oracle alone.
 
 Run from the repository root:
-    python tests/golden/make_golden.py [--skip-config1] [--config2] [--ritz]
+    python tests/golden/make_golden.py [--skip-config1] [--config2] [--ritz [--only=name,...]]
+(--config2 writes the oracle's iteration counts to 1e-6 Ha of monolayer
+elements 0 and 7, which the benchmark's CPU baseline extrapolates with.)
 Calls only oracle/ and synth/ (no GPU code).
 
 --ritz writes, for the elements the GPU parity tests solve (monolayer
@@ -43,13 +45,6 @@ def config2(elems):
                    fmt="%d",
                    header=f"oracle LOBPCG iterations to residual 1e-6 on extended element {k} of the\n"
                           "576-atom monolayer from the seeded random block (Sec. II.B).")
-        out = lobpcg.lobpcg(el, first["X"], tol=1e-8, maxit=3000)
-        assert out["converged"]
-        np.savetxt(os.path.join(HERE, f"config2_elem{k}_eigenvalues.txt"), out["theta"],
-                   fmt="%.14f",
-                   header=f"48 lowest eigenvalues (Ha) of extended element {k} of the 576-atom\n"
-                          "monolayer on 48x64x40, oracle LOBPCG to residual 1e-8 on the kept 40\n"
-                          "(Eq. localproblem; Sec. II.B).")
 
 
 # Elements whose full solves the GPU tests compare with these values.
@@ -63,24 +58,31 @@ def ritz_targets():
     return out
 
 
+# monolayer element 0 also serves the tight subspace test (FP64 to 1e-10),
+# whose Davis-Kahan bound needs the oracle's own residuals near 1e-11
+RITZ_TOL = {"config2_elem0": 1e-11}
+
+
 def ritz(names=None, tol=1e-9):
     """Oracle LOBPCG (Sec. II.B) run until the lowest J + 4 Ritz pairs have
-    residual <= tol.  The block is the seeded m-block plus max(8, m/4) more
-    seeded rows, so that the last kept pair is well inside the block."""
+    residual <= tol (RITZ_TOL where set).  The block is the seeded m-block
+    plus max(8, m/4) more seeded rows, so that the last kept pair is well
+    inside the block."""
     for name, make in ritz_targets():
         if names and name not in names:
             continue
+        el_tol = RITZ_TOL.get(name, tol)
         el = make()
         keep = min(el.m, el.J + 4)
         extra = np.random.default_rng([*el.seed_key, 101]).standard_normal((max(8, el.m // 4), el.ng))
         x0 = np.vstack([synth.initial_block(el), extra])
-        out = lobpcg.lobpcg(el, x0, tol=tol, maxit=4000, keep=keep)
+        out = lobpcg.lobpcg(el, x0, tol=el_tol, maxit=4000, keep=keep)
         assert out["converged"], name
         data = np.column_stack([out["theta"][:keep], out["res"][:keep]])
         np.savetxt(os.path.join(HERE, f"{name}_ritz.txt"), data, fmt="%.15e",
                    header=f"{name}: grid {el.n}, m = {el.m}, J = {el.J}.  Lowest {keep} Ritz values (Ha)\n"
                           f"and residuals |H x - theta x| / |x| (Ha) of the oracle LOBPCG run to residual\n"
-                          f"{tol:g} on all {keep} (Eq. localproblem; Sec. II.B); "
+                          f"{el_tol:g} on all {keep} (Eq. localproblem; Sec. II.B); "
                           f"{out['iterations']} iterations from a seeded random block of {x0.shape[0]}.")
         print(name, "iterations", out["iterations"], flush=True)
 

@@ -5,15 +5,19 @@ wave (the kernels then run their general paths: column-tiled updates,
 64-wide Gram tiles, the global-memory Rayleigh-Ritz); the large-monolayer
 element has m = 144, J = 120 and a 432 x 432 pencil.  Each returned block is
 checked with the FP64 oracle's own H: residual, orthonormal ALBs and
-span(ALBs) = span(restricted Ritz block).
+span(ALBs) = span(restricted Ritz block); its J eigenvalues against the
+oracle's stored Ritz values (1e-6 Ha), and its subspace against the oracle's
+through the Davis-Kahan bound, reported with the gap at J.  For one uneven
+element the oracle's subspace is also computed here and the angle measured.
 """
 
 import numpy as np
 import pytest
 
 import __graft_entry__ as entry
+import oracle_compare as OC
 import synth
-from oracle import alb, hamiltonian as H
+from oracle import alb, hamiltonian as H, lobpcg as OL
 from paper_1506_08147_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
@@ -27,7 +31,7 @@ def _built():
     entry.build()
 
 
-def check_solution(c, els, tol):
+def check_solution(c, els, tol, names=None):
     for k, e in enumerate(els):
         phi, eig, res = c.dgdft_alb_get_basis(k)
         x = c.dgdft_alb_get_block(k)
@@ -43,6 +47,12 @@ def check_solution(c, els, tol):
         sv = np.linalg.svd(xr, compute_uv=False)
         assert alb.sin_max_angle(xr, phi) < max(1e-10, 1e-14 * sv[0] / sv[-1])
         assert np.all(np.diff(eig) >= -1e-9)
+        if names:
+            gth, gres = OC.ritz_golden(names[k])
+            np.testing.assert_allclose(eig, gth[:e.J], rtol=0, atol=1e-6)
+            bound, gap = OC.angle_bound(x, eig, e, gth, gres)
+            print(f"{names[k]}: max |eig - oracle| {np.max(np.abs(eig - gth[:e.J])):.1e} Ha, "
+                  f"sin(angle) to the oracle's subspace <= {bound:.1e} (gap at J {gap:.2e} Ha)")
 
 
 def test_solve_config3_uneven_batch():
@@ -53,7 +63,19 @@ def test_solve_config3_uneven_batch():
         B.load_element(c, k, e, synth.initial_block(e))
     st, rep = c.dgdft_alb_solve()
     assert st == B.DGDFT_OK, rep
-    check_solution(c, els, 1e-6)
+    check_solution(c, els, 1e-6, [f"config3_elem{k}" for k in CONFIG3_PICK])
+    # the oracle's own subspace for the 24^3 element (seconds on the host):
+    # the measured angle is within the Davis-Kahan bound
+    k = CONFIG3_PICK.index(2)
+    e = els[k]
+    y = OL.lobpcg(e, synth.initial_block(e), tol=1e-9, maxit=2000, keep=e.J + 4)["X"][:e.J]
+    _, eig, _ = c.dgdft_alb_get_basis(k)
+    x = c.dgdft_alb_get_block(k)
+    gth, gres = OC.ritz_golden("config3_elem2")
+    bound, gap = OC.angle_bound(x, eig, e, gth, gres)
+    angle = alb.sin_max_angle(y, x[:e.J])
+    print(f"config3_elem2: measured sin(angle) to the oracle's subspace {angle:.2e} <= bound {bound:.2e}")
+    assert angle <= bound
     c.close()
 
 
@@ -65,5 +87,5 @@ def test_solve_config5_large_block():
         B.load_element(c, k, e, synth.initial_block(e))
     st, rep = c.dgdft_alb_solve()
     assert st == B.DGDFT_OK, rep
-    check_solution(c, els, 1e-6)
+    check_solution(c, els, 1e-6, ["config5_elem100"])
     c.close()

@@ -16,6 +16,7 @@ import scipy.linalg as sla
 
 import __graft_entry__ as entry
 import synth
+import oracle_compare as OC
 from oracle import alb, hamiltonian as H, lobpcg as OL, teter as T
 from paper_1506_08147_gb300 import binding as B
 
@@ -188,21 +189,26 @@ def lobpcg_blocks(el, gen, kind):
     return np.stack([x, w, p, hx, hw, hp])
 
 
-# (precision, SIMT Gram): the FP64 kernels, the compensated FP32 SIMT
-# kernel, the tensor-core TF32-split kernel (default of the mixed form)
-LOBPCG_GRAM_KINDS = [(B.DGDFT_PREC_FP64, False), (B.DGDFT_PREC_MIXED, True), (B.DGDFT_PREC_MIXED, False)]
+# (precision, SIMT Gram, stage): the plain FP64 kernels, the compensated
+# FP32 SIMT kernel, the tensor-core TF32-split kernel (default of the mixed
+# form), and the mixed form's double-float FP64-stage kernel
+LOBPCG_GRAM_KINDS = [(B.DGDFT_PREC_FP64, False, 0), (B.DGDFT_PREC_MIXED, True, 0), (B.DGDFT_PREC_MIXED, False, 0),
+                     (B.DGDFT_PREC_MIXED, False, 1)]
 
 
-@pytest.mark.parametrize("prec,simt", LOBPCG_GRAM_KINDS)
+@pytest.mark.parametrize("prec,simt,stage", LOBPCG_GRAM_KINDS)
 @pytest.mark.parametrize("which", ["small", "ragged", "cfg2"])
 @pytest.mark.parametrize("has_p", [True, False])
 @pytest.mark.parametrize("kind", ["random", "ortho"])
-def test_lobpcg_gram(prec, simt, which, has_p, kind):
+def test_lobpcg_gram(prec, simt, stage, which, has_p, kind):
     """The Gram products of one LOBPCG iteration through the solver's own
     kernels, against NumPy FP64 products of the same (working-precision)
     inputs, entry by entry relative to sum_k |a_k| |b_k| (the scale of the
-    rounding of any summation order): FP64 to 1e-13, the compensated SIMT
-    kernel to 2e-7, the TF32-split tensor-core kernel to 2^-20 (two TF32
+    rounding of any summation order): FP64 to 1e-13, double-float to 4e-12
+    (~2^-44 per product plus the FP32 rounding of the low parts' running
+    sums, renormalised every 16 rows), the compensated SIMT kernel to 2e-7,
+    the TF32-split tensor-core
+    kernel to 2^-20 (two TF32
     parts carry ~2^-22 of each value) except on one-signed sums (the
     diagonals of the diagonal blocks, x^T x and x^T (H x) of a near
     eigenvector): there the tensor core's FP32 accumulation, which does not
@@ -212,9 +218,10 @@ def test_lobpcg_gram(prec, simt, which, has_p, kind):
     gen = np.random.default_rng(31)
     blk = lobpcg_blocks(el, gen, kind)
     c = ctx_for(el, prec, simt_gram=simt)
-    a, b, xtw = c.dgdft_alb_lobpcg_gram(0, blk, has_p)
+    a, b, xtw = c.dgdft_alb_lobpcg_gram(0, blk, has_p, stage=stage)
     c.close()
-    if prec == B.DGDFT_PREC_MIXED:
+    fp32 = prec == B.DGDFT_PREC_MIXED and stage == 0
+    if fp32:
         blk = blk.astype(np.float32).astype(np.float64)
     x, w, p, hx, hw, hp = blk
     m = el.m
@@ -223,7 +230,7 @@ def test_lobpcg_gram(prec, simt, which, has_p, kind):
     ref_a, ref_b = hs @ s_.T, s_ @ s_.T
     sc_a, sc_b = np.abs(hs) @ np.abs(s_).T, np.abs(s_) @ np.abs(s_).T
     nb = 3 if has_p else 2
-    tol = {B.DGDFT_PREC_FP64: 1e-13}.get(prec, 2e-7 if simt else 2.0 ** -20)
+    tol = 1e-13 if prec == B.DGDFT_PREC_FP64 else (4e-12 if stage == 1 else (2e-7 if simt else 2.0 ** -20))
     worst = worst_diag = 0.0
     for bi in range(3):
         for bj in range(3):
@@ -233,14 +240,14 @@ def test_lobpcg_gram(prec, simt, which, has_p, kind):
                 continue
             for got, ref, sc in ((a, ref_a, sc_a), (b, ref_b, sc_b)):
                 e = np.abs(got[rs, cs] - ref[rs, cs]) / sc[rs, cs]
-                if bi == bj and prec == B.DGDFT_PREC_MIXED and not simt:
+                if bi == bj and fp32 and not simt:
                     diag = float(np.max(np.diag(e)))
                     worst_diag = max(worst_diag, diag)
                     assert diag < 4e-6
                     e = e - np.diag(np.diag(e))
                 worst = max(worst, float(np.max(e)))
     e_xtw = float(np.max(np.abs(xtw - x @ w.T) / (np.abs(x) @ np.abs(w).T)))
-    print(f"{which} {kind} has_p={has_p} prec={prec} simt={simt}: pencil {worst:.2e} "
+    print(f"{which} {kind} has_p={has_p} prec={prec} simt={simt} stage={stage}: pencil {worst:.2e} "
           f"(one-signed diagonals {worst_diag:.2e}), X^T W {e_xtw:.2e}")
     assert worst < tol and e_xtw < tol
 
@@ -390,11 +397,69 @@ def test_solve_config2_elements(prec, simt):
         assert np.max(np.linalg.norm(r, axis=1)) <= 1.05e-6
         np.testing.assert_allclose(phi @ phi.T * e.dv, np.eye(e.J), atol=1e-12)
         assert alb.sin_max_angle(alb.restrict(x, e), phi) < 1e-10
-        gold = os.path.join(GOLDEN, f"config2_elem{[0, 7][k]}_eigenvalues.txt")
-        if os.path.exists(gold):
-            ref = np.loadtxt(gold)[:e.J]
-            np.testing.assert_allclose(eig, ref, atol=1e-6 if prec == B.DGDFT_PREC_MIXED else 1e-8)
+        # eigenvalues against the oracle's (error ~ residual^2 / gap, below
+        # the tolerance); the subspace through its Davis-Kahan bound, reported
+        # with the gap at J (at residual 1e-6 it does not reach 1e-5 here:
+        # see test_solve_config2_tight_subspace)
+        gth, gres = OC.ritz_golden(f"config2_elem{[0, 7][k]}")
+        np.testing.assert_allclose(eig, gth[:e.J], rtol=0,
+                                   atol=1e-6 if prec == B.DGDFT_PREC_MIXED else 1e-8)
+        bound, gap = OC.angle_bound(x, eig, e, gth, gres)
+        print(f"config-2 element {[0, 7][k]} (prec {prec}, simt {simt}): max |eig - oracle| "
+              f"{np.max(np.abs(eig - gth[:e.J])):.1e} Ha; sin(angle) to the oracle's subspace <= {bound:.1e} "
+              f"(gap at J {gap:.2e} Ha)")
     c.close()
+
+
+def test_solve_config2_workload():
+    """All 36 monolayer elements in one solve, in the launch configuration the
+    benchmark times (mixed form, tensor-core Gram, two half batches): every
+    element converges with orthonormal ALBs; sampled elements' Ritz pairs are
+    re-checked with the oracle's H, and elements 0 and 7 against the
+    oracle's eigenvalues."""
+    els = synth.config2()
+    c = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_MIXED, tol=1e-6, maxit=600,
+                  keep_block=True)
+    for k, e in enumerate(els):
+        B.load_element(c, k, e, synth.initial_block(e))
+    st, rep = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    assert all(r["restarts"] == 0 for r in rep)
+    for k, e in enumerate(els):
+        phi, eig, res = c.dgdft_alb_get_basis(k)
+        assert np.max(res) <= 1e-6
+        np.testing.assert_allclose(phi @ phi.T * e.dv, np.eye(e.J), atol=1e-12)
+        if k in (0, 7, 17, 35):
+            x = c.dgdft_alb_get_block(k)
+            r = H.apply_h(x[:e.J], e) - eig[:, None] * x[:e.J]
+            assert np.max(np.linalg.norm(r, axis=1)) <= 1.05e-6
+        if k in (0, 7):
+            gth, _ = OC.ritz_golden(f"config2_elem{k}")
+            np.testing.assert_allclose(eig, gth[:e.J], rtol=0, atol=1e-6)
+    print("iterations (mean / max):", np.mean([r["iterations"] for r in rep]), max(r["iterations"] for r in rep))
+    c.close()
+
+
+@pytest.mark.parametrize("prec,tol,angle_tol", [(B.DGDFT_PREC_FP64, 1e-10, 1e-7), (B.DGDFT_PREC_MIXED, 1e-9, 1e-5)])
+def test_solve_config2_tight_subspace(prec, tol, angle_tol):
+    """The subspace tolerances (FP64 1e-7, mixed 1e-5) need residual <~
+    gap x tolerance; with the 4.6 mHa gap at J of monolayer element 0 that is
+    a tighter solve.  Both forms get there (the mixed form through its FP64
+    stage) and the Davis-Kahan bound then proves the angle to the oracle's
+    subspace within tolerance; eigenvalues within 1e-8 Ha."""
+    e = cfg2_element(0)
+    c = B.Context([B.element_dict(e)], precision=prec, tol=tol, maxit=1200, keep_block=True)
+    B.load_element(c, 0, e, synth.initial_block(e))
+    st, rep = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    _, eig, res = c.dgdft_alb_get_basis(0)
+    x = c.dgdft_alb_get_block(0)
+    c.close()
+    gth, gres = OC.ritz_golden("config2_elem0")
+    np.testing.assert_allclose(eig, gth[:e.J], rtol=0, atol=1e-8)
+    bound, gap = OC.angle_bound(x, eig, e, gth, gres)
+    print(f"tight solve (prec {prec}, tol {tol:g}): sin(angle) <= {bound:.2e}, gap at J {gap:.2e} Ha")
+    assert bound <= angle_tol
 
 
 def test_nonfinite_potential_rejected():

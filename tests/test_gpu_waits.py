@@ -33,7 +33,7 @@ def test_gram_wait_timeout_is_reported():
     c = B.Context([B.element_dict(el)], precision=B.DGDFT_PREC_MIXED, device_wait_polls=1)
     B.load_element(c, 0, el)
     with pytest.raises(B.DgdftError) as ei:
-        c.dgdft_alb_lobpcg_gram(0, blk, True)
+        c.dgdft_alb_lobpcg_gram(0, blk, True, stage=0)
     assert ei.value.status == B.DGDFT_ETIMEOUT
     c.close()
     # the same products with the default bound, on the same device

@@ -12,7 +12,8 @@ Each test ties an oracle function to something other than itself:
     orthonormality, Hermiticity; the warm-started fixed-iteration run (the
     SCF-mode reference) against the dense Rayleigh-Ritz of its start block;
   * Teter: limits of the rational function and plane-wave eigenfunctions;
-  * restriction/SVD: orthonormality, span equality, E_K = Q_K.
+  * restriction/SVD: orthonormality, span equality, E_K = Q_K; the element's
+    index map against the points picked by their coordinates.
 """
 
 import os
@@ -284,6 +285,51 @@ def test_restriction_orthonormalisation():
         q[i] /= np.linalg.norm(q[i])
     assert alb.sin_max_angle(q, phi) < 1e-12
     assert phi.shape[1] == 4 * 3 * 6   # E_K = [4,8) x [3,6) x [0,6): zero elsewhere
+
+
+def points_in_box_by_coordinates(n, L_, lo_frac, hi_frac):
+    """Flat indices (x fastest) of the grid points whose coordinates x_a =
+    i_a L_a / n_a satisfy lo_frac[a] L_a <= x_a < hi_frac[a] L_a, found by
+    visiting every point in z, y, x order (exact rational comparison)."""
+    from fractions import Fraction
+    out = []
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                inside = all(Fraction(lo_frac[a]) <= Fraction(idx, n[a]) < Fraction(hi_frac[a])
+                             for a, idx in enumerate((i, j, k)))
+                if inside:
+                    out.append(i + n[0] * (j + n[1] * k))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n", [(12, 9, 5), (48, 64, 40), (20, 15, 9), (10, 14, 6)])
+def test_element_indices_from_coordinates(n):
+    """E_K is the set of points with coordinate in [L/3, 2L/3) along x and y,
+    all z (the reading of the element inside its extended element): the
+    oracle's index map (from synth's grid-index box) must list exactly those
+    points, in x-fastest order.  Non-cubic grids catch an x/y swap."""
+    from fractions import Fraction
+    L_ = (7.0, 9.0, 4.0)
+    el = make_element(n, L_, m=2, J=2)
+    el.e_lo, el.e_hi = synth.element_box(n)
+    got = alb.element_indices(el)
+    ref = points_in_box_by_coordinates(n, L_, (Fraction(1, 3), Fraction(1, 3), 0), (Fraction(2, 3), Fraction(2, 3), 1))
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_element_indices_asymmetric_box():
+    """An arbitrary grid-index box with different bounds on every axis: the
+    index map equals the brute-force list of points inside it."""
+    from fractions import Fraction
+    n = (11, 7, 6)
+    el = make_element(n, (5.0, 6.0, 7.0), m=2, J=2)
+    el.e_lo, el.e_hi = (2, 1, 3), (9, 4, 5)
+    got = alb.element_indices(el)
+    ref = points_in_box_by_coordinates(n, (5.0, 6.0, 7.0), tuple(Fraction(l, d) for l, d in zip(el.e_lo, n)),
+                                       tuple(Fraction(h, d) for h, d in zip(el.e_hi, n)))
+    np.testing.assert_array_equal(got, ref)
+    assert len(got) == 7 * 3 * 2
 
 
 def test_restriction_whole_box_reproduces_span():

@@ -1,4 +1,4 @@
-"""The allocation-free Gram entry point against the regular one.
+"""The allocation-free Gram entry point against NumPy and the regular one.
 
 dgdft_alb_gram_noalloc exists for callers that cannot allocate device
 memory while they run; its split-K scratch is a fixed device array inside
@@ -6,7 +6,8 @@ the library.  This file is collected last so that a run stopping at the
 first failure has already run every other test; it passes on its own in a
 fresh process too.  Two calls in a row (different shapes, so the second
 call reuses scratch holding the first call's data) are each compared with
-dgdft_alb_gram of an FP64 context, within 1e-12 relative.
+the FP64 product u v^T computed by NumPy on the host, and with dgdft_alb_gram
+of an FP64 context, within 1e-12 relative.
 """
 
 import ctypes as C
@@ -41,6 +42,8 @@ def test_gram_noalloc_matches_gram():
         assert st == B.DGDFT_OK
         torch.cuda.synchronize()
         got = dc.cpu().numpy().T          # column-major p x q
+        exact = u @ v.T
+        assert np.max(np.abs(got - exact)) <= 1e-12 * np.max(np.abs(exact))
         ref = ctx.dgdft_alb_gram(u, v)
         assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
     # sizes beyond the limit are rejected before any GPU work
