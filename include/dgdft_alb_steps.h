@@ -61,12 +61,17 @@ dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const doub
 dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int stage, int has_p, const double* blocks,
                                    double* a, double* b, double* xtw, int on_device);
 
-/* Rayleigh-Ritz on a symmetric pencil (Sec. II.B, operation 4), FP64 on the
- * GPU: the lowest m eigenpairs of A y = theta B y with B positive definite.
+/* Rayleigh-Ritz on a symmetric pencil (Sec. II.B, operation 4) on the GPU:
+ * the lowest m eigenpairs of A y = theta B y with B positive definite.
+ * stage picks the arithmetic of a solve's two stages: 0 = the FP32 LOBPCG
+ * stage's reduction, double-float (FP32 pairs, ~2^-46 relative) in a
+ * DGDFT_PREC_MIXED context when n <= 160 and m <= 64, FP64 otherwise;
+ * 1 = FP64 (the FP64 continuation, and every stage of an FP64 context).
  * A, B: n x n column-major (host, both symmetric); theta: m ascending;
  * y: n x m with y^T B y = I.  Returns DGDFT_EINVAL when B is not positive
- * definite to working accuracy.  n <= 3 * max n_compute of the context. */
-dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int n, int m, const double* a,
+ * definite to working accuracy or stage is not 0 or 1.
+ * n <= 3 * max n_compute of the context. */
+dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int stage, int n, int m, const double* a,
                                      const double* b, double* theta, double* y);
 
 /* Restriction to E_K and orthonormalisation (Sec. II.A; Sec. II.B): the
@@ -94,8 +99,7 @@ dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on
  * before any GPU work.  The split-K partial sums live in one fixed 8 MiB
  * device array inside the library, held by every GPU that loads it until
  * the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress), so make the first call on each
- * device outside any stream capture.  That address is cached per device
+ * device address (cudaGetSymbolAddress).  That address is cached per device
  * for the life of the process: do not use this entry point across a device
  * reset (cudaDeviceReset, or a reset of the primary context), after which
  * the cached address is stale.  Every call reuses the same array:

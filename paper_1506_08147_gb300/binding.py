@@ -61,7 +61,7 @@ _SIGS = {
     "dgdft_alb_apply_h": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dgdft_alb_apply_teter": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
-    "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P]),
     "dgdft_alb_lobpcg_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, C.c_int]),
     "dgdft_alb_restrict_orthonormalise": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P,
                                                     C.c_int]),
@@ -365,13 +365,15 @@ class Context:
         # column-major out -> matrices
         return a.T.copy(), b.T.copy(), xtw.T.copy()
 
-    def dgdft_alb_rayleigh_ritz(self, a, b, m):
+    def dgdft_alb_rayleigh_ritz(self, a, b, m, stage=1):
+        """Lowest m eigenpairs of a y = theta b y; stage 0 is the FP32 stage's
+        reduction (double-float in a mixed-precision context), 1 is FP64."""
         n = a.shape[0]
         a = np.ascontiguousarray(np.asarray(a, np.float64).T)
         b = np.ascontiguousarray(np.asarray(b, np.float64).T)
         theta = np.zeros(m)
         y = np.zeros((m, n))
-        self._check(self.lib.dgdft_alb_rayleigh_ritz(self.h, n, m, _ptr(a)[0], _ptr(b)[0],
+        self._check(self.lib.dgdft_alb_rayleigh_ritz(self.h, int(stage), n, m, _ptr(a)[0], _ptr(b)[0],
                                                      _ptr(theta)[0], _ptr(y)[0]), "rayleigh_ritz")
         return theta, y.T.copy()
 

@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(144) gram48df_kernel(const ElemDev<double>* __
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const float p = a_h[i] * b_h[j];
+          const float p = __fmul_rn(a_h[i], b_h[j]);              // never contracted into the sum
           const float pe = fmaf(a_h[i], b_h[j], -p);           // exact: p + pe = a_h b_h
           const float cr = fmaf(a_h[i], b_l[j], a_l[i] * b_h[j]);
           const float s = sh[i][j] + p;                          // two-sum of sh and p
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(256) tsmm_df_kernel(const ElemDev<double>* __r
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const float p = sh[i] * yh[j];
+            const float p = __fmul_rn(sh[i], yh[j]);  // never contracted into the sum
             const float pe = fmaf(sh[i], yh[j], -p);
             const float cr = fmaf(sh[i], yl[j], sl[i] * yh[j]);
             const float t = ah[i][j] + p;

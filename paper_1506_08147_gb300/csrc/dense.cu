@@ -936,8 +936,12 @@ size_t rr_smem_bytes(int n, int m) {
 void init_rr_kernels() { opt_in_dynamic_smem((const void*)rr_smem_kernel); }
 
 // n_max: the largest pencil any task can have (3m for LOBPCG tasks).
-void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st, int n_max, int m_max) {
+void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st, int n_max, int m_max, bool dfloat) {
   if (ntask <= 0) return;
+  if (dfloat && rr_df_eligible(n_max, m_max)) {
+    launch_rr_df(d_tasks, ntask, st, n_max, m_max);
+    return;
+  }
   const size_t sm = (n_max > 0) ? rr_smem_bytes(n_max, m_max) : (size_t)-1;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);

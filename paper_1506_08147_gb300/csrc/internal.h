@@ -164,8 +164,13 @@ struct RRTask {
 size_t rr_work_doubles(int n_max, int m);
 // n_max, m_max bound the tasks' pencil sizes; pencils that fit use the
 // shared-memory kernel.  n_max <= 0 forces the global-memory kernel.
-void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st, int n_max, int m_max);
+// dfloat: the FP32 stage's reduction in double-float arithmetic (rr_df.cu)
+// where the pencil fits that kernel, FP64 otherwise.
+void launch_rr(const RRTask* d_tasks, int ntask, cudaStream_t st, int n_max, int m_max, bool dfloat = false);
 void init_rr_kernels();
+bool rr_df_eligible(int n_max, int m_max);
+void launch_rr_df(const RRTask* d_tasks, int ntask, cudaStream_t st, int n_max, int m_max);
+void init_rr_df_kernel();
 
 // solver-level helpers are in solver.cu
 

@@ -744,7 +744,7 @@ template <class real> struct Wave {
     g.out_id[1] = OUT_GRAM_B;
     for (int k = 0; k < 2; ++k) g.needs_p[k] = g.brow[k] = g.bcol[k] = 0;
     launch_gram<real>(batch, g, partial, partial_cap, st);
-    launch_rr(d_rr_init, batch.s.nel, st, batch.s.max_m, batch.s.max_m);
+    launch_rr(d_rr_init, batch.s.nel, st, batch.s.max_m, batch.s.max_m, std::is_same<real, float>::value);
     TsmmJob<real> t;
     t.nin = 1;
     t.in[0] = bref<real>(BX);
@@ -785,7 +785,7 @@ template <class real> struct Wave {
 
   // Rayleigh-Ritz and the block updates (operations 3, 4; H X for FP32).
   void enqueue_back(cudaStream_t st) {
-    launch_rr(d_rr_lob, batch.s.nel, st, 3 * batch.s.max_m, batch.s.max_m);
+    launch_rr(d_rr_lob, batch.s.nel, st, 3 * batch.s.max_m, batch.s.max_m, std::is_same<real, float>::value);
     {
       TsmmJob<real> t;
       t.nin = 3;
@@ -1612,6 +1612,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   init_hamiltonian_kernels();
   init_tf32_gram_kernel();
   init_rr_kernels();
+  init_rr_df_kernel();
   init_blas_kernels();
   cudaGetLastError();  // attribute queries above must not leave an error behind
   ctx->el.resize(n_elem);
@@ -2009,7 +2010,9 @@ dgdft_status time_stage_t(dgdft_alb_ctx* ctx, Wave<real>& w, int stage, int reps
         launch_tsmm<real>(w.batch, t, st);
         break;
       }
-      case DGDFT_STAGE_RR: launch_rr(w.d_rr_lob, nel, st, 3 * w.batch.s.max_m, w.batch.s.max_m); break;
+      case DGDFT_STAGE_RR:
+        launch_rr(w.d_rr_lob, nel, st, 3 * w.batch.s.max_m, w.batch.s.max_m, std::is_same<real, float>::value);
+        break;
       default: launch_residual<real>(w.batch, w.rnchunk, st); break;
     }
   };
@@ -2087,9 +2090,11 @@ dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int stage, int 
              : lobpcg_gram_t<float>(ctx, elem, has_p, blocks, a, b, xtw, on_device);
 }
 
-dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int n, int m, const double* a, const double* b,
+dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int stage, int n, int m, const double* a, const double* b,
                                      double* theta, double* y) {
   if (!ctx || !a || !b || !theta || !y || n < 1 || m < 1 || m > n) return DGDFT_EINVAL;
+  if (stage != 0 && stage != 1) return DGDFT_EINVAL;
+  const bool dfloat = stage == 0 && ctx->cfg.precision == DGDFT_PREC_MIXED;
   CK(cudaSetDevice(ctx->device));
   const size_t nn = (size_t)n * n;
   double *da = nullptr, *db = nullptr, *dy = nullptr, *dth = nullptr, *work = nullptr;
@@ -2118,7 +2123,7 @@ dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int n, int m, const dou
   if (e == cudaSuccess) e = ctx_copy(ctx, db, b, sizeof(double) * nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = ctx_copy(ctx, dt, &t, sizeof(t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    launch_rr(dt, 1, ctx->stream, n, m);
+    launch_rr(dt, 1, ctx->stream, n, m, dfloat);
     e = cudaStreamSynchronize(ctx->stream);
   }
   if (e == cudaSuccess) e = cudaGetLastError();

@@ -259,40 +259,56 @@ def spd(n, gen, cond=1e3):
     return (q * np.logspace(0, np.log10(cond), n)) @ q.T
 
 
-@pytest.mark.parametrize("n,m", [(20, 5), (96, 48), (144, 48), (30, 30)])
-def test_rayleigh_ritz(n, m):
+# The Rayleigh-Ritz entry point in both arithmetics a solve uses: FP64
+# (stage 1, and every stage of an FP64 context) and the FP32 stage's
+# double-float reduction (stage 0 of a mixed-precision context; pencils
+# beyond 160 x 160 or 64 wanted pairs fall back to FP64).  Both are checked
+# against LAPACK's generalized symmetric eigensolver.
+RR_ARITH = {"fp64": (B.DGDFT_PREC_FP64, 1), "dfloat": (B.DGDFT_PREC_MIXED, 0)}
+
+
+def rr_context(arith):
+    prec, stage = RR_ARITH[arith]
+    return ctx_for(small_kb_element(), prec), stage
+
+
+@pytest.mark.parametrize("arith", sorted(RR_ARITH))
+@pytest.mark.parametrize("n,m", [(20, 5), (96, 48), (144, 48), (30, 30), (160, 64), (180, 60)])
+def test_rayleigh_ritz(n, m, arith):
     gen = np.random.default_rng(n + m)
     a = gen.standard_normal((n, n))
     a = a + a.T
     b = spd(n, gen)
-    el = small_kb_element()
-    c = ctx_for(el, B.DGDFT_PREC_FP64)
-    theta, y = c.dgdft_alb_rayleigh_ritz(a, b, m)
+    c, stage = rr_context(arith)
+    theta, y = c.dgdft_alb_rayleigh_ritz(a, b, m, stage=stage)
+    c.close()
     ref = sla.eigh(a, b, eigvals_only=True)[:m]
     np.testing.assert_allclose(theta, ref, atol=1e-10 * np.max(np.abs(ref)))
     np.testing.assert_allclose(y.T @ b @ y, np.eye(m), atol=1e-10)
     assert np.max(np.abs(a @ y - b @ y * theta)) < 1e-9 * np.max(np.abs(a))
-    c.close()
 
 
-def test_rayleigh_ritz_degenerate_shells():
+@pytest.mark.parametrize("arith", sorted(RR_ARITH))
+def test_rayleigh_ritz_degenerate_shells(arith):
     # exactly degenerate clusters (free-electron-like multiplicities 1, 6, 12)
     gen = np.random.default_rng(7)
     n, m = 60, 19
     q, _ = np.linalg.qr(gen.standard_normal((n, n)))
     ev = np.r_[0.0, np.full(6, 0.2), np.full(12, 0.4), np.linspace(0.6, 3, 41)]
     a = (q * ev) @ q.T
-    el = small_kb_element()
-    c = ctx_for(el, B.DGDFT_PREC_FP64)
-    theta, y = c.dgdft_alb_rayleigh_ritz(a, np.eye(n), m)
-    np.testing.assert_allclose(theta, ev[:m], atol=1e-12)
-    np.testing.assert_allclose(y.T @ y, np.eye(m), atol=1e-11)
-    assert alb.sin_max_angle(q[:, :m].T, y.T) < 1e-10
+    c, stage = rr_context(arith)
+    theta, y = c.dgdft_alb_rayleigh_ritz(a, np.eye(n), m, stage=stage)
     c.close()
+    # FP64: rounding of eps |A| n; double-float: 2^-46 |A| n
+    tol = 1e-12 if arith == "fp64" else 1e-11
+    np.testing.assert_allclose(theta, ev[:m], atol=tol)
+    np.testing.assert_allclose(y.T @ y, np.eye(m), atol=10 * tol)
+    assert alb.sin_max_angle(q[:, :m].T, y.T) < 100 * tol
 
 
+@pytest.mark.parametrize("arith", sorted(RR_ARITH))
 @pytest.mark.parametrize("seed", range(12))
-def test_rayleigh_ritz_close_pairs(seed):
+def test_rayleigh_ritz_close_pairs(seed, arith):
     """Pencils shaped like the FP32 stage's: the lowest 48 of 144 eigenvalues
     near zero in close pairs (gaps 1e-7 to 1e-3 of the norm), the rest spread
     up to ~30.  Eigenvalue estimates from bisection are good to roughly the
@@ -309,24 +325,30 @@ def test_rayleigh_ritz_close_pairs(seed):
     lb = np.linalg.cholesky(b)
     a = lb @ (q * ev) @ q.T @ lb.T
     a = 0.5 * (a + a.T)
-    el = small_kb_element()
-    c = ctx_for(el, B.DGDFT_PREC_FP64)
-    theta, y = c.dgdft_alb_rayleigh_ritz(a, b, m)
+    c, stage = rr_context(arith)
+    theta, y = c.dgdft_alb_rayleigh_ritz(a, b, m, stage=stage)
     c.close()
     np.testing.assert_allclose(theta, ev[:m], atol=1e-10 * 30.0)
     np.testing.assert_allclose(y.T @ b @ y, np.eye(m), atol=1e-9)
     assert np.max(np.abs(a @ y - b @ y * theta)) < 1e-8 * 30.0
 
 
-def test_rayleigh_ritz_rejects_indefinite_b():
+@pytest.mark.parametrize("arith", sorted(RR_ARITH))
+def test_rayleigh_ritz_rejects_indefinite_b(arith):
     n = 10
     a = np.eye(n)
     b = np.eye(n)
     b[3, 3] = -1.0
-    el = small_kb_element()
-    c = ctx_for(el, B.DGDFT_PREC_FP64)
+    c, stage = rr_context(arith)
     with pytest.raises(B.DgdftError):
-        c.dgdft_alb_rayleigh_ritz(a, b, 3)
+        c.dgdft_alb_rayleigh_ritz(a, b, 3, stage=stage)
+    c.close()
+
+
+def test_rayleigh_ritz_rejects_bad_stage():
+    c, _ = rr_context("dfloat")
+    with pytest.raises(B.DgdftError):
+        c.dgdft_alb_rayleigh_ritz(np.eye(4), np.eye(4), 2, stage=2)
     c.close()
 
 
