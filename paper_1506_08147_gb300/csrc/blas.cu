@@ -826,34 +826,81 @@ __global__ void __launch_bounds__(256) residual_kernel(const ElemDev<real>* __re
   if (!e.state[ST_ACTIVE]) return;
   const int j = blockIdx.y;
   if (j >= e.m) return;
-  const int kc = (e.ng + nchunk - 1) / nchunk;
+  const int kc = (((e.ng + nchunk - 1) / nchunk) + 3) & ~3;  // chunks of whole 16-byte groups
   const int beg = blockIdx.x * kc, end = min(e.ng, beg + kc);
   const real* X = cur_blk(e, BX) + (size_t)j * e.ng;
   const real* HX = cur_blk(e, BHX) + (size_t)j * e.ng;
   real* R = e.blk[BW][0] + (size_t)j * e.ng;
   const real th = (real)e.theta[j];
   real s[4] = {0, 0, 0, 0};
-  for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    const real x = X[i], hx = HX[i];
-    const real r = hx - th * x;
-    R[i] = r;
-    s[0] += r * r;
-    s[1] += x * x;
-    s[2] += x * hx;
-    s[3] += e.V[i] * x * x;
-  }
-  __shared__ double red[4][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (sizeof(real) == sizeof(float)) {
+    // FP32: 16-byte accesses where the columns allow, and a block reduction
+    // in FP32 (the FP64 pipe of this part is ~55x slower; these are partial
+    // sums of at most a few thousand terms, converted to FP64 per chunk)
+    const bool vec = ((beg | end) & 3) == 0 && ((e.ng & 3) == 0) &&
+                     ((((uintptr_t)X) | ((uintptr_t)HX) | ((uintptr_t)R) | ((uintptr_t)e.V)) & 15) == 0;
+    if (vec) {
+      const float4* X4 = reinterpret_cast<const float4*>(X);
+      const float4* H4 = reinterpret_cast<const float4*>(HX);
+      const float4* V4 = reinterpret_cast<const float4*>(e.V);
+      float4* R4 = reinterpret_cast<float4*>(R);
+#pragma unroll 2
+      for (int i = (beg >> 2) + threadIdx.x; i < (end >> 2); i += blockDim.x) {
+        const float4 x = X4[i], hx = H4[i], v = V4[i];
+        const float4 r = make_float4(hx.x - th * x.x, hx.y - th * x.y, hx.z - th * x.z, hx.w - th * x.w);
+        R4[i] = r;
+        s[0] += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+        s[1] += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+        s[2] += x.x * hx.x + x.y * hx.y + x.z * hx.z + x.w * hx.w;
+        s[3] += v.x * x.x * x.x + v.y * x.y * x.y + v.z * x.z * x.z + v.w * x.w * x.w;
+      }
+    } else {
+      for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        const real x = X[i], hx = HX[i];
+        const real r = hx - th * x;
+        R[i] = r;
+        s[0] += r * r;
+        s[1] += x * x;
+        s[2] += x * hx;
+        s[3] += e.V[i] * x * x;
+      }
+    }
+    __shared__ float redf[4][8];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    double v = warp_sum((double)s[q]);
-    if (lane == 0) red[q][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-    e.rpart[((size_t)j * nchunk + blockIdx.x) * 4 + threadIdx.x] = v;
+    for (int q = 0; q < 4; ++q) {
+      float v = s[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) redf[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      float v = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += redf[threadIdx.x][w];
+      e.rpart[((size_t)j * nchunk + blockIdx.x) * 4 + threadIdx.x] = (double)v;
+    }
+  } else {
+    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+      const real x = X[i], hx = HX[i];
+      const real r = hx - th * x;
+      R[i] = r;
+      s[0] += r * r;
+      s[1] += x * x;
+      s[2] += x * hx;
+      s[3] += e.V[i] * x * x;
+    }
+    __shared__ double red[4][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double v = warp_sum((double)s[q]);
+      if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+      e.rpart[((size_t)j * nchunk + blockIdx.x) * 4 + threadIdx.x] = v;
+    }
   }
 }
 

@@ -261,8 +261,10 @@ __global__ void __launch_bounds__(ZTHREADS)
   const float scalef = (float)e.scale;
   float inv_tk = 1.f;
   if (MODE == ZM_TETER) {
-    const double tk = tkin_override ? tkin_override[j] : e.tkin[j];
-    inv_tk = (float)(1.0 / fmax(tk, 1e-8));
+    // FP32 reciprocal: one FP64 division per thread costs ~16 FP64-pipe
+    // cycles per instruction here
+    const float tk = (float)(tkin_override ? tkin_override[j] : e.tkin[j]);
+    inv_tk = 1.0f / fmaxf(tk, 1e-8f);
   }
 #pragma unroll
   for (int z = 0; z < NZ; ++z) {

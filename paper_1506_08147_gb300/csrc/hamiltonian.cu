@@ -141,10 +141,10 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
     C* s = cur ? buf1 : buf0;
     double tk = 1.0;
     if (MODE == ZM_TETER) tk = tkin_override ? tkin_override[j] : e.tkin[j];
-    const double inv_tk = 1.0 / fmax(tk, 1e-8);
     if constexpr (sizeof(TZ) == sizeof(float)) {
-      // FP32 symbols and Teter factor: no FP64 arithmetic per point
-      const float inv_tkf = (float)inv_tk, scalef = (float)e.scale;
+      // FP32 symbols and Teter factor: no FP64 arithmetic per point (nor a
+      // per-thread FP64 division)
+      const float inv_tkf = 1.0f / fmaxf((float)tk, 1e-8f), scalef = (float)e.scale;
       for (int t = threadIdx.x; t < nz * ZTILE; t += blockDim.x) {
         const int gz = t / ZTILE, cc = t - gz * ZTILE;
         const int c = c0 + cc;
@@ -166,7 +166,7 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
         if (c >= nplane) continue;
         const int y = udiv_small(c, mag_nxh), kx = c - y * e.nxh;
         const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
-        double f = (MODE == ZM_KINETIC) ? g : teter_factor(g * inv_tk);
+        double f = (MODE == ZM_KINETIC) ? g : teter_factor(g / fmax(tk, 1e-8));
         f *= e.scale;
         s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (TZ)f);
       }

@@ -509,6 +509,9 @@ __global__ void __launch_bounds__(RD_THREADS, 1) rr_df_kernel(const RRTask* __re
         S[c + (size_t)r * ld] = a;
       }
     __syncthreads();
+    // each pass solves L Y = S column by column, leaving row k unscaled
+    // (S[k, c] L_kk = Y[k, c]); the scaling by 1/L_kk is folded into the
+    // transpose after pass 0 and the symmetrisation after pass 1
     for (int pass = 0; pass < 2; ++pass) {
       for (int k = 0; k < n; ++k) {
         const int rows = (n - k - 1 + 31) >> 5;
@@ -519,34 +522,38 @@ __global__ void __launch_bounds__(RD_THREADS, 1) rr_df_kernel(const RRTask* __re
           lk[r] = (r < rows && i < n) ? WL[i + (size_t)k * ldw] : dfl_of(0.0f);
         }
         const dfl dk = dinv[k];
+#pragma unroll 2
         for (int c = warp; c < n; c += RD_WARPS) {
           dfl* col = S + (size_t)c * ld;
-          const dfl skc = dfl_mul(col[k], dk);
-          __syncwarp();
-          if (lane == 0) col[k] = skc;
+          const dfl y = dfl_mul(col[k], dk);
 #pragma unroll
           for (int r = 0; r < RD_RPL; ++r) {
             const int i = k + 1 + lane + 32 * r;
-            if (r < rows && i < n) col[i] = dfl_fnma(lk[r], skc, col[i]);
+            if (r < rows && i < n) col[i] = dfl_fnma(lk[r], y, col[i]);
           }
         }
         __syncwarp();
       }
       __syncthreads();
       if (pass == 0) {
+        // S <- (D^-1 S)^T with D = diag(L)
         for (int c = warp; c < n; c += RD_WARPS)
-          for (int r = lane; r < c; r += 32) {
-            const dfl t = S[r + (size_t)c * ld];
-            S[r + (size_t)c * ld] = S[c + (size_t)r * ld];
-            S[c + (size_t)r * ld] = t;
+          for (int r = lane; r <= c; r += 32) {
+            const dfl a = dfl_mul(S[r + (size_t)c * ld], dinv[r]);
+            const dfl b = dfl_mul(S[c + (size_t)r * ld], dinv[c]);
+            S[r + (size_t)c * ld] = b;
+            S[c + (size_t)r * ld] = a;
           }
         __syncthreads();
       }
     }
-    // symmetrise: the lower triangle takes the mean of C and C^T
+    // C = D^-1 S; its lower triangle takes the mean of C and C^T
     for (int c = warp; c < n; c += RD_WARPS)
-      for (int r = c + 1 + lane; r < n; r += 32)
-        S[r + (size_t)c * ld] = dfl_scale2(dfl_add(S[r + (size_t)c * ld], S[c + (size_t)r * ld]), 0.5f);
+      for (int r = c + lane; r < n; r += 32) {
+        const dfl a = dfl_mul(S[r + (size_t)c * ld], dinv[r]);
+        const dfl b = dfl_mul(S[c + (size_t)r * ld], dinv[c]);
+        S[r + (size_t)c * ld] = (r == c) ? a : dfl_scale2(dfl_add(a, b), 0.5f);
+      }
     __syncthreads();
     // 3. Householder tridiagonalisation on the lower triangle; reflector k
     // (unit vector v, H = I - 2 v v^T) kept in S[k+1.., k].  A step: p = C v
@@ -723,11 +730,12 @@ __global__ void __launch_bounds__(RD_THREADS, 1) rr_df_kernel(const RRTask* __re
     }
     for (int k = n - 3; k >= 0; --k) {
       const dfl* vk = S + (size_t)k * ld;
+      const int rlo = (k + 1) >> 5;  // row chunks below rlo are untouched by H_k
       dfl v[RD_RPL];
 #pragma unroll
       for (int r = 0; r < RD_RPL; ++r) {
         const int i = lane + 32 * r;
-        v[r] = (i > k && i < n) ? vk[i] : dfl_of(0.0f);
+        v[r] = (r >= rlo && i > k && i < n) ? vk[i] : dfl_of(0.0f);
       }
       dfl s[RD_CPW];
 #pragma unroll
@@ -735,7 +743,8 @@ __global__ void __launch_bounds__(RD_THREADS, 1) rr_df_kernel(const RRTask* __re
         dfl a = dfl_of(0.0f);
         if (cc < ncw)
 #pragma unroll
-          for (int r = 0; r < RD_RPL; ++r) a = dfl_fma(v[r], z[cc][r], a);
+          for (int r = 0; r < RD_RPL; ++r)
+            if (r >= rlo) a = dfl_fma(v[r], z[cc][r], a);
         s[cc] = a;
       }
 #pragma unroll
@@ -752,7 +761,8 @@ __global__ void __launch_bounds__(RD_THREADS, 1) rr_df_kernel(const RRTask* __re
           const dfl t = dfl_scale2(
               dfl{__shfl_sync(0xffffffffu, s[cc].h, 0), __shfl_sync(0xffffffffu, s[cc].l, 0)}, 2.0f);
 #pragma unroll
-          for (int r = 0; r < RD_RPL; ++r) z[cc][r] = dfl_fnma(t, v[r], z[cc][r]);
+          for (int r = 0; r < RD_RPL; ++r)
+            if (r >= rlo) z[cc][r] = dfl_fnma(t, v[r], z[cc][r]);
         }
     }
     __syncthreads();
@@ -781,7 +791,7 @@ __global__ void __launch_bounds__(RD_THREADS, 1) rr_df_kernel(const RRTask* __re
 #pragma unroll
         for (int r = 0; r < RD_RPL; ++r) {
           if (r == ri && lane == src) z[cc][r] = yi;
-          else z[cc][r] = dfl_fnma(li[r], yi, z[cc][r]);
+          else if (r <= ri) z[cc][r] = dfl_fnma(li[r], yi, z[cc][r]);  // rows k < i only
         }
       }
     }
