@@ -150,11 +150,14 @@ def stage_bytes(name, e, s):
     return 0
 
 
-# launches of each stage per FP32 LOBPCG iteration: the three FFT passes run
-# for H W, for H X' and for the Teter preconditioner; one 12-pair Gram
-# (X^T W is a small extra Gram); three block updates (X' with P', HP', the
-# projection of W); one Rayleigh-Ritz; one residual pass
-STAGE_PER_ITER = {"xy_fwd": 3, "z_mult": 3, "xy_inv": 3, "gram": 1, "update": 3, "rayleigh_ritz": 1,
+# launches of each stage per FP32 LOBPCG iteration, in units of the timed
+# launch: the three FFT passes run for H W, for H X' and for the Teter
+# preconditioner; one 12-pair Gram (X^T W is a small extra Gram); the block
+# updates are X' = [X W P] Y (with P' on the way, the timed launch's 3m-term
+# sums), HP' = [HW HP] Y_wp (2m terms) and the projection W - X (X^T W)
+# (m terms): two timed launches' worth of the FP32 FMA work that bounds the
+# SIMT update kernel; one Rayleigh-Ritz; one residual pass
+STAGE_PER_ITER = {"xy_fwd": 3, "z_mult": 3, "xy_inv": 3, "gram": 1, "update": 2, "rayleigh_ritz": 1,
                   "residual": 1}
 
 # DRAM bytes (read + write) of one element's share of the FP32 stage's Gram
