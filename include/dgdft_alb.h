@@ -56,15 +56,18 @@ typedef enum {
   DGDFT_ESTATE = 6    /* call out of order (e.g. get_basis before solve)    */
 } dgdft_status;
 
-/* Arithmetic of the bulk LOBPCG operations (H apply, preconditioner, Gram
- * products, block updates).  The Cholesky factorisation, the Rayleigh-Ritz
- * eigensolve and the final orthonormalisation are FP64 in every mode.      */
+/* Arithmetic of the LOBPCG operations (H apply, preconditioner, Gram
+ * products, block updates, Rayleigh-Ritz).  The final restriction and
+ * orthonormalisation are FP64 in every mode.                               */
 enum {
   DGDFT_PREC_FP64 = 0,  /* plain: FP64 everywhere                             */
-  DGDFT_PREC_MIXED = 1  /* chosen form: FP32 storage, FFTs and block updates,
-                           Gram products with compensated FP32 accumulation
-                           (see bulk_kernels), FP64 Rayleigh-Ritz; then the
-                           FP64 check and FP64 iterations to the tolerance     */
+  DGDFT_PREC_MIXED = 1  /* chosen form: an FP32 stage (FP32 storage, FFTs
+                           and block updates, Gram products on tensor cores
+                           or compensated SIMT (see bulk_kernels), the
+                           Rayleigh-Ritz in double-float, ~2^-46), then the
+                           FP64 check and FP64-accurate iterations to the
+                           tolerance (FP64 FFTs and Rayleigh-Ritz,
+                           double-float Gram and update products)          */
 };
 
 enum {
@@ -93,15 +96,19 @@ typedef struct {
   int device;             /* CUDA device ordinal; -1 = current device         */
   int keep_block;         /* 1: keep each converged N_g x m Ritz block on the
                              host after solve (for dgdft_alb_get_block)        */
-  int bulk_kernels;       /* Gram products of the FP32 stage.  0 (default):
-                             tcgen05 tensor cores where every element of a
-                             wave has m <= 48 and N_g % 4 == 0 (TMA copies of
-                             the blocks, each FP32 value split into two TF32
+  int bulk_kernels;       /* Gram products and block updates of the FP32
+                             stage.  0 (default): Gram products on tcgen05
+                             tensor cores where every element of a wave has
+                             m <= 48 and N_g % 4 == 0 (TMA copies of the
+                             blocks, each FP32 value split into two TF32
                              parts, ~2^-22 relative per product, FP32
                              accumulation in tensor memory over 256 rows,
-                             then compensated), else the SIMT kernel; 1: the
-                             SIMT FP32 kernel with compensated accumulation
-                             everywhere.  Other values give DGDFT_EINVAL.  */
+                             then compensated), else the SIMT kernel; block
+                             updates in SIMT FP32.  1: SIMT FP32 kernels
+                             only (compensated Gram accumulation).  2: as 0,
+                             and the block updates on tensor cores too (the
+                             same split, sums of up to 3m products in tensor
+                             memory).  Other values give DGDFT_EINVAL.     */
   int h_fp64_forward;     /* FP64 forward FFT in the FP32 stage's H apply
                              (its rounding, amplified by |G|^2/2, sets the
                              stage's residual floor near 2e-6 Ha): 0 never;

@@ -61,6 +61,21 @@ dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const doub
 dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int stage, int has_p, const double* blocks,
                                    double* a, double* b, double* xtw, int on_device);
 
+/* The block updates of one LOBPCG iteration (Sec. II.B, operation 4: the
+ * paper's Phi C products), computed on caller blocks by the same kernels
+ * and precision choices as the solver for element `elem` in stage `stage`
+ * (0: the bulk stage, in DGDFT_PREC_MIXED the FP32 stage, tensor cores when
+ * bulk_kernels = 2; 1: the FP64 stage, double-float in DGDFT_PREC_MIXED).
+ * blocks holds six N_g x m column-major blocks: X, W, P, H X, H W, H P (P
+ * and H P ignored when has_p = 0); y is the 3m x m column-major coefficient
+ * block [Y_x; Y_w; Y_p] of a Rayleigh-Ritz step.  out receives three N_g x m
+ * blocks: X' = [X W P] Y, P' = [W P] [Y_w; Y_p] and (H P)' = [H W H P]
+ * [Y_w; Y_p] (the P terms dropped when has_p = 0).  blocks and out are on
+ * the device when on_device = 1, else host arrays; y is a host array.
+ * DGDFT_ETIMEOUT when a bounded device wait ran out. */
+dgdft_status dgdft_alb_lobpcg_update(dgdft_alb_ctx* ctx, int elem, int stage, int has_p, const double* blocks,
+                                     const double* y, double* out, int on_device);
+
 /* Rayleigh-Ritz on a symmetric pencil (Sec. II.B, operation 4) on the GPU:
  * the lowest m eigenpairs of A y = theta B y with B positive definite.
  * stage picks the arithmetic of a solve's two stages: 0 = the FP32 LOBPCG

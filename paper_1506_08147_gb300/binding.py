@@ -63,6 +63,7 @@ _SIGS = {
     "dgdft_alb_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P]),
     "dgdft_alb_lobpcg_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, C.c_int]),
+    "dgdft_alb_lobpcg_update": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_restrict_orthonormalise": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P,
                                                     C.c_int]),
     "dgdft_alb_get_block": (C.c_int, [_P, C.c_int, _P, C.c_int]),
@@ -136,7 +137,8 @@ class Context:
 
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
-                 precond_weights=None, simt_gram=False, h_fp64_forward=False, device_wait_polls=0):
+                 precond_weights=None, simt_gram=False, h_fp64_forward=False, device_wait_polls=0,
+                 tc_update=False):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -146,7 +148,7 @@ class Context:
         cfg.maxit = maxit
         cfg.check_every = check_every
         cfg.keep_block = int(keep_block)
-        cfg.bulk_kernels = int(simt_gram)
+        cfg.bulk_kernels = 1 if simt_gram else (2 if tc_update else 0)
         cfg.device_wait_polls = int(device_wait_polls)
         cfg.h_fp64_forward = int(h_fp64_forward)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
@@ -364,6 +366,17 @@ class Context:
                                                    _ptr(a)[0], _ptr(b)[0], _ptr(xtw)[0], 0), "lobpcg_gram")
         # column-major out -> matrices
         return a.T.copy(), b.T.copy(), xtw.T.copy()
+
+    def dgdft_alb_lobpcg_update(self, elem, blocks, y, has_p=True, stage=0):
+        """blocks: (6, m, N_g) rows X, W, P, HX, HW, HP; y: the 3m x m
+        coefficient matrix.  Returns (3, m, N_g): X', P', HP' as rows."""
+        blk = np.ascontiguousarray(blocks, np.float64)
+        m, ng = blk.shape[1], blk.shape[2]
+        ycm = np.ascontiguousarray(np.asarray(y, np.float64).T)  # column-major 3m x m
+        out = np.zeros((3, m, ng))
+        self._check(self.lib.dgdft_alb_lobpcg_update(self.h, elem, int(stage), int(bool(has_p)), _ptr(blk)[0],
+                                                     _ptr(ycm)[0], _ptr(out)[0], 0), "lobpcg_update")
+        return out
 
     def dgdft_alb_rayleigh_ritz(self, a, b, m, stage=1):
         """Lowest m eigenpairs of a y = theta b y; stage 0 is the FP32 stage's

@@ -186,6 +186,15 @@ bool tf32_gram_eligible(const BatchShape& s);
 // host_out; returns "" or the reason it could not
 std::string encode_tf32_gram_maps(const ElemDev<float>* h, int nel, void* host_out);
 void init_tf32_gram_kernel();
+// Tensor-core block updates of the FP32 stage (tf32_update.cu): the same
+// jobs as launch_tsmm for blocks of the batch's elements (m <= 48, N_g a
+// multiple of 4, default rows/columns/leading dimensions); false when the
+// job or batch is not eligible and the SIMT kernel must run.
+bool tf32_update_eligible(const BatchShape& s);
+std::string encode_tf32_update_maps(const ElemDev<float>* h, int nel, void* host_out);
+void init_tf32_update_kernel();
+bool launch_tf32_update(const Batch<float>& b, const TsmmJob<float>& job, const void* d_maps, uint32_t polls,
+                        cudaStream_t st);
 // mode 0: the 12 LOBPCG Gram blocks into gram (A, B); mode 1: X^T W into gxw.
 // polls: bound of every device wait (0: the default, about a second).
 // Returns false (nothing launched) when the partial buffer is too small.

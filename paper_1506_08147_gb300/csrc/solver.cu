@@ -204,7 +204,7 @@ void default_x0(std::vector<double>& x, int elem);
 // unless the SIMT kernels are selected, when every element has m <= 48 and
 // N_g a multiple of 4 (16-byte column starts for the copies).
 inline bool tf32_selected(const dgdft_alb_config& c, const BatchShape& s) {
-  return c.bulk_kernels == 0 && tf32_gram_eligible(s);
+  return (c.bulk_kernels == 0 || c.bulk_kernels == 2) && tf32_gram_eligible(s);
 }
 
 template <class real> struct Wave {
@@ -234,11 +234,16 @@ template <class real> struct Wave {
     double* partial = nullptr;
     size_t partial_cap = 0;
     const unsigned char* maps = nullptr;
+    const unsigned char* umaps = nullptr;
   };
   // TMA tensor maps of every element's blocks (FP32 waves on the tensor-core
   // Gram), 10 x 128 bytes per element; nullptr when the SIMT Gram runs
   unsigned char* d_maps = nullptr;
   const unsigned char* maps = nullptr;  // of the current view
+  // the same blocks' tensor maps for the tensor-core block updates (boxes of
+  // 128 rows x 16 columns)
+  unsigned char* d_umaps = nullptr;
+  const unsigned char* umaps = nullptr;
   SubView full, sub[2];
   bool split = false;
   bool hx64 = false;            // capture H X' with the FP64 forward transform
@@ -262,6 +267,7 @@ template <class real> struct Wave {
     partial = v.partial;
     partial_cap = v.partial_cap;
     maps = v.maps;
+    umaps = v.umaps;
   }
 
   // Half-batch views; split only FP32 waves of >= 2 elements without the
@@ -274,6 +280,8 @@ template <class real> struct Wave {
     full.partial_cap = partial_cap;
     full.maps = d_maps;
     maps = d_maps;
+    full.umaps = d_umaps;
+    umaps = d_umaps;
     const int nel = batch.s.nel;
     if (!std::is_same<real, float>::value || learned || nel < 2) return DGDFT_OK;
     const int h0 = nel / 2;
@@ -289,6 +297,7 @@ template <class real> struct Wave {
       v.partial = partial + per * off;
       v.partial_cap = per * cnt;
       v.maps = d_maps ? d_maps + (size_t)off * 10 * 128 : nullptr;
+      v.umaps = d_umaps ? d_umaps + (size_t)off * 10 * 128 : nullptr;
     }
     CK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
@@ -364,7 +373,7 @@ template <class real> struct Wave {
     total += sizeof(double) * pcap + ALIGN;
     total += (sizeof(ElemDev<real>) + 2 * sizeof(RRTask)) * nel + 4 * ALIGN;
     const bool want_maps = std::is_same<real, float>::value && tf32_selected(ctx->cfg, s);
-    if (want_maps) total += (size_t)nel * 10 * 128 + ALIGN;
+    if (want_maps) total += 2 * ((size_t)nel * 10 * 128 + ALIGN);
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, total);
     if (e != cudaSuccess) return ctx->fail(DGDFT_ENOMEM, "device allocation of a wave failed: " + cuda_err_string(e));
@@ -412,6 +421,17 @@ template <class real> struct Wave {
       if (err.empty() && dm) {
         CK(ctx_copy(ctx, dm, hm.data(), hm.size(), cudaMemcpyHostToDevice));
         d_maps = dm;
+      }
+      err.clear();
+      if constexpr (std::is_same<real, float>::value)
+        if (ctx->cfg.bulk_kernels == 2 && tf32_update_eligible(s))
+          err = encode_tf32_update_maps(h.data(), nel, hm.data());
+        else
+          err = "not selected";
+      unsigned char* du = (unsigned char*)arena.take(hm.size());
+      if (err.empty() && du) {
+        CK(ctx_copy(ctx, du, hm.data(), hm.size(), cudaMemcpyHostToDevice));
+        d_umaps = du;
       }
     }
     CK(ctx_copy(ctx, d_elems, h.data(), sizeof(ElemDev<real>) * nel, cudaMemcpyHostToDevice));
@@ -690,6 +710,15 @@ template <class real> struct Wave {
     return false;
   }
 
+  // Block update out = alpha sum in_i Y_i + beta out: tensor cores in the
+  // FP32 stage when selected (the TF32-split tcgen05 kernel), else SIMT.
+  void update(const TsmmJob<real>& t, cudaStream_t st) {
+    if constexpr (std::is_same<real, float>::value) {
+      if (umaps && launch_tf32_update(batch, t, umaps, (uint32_t)ctx->wait_polls, st)) return;
+    }
+    launch_tsmm<real>(batch, t, st);
+  }
+
   GramJob<real> gram12() const {
     GramJob<real> g;
     // A(i, j) for block(i) < block(j) is taken as (H s_i)^T s_j, H on the
@@ -749,10 +778,10 @@ template <class real> struct Wave {
     t.nin = 1;
     t.in[0] = bref<real>(BX);
     t.out = bref<real>(BX, 1);
-    launch_tsmm<real>(batch, t, st);
+    update(t, st);
     t.in[0] = bref<real>(BHX);
     t.out = bref<real>(BHX, 1);
-    launch_tsmm<real>(batch, t, st);
+    update(t, st);
     launch_iter_finish<real>(batch, 0, st);
   }
 
@@ -777,7 +806,7 @@ template <class real> struct Wave {
       t.out = bref<real>(BW);
       t.alpha = -1.0;
       t.beta = 1.0;
-      launch_tsmm<real>(batch, t, st);
+      update(t, st);
     }
     launch_apply_h<real>(batch, bref<real>(BW), bref<real>(BHW), 0, st, fwd64());
     gram_pencil(st);
@@ -803,7 +832,7 @@ template <class real> struct Wave {
         t.from2 = 1;
         t.out2 = bref<real>(BP, 1);
       }
-      launch_tsmm<real>(batch, t, st);
+      update(t, st);
       t.from2 = -1;
       if (std::is_same<real, double>::value) {
         // FP64: H X' by the FFT (three FP64 passes cost less than the FP64
@@ -833,7 +862,7 @@ template <class real> struct Wave {
         u.in[0] = bref<real>(BHW);
         u.in[1] = bref<real>(BHP);
         u.out = bref<real>(BHP, 1);
-        launch_tsmm<real>(batch, u, st);
+        update(u, st);
       }
     }
     launch_iter_finish<real>(batch, 1, st);
@@ -1568,7 +1597,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   if (cfg->precision != DGDFT_PREC_FP64 && cfg->precision != DGDFT_PREC_MIXED) return DGDFT_EINVAL;
   if (cfg->precond != DGDFT_PRECOND_TETER && cfg->precond != DGDFT_PRECOND_LEARNED) return DGDFT_EINVAL;
   if (!(cfg->tol > 0.0) || cfg->maxit <= 0) return DGDFT_EINVAL;
-  if (cfg->bulk_kernels != 0 && cfg->bulk_kernels != 1) return DGDFT_EINVAL;
+  if (cfg->bulk_kernels < 0 || cfg->bulk_kernels > 2) return DGDFT_EINVAL;
   for (int i = 0; i < n_elem; ++i) {
     const dgdft_element_desc& d = elems[i];
     FftPlan p;
@@ -1611,6 +1640,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   }
   init_hamiltonian_kernels();
   init_tf32_gram_kernel();
+  init_tf32_update_kernel();
   init_rr_kernels();
   init_rr_df_kernel();
   init_blas_kernels();
@@ -1981,6 +2011,71 @@ dgdft_status lobpcg_gram_t(dgdft_alb_ctx* ctx, int elem, int has_p, const double
 }
 
 template <class real>
+dgdft_status lobpcg_update_t(dgdft_alb_ctx* ctx, int elem, int has_p, const double* blocks, const double* y,
+                             double* out, int on_device) {
+  Wave<real> w;
+  dgdft_status s = with_step_wave<real>(ctx, elem, w);
+  if (s != DGDFT_OK) return s;
+  ElemDev<real>& E = w.h[0];
+  const int m = E.m;
+  const size_t n = (size_t)E.ng * m;
+  const int order[6] = {BX, BW, BP, BHX, BHW, BHP};
+  for (int q = 0; q < 6; ++q)
+    if ((s = step_in<real>(ctx, E.blk[order[q]][0], blocks + q * n, n, on_device)) != DGDFT_OK) return s;
+  for (int q = 0; q < 3 * m * m; ++q)
+    if (!std::isfinite(y[q])) return ctx->fail(DGDFT_EINVAL, "lobpcg_update: non-finite coefficient");
+  const int hp = has_p ? 1 : 0;
+  CK(ctx_copy(ctx, E.state + ST_HAS_P, &hp, sizeof(int), cudaMemcpyHostToDevice));
+  CK(ctx_copy(ctx, E.Y, y, sizeof(double) * 3 * m * m, cudaMemcpyHostToDevice));
+  if (E.Yf) {
+    std::vector<float> yf(3 * (size_t)m * m);
+    for (size_t q = 0; q < yf.size(); ++q) yf[q] = (float)y[q];
+    CK(ctx_copy(ctx, E.Yf, yf.data(), sizeof(float) * yf.size(), cudaMemcpyHostToDevice));
+  }
+  cudaStream_t st = ctx->stream;
+  TsmmJob<real> t;
+  t.nin = 3;
+  t.in[0] = bref<real>(BX);
+  t.in[1] = bref<real>(BW);
+  t.in[2] = bref<real>(BP);
+  t.yrow[0] = 0;
+  t.yrow[1] = 1;
+  t.yrow[2] = 2;
+  t.needs_p[2] = 1;
+  t.out = bref<real>(BX, 1);
+  TsmmJob<real> u;
+  u.nin = 2;
+  u.in[0] = bref<real>(BW);
+  u.in[1] = bref<real>(BP);
+  u.yrow[0] = 1;
+  u.yrow[1] = 2;
+  u.needs_p[1] = 1;
+  u.out = bref<real>(BP, 1);
+  if (std::is_same<real, float>::value) {
+    // as the FP32 stage: P' on the way to X'
+    t.from2 = 1;
+    t.out2 = bref<real>(BP, 1);
+    w.update(t, st);
+  } else {
+    w.update(t, st);
+    w.update(u, st);
+  }
+  u.in[0] = bref<real>(BHW);
+  u.in[1] = bref<real>(BHP);
+  u.out = bref<real>(BHP, 1);
+  w.update(u, st);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  int err = 0;
+  CK(ctx_copy(ctx, &err, E.state + ST_ERROR, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err & ERR_TIMEOUT) return ctx->fail(DGDFT_ETIMEOUT, "lobpcg_update: a bounded device wait ran out");
+  const int outs[3] = {BX, BP, BHP};
+  for (int q = 0; q < 3; ++q)
+    if ((s = step_out<real>(ctx, out + q * n, E.blk[outs[q]][1], n, on_device)) != DGDFT_OK) return s;
+  return DGDFT_OK;
+}
+
+template <class real>
 dgdft_status time_stage_t(dgdft_alb_ctx* ctx, Wave<real>& w, int stage, int reps, double* ms) {
   const int nel = (int)w.ids.size();
   std::vector<int> saved = w.h_state;
@@ -2007,7 +2102,7 @@ dgdft_status time_stage_t(dgdft_alb_ctx* ctx, Wave<real>& w, int stage, int reps
         t.yrow[2] = 2;
         t.needs_p[2] = 1;
         t.out = bref<real>(BX, 1);
-        launch_tsmm<real>(w.batch, t, st);
+        w.update(t, st);
         break;
       }
       case DGDFT_STAGE_RR:
@@ -2088,6 +2183,16 @@ dgdft_status dgdft_alb_lobpcg_gram(dgdft_alb_ctx* ctx, int elem, int stage, int 
   return (ctx->cfg.precision == DGDFT_PREC_FP64 || stage == 1)
              ? lobpcg_gram_t<double>(ctx, elem, has_p, blocks, a, b, xtw, on_device)
              : lobpcg_gram_t<float>(ctx, elem, has_p, blocks, a, b, xtw, on_device);
+}
+
+dgdft_status dgdft_alb_lobpcg_update(dgdft_alb_ctx* ctx, int elem, int stage, int has_p, const double* blocks,
+                                     const double* y, double* out, int on_device) {
+  if (!ctx || !blocks || !y || !out || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  if (stage != 0 && stage != 1) return DGDFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  return (ctx->cfg.precision == DGDFT_PREC_FP64 || stage == 1)
+             ? lobpcg_update_t<double>(ctx, elem, has_p, blocks, y, out, on_device)
+             : lobpcg_update_t<float>(ctx, elem, has_p, blocks, y, out, on_device);
 }
 
 dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int stage, int n, int m, const double* a, const double* b,

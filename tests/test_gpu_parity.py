@@ -252,6 +252,54 @@ def test_lobpcg_gram(prec, simt, stage, which, has_p, kind):
     assert worst < tol and e_xtw < tol
 
 
+# ---------------------------------------------------- block updates
+
+# (precision, update kernels, stage): plain FP64; the mixed form's FP32 stage
+# with SIMT updates (default) and with tensor-core updates (bulk_kernels = 2);
+# the mixed form's double-float FP64 stage
+LOBPCG_UPDATE_KINDS = [(B.DGDFT_PREC_FP64, "simt", 0), (B.DGDFT_PREC_MIXED, "simt", 0),
+                       (B.DGDFT_PREC_MIXED, "tc", 0), (B.DGDFT_PREC_MIXED, "simt", 1)]
+# worst-case bounds relative to sum_k |s_k| |y_k| over K <= 3m = 144 terms:
+# FP64 and double-float as for the Gram; FP32 with round-to-nearest
+# accumulation K 2^-24; TF32 split (3 2^-22 per product) plus the tensor
+# core's FP32 accumulation, which does not round to nearest (K 2^-23)
+UPDATE_TOL = {(B.DGDFT_PREC_FP64, "simt", 0): 1e-13, (B.DGDFT_PREC_MIXED, "simt", 0): 144 * 2.0 ** -24,
+              (B.DGDFT_PREC_MIXED, "tc", 0): 3 * 2.0 ** -22 + 144 * 2.0 ** -23,
+              (B.DGDFT_PREC_MIXED, "simt", 1): 4e-12}
+
+
+@pytest.mark.parametrize("prec,kernels,stage", LOBPCG_UPDATE_KINDS)
+@pytest.mark.parametrize("which", ["small", "ragged", "cfg2"])
+@pytest.mark.parametrize("has_p", [True, False])
+def test_lobpcg_update(prec, kernels, stage, which, has_p):
+    """X' = [X W P] Y, P' = [W P] Y_wp and HP' = [HW HP] Y_wp (the paper's
+    Phi C products) through the solver's own kernels, against NumPy FP64
+    products of the same working-precision inputs, entry by entry relative
+    to sum_k |s_k| |y_k| (UPDATE_TOL); without P the P terms are dropped."""
+    el = {"small": small_kb_element, "ragged": ragged_element, "cfg2": cfg2_element}[which]()
+    gen = np.random.default_rng(41)
+    m = el.m
+    blk = gen.standard_normal((6, m, el.ng))
+    y = gen.standard_normal((3 * m, m))
+    c = ctx_for(el, prec, tc_update=(kernels == "tc"))
+    out = c.dgdft_alb_lobpcg_update(0, blk, y, has_p, stage=stage)
+    c.close()
+    if prec == B.DGDFT_PREC_MIXED and stage == 0:
+        blk = blk.astype(np.float32).astype(np.float64)
+        y = y.astype(np.float32).astype(np.float64)
+    k = 3 if has_p else 2
+    s_x = np.vstack(blk[:k])
+    s_wp, s_hwp = np.vstack(blk[1:k]), np.vstack(blk[4:3 + k])
+    y_x, y_wp = y[:k * m], y[m:k * m]
+    worst = 0.0
+    for got, yy, ss in ((out[0], y_x, s_x), (out[1], y_wp, s_wp), (out[2], y_wp, s_hwp)):
+        ref = yy.T @ ss
+        scale = np.abs(yy).T @ np.abs(ss)
+        worst = max(worst, float(np.max(np.abs(got - ref) / scale)))
+    print(f"{which} has_p={has_p} prec={prec} {kernels} stage={stage}: max error {worst:.2e} of sum |s||y|")
+    assert worst <= UPDATE_TOL[(prec, kernels, stage)]
+
+
 # ---------------------------------------------------- Rayleigh-Ritz
 
 def spd(n, gen, cond=1e3):
