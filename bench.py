@@ -188,7 +188,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
-                    stream=stream.cuda_stream, simt_gram=args.simt_gram, h_fp64_forward=args.fwd64)
+                    stream=stream.cuda_stream, simt_gram=args.simt_gram, h_fp64_forward=args.fwd64,
+                    tc_update=args.tc_update)
     dev_x0 = []
     for k, e in enumerate(els):
         B.load_element(ctx, k, e)
@@ -199,6 +200,15 @@ def run_ours(args):
     for _ in range(args.warmup):
         ctx.dgdft_alb_solve()
     torch.cuda.synchronize()
+    if args.only_stage:
+        # profiling mode: one stage of the resident workload, launched
+        # --stage-reps times on the library's stream, then exit (no bench line)
+        t_ms, nel, sbytes = ctx.dgdft_alb_time_stage(B.STAGES[args.only_stage], reps=args.stage_reps)
+        if rank == 0:
+            print(json.dumps({"stage": args.only_stage, "ms_per_launch": t_ms, "elements": nel,
+                              "launches": args.stage_reps + 1}))
+        ctx.close()
+        return
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -579,6 +589,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--scf-steps", type=int, default=4, help="timed SCF-mode steps (0: skip)")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--only-stage", default=None,
+                    choices=["xy_fwd", "z_mult", "xy_inv", "gram", "update", "rayleigh_ritz", "residual"],
+                    help="profiling mode: after the warm-up solves, launch one stage --stage-reps times and exit")
+    ap.add_argument("--tc-update", action="store_true",
+                    help="block updates on tensor cores too (bulk_kernels = 2; default: SIMT FP32)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=3)
     ap.add_argument("--simt-gram", action="store_true",
