@@ -160,13 +160,15 @@ def stage_bytes(name, e, s):
 STAGE_PER_ITER = {"xy_fwd": 3, "z_mult": 3, "xy_inv": 3, "gram": 1, "update": 2, "rayleigh_ritz": 1,
                   "residual": 1}
 
-# DRAM bytes (read + write) of one element's share of the FP32 stage's Gram
-# launch (12 pairs), from the ncu captures summarised in profiles/: the
-# compensated SIMT kernel (a 2-element launch scaled per element: the blocks
-# of every element are read once, so traffic grows with the element count);
-# the tensor-core kernel has no full-launch capture
+# DRAM bytes (read + write) of one element's share of a launch, from the ncu
+# captures summarised in profiles/ (small launches scaled per element: the
+# blocks of every element are read once, so traffic grows with the element
+# count): the compensated SIMT Gram (2 elements), the tensor-core Gram and
+# the SIMT block update with 3 inputs and 1 output (8 elements: 1,418.6 MB
+# and 734.4 MB per launch)
 GRAM48_TRAFFIC_PER_ELEMENT = 151.4e6
-GRAM_TRAFFIC_PER_ELEMENT = None
+GRAM_TRAFFIC_PER_ELEMENT = 177.3e6
+UPDATE_TRAFFIC_PER_ELEMENT = 91.8e6
 
 
 def run_ours(args):
@@ -276,6 +278,9 @@ def run_ours(args):
             roof["traffic"] = per_el * len(els) if per_el else None
             # secondary: useful flops of the 12 blocks (symmetric halves)
             roof["useful_tflops"] = sum(2.0 * e.ng * (3 * e.m) ** 2 for e in els) / (dom_ms / 1e3) / 1e12
+        if dom == "update" and not args.tc_update:
+            roof["kernel"] = "tsmm_rows (SIMT FP32 block update X' = [X W P] Y, FP32 stage)"
+            roof["traffic"] = UPDATE_TRAFFIC_PER_ELEMENT * len(els)
     # whole solve on the same basis: 20 N_g m s algorithmic bytes per
     # element-iteration (H W, Teter, Gram, updates, residual), over the
     # measured step time at the measured iteration counts
