@@ -122,6 +122,14 @@ typedef struct {
                              how failure handling is tested: the element's
                              report (and the call) then return
                              DGDFT_ETIMEOUT.  Negative gives DGDFT_EINVAL. */
+  int restrict_all;       /* restriction and orthonormalisation (Sec. II.A;
+                             Eq. orthonormal).  0 (default, the paper's
+                             procedure): the lowest J Ritz vectors are
+                             restricted to E_K and all J left singular
+                             vectors kept.  1: all m computed vectors are
+                             restricted and the J left singular vectors of
+                             the largest singular values kept.  Other
+                             values give DGDFT_EINVAL.                      */
 } dgdft_alb_config;
 
 /* Per-element outcome of dgdft_alb_solve. */

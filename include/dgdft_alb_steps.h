@@ -92,7 +92,9 @@ dgdft_status dgdft_alb_rayleigh_ritz(dgdft_alb_ctx* ctx, int stage, int n, int m
 /* Restriction to E_K and orthonormalisation (Sec. II.A; Sec. II.B): the
  * first J columns of the N_g x k block x are restricted to E_K's points and
  * replaced by the left singular vectors of that n_E x J block, scaled by
- * 1/sqrt(dV).  phi: n_E x J column-major.  J <= k. */
+ * 1/sqrt(dV); with the context's restrict_all = 1, all k columns are
+ * restricted and the J left singular vectors of the largest singular values
+ * kept.  phi: n_E x J column-major.  J <= k. */
 dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int k,
                                                int J, const double* x, double* phi,
                                                int on_device);

@@ -6,8 +6,10 @@ to zero outside E_K, which makes the ALB overlap matrix the identity
 (Eq. orthonormal).  Sec. II.B repeats this after LOBPCG.  The paper does not
 name the orthonormalisation; the reading used is the thin SVD
 Phi~ = U Sigma V^T keeping all J left singular vectors, scaled by
-1/sqrt(dV) so that sum_pts phi_i phi_j dV = delta_ij.  Results are compared
-as spans (principal angles), never column by column.
+1/sqrt(dV) so that sum_pts phi_i phi_j dV = delta_ij.  A variant restricts
+all m computed vectors and keeps the J left singular vectors of the largest
+singular values (orthonormalise_top).  Results are compared as spans
+(principal angles), never column by column.
 """
 
 from __future__ import annotations
@@ -35,6 +37,14 @@ def orthonormalise(phi_t: np.ndarray, dv: float) -> np.ndarray:
     """Left singular vectors of the (N_E x J) restricted block, L2-scaled."""
     u, _, _ = np.linalg.svd(phi_t.T, full_matrices=False)
     return u.T / np.sqrt(dv)
+
+
+def orthonormalise_top(phi_t: np.ndarray, dv: float, keep: int) -> np.ndarray:
+    """Variant of the restriction step: the (k, N_E) restricted block of all
+    k computed vectors -> the `keep` left singular vectors of the largest
+    singular values, L2-scaled (rows)."""
+    u, _, _ = np.linalg.svd(phi_t.T, full_matrices=False)  # singular values descending
+    return u[:, :keep].T / np.sqrt(dv)
 
 
 def generate_alb(el, x0: np.ndarray, **kw):

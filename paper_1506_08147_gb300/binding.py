@@ -35,7 +35,7 @@ class dgdft_alb_config(C.Structure):
                 ("cuda_stream", C.c_void_p), ("device", C.c_int), ("keep_block", C.c_int),
                 ("bulk_kernels", C.c_int), ("h_fp64_forward", C.c_int),
                 ("autotune_cache", C.c_char_p), ("precond_weights", C.c_char_p),
-                ("device_wait_polls", C.c_int)]
+                ("device_wait_polls", C.c_int), ("restrict_all", C.c_int)]
 
 
 class dgdft_solve_report(C.Structure):
@@ -138,7 +138,7 @@ class Context:
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
                  precond_weights=None, simt_gram=False, h_fp64_forward=False, device_wait_polls=0,
-                 tc_update=False):
+                 tc_update=False, restrict_all=False):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -150,6 +150,7 @@ class Context:
         cfg.keep_block = int(keep_block)
         cfg.bulk_kernels = 1 if simt_gram else (2 if tc_update else 0)
         cfg.device_wait_polls = int(device_wait_polls)
+        cfg.restrict_all = int(bool(restrict_all))
         cfg.h_fp64_forward = int(h_fp64_forward)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
         cfg.cuda_stream = stream

@@ -99,16 +99,17 @@ __global__ void ortho_gram_reduce_kernel(const OrthoTask* __restrict__ tasks, in
   }
 }
 
-// out = A Y (rows x J times J x J): a thread per row, 32 output columns per
+// out = A Y (rows x K times K x J): a thread per row, 32 output columns per
 // CTA, the Y columns staged in shared memory.
 __global__ void __launch_bounds__(256) ortho_apply_kernel(const OrthoTask* __restrict__ tasks) {
   const OrthoTask T = tasks[blockIdx.z];
   const int c0 = blockIdx.y * OT;
   if (c0 >= T.J) return;
-  extern __shared__ double ys[];  // J x OT
-  for (int idx = threadIdx.x; idx < T.J * OT; idx += blockDim.x) {
+  const int K = T.K > 0 ? T.K : T.J;
+  extern __shared__ double ys[];  // K x OT
+  for (int idx = threadIdx.x; idx < K * OT; idx += blockDim.x) {
     const int k = idx / OT, c = idx - k * OT;
-    ys[idx] = (c0 + c < T.J) ? T.y[k + (size_t)(c0 + c) * T.J] : 0.0;
+    ys[idx] = (c0 + c < T.J) ? T.y[k + (size_t)(c0 + c) * K] : 0.0;
   }
   __syncthreads();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) ortho_apply_kernel(const OrthoTask* __res
   double acc[OT];
 #pragma unroll
   for (int c = 0; c < OT; ++c) acc[c] = 0.0;
-  for (int k = 0; k < T.J; ++k) {
+  for (int k = 0; k < K; ++k) {
     const double a = T.a[r + (size_t)k * T.rows];
 #pragma unroll
     for (int c = 0; c < OT; ++c) acc[c] += a * ys[k * OT + c];
@@ -142,9 +143,9 @@ void launch_ortho_gram(const OrthoTask* d_tasks, int ntask, int max_rows, int ma
   ortho_gram_reduce_kernel<<<dim3(tiles * tiles, 1, ntask), 256, 0, st>>>(d_tasks, tiles, nchunk, partial);
 }
 
-void launch_ortho_apply(const OrthoTask* d_tasks, int ntask, int max_rows, int max_J, cudaStream_t st) {
+void launch_ortho_apply(const OrthoTask* d_tasks, int ntask, int max_rows, int max_J, int max_K, cudaStream_t st) {
   if (ntask <= 0) return;
-  const size_t smem = sizeof(double) * (size_t)max_J * OT;
+  const size_t smem = sizeof(double) * (size_t)(max_K > max_J ? max_K : max_J) * OT;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute((const void*)ortho_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   ortho_apply_kernel<<<dim3((max_rows + 255) / 256, (max_J + OT - 1) / OT, ntask), 256, smem, st>>>(d_tasks);

@@ -205,17 +205,18 @@ bool launch_tf32_gram(const Batch<float>& b, const void* d_maps, int mode, doubl
 // One product of the FP64 orthonormalisation for one element: the Gram
 // out = A^T A (J x J) or the update out = A Y (rows x J); column-major.
 struct OrthoTask {
-  const double* a;  // rows x J
-  const double* y;  // J x J (update only)
+  const double* a;  // rows x K (K = J for a Gram task: the J x J Gram of a)
+  const double* y;  // K x J (update only)
   double* out;
   int rows, J;
+  int K;            // columns of a in an update task (0: J)
 };
 constexpr int ORTHO_CHUNK = 1024;  // rows per CTA of the Gram
 size_t ortho_partial_doubles(int ntask, int max_rows, int max_J);
 void launch_ortho_gram(const OrthoTask* d_tasks, int ntask, int max_rows, int max_J, double* partial,
                        cudaStream_t st);
-// the J x 32 Y columns of a CTA are staged in shared memory (J <= 900)
-void launch_ortho_apply(const OrthoTask* d_tasks, int ntask, int max_rows, int max_J, cudaStream_t st);
+// the K x 32 Y columns of a CTA are staged in shared memory (K <= 900)
+void launch_ortho_apply(const OrthoTask* d_tasks, int ntask, int max_rows, int max_J, int max_K, cudaStream_t st);
 template <class real>
 void launch_restrict(const real* x, int ng, int nx, int ny, const int* lo, const int* hi, int J, double* out,
                      cudaStream_t st);

@@ -1124,32 +1124,38 @@ void default_x0(std::vector<double>& x, int elem) {
 }
 
 // FP64 restriction + orthonormalisation (Sec. II.A; Eq. orthonormal) of the
-// blocks xs[q] (first J[q] columns) of wave elements idx[q] into out[q]:
-// Phi~ = X restricted to E_K; G = Phi~^T Phi~; the pencil I y = th G y gives
-// Y1 with Y1^T G Y1 = I, U = Phi~ Y1 (the left singular vectors up to
-// rotation); one more pass on U restores orthonormality to rounding; scaled
-// by 1/sqrt(dV).  Everything is enqueued on the context's stream with one
+// blocks xs[q] of wave elements idx[q] into out[q]: Phi~ = the first K[q]
+// columns of X restricted to E_K; G = Phi~^T Phi~; the lowest J[q]
+// eigenpairs of the pencil I y = th G y (th = 1 / sigma^2: the largest
+// singular values) give Y1 with Y1^T G Y1 = I, U = Phi~ Y1 (those left
+// singular vectors up to rotation); one more pass on U restores
+// orthonormality to rounding; scaled by 1/sqrt(dV).  K = J is the paper's
+// procedure (all J restricted vectors kept); K = m restricts all computed
+// vectors and keeps the top J.  Everything is enqueued on the context's stream with one
 // scratch allocation and one synchronisation for all listed elements;
 // rank_ok[q] is false where the restricted block is rank deficient.
 dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vector<int>& idx,
                             const std::vector<const double*>& xs, const std::vector<int>& Js,
-                            const std::vector<double*>& out, std::vector<char>& rank_ok) {
+                            const std::vector<int>& Ks, const std::vector<double*>& out,
+                            std::vector<char>& rank_ok) {
   cudaStream_t st = ctx->stream;
   const size_t nq = idx.size();
   rank_ok.assign(nq, 0);
   if (nq == 0) return DGDFT_OK;
-  int Jmax = 1;
+  int Jmax = 1, Kmax = 1;
   size_t nemax = 1;
   for (size_t q = 0; q < nq; ++q) {
     Jmax = std::max(Jmax, Js[q]);
+    Kmax = std::max(Kmax, Ks[q]);
     nemax = std::max(nemax, (size_t)ctx->el[w.ids[idx[q]]].ne());
   }
-  const size_t jj = (size_t)Jmax * Jmax;
-  // per element: phi_t, U (ne x J), G, G2, Y1, Y2, I, diag(1..J) (J x J),
-  // theta, Rayleigh-Ritz work; then the task arrays, the Gram partials and
-  // the checks, so that each phase is one launch over all elements
-  const size_t per = 2 * nemax * Jmax + 6 * jj + Jmax + rr_work_doubles(Jmax, Jmax);
-  const size_t npart = ortho_partial_doubles((int)nq, (int)nemax, Jmax);
+  const size_t jj = (size_t)Jmax * Jmax, kk = (size_t)Kmax * Kmax;
+  // per element: phi_t (ne x K), U (ne x J), G (K x K), G2 (J x J), Y1
+  // (K x J), Y2 (J x J), I (K x K), diag(1..J) (J x J), theta, Rayleigh-Ritz
+  // work; then the task arrays, the Gram partials and the checks, so that
+  // each phase is one launch over all elements
+  const size_t per = nemax * Kmax + nemax * Jmax + 3 * kk + 3 * jj + Kmax + rr_work_doubles(Kmax, Kmax);
+  const size_t npart = ortho_partial_doubles((int)nq, (int)nemax, Kmax);
   const size_t nbytes = sizeof(double) * (per * nq + nq + npart) + 2 * nq * sizeof(RRTask) +
                         4 * nq * sizeof(OrthoTask) + (10 * nq + 32) * ALIGN;
   void* base = nullptr;
@@ -1164,15 +1170,15 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
   std::vector<Slot> sl(nq);
   for (size_t q = 0; q < nq; ++q) {
     Slot& z = sl[q];
-    z.phit = (double*)a.take(sizeof(double) * nemax * Jmax);
+    z.phit = (double*)a.take(sizeof(double) * nemax * Kmax);
     z.U = (double*)a.take(sizeof(double) * nemax * Jmax);
-    z.G = (double*)a.take(sizeof(double) * jj);
+    z.G = (double*)a.take(sizeof(double) * kk);
     z.G2 = (double*)a.take(sizeof(double) * jj);
-    z.Y1 = (double*)a.take(sizeof(double) * jj);
+    z.Y1 = (double*)a.take(sizeof(double) * kk);
     z.Y2 = (double*)a.take(sizeof(double) * jj);
-    z.mats = (double*)a.take(sizeof(double) * 2 * jj);
-    z.th = (double*)a.take(sizeof(double) * Jmax);
-    z.work = (double*)a.take(sizeof(double) * rr_work_doubles(Jmax, Jmax));
+    z.mats = (double*)a.take(sizeof(double) * (kk + jj));
+    z.th = (double*)a.take(sizeof(double) * Kmax);
+    z.work = (double*)a.take(sizeof(double) * rr_work_doubles(Kmax, Kmax));
   }
   double* chk = (double*)a.take(sizeof(double) * nq);
   double* part = (double*)a.take(sizeof(double) * npart);
@@ -1180,38 +1186,37 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
   // [0, nq): Gram of Phi~, then U = Phi~ Y1, Gram of U, out = U Y2
   OrthoTask* ot = (OrthoTask*)a.take(4 * nq * sizeof(OrthoTask));
   if (!chk || !dt || !ot || !part || !sl.back().work) return ctx->fail(DGDFT_ENOMEM, "orthonormalisation scratch");
-  std::vector<double> hm(2 * jj * nq, 0.0);
+  std::vector<double> hm((kk + jj) * nq, 0.0);
   std::vector<RRTask> ht(2 * nq);
   std::vector<OrthoTask> hot(4 * nq);
   for (size_t q = 0; q < nq; ++q) {
-    const int J = Js[q], ne = ctx->el[w.ids[idx[q]]].ne();
-    double* id = hm.data() + 2 * jj * q;
-    double* dg = id + jj;
-    for (int c = 0; c < J; ++c) {
-      id[c + (size_t)c * J] = 1.0;
-      dg[c + (size_t)c * J] = 1.0 + c;
-    }
+    const int J = Js[q], K = Ks[q], ne = ctx->el[w.ids[idx[q]]].ne();
+    double* id = hm.data() + (kk + jj) * q;  // K x K identity
+    double* dg = id + kk;                    // diag(1..J)
+    for (int c = 0; c < K; ++c) id[c + (size_t)c * K] = 1.0;
+    for (int c = 0; c < J; ++c) dg[c + (size_t)c * J] = 1.0 + c;
     for (int k = 0; k < 2; ++k) {
+      const int n = k ? J : K;
       RRTask& t = ht[k * nq + q];
       t = RRTask{};
-      t.A = sl[q].mats + (k ? jj : 0);
+      t.A = sl[q].mats + (k ? kk : 0);
       t.B = k ? sl[q].G2 : sl[q].G;
-      t.ld = J;
+      t.ld = n;
       t.mode = RR_FIXED;
-      t.n_fixed = J;
+      t.n_fixed = n;
       t.m = J;
       t.Y = k ? sl[q].Y2 : sl[q].Y1;
-      t.ldy = J;
+      t.ldy = n;
       t.theta = sl[q].th;
       t.work = sl[q].work;
       t.state = nullptr;
       t.cond_max = 1e30;
     }
-    hot[q] = OrthoTask{sl[q].phit, nullptr, sl[q].G, ne, J};
-    hot[nq + q] = OrthoTask{sl[q].phit, sl[q].Y1, sl[q].U, ne, J};
-    hot[2 * nq + q] = OrthoTask{sl[q].U, nullptr, sl[q].G2, ne, J};
-    hot[3 * nq + q] = OrthoTask{sl[q].U, sl[q].Y2, out[q], ne, J};
-    CK(cudaMemcpyAsync(sl[q].mats, id, sizeof(double) * 2 * jj, cudaMemcpyHostToDevice, st));
+    hot[q] = OrthoTask{sl[q].phit, nullptr, sl[q].G, ne, K, 0};
+    hot[nq + q] = OrthoTask{sl[q].phit, sl[q].Y1, sl[q].U, ne, J, K};
+    hot[2 * nq + q] = OrthoTask{sl[q].U, nullptr, sl[q].G2, ne, J, 0};
+    hot[3 * nq + q] = OrthoTask{sl[q].U, sl[q].Y2, out[q], ne, J, 0};
+    CK(cudaMemcpyAsync(sl[q].mats, id, sizeof(double) * (kk + jj), cudaMemcpyHostToDevice, st));
   }
   CK(cudaMemcpyAsync(dt, ht.data(), sizeof(RRTask) * ht.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ot, hot.data(), sizeof(OrthoTask) * hot.size(), cudaMemcpyHostToDevice, st));
@@ -1220,15 +1225,15 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
   for (size_t q = 0; q < nq; ++q) {
     const ElemHost& eh = ctx->el[w.ids[idx[q]]];
     const dgdft_element_desc& d = eh.d;
-    launch_restrict<double>(xs[q], eh.ng(), d.nx, d.ny, d.e_lo, d.e_hi, Js[q], sl[q].phit, st);
+    launch_restrict<double>(xs[q], eh.ng(), d.nx, d.ny, d.e_lo, d.e_hi, Ks[q], sl[q].phit, st);
   }
-  launch_ortho_gram(ot, nqi, nem, Jmax, part, st);
-  launch_rr(dt, nqi, st, Jmax, Jmax);
+  launch_ortho_gram(ot, nqi, nem, Kmax, part, st);
+  launch_rr(dt, nqi, st, Kmax, Jmax);
   // U = Phi~ Y1 and its Gram, second Rayleigh-Ritz launch
-  launch_ortho_apply(ot + nq, nqi, nem, Jmax, st);
+  launch_ortho_apply(ot + nq, nqi, nem, Jmax, Kmax, st);
   launch_ortho_gram(ot + 2 * nq, nqi, nem, Jmax, part, st);
   launch_rr(dt + nq, nqi, st, Jmax, Jmax);
-  launch_ortho_apply(ot + 3 * nq, nqi, nem, Jmax, st);
+  launch_ortho_apply(ot + 3 * nq, nqi, nem, Jmax, Jmax, st);
   for (size_t q = 0; q < nq; ++q) {
     const ElemHost& eh = ctx->el[w.ids[idx[q]]];
     launch_scale(out[q], (size_t)eh.ne() * Js[q], 1.0 / std::sqrt(eh.dv()), st);
@@ -1242,10 +1247,10 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
   return DGDFT_OK;
 }
 
-dgdft_status alb_orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, int i, const double* x, int J,
+dgdft_status alb_orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, int i, const double* x, int J, int K,
                                 double* phi_dev_out) {
   std::vector<char> ok;
-  dgdft_status s = orthonormalise(ctx, w, {i}, {x}, {J}, {phi_dev_out}, ok);
+  dgdft_status s = orthonormalise(ctx, w, {i}, {x}, {J}, {K}, {phi_dev_out}, ok);
   if (s != DGDFT_OK) return s;
   if (!ok[0]) return ctx->fail(DGDFT_ENOTCONV, "orthonormalisation: restricted block is rank deficient");
   return DGDFT_OK;
@@ -1264,7 +1269,7 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
                          const std::vector<int>& restarts, bool scf = false,
                          const std::vector<int>& bulk_err = std::vector<int>()) {
   const size_t nel = w.ids.size();
-  std::vector<int> idx(nel), Js(nel);
+  std::vector<int> idx(nel), Js(nel), Ks(nel);
   std::vector<const double*> xs(nel);
   std::vector<double*> outs(nel);
   for (size_t i = 0; i < nel; ++i) {
@@ -1277,6 +1282,7 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     }
     idx[i] = (int)i;
     Js[i] = J;
+    Ks[i] = ctx->cfg.restrict_all ? w.h[i].m : J;
     xs[i] = w.current_x((int)i);
     outs[i] = eh.d_phi;
     CK(cudaMemcpyAsync(eh.d_eig, w.h[i].theta, sizeof(double) * J, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1284,7 +1290,7 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
   }
   std::vector<char> rank_ok;
   {
-    dgdft_status so = orthonormalise(ctx, w, idx, xs, Js, outs, rank_ok);
+    dgdft_status so = orthonormalise(ctx, w, idx, xs, Js, Ks, outs, rank_ok);
     if (so != DGDFT_OK) return so;
   }
   for (size_t i = 0; i < nel; ++i) {
@@ -1598,6 +1604,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   if (cfg->precond != DGDFT_PRECOND_TETER && cfg->precond != DGDFT_PRECOND_LEARNED) return DGDFT_EINVAL;
   if (!(cfg->tol > 0.0) || cfg->maxit <= 0) return DGDFT_EINVAL;
   if (cfg->bulk_kernels < 0 || cfg->bulk_kernels > 2) return DGDFT_EINVAL;
+  if (cfg->restrict_all != 0 && cfg->restrict_all != 1) return DGDFT_EINVAL;
   for (int i = 0; i < n_elem; ++i) {
     const dgdft_element_desc& d = elems[i];
     FftPlan p;
@@ -2258,7 +2265,7 @@ dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int
   double* out = nullptr;
   CK(cudaMalloc(&out, sizeof(double) * (size_t)eh.ne() * J));
   std::unique_ptr<void, decltype(&cudaFree)> guard(out, &cudaFree);
-  if ((s = alb_orthonormalise(ctx, w, 0, xs, J, out)) != DGDFT_OK) return s;
+  if ((s = alb_orthonormalise(ctx, w, 0, xs, J, ctx->cfg.restrict_all ? k : J, out)) != DGDFT_OK) return s;
   CK(ctx_copy(ctx, phi, out, sizeof(double) * (size_t)eh.ne() * J,
                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
   return DGDFT_OK;

@@ -418,6 +418,57 @@ def test_restrict_orthonormalise(which):
     c.close()
 
 
+@pytest.mark.parametrize("which", ["small", "cfg2"])
+def test_restrict_orthonormalise_top(which):
+    """The restriction variant (restrict_all = 1): all k columns restricted,
+    the J left singular vectors of the largest singular values kept, against
+    the oracle's SVD.  The angle tolerance follows the gap between the J-th
+    and (J+1)-th singular values of the restricted block (the GPU works on
+    its Gram, sigma^2, in FP64)."""
+    el = small_kb_element() if which == "small" else cfg2_element()
+    if which == "small":
+        el.e_lo, el.e_hi = synth.element_box(el.n)
+    gen = np.random.default_rng(5)
+    k, J = (10, 6) if which == "small" else (48, 40)
+    x = OL.cholesky_qr(gen.standard_normal((k, el.ng)))
+    c = ctx_for(el, B.DGDFT_PREC_FP64, restrict_all=True)
+    phi = c.dgdft_alb_restrict_orthonormalise(0, x, J)
+    c.close()
+    phit = alb.restrict(x, el, k)
+    ref = alb.orthonormalise_top(phit, el.dv, J)
+    sv = np.linalg.svd(phit, compute_uv=False)
+    rel_gap = (sv[J - 1] ** 2 - sv[J] ** 2) / sv[0] ** 2
+    ang = alb.sin_max_angle(ref, phi)
+    print(f"{which}: sin(angle) {ang:.1e}, relative sigma^2 gap at J {rel_gap:.2e}")
+    np.testing.assert_allclose(phi @ phi.T * el.dv, np.eye(J), atol=1e-12)
+    assert ang < max(1e-11, 1e-13 / rel_gap)
+
+
+def test_solve_restrict_all_variant():
+    """A mixed-form solve of a monolayer element with restrict_all = 1: the
+    returned ALBs are orthonormal and span the oracle's top-J left singular
+    subspace of the GPU's own restricted Ritz block (all m columns)."""
+    e = cfg2_element(0)
+    c = B.Context([B.element_dict(e)], precision=B.DGDFT_PREC_MIXED, tol=1e-6, maxit=600, keep_block=True,
+                  restrict_all=True)
+    B.load_element(c, 0, e, synth.initial_block(e))
+    st, rep = c.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    phi, eig, res = c.dgdft_alb_get_basis(0)
+    x = c.dgdft_alb_get_block(0)
+    c.close()
+    assert np.max(res) <= 1e-6
+    np.testing.assert_allclose(phi @ phi.T * e.dv, np.eye(e.J), atol=1e-12)
+    phit = alb.restrict(x, e, e.m)
+    ref = alb.orthonormalise_top(phit, e.dv, e.J)
+    sv = np.linalg.svd(phit, compute_uv=False)
+    rel_gap = (sv[e.J - 1] ** 2 - sv[e.J] ** 2) / sv[0] ** 2
+    ang = alb.sin_max_angle(ref, phi)
+    print(f"restrict_all solve: sin(angle) to the oracle's top-J subspace {ang:.1e}, "
+          f"relative sigma^2 gap at J {rel_gap:.2e}")
+    assert ang < max(1e-11, 1e-13 / rel_gap)
+
+
 # -------------------------------------------------------------- full solves
 
 def _gap_ok(gap, tol, bound):

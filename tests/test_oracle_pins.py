@@ -339,3 +339,22 @@ def test_restriction_whole_box_reproduces_span():
     phi = alb.orthonormalise(alb.restrict(x, el), el.dv)
     assert alb.sin_max_angle(x, phi) < 1e-13
     np.testing.assert_allclose(phi @ phi.T * el.dv, np.eye(5), atol=1e-12)
+
+
+def test_orthonormalise_top_keeps_the_largest_singular_directions():
+    """The restriction variant (all k vectors restricted, the J left singular
+    vectors of the largest singular values kept), on a block built from
+    known singular vectors and values: the kept rows span exactly the first
+    J of them, are orthonormal in the dV inner product, and with J = k span
+    the same space as the paper's procedure."""
+    from oracle import alb
+    gen = np.random.default_rng(3)
+    ne, k, J, dv = 500, 12, 8, 0.3
+    u0, _ = np.linalg.qr(gen.standard_normal((ne, k)))
+    v0, _ = np.linalg.qr(gen.standard_normal((k, k)))
+    s = np.geomspace(10.0, 0.01, k)
+    phit = ((u0 * s) @ v0.T).T  # (k, ne): rows are the restricted vectors
+    phi = alb.orthonormalise_top(phit, dv, J)
+    np.testing.assert_allclose(phi @ phi.T * dv, np.eye(J), atol=1e-12)
+    assert alb.sin_max_angle(u0[:, :J].T, phi) < 1e-10
+    assert alb.sin_max_angle(alb.orthonormalise(phit, dv), alb.orthonormalise_top(phit, dv, k)) < 1e-10
