@@ -191,7 +191,7 @@ def run_ours(args):
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
                     stream=stream.cuda_stream, simt_gram=args.simt_gram, h_fp64_forward=args.fwd64,
-                    tc_update=args.tc_update)
+                    tc_update=args.tc_update, autotune_cache=args.autotune_cache or None)
     dev_x0 = []
     for k, e in enumerate(els):
         B.load_element(ctx, k, e)
@@ -597,6 +597,8 @@ def main():
     ap.add_argument("--only-stage", default=None,
                     choices=["xy_fwd", "z_mult", "xy_inv", "gram", "update", "rayleigh_ritz", "residual"],
                     help="profiling mode: after the warm-up solves, launch one stage --stage-reps times and exit")
+    ap.add_argument("--autotune-cache", default=os.path.join(tempfile.gettempdir(), "dgdft_alb_autotune.json"),
+                    help="autotuner cache (tuned when the wave is built, in the warm-up); '' to disable")
     ap.add_argument("--tc-update", action="store_true",
                     help="block updates on tensor cores too (bulk_kernels = 2; default: SIMT FP32)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

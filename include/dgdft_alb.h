@@ -114,7 +114,16 @@ typedef struct {
                              stage's residual floor near 2e-6 Ha): 0 never;
                              1 every apply (~4x slower passes); 2 only H X'
                              once the median residual is below 1e-5        */
-  const char* autotune_cache;   /* optional JSON path; NULL = none            */
+  const char* autotune_cache;   /* optional path of the autotuner's JSON cache
+                                   (a flat object of "key": integer launch
+                                   shapes per batch shape), read when a wave is
+                                   built; missing keys are tuned then (timed on
+                                   the wave's own blocks) and written back.
+                                   Tuned today: the FP32 block update's
+                                   128-row tiles per CTA (2, 4, 8 or 16), a
+                                   launch shape that changes no result.  NULL
+                                   = no tuning (defaults).  The string is
+                                   copied at create.                         */
   const char* precond_weights;  /* learned preconditioner weights; NULL = none */
   int device_wait_polls;  /* bound on every device-side wait of the tensor-core
                              kernels, in polls: 0 (default) about a second;

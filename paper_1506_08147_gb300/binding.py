@@ -138,7 +138,7 @@ class Context:
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
                  precond_weights=None, simt_gram=False, h_fp64_forward=False, device_wait_polls=0,
-                 tc_update=False, restrict_all=False):
+                 tc_update=False, restrict_all=False, autotune_cache=None):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -156,6 +156,8 @@ class Context:
         cfg.cuda_stream = stream
         self._weights = precond_weights.encode() if precond_weights else None
         cfg.precond_weights = self._weights
+        self._tune = str(autotune_cache).encode() if autotune_cache else None
+        cfg.autotune_cache = self._tune
         self.cfg = cfg
         n = len(elems)
         arr = (dgdft_element_desc * n)()

@@ -1102,10 +1102,11 @@ void launch_tsmm(const Batch<real>& b, const TsmmJob<real>& job, cudaStream_t st
     const size_t smem = tsmm_rows_smem(job.nin, nc);
     if (smem <= 160 * 1024) {
       const int rows = job.rows > 0 ? job.rows : s.max_ng;
-      // eight 128-row tiles per CTA: the Y staging (ktot x 48 coefficients
-      // per CTA) is amortised; 1.87 ms against 2.24 ms with two tiles on the
-      // 36-element monolayer workload, the grid still ~7 waves of the SMs
-      const int gx = std::max(1, (rows + 8 * TS_TR - 1) / (8 * TS_TR));
+      // s.tsmm_tiles 128-row tiles per CTA (default 8, or the autotuner's
+      // choice): the Y staging (ktot x 48 coefficients per CTA) is amortised;
+      // 1.87 ms against 2.24 ms with two tiles on the 36-element monolayer
+      const int tpc = s.tsmm_tiles > 0 ? s.tsmm_tiles : 8;
+      const int gx = std::max(1, (rows + tpc * TS_TR - 1) / (tpc * TS_TR));
       tsmm_rows_kernel<<<dim3(gx, (nc + TS_CT - 1) / TS_CT, s.nel), TS_THREADS, smem, st>>>(b.d_elems, job);
       return;
     }

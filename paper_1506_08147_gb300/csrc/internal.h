@@ -38,6 +38,10 @@ struct BatchShape {
   // FP64 wave of the mixed form: Gram products in double-float arithmetic
   // (FP32 pairs) instead of on the FP64 pipe
   bool dfloat = false;
+  // 128-row tiles per CTA of the FP32 block update (tsmm_rows_kernel); a
+  // launch shape only (each output's arithmetic is the same), tuned per
+  // batch shape when the context has an autotune cache
+  int tsmm_tiles = 8;
 };
 
 template <class real> struct Batch {

@@ -13,7 +13,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <memory>
+#include <sstream>
 #include <random>
 #include <string>
 #include <type_traits>
@@ -138,6 +141,48 @@ struct dgdft_alb_ctx {
   std::vector<int> cache_proj_version;
   ConvNet* net = nullptr;  // learned preconditioner, created on first use
   int wait_polls = 0;      // bounded device waits: polls before giving up (0: default)
+  // autotuner: launch shapes per batch-shape key, read from and written to
+  // the JSON file named by the config (empty path: no tuning, defaults)
+  std::string tune_path;
+  std::map<std::string, int> tune;
+  bool tune_loaded = false;
+  void tune_load() {
+    if (tune_loaded || tune_path.empty()) return;
+    tune_loaded = true;
+    std::ifstream f(tune_path);
+    if (!f) return;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string t = ss.str();
+    // a flat object of "key": integer pairs
+    size_t p = 0;
+    while ((p = t.find('"', p)) != std::string::npos) {
+      const size_t q = t.find('"', p + 1);
+      if (q == std::string::npos) break;
+      const std::string key = t.substr(p + 1, q - p - 1);
+      size_t c = t.find_first_not_of(" \t\r\n", q + 1);
+      if (c == std::string::npos || t[c] != ':') {
+        p = q + 1;
+        continue;
+      }
+      char* end = nullptr;
+      const long v = std::strtol(t.c_str() + c + 1, &end, 10);
+      if (end != t.c_str() + c + 1) tune[key] = (int)v;
+      p = (size_t)(end - t.c_str());
+    }
+  }
+  void tune_save() const {
+    if (tune_path.empty()) return;
+    std::ofstream f(tune_path, std::ios::trunc);
+    if (!f) return;
+    f << "{";
+    bool first = true;
+    for (const auto& kv : tune) {
+      f << (first ? "\n" : ",\n") << "  \"" << kv.first << "\": " << kv.second;
+      first = false;
+    }
+    f << "\n}\n";
+  }
   void drop_cache() {
     if (cache && cache_free) cache_free(cache);
     cache = nullptr;
@@ -439,9 +484,81 @@ template <class real> struct Wave {
     CK(ctx_copy(ctx, d_rr_lob, rr_lob.data(), sizeof(RRTask) * nel, cudaMemcpyHostToDevice));
     batch.d_elems = d_elems;
     batch.s = s;
+    if constexpr (std::is_same<real, float>::value) {
+      dgdft_status ts = autotune_update();
+      if (ts != DGDFT_OK) return ts;
+    }
     dgdft_status ls = setup_learned();
     if (ls != DGDFT_OK) return ls;
     return setup_split();
+  }
+
+  // Autotuner: the FP32 block update's 128-row tiles per CTA for this batch
+  // shape, from the context's cache or, when missing, timed here on the
+  // wave's own blocks (every element marked active with P for the timing,
+  // the state words restored after; the output is the next X buffer, scratch
+  // before the first iteration).  The choice changes no result.
+  dgdft_status autotune_update() {
+    if (ctx->tune_path.empty()) return DGDFT_OK;
+    ctx->tune_load();
+    const BatchShape& s = batch.s;
+    const std::string key = "tsmm_rows_tiles nel=" + std::to_string(s.nel) + " m=" + std::to_string(s.max_m) +
+                            " ng=" + std::to_string(s.max_ng);
+    auto it = ctx->tune.find(key);
+    if (it != ctx->tune.end() && it->second > 0) {
+      batch.s.tsmm_tiles = it->second;
+      return DGDFT_OK;
+    }
+    const int nel = s.nel;
+    std::vector<int> saved((size_t)nel * STATE_WORDS), on((size_t)nel * STATE_WORDS, 0);
+    for (int i = 0; i < nel; ++i)
+      CK(ctx_copy(ctx, &saved[(size_t)i * STATE_WORDS], h[i].state, sizeof(int) * STATE_WORDS,
+                  cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nel; ++i) {
+      on[(size_t)i * STATE_WORDS + ST_ACTIVE] = 1;
+      on[(size_t)i * STATE_WORDS + ST_HAS_P] = 1;
+      CK(ctx_copy(ctx, h[i].state, &on[(size_t)i * STATE_WORDS], sizeof(int) * STATE_WORDS,
+                  cudaMemcpyHostToDevice));
+    }
+    TsmmJob<real> t;
+    t.nin = 3;
+    t.in[0] = bref<real>(BX);
+    t.in[1] = bref<real>(BW);
+    t.in[2] = bref<real>(BP);
+    t.yrow[1] = 1;
+    t.yrow[2] = 2;
+    t.needs_p[2] = 1;
+    t.out = bref<real>(BX, 1);
+    cudaStream_t st = ctx->stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = 8;
+    float best_ms = 1e30f;
+    for (int tiles : {2, 4, 8, 16}) {
+      batch.s.tsmm_tiles = tiles;
+      launch_tsmm<real>(batch, t, st);
+      CK(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) launch_tsmm<real>(batch, t, st);
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = tiles;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    for (int i = 0; i < nel; ++i)
+      CK(ctx_copy(ctx, h[i].state, &saved[(size_t)i * STATE_WORDS], sizeof(int) * STATE_WORDS,
+                  cudaMemcpyHostToDevice));
+    batch.s.tsmm_tiles = best;
+    ctx->tune[key] = best;
+    ctx->tune_save();
+    return DGDFT_OK;
   }
 
   template <class T> T* take(size_t count) { return (T*)arena.take(sizeof(T) * std::max<size_t>(count, 1)); }
@@ -1627,6 +1744,9 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   }
   std::unique_ptr<dgdft_alb_ctx> ctx(new dgdft_alb_ctx());
   ctx->cfg = *cfg;
+  // the caller's strings need not outlive the call
+  if (cfg->autotune_cache) ctx->tune_path = cfg->autotune_cache;
+  ctx->cfg.autotune_cache = nullptr;
   if (ctx->cfg.check_every < 1) ctx->cfg.check_every = 1;
   if (cfg->device_wait_polls < 0) return DGDFT_EINVAL;
   ctx->wait_polls = cfg->device_wait_polls;
