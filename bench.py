@@ -97,6 +97,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def workload_config3(limit=None):
+    """The uneven batch: 128 standalone boxes (four grid shapes, m from 24 to
+    120), or its first `limit` elements."""
+    import synth
+    els = synth.config3(elems=list(range(128 if limit is None else limit)))
+    return els, [synth.initial_block(e) for e in els]
+
+
 def workload(limit=None, rank=0, world=1):
     """This rank's elements.  One rank: the 36 elements of the monolayer.  N
     ranks (weak scaling): N monolayer replicas -- replica 0 is that
@@ -186,7 +194,13 @@ def run_ours(args):
         dist.init_process_group("nccl")
     import __graft_entry__ as entry
     entry.build()
-    els, x0 = workload(args.elements, rank, world)
+    if args.config == 3:
+        # the uneven batch: its own line, without the comparators that need
+        # the monolayer (plain FP64 solve, oracle sample, e2e, SCF steps)
+        els, x0 = workload_config3(args.elements)
+        args.plain, args.cpu_seconds, args.e2e_steps, args.scf_steps = False, 0, 0, 0
+    else:
+        els, x0 = workload(args.elements, rank, world)
     stream = torch.cuda.current_stream()
     descs = [B.element_dict(e) for e in els]
     ctx = B.Context(descs, precision=B.DGDFT_PREC_MIXED, tol=TOL, maxit=args.maxit,
@@ -422,8 +436,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded puckered monolayer, Z=5 Gaussian pseudopotentials)",
-        "config": {"workload": "36 extended elements of the 576-atom monolayer, 48x64x40 grid, "
-                               "m=48 computed, J=40 kept, tol 1e-6 Ha, random start",
+        "config": {"workload": ("36 extended elements of the 576-atom monolayer, 48x64x40 grid, "
+                                "m=48 computed, J=40 kept, tol 1e-6 Ha, random start") if args.config == 2 else
+                               (f"{len(els)} uneven standalone boxes (grids 24^3 to 48x48x64, m 24 to 120, "
+                                "J 16 to 96), tol 1e-6 Ha, random start"),
                    "elements": len(els), "precision": "mixed: FP32 bulk + FP64 RR/refinement/SVD",
                    "l2": "working set ~10 GB >> 129 MB L2 (no flush needed)",
                    "parallelism": ("elements batched on 1 GPU" if world == 1 else
@@ -589,6 +605,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--elements", type=int, default=None, help="first k elements only (debug)")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3],
+                    help="2: the 36-element monolayer (the metric's workload); 3: the 128-element uneven batch")
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--stage-reps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=2)
