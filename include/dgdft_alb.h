@@ -66,8 +66,9 @@ enum {
                            or compensated SIMT (see bulk_kernels), the
                            Rayleigh-Ritz in double-float, ~2^-46), then the
                            FP64 check and FP64-accurate iterations to the
-                           tolerance (FP64 FFTs and Rayleigh-Ritz,
-                           double-float Gram and update products)          */
+                           tolerance (FP64 storage and Rayleigh-Ritz,
+                           double-float FFT passes, Gram and update
+                           products, ~2^-46 relative)                      */
 };
 
 enum {

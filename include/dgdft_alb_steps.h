@@ -20,10 +20,14 @@ extern "C" {
 
 /* H applied to k vectors (Sec. II.B, operation 1; Eq. localproblem):
  * hx = -1/2 Lap x + V_eff x + sum_p gamma_p v_p (v_p^T x).  The Laplacian is
- * spectral over every G of the FFT grid, Nyquist plane included.
+ * spectral over every G of the FFT grid, Nyquist plane included.  stage
+ * picks the solver stage whose kernels run: 0 the bulk stage (FP32 in
+ * DGDFT_PREC_MIXED), 1 the FP64 stage (in DGDFT_PREC_MIXED FP64 vectors with
+ * the transforms in double-float arithmetic, ~2^-46 per operation; plain
+ * FP64 in DGDFT_PREC_FP64, where both stages are the same).
  * x, hx: N_g x k column-major.  1 <= k <= n_compute. */
-dgdft_status dgdft_alb_apply_h(dgdft_alb_ctx* ctx, int elem, int k, const double* x,
-                               double* hx, int on_device);
+dgdft_status dgdft_alb_apply_h(dgdft_alb_ctx* ctx, int elem, int stage, int k, const double* x, double* hx,
+                               int on_device);
 
 /* Teter-Payne-Allan preconditioner (Sec. II.B, operation 5), per column:
  * w_i = F^-1 [ K((|G|^2/2) / t_kin[i]) F r_i ] with

@@ -58,7 +58,7 @@ _SIGS = {
     "dgdft_alb_get_basis": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_last_error": (C.c_char_p, [_P]),
     "dgdft_alb_destroy": (None, [_P]),
-    "dgdft_alb_apply_h": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "dgdft_alb_apply_h": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dgdft_alb_apply_teter": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P]),
@@ -329,10 +329,10 @@ class Context:
         return r, t, sig, cg
 
     # step entry points -------------------------------------------------
-    def dgdft_alb_apply_h(self, elem, x):
+    def dgdft_alb_apply_h(self, elem, x, stage=0):
         x = np.ascontiguousarray(x, np.float64)
         out = np.zeros_like(x)
-        self._check(self.lib.dgdft_alb_apply_h(self.h, elem, x.shape[0], _ptr(x)[0], _ptr(out)[0], 0),
+        self._check(self.lib.dgdft_alb_apply_h(self.h, elem, int(stage), x.shape[0], _ptr(x)[0], _ptr(out)[0], 0),
                     "apply_h")
         return out
 

@@ -14,12 +14,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dgdft {
 
 template <class real> struct cplx_of;
 template <> struct cplx_of<double> { using type = double2; };
 template <> struct cplx_of<float> { using type = float2; };
 template <class real> using cplx_t = typename cplx_of<real>::type;
+struct dff;  // double-float scalar (dfloat.cuh)
 
 template <class C> __host__ __device__ __forceinline__ C cmake(decltype(C::x) a, decltype(C::x) b) {
   C c; c.x = a; c.y = b; return c;
@@ -75,6 +78,9 @@ template <class real> struct ElemDev {
   // in working precision and in FP64 (the same table for FP64 waves)
   const C* tw[4];
   const double2* tw64[4];
+  // the FP64 tables as FP32 pairs (hi, lo of re, hi, lo of im), FP64 waves
+  // only: for FFT passes in double-float arithmetic
+  const float4* twdf[4];
   const double* gx2;        // (2 pi kx / Lx)^2 / 2, kx = 0..nh
   const double* gy2;        // (2 pi f_y / Ly)^2 / 2 over y index (|f| <= ny/2)
   const double* gz2;
@@ -150,7 +156,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Twiddle table of axis `a` in the transform's compute precision TC.
 template <class TC, class real>
 __device__ __forceinline__ const cplx_t<TC>* twp(const ElemDev<real>& e, int a) {
-  if constexpr (sizeof(TC) == sizeof(double)) {
+  if constexpr (std::is_same<TC, dff>::value) {
+    return reinterpret_cast<const cplx_t<TC>*>(e.twdf[a]);
+  } else if constexpr (sizeof(TC) == sizeof(double)) {
     return e.tw64[a];
   } else {
     return reinterpret_cast<const cplx_t<TC>*>(e.tw[a]);

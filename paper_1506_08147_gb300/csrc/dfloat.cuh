@@ -10,6 +10,8 @@
 // error analyses of Cholesky and Householder reductions assume.
 #pragma once
 
+#include "common.cuh"
+
 namespace dgdft {
 
 struct dfl {
@@ -95,5 +97,38 @@ __device__ __forceinline__ dfl dfl_warp_sum(dfl v) {
   }
   return {__shfl_sync(0xffffffffu, v.h, 0), __shfl_sync(0xffffffffu, v.l, 0)};
 }
+
+// The same arithmetic as a scalar type with conversions and operators, for
+// kernels templated on their arithmetic type (the FFT passes): converts from
+// FP64 on construction and back to FP64 explicitly.
+struct dff {
+  float h, l;
+  dff() = default;
+  __host__ __device__ dff(double x) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+  }
+  __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
+};
+__device__ __forceinline__ dfl as_dfl(dff a) { return {a.h, a.l}; }
+__device__ __forceinline__ dff as_dff(dfl a) {
+  dff r;
+  r.h = a.h;
+  r.l = a.l;
+  return r;
+}
+__device__ __forceinline__ dff operator+(dff a, dff b) { return as_dff(dfl_add(as_dfl(a), as_dfl(b))); }
+__device__ __forceinline__ dff operator-(dff a, dff b) { return as_dff(dfl_sub(as_dfl(a), as_dfl(b))); }
+__device__ __forceinline__ dff operator*(dff a, dff b) { return as_dff(dfl_mul(as_dfl(a), as_dfl(b))); }
+__device__ __forceinline__ dff operator-(dff a) { return as_dff(dfl_neg(as_dfl(a))); }
+__device__ __forceinline__ dff& operator+=(dff& a, dff b) { return a = a + b; }
+__device__ __forceinline__ dff& operator-=(dff& a, dff b) { return a = a - b; }
+__device__ __forceinline__ dff& operator*=(dff& a, dff b) { return a = a * b; }
+
+// complex double-float: the same 16 bytes as double2
+struct __align__(16) dffc {
+  dff x, y;
+};
+template <> struct cplx_of<dff> { using type = dffc; };
 
 }  // namespace dgdft

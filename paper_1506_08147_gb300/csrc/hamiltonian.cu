@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "fft.cuh"
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace dgdft {
@@ -335,12 +336,30 @@ void apply_h_prec(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncol
   launch_xy_inv<real, F, real, XI_HAMILTONIAN>(b, dst, src, ncols, 0, st);
 }
 
+// FP64 vectors with the transforms in double-float arithmetic (FP32 pairs,
+// ~2^-46 relative per operation): the FP64 waves of the mixed form, whose
+// FP64 FFT passes would run on the FP64 pipe (1/55 of the FP32 rate here).
+void apply_h_dfloat(const Batch<double>& b, BRef<double> src, BRef<double> dst, int ncols, cudaStream_t st) {
+  const BatchShape& s = b.s;
+  if (s.max_nproj > 0)
+    proj_coef_kernel<double><<<dim3(s.max_nproj, 1, s.nel), 128, 0, st>>>(b.d_elems, src, ncols);
+  launch_xy_fwd<double, dff, dff>(b, src, ncols, 0, st);
+  launch_z_mult<double, dff, ZM_KINETIC>(b, ncols, nullptr, 0, st);
+  launch_xy_inv<double, dff, dff, XI_HAMILTONIAN>(b, dst, src, ncols, 0, st);
+}
+
 // fwd64: run the forward transform (passes 1-2) in FP64 with an FP64
 // intermediate even for FP32 vectors (the rounding of the forward transform
 // is what |G|^2/2 amplifies); pass 3 stays in the working precision.
 template <class real>
 void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st,
                     bool fwd64) {
+  if constexpr (std::is_same<real, double>::value) {
+    if (b.s.dfloat) {
+      apply_h_dfloat(b, src, dst, ncols, st);
+      return;
+    }
+  }
   if (fwd64)
     apply_h_prec<real, double>(b, src, dst, ncols, st);
   else
@@ -353,6 +372,14 @@ template <class real>
 void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const double* tkin_override,
                   int ncols, cudaStream_t st, int only_teter_elems) {
   const int f = only_teter_elems;
+  if constexpr (std::is_same<real, double>::value) {
+    if (b.s.dfloat) {
+      launch_xy_fwd<double, dff, dff>(b, src, ncols, f, st);
+      launch_z_mult<double, dff, ZM_TETER>(b, ncols, tkin_override, f, st);
+      launch_xy_inv<double, dff, dff, XI_PLAIN>(b, dst, src, ncols, f, st);
+      return;
+    }
+  }
   launch_xy_fwd<real, real, real>(b, src, ncols, f, st);
   launch_z_mult<real, real, ZM_TETER>(b, ncols, tkin_override, f, st);
   launch_xy_inv<real, real, real, XI_PLAIN>(b, dst, src, ncols, f, st);
@@ -393,10 +420,26 @@ void opt_in_dynamic_smem(const void* kernel) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
+static void opt_in_smem_dfloat() {
+  opt_in_dynamic_smem((const void*)xy_fwd_kernel<double, dff, dff, 24, 64>);
+  opt_in_dynamic_smem((const void*)xy_fwd_kernel<double, dff, dff>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<double, dff, dff, XI_HAMILTONIAN, 24, 64>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<double, dff, dff, XI_HAMILTONIAN>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<double, dff, dff, XI_PLAIN, 24, 64>);
+  opt_in_dynamic_smem((const void*)xy_inv_kernel<double, dff, dff, XI_PLAIN>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_KINETIC, 40>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_KINETIC, 48>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_KINETIC>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_TETER, 40>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_TETER, 48>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_TETER>);
+}
+
 void init_hamiltonian_kernels() {
   init_mono_kernels();
   opt_in_smem_t<double>();
   opt_in_smem_t<float>();
+  opt_in_smem_dfloat();
 }
 
 // One pass of the H apply in isolation (0: xy forward, 1: z multiply,

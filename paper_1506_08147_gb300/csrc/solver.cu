@@ -600,6 +600,17 @@ template <class real> struct Wave {
       E.tw[axis] = dp;
       if (sizeof(real) == sizeof(double)) {
         E.tw64[axis] = reinterpret_cast<const double2*>(dp);
+        // FP32-pair copy for double-float FFT passes (fits the FP64 table
+        // budget that FP64 waves do not use)
+        std::vector<float4> tf(count);
+        for (int q = 0; q < count; ++q) {
+          const double re = t[2 * q], im = t[2 * q + 1];
+          const float rh = (float)re, ih = (float)im;
+          tf[q] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+        }
+        float4* fp = take<float4>(count);
+        if (!fp || put(fp, tf.data(), count) != DGDFT_OK) return false;
+        E.twdf[axis] = fp;
       } else {
         std::vector<double2> td(count);
         for (int q = 0; q < count; ++q) td[q] = make_double2(t[2 * q], t[2 * q + 1]);
@@ -2277,11 +2288,12 @@ dgdft_status dgdft_alb_time_stage(dgdft_alb_ctx* ctx, int stage, int reps, doubl
   return time_stage_t<double>(ctx, *wp->w64, stage, reps, ms_per_launch);
 }
 
-dgdft_status dgdft_alb_apply_h(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* hx, int on_device) {
+dgdft_status dgdft_alb_apply_h(dgdft_alb_ctx* ctx, int elem, int stage, int k, const double* x, double* hx,
+                               int on_device) {
   if (!ctx || !x || !hx || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
-  if (k < 1 || k > ctx->el[elem].d.n_compute) return DGDFT_EINVAL;
-  return ctx->cfg.precision == DGDFT_PREC_FP64 ? apply_h_t<double>(ctx, elem, k, x, hx, on_device)
-                                                : apply_h_t<float>(ctx, elem, k, x, hx, on_device);
+  if (k < 1 || k > ctx->el[elem].d.n_compute || (stage != 0 && stage != 1)) return DGDFT_EINVAL;
+  return (ctx->cfg.precision == DGDFT_PREC_FP64 || stage == 1) ? apply_h_t<double>(ctx, elem, k, x, hx, on_device)
+                                                               : apply_h_t<float>(ctx, elem, k, x, hx, on_device);
 }
 
 dgdft_status dgdft_alb_apply_teter(dgdft_alb_ctx* ctx, int elem, int k, const double* r, const double* t_kin,
