@@ -15,7 +15,10 @@ What it computes, per extended element Q_K (Sec. II.A, Eq. localproblem):
   * restriction of the lowest J eigenvectors to E_K and their
     orthonormalisation by SVD (``alb``; Sec. II.A, Sec. II.B);
   * the learned preconditioner's 3-D convolutional network, forward and
-    backward (``convnet``).
+    backward (``convnet``);
+  * the DG Hamiltonian assembled from the ALBs (Eq. DGHamiltonian): LGL
+    quadrature and differentiation, trigonometric interpolation from Q_K's
+    grid, the volume, KB and interior-penalty face blocks (``dg``).
 
 Pins (tests/test_oracle_*.py) tie every function to closed forms, brute-force
 diagonalisation and invariants rather than to itself.  Functions whose
