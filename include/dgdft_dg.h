@@ -1,0 +1,129 @@
+/* DG Hamiltonian assembly from the adaptive local basis functions.
+ *
+ * Eq. DGHamiltonian defines H^DG_{K',j';K,j} in three groups:
+ *   (1) 1/2 <grad phi_{K,j'}, grad phi_{K,j}> + <phi_{K,j'}, V_eff phi_{K,j}>
+ *       over E_K (diagonal blocks);
+ *   (2) sum_p gamma_p <phi_{K',j'}, b_p> <b_p, phi_{K,j}> (the blocks of every
+ *       pair of elements a projector b_p touches);
+ *   (3) -1/2 <[phi'], {grad phi}> - 1/2 <{grad phi'}, [phi]> + alpha <[phi'], [phi]>
+ *       over the faces shared by neighbouring elements.
+ * Sec. II.B ("Construction of the DG Hamiltonian") evaluates every integral by
+ * Legendre-Gauss-Lobatto (LGL) quadrature on each element and the gradients by
+ * LGL differentiation matrices; Sec. III uses twice as many LGL points per
+ * direction as the uniform grid has.  The K-th block row is assembled from E_K
+ * and its neighbours, as in the paper's per-element ownership.
+ *
+ * Readings (the paper is silent on them):
+ *   - the ALB functions of E_K are the real trigonometric interpolants over the
+ *     periodic box Q_K of J columns given on Q_K's uniform grid (after an ALB
+ *     solve: the lowest J Ritz vectors), restricted to E_K;
+ *   - Eq. orthonormal is imposed under the LGL quadrature by the Cholesky factor
+ *     of the mass matrix, M = L L^T, phi = phi~ L^-T (unique given the
+ *     columns), before any integral of H^DG is evaluated;
+ *   - on the face between E_a and its +e_d neighbour E_b the jump is
+ *     (u_a - u_b) e_d and the average of the normal derivative
+ *     (d_d u_a + d_d u_b) / 2; with one element along d the face joins the
+ *     element to itself across the periodic boundary.
+ *
+ * Arithmetic: FP64.  All compute runs on the GPU on the stream of the
+ * configuration; there is no CPU path.
+ */
+#ifndef DGDFT_DG_H
+#define DGDFT_DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "dgdft_alb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgdft_dg dgdft_dg;
+
+typedef struct {
+  int ne[3];          /* elements per direction of the periodic cell;
+                         element K = ix + ne[0] (iy + ne[1] iz)            */
+  double cell[3];     /* periodic cell (bohr)                              */
+  int q_span[3];      /* elements per direction spanned by Q_K: 3, or 1 when
+                         ne = 1 (Q_K then spans the cell along that axis)   */
+  int nq[3];          /* Q_K's uniform grid (x, y, z), each >= 2            */
+  int nl[3];          /* LGL points per direction on E_K, 2..128           */
+  int J;              /* basis functions per element, 1..128               */
+  double alpha;       /* interior-penalty parameter of Eq. DGvar, >= 0      */
+  int n_proj;         /* projectors of the system (ids 0..n_proj-1)         */
+  void* cuda_stream;  /* cudaStream_t to run on; NULL = the legacy stream   */
+  int device;         /* CUDA device ordinal                               */
+  size_t hbm_cap_bytes; /* bound on the per-batch scratch (0 = a quarter of
+                           the free device memory); elements are processed
+                           in batches that fit it                          */
+} dgdft_dg_config;
+
+/* Validate the configuration, build the LGL, differentiation and
+ * interpolation tables and allocate the per-element storage.
+ * DGDFT_EINVAL on an invalid field, DGDFT_ECUDA without a usable sm_103
+ * device, DGDFT_ENOMEM when the storage does not fit.  Whenever out and cfg
+ * are non-NULL, *out receives a handle, on failure too (its
+ * dgdft_dg_last_error says why); the caller frees it with dgdft_dg_destroy. */
+dgdft_status dgdft_dg_create(const dgdft_dg_config* cfg, dgdft_dg** out);
+
+/* The LGL nodes of element `elem` in cell coordinates (bohr): x[nl[0]],
+ * y[nl[1]], z[nl[2]] (host arrays, ascending), so the caller can evaluate
+ * V_eff and the projectors there.  DGDFT_EINVAL on a bad element.          */
+dgdft_status dgdft_dg_lgl_points(dgdft_dg* dg, int elem, double* x, double* y, double* z);
+
+/* V_eff of element `elem` at its LGL points: n = nl[0] nl[1] nl[2] values,
+ * x fastest (host or device pointer per on_device; copied).                */
+dgdft_status dgdft_dg_set_potential(dgdft_dg* dg, int elem, const double* v, int on_device);
+
+/* Projection weights gamma[n_proj] (host, copied).                          */
+dgdft_status dgdft_dg_set_gamma(dgdft_dg* dg, const double* gamma);
+
+/* The projectors touching element `elem`, sampled at its LGL points (host
+ * arrays, copied): n_p projectors with global ids pid[n_p] (distinct, in
+ * [0, n_proj)), CSR row_ptr[n_p + 1] over idx (flat LGL index, x fastest)
+ * and val (b_p at that point, no quadrature weight).  Replaces any earlier
+ * set for the element.  DGDFT_EINVAL on an id or index out of range.        */
+dgdft_status dgdft_dg_set_projectors(dgdft_dg* dg, int elem, int n_p, const int* pid,
+                                     const int64_t* row_ptr, const int* idx, const double* val);
+
+/* Assemble every block row of H^DG.  z[K] (K = 0 .. n_elem-1) points to the
+ * J columns of element K on Q_K's uniform grid: nq[0] nq[1] nq[2] x J,
+ * column-major, x fastest (device pointers when on_device, else host; read
+ * only, not retained).  Results stay on the device until dgdft_dg_get_row.
+ * DGDFT_EINVAL on a NULL pointer; DGDFT_ENOTCONV when a mass matrix is not
+ * positive definite (columns linearly dependent on E_K; the element is named
+ * in dgdft_dg_last_error); DGDFT_ECUDA on a CUDA error.                     */
+dgdft_status dgdft_dg_assemble(dgdft_dg* dg, const double* const* z, int on_device);
+
+/* The distinct elements of the 3 x 3 x 3 periodic neighbourhood of `elem`,
+ * ascending: nb[*n_nb] (host, room for 27).  Block s of the row couples elem
+ * with nb[s].                                                             */
+dgdft_status dgdft_dg_neighbours(dgdft_dg* dg, int elem, int* nb, int* n_nb);
+
+/* Block row `elem` after dgdft_dg_assemble: n_nb blocks of J x J, block s
+ * holding H_{elem, nb[s]} row-major (row i = basis function i of elem,
+ * column j = basis function j of nb[s]).  DGDFT_ESTATE before assembly.      */
+dgdft_status dgdft_dg_get_row(dgdft_dg* dg, int elem, double* blocks, int on_device);
+
+/* The orthonormal ALBs of element `elem` on its LGL grid from its columns z
+ * (as in assemble, z_on_device): phi (n_LGL x J column-major, x fastest).   */
+dgdft_status dgdft_dg_lgl_basis(dgdft_dg* dg, int elem, const double* z, int z_on_device, double* phi,
+                                int on_device);
+
+/* Kernel time of the last assembly per stage (CUDA events on the stream):
+ * ms[0] interpolation, ms[1] orthonormalisation and gradients, ms[2] volume
+ * integrals, ms[3] face traces and KB coefficients, ms[4] face integrals,
+ * ms[5] block assembly; *launches = kernels launched.  n = entries of ms
+ * (<= 6).                                                                 */
+dgdft_status dgdft_dg_last_timing(dgdft_dg* dg, double* ms, int n, int* launches);
+
+const char* dgdft_dg_last_error(const dgdft_dg* dg);
+void dgdft_dg_destroy(dgdft_dg* dg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGDFT_DG_H */

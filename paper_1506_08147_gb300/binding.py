@@ -1,4 +1,5 @@
-"""ctypes binding of the C-ABI in include/dgdft_alb.h and dgdft_alb_steps.h.
+"""ctypes binding of the C-ABI in include/dgdft_alb.h, dgdft_alb_steps.h and
+dgdft_dg.h.
 
 Argument marshalling only: every step of ALB generation runs in the CUDA
 library.  Functions keep the C names.  Arrays may be NumPy (host) or torch
@@ -45,6 +46,13 @@ class dgdft_solve_report(C.Structure):
                 ("restarts", C.c_int)]
 
 
+class dgdft_dg_config(C.Structure):
+    _fields_ = [("ne", C.c_int * 3), ("cell", C.c_double * 3), ("q_span", C.c_int * 3),
+                ("nq", C.c_int * 3), ("nl", C.c_int * 3), ("J", C.c_int), ("alpha", C.c_double),
+                ("n_proj", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
+                ("hbm_cap_bytes", C.c_size_t)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "dgdft_alb_config_init": (None, [C.POINTER(dgdft_alb_config)]),
@@ -82,6 +90,18 @@ _SIGS = {
                                           C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double),
                                           C.POINTER(C.c_double)]),
     "dgdft_alb_precond_make_data": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
+    "dgdft_dg_create": (C.c_int, [C.POINTER(dgdft_dg_config), C.POINTER(_P)]),
+    "dgdft_dg_lgl_points": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dgdft_dg_set_potential": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "dgdft_dg_set_gamma": (C.c_int, [_P, _P]),
+    "dgdft_dg_set_projectors": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "dgdft_dg_assemble": (C.c_int, [_P, _P, C.c_int]),
+    "dgdft_dg_neighbours": (C.c_int, [_P, C.c_int, _P, _P]),
+    "dgdft_dg_get_row": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "dgdft_dg_lgl_basis": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int]),
+    "dgdft_dg_last_timing": (C.c_int, [_P, _P, C.c_int, _P]),
+    "dgdft_dg_last_error": (C.c_char_p, [_P]),
+    "dgdft_dg_destroy": (None, [_P]),
 }
 
 PRECOND_PARAMS = 15169
@@ -243,10 +263,13 @@ class Context:
                     "get_basis")
         return phi, eig, resid
 
-    def dgdft_alb_get_block(self, elem):
+    def dgdft_alb_get_block(self, elem, out=None):
+        """The Ritz block as (m, N_g) rows; with out (a contiguous device
+        tensor of N_g * m doubles) the copy goes there instead."""
         d = self.descs[elem]
-        x = np.zeros((d.n_compute, d.nx * d.ny * d.nz))
-        self._check(self.lib.dgdft_alb_get_block(self.h, elem, _ptr(x)[0], 0), "get_block")
+        x = np.zeros((d.n_compute, d.nx * d.ny * d.nz)) if out is None else out
+        p, dev = _ptr(x)
+        self._check(self.lib.dgdft_alb_get_block(self.h, elem, p, dev), "get_block")
         return x
 
     def dgdft_alb_time_stage(self, stage, reps=10):
@@ -420,3 +443,117 @@ def load_element(ctx: Context, k: int, el, x0=None):
 
 STAGES = {"xy_fwd": 0, "z_mult": 1, "xy_inv": 2, "gram": 3, "update": 4, "rayleigh_ritz": 5,
           "residual": 6}
+
+
+DG_STAGES = ("interpolation", "orthonormalise_gradients", "volume", "traces_kb", "faces", "blocks")
+
+
+class DG:
+    """Owns one dgdft_dg handle (include/dgdft_dg.h); methods mirror the C
+    entry points.  Arrays may be NumPy (host) or torch CUDA tensors."""
+
+    def __init__(self, ne, cell, q_span, nq, nl, J, alpha, n_proj, stream=None, device=0,
+                 hbm_cap_bytes=0):
+        self.lib = load()
+        c = dgdft_dg_config()
+        c.ne[:] = [int(v) for v in ne]
+        c.cell[:] = [float(v) for v in cell]
+        c.q_span[:] = [int(v) for v in q_span]
+        c.nq[:] = [int(v) for v in nq]
+        c.nl[:] = [int(v) for v in nl]
+        c.J, c.alpha, c.n_proj = int(J), float(alpha), int(n_proj)
+        c.cuda_stream = stream
+        c.device = int(device)
+        c.hbm_cap_bytes = int(hbm_cap_bytes)
+        self.cfg = c
+        self.J = int(J)
+        self.nl = tuple(int(v) for v in nl)
+        self.n_lgl = int(np.prod(self.nl))
+        self.n_elem = int(np.prod(ne))
+        self.h = C.c_void_p()
+        st = self.lib.dgdft_dg_create(C.byref(c), C.byref(self.h))
+        if st != DGDFT_OK:
+            msg = self.lib.dgdft_dg_last_error(self.h).decode()
+            self.lib.dgdft_dg_destroy(self.h)
+            self.h = None
+            raise DgdftError(st, msg)
+
+    def _check(self, st, what):
+        if st != DGDFT_OK:
+            raise DgdftError(st, f"{what}: {self.lib.dgdft_dg_last_error(self.h).decode()}")
+
+    def close(self):
+        if self.h:
+            self.lib.dgdft_dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dgdft_dg_lgl_points(self, elem):
+        out = [np.zeros(n) for n in self.nl]
+        self._check(self.lib.dgdft_dg_lgl_points(self.h, elem, *[_ptr(a)[0] for a in out]), "lgl_points")
+        return out
+
+    def dgdft_dg_set_potential(self, elem, v):
+        p, dev = _ptr(v)
+        self._check(self.lib.dgdft_dg_set_potential(self.h, elem, p, dev), "set_potential")
+
+    def dgdft_dg_set_gamma(self, gamma):
+        g = np.ascontiguousarray(gamma, np.float64)
+        self._check(self.lib.dgdft_dg_set_gamma(self.h, _ptr(g)[0]), "set_gamma")
+
+    def dgdft_dg_set_projectors(self, elem, pid, row_ptr, idx, val):
+        pid = np.ascontiguousarray(pid, np.int32)
+        rp = np.ascontiguousarray(row_ptr, np.int64)
+        idx = np.ascontiguousarray(idx, np.int32)
+        val = np.ascontiguousarray(val, np.float64)
+        self._check(self.lib.dgdft_dg_set_projectors(self.h, elem, len(pid), _ptr(pid)[0], _ptr(rp)[0],
+                                                     _ptr(idx)[0], _ptr(val)[0]), "set_projectors")
+
+    def dgdft_dg_assemble(self, blocks):
+        """blocks[K]: the J columns of element K on Q_K's grid, as (J, N_gQ)
+        rows (NumPy) or a contiguous N_gQ x J column-major device tensor."""
+        ptrs = (C.c_void_p * self.n_elem)()
+        keep = []
+        dev = None
+        for k, z in enumerate(blocks):
+            if isinstance(z, np.ndarray):
+                z = np.ascontiguousarray(z, np.float64)
+            keep.append(z)
+            p, d = _ptr(z)
+            if dev is None:
+                dev = d
+            elif dev != d:
+                raise ValueError("blocks must all be on the host or all on the device")
+            ptrs[k] = p
+        self._check(self.lib.dgdft_dg_assemble(self.h, ptrs, int(dev or 0)), "assemble")
+
+    def dgdft_dg_neighbours(self, elem):
+        nb = np.zeros(27, np.int32)
+        n = C.c_int()
+        self._check(self.lib.dgdft_dg_neighbours(self.h, elem, _ptr(nb)[0], C.byref(n)), "neighbours")
+        return [int(v) for v in nb[:n.value]]
+
+    def dgdft_dg_get_row(self, elem):
+        """{K': H_{elem, K'} (J x J, rows = basis of elem)}."""
+        nb = self.dgdft_dg_neighbours(elem)
+        out = np.zeros((len(nb), self.J, self.J))
+        self._check(self.lib.dgdft_dg_get_row(self.h, elem, _ptr(out)[0], 0), "get_row")
+        return {k: out[s] for s, k in enumerate(nb)}
+
+    def dgdft_dg_lgl_basis(self, elem, z):
+        """Orthonormal ALBs on the LGL grid as (J, n_LGL) rows."""
+        z = np.ascontiguousarray(z, np.float64)
+        phi = np.zeros((self.J, self.n_lgl))
+        self._check(self.lib.dgdft_dg_lgl_basis(self.h, elem, _ptr(z)[0], 0, _ptr(phi)[0], 0), "lgl_basis")
+        return phi
+
+    def dgdft_dg_last_timing(self):
+        ms = np.zeros(6)
+        n = C.c_int()
+        self._check(self.lib.dgdft_dg_last_timing(self.h, _ptr(ms)[0], 6, C.byref(n)), "last_timing")
+        return dict(zip(DG_STAGES, ms.tolist())), n.value

@@ -27,7 +27,7 @@ def declared_functions():
             continue
         text = open(os.path.join(inc, f)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names |= set(re.findall(r"\b(dgdft_alb_\w+)\s*\(", text))
+        names |= set(re.findall(r"\b(dgdft_(?:alb|dg)_\w+)\s*\(", text))
     return sorted(names)
 
 
@@ -39,7 +39,7 @@ def lib():
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
-    assert len(names) >= 15
+    assert len(names) >= 15 and any(n.startswith("dgdft_dg_") for n in names)
     for n in names:
         assert hasattr(lib, n), n
         assert n in B._SIGS, f"binding lacks {n}"
@@ -96,3 +96,48 @@ def test_null_context_rejected(lib):
     assert lib.dgdft_alb_scf_step(None, 3, None) == B.DGDFT_EINVAL
     assert lib.dgdft_alb_set_initial(None, 0, None, 0) == B.DGDFT_EINVAL
     assert lib.dgdft_alb_get_basis(None, 0, None, None, None, 0) == B.DGDFT_EINVAL
+
+
+def _dg_cfg(**kw):
+    c = B.dgdft_dg_config()
+    c.ne[:] = kw.get("ne", (3, 3, 1))
+    c.cell[:] = (18.0, 18.0, 24.0)
+    c.q_span[:] = kw.get("q_span", (3, 3, 1))
+    c.nq[:] = kw.get("nq", (24, 24, 30))
+    c.nl[:] = kw.get("nl", (16, 16, 60))
+    c.J = kw.get("J", 8)
+    c.alpha = kw.get("alpha", 20.0)
+    c.n_proj = 4
+    return c
+
+
+@pytest.mark.parametrize("kw", [
+    dict(ne=(0, 3, 1)),
+    dict(q_span=(2, 3, 1)),          # Q_K spans 3 elements, or the cell (1 with ne = 1)
+    dict(q_span=(1, 3, 1)),          # q_span 1 with ne = 3
+    dict(nl=(1, 16, 60)),
+    dict(nl=(16, 16, 200)),          # above 128 LGL points
+    dict(J=0),
+    dict(J=200),
+    dict(alpha=-1.0),
+])
+def test_dg_invalid_configs_rejected(lib, kw):
+    h = C.c_void_p()
+    assert lib.dgdft_dg_create(C.byref(_dg_cfg(**kw)), C.byref(h)) == B.DGDFT_EINVAL
+    assert lib.dgdft_dg_last_error(h)
+    lib.dgdft_dg_destroy(h)
+
+
+def test_dg_no_cpu_fallback_without_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    assert lib.dgdft_dg_create(C.byref(_dg_cfg()), C.byref(h)) == B.DGDFT_ECUDA
+    lib.dgdft_dg_destroy(h)
+
+
+def test_dg_null_handle_rejected(lib):
+    assert lib.dgdft_dg_assemble(None, None, 0) == B.DGDFT_EINVAL
+    assert lib.dgdft_dg_get_row(None, 0, None, 0) == B.DGDFT_EINVAL
+    assert lib.dgdft_dg_set_gamma(None, None) == B.DGDFT_EINVAL
