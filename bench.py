@@ -179,6 +179,85 @@ GRAM_TRAFFIC_PER_ELEMENT = 177.3e6
 UPDATE_TRAFFIC_PER_ELEMENT = 91.8e6
 
 
+FP64_PEAK_TFLOPS = 1.91 * 152 * 2.07e9 * 2 / 1e12  # measured FP64 FMA/clk/SM x SMs x max clock
+
+
+def dg_flops_per_element(dom):
+    """Algorithmic FP64 flops of the DG assembly per element: interpolation
+    (three axis passes), mass matrix and phi~ L^-T (symmetric halves),
+    gradients (three axis passes), V and kinetic volume integrals (symmetric
+    halves), seven face products per face (three faces per element)."""
+    J, (lx, ly, lz), (qx, qy, qz) = dom.J, dom.nl, dom.nq
+    nL = lx * ly * lz
+    half = J * (J + 1) / 2
+    interp = J * (lx * qx * qy * qz + ly * qy * lx * qz + lz * qz * lx * ly)
+    ortho = 2 * half * nL
+    grads = J * nL * (lx + ly + lz)
+    volume = 4 * half * nL
+    faces = 7 * J * J * (ly * lz + lx * lz + lx * ly)
+    return 2.0 * (interp + ortho + grads + volume + faces)
+
+
+def dg_load_inputs(B, d, dom):
+    import synth.dg as sdg
+    d.dgdft_dg_set_gamma(sdg.gamma_table(dom))
+    for k in range(dom.n_elem):
+        pts = d.dgdft_dg_lgl_points(k)
+        d.dgdft_dg_set_potential(k, np.ascontiguousarray(sdg.potential_at(dom, *pts).reshape(-1)))
+        pid, rp, idx, val = sdg.projectors_at(dom, *pts)
+        d.dgdft_dg_set_projectors(k, pid, rp, idx, val)
+
+
+def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0):
+    """Time the DG assembly (Eq. DGHamiltonian) of every element from the
+    given device columns with CUDA events on the library's stream."""
+    import torch
+    d = B.DG(dom.ne, dom.cell, dom.q_span, dom.nq, dom.nl, dom.J, dom.alpha, 2 * len(dom.atoms),
+             stream=stream.cuda_stream, hbm_cap_bytes=cap_bytes)
+    dg_load_inputs(B, d, dom)
+    for _ in range(max(1, warmup)):
+        d.dgdft_dg_assemble(blocks)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        d.dgdft_dg_assemble(blocks)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stage_ms, launches = d.dgdft_dg_last_timing()
+    nblk = sum(len(d.dgdft_dg_neighbours(k)) for k in range(dom.n_elem))
+    d.close()
+    flops = dg_flops_per_element(dom) * dom.n_elem
+    achieved = flops / (ms / 1e3) / 1e12
+    dominant = max(stage_ms, key=stage_ms.get)
+    return {"ms_per_assembly": round(ms, 3), "elements": dom.n_elem, "J": dom.J,
+            "lgl_points": list(dom.nl), "blocks": nblk,
+            "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()}, "launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": f"DG assembly (FP64 SIMT; dominant stage {dominant})",
+                         "peak_source": "FP64 pipe: measured 1.91 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                         "algorithmic_flops": flops}}
+
+
+def run_dg_only(args):
+    """Profiling mode: the DG assembly alone on seeded smooth columns."""
+    import torch
+
+    import __graft_entry__ as entry
+    import synth.dg as sdg
+    from paper_1506_08147_gb300 import binding as B
+    entry.build()
+    dom = sdg.dg_config2() if args.dg == "monolayer" else sdg.dg_small_layer()
+    blocks = [torch.from_numpy(np.ascontiguousarray(sdg.smooth_block(dom, k))).cuda() for k in range(dom.n_elem)]
+    stream = torch.cuda.current_stream()
+    out = dg_measure(B, dom, blocks, stream, args.steps, args.warmup, int(args.dg_cap_mb * 2 ** 20))
+    out["workload"] = args.dg
+    print(json.dumps({"dg_assembly": out}))
+
+
 def run_ours(args):
     import torch
 
@@ -242,6 +321,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     pairs = count_pairs(ctx, els)
+    # the Ritz blocks of the last timed solve: the DG assembly's input
+    ritz = None
+    if args.dg_steps > 0 and args.config == 2 and world == 1 and not args.elements:
+        ritz = []
+        for k, e in enumerate(els):
+            x = torch.empty(e.m * e.ng, dtype=torch.float64, device="cuda")
+            ctx.dgdft_alb_get_block(k, out=x)
+            ritz.append(x[:e.J * e.ng])
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -363,6 +450,14 @@ def run_ours(args):
                "potential_update": "alternating V_eff and V_eff + 0.02 Ha smooth field; "
                                    "before = FP64 residual of the starting block's Ritz pairs"}
 
+    # DG Hamiltonian assembly (Eq. DGHamiltonian) from the ALBs of the solve
+    dg = None
+    if ritz is not None:
+        import synth.dg as sdg
+        dg = dg_measure(B, sdg.dg_config2(), ritz, stream, args.dg_steps, 1)
+        dg["input"] = "the lowest J = 40 Ritz vectors of each element from the timed solve"
+        del ritz
+
     # end to end through the public API from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -452,6 +547,7 @@ def run_ours(args):
         "fp32_restarts": int(sum(r["restarts"] for r in reps)),
         "iterations_max": int(max(iters)) if iters else None,
         "roofline": roof, "step_roofline": step_roof, "stages": stage_report, "scf_step": scf,
+        "dg_assembly": dg,
         "plain_fp64": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
         "cpu_baseline": cpu,
@@ -625,7 +721,16 @@ def main():
                     help="compensated SIMT Gram in the FP32 stage (default: tcgen05 TF32-split tensor cores)")
     ap.add_argument("--fwd64", type=int, default=0, choices=[0, 1, 2],
                     help="FP64 forward FFT in the FP32 stage's H apply: 1 always, 2 for H X near convergence")
+    ap.add_argument("--dg-steps", type=int, default=3,
+                    help="timed DG Hamiltonian assemblies from the solve's ALBs (0: skip)")
+    ap.add_argument("--dg", default=None, choices=["monolayer", "small"],
+                    help="profiling mode: the DG assembly alone on seeded smooth columns, then exit")
+    ap.add_argument("--dg-cap-mb", type=float, default=0,
+                    help="with --dg: bound on the assembly's per-batch scratch (MiB; 0 = library default)")
     args = ap.parse_args()
+    if args.dg:
+        run_dg_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -39,7 +39,6 @@ constexpr int AX_MAXR = 32;                    // output rows per thread: n_out 
 constexpr int MAX_NL = AX_MAXR * AX_NR;
 constexpr int MAX_J = 128;
 
-constexpr int GR_TILE = 64;                    // Gram output tile (16 x 16 threads, 4 x 4 each)
 constexpr int GR_R = 16;                       // staged points per step
 constexpr int GR_CH = 2048;                    // points per split-K chunk
 
@@ -47,20 +46,24 @@ constexpr double PI = 3.14159265358979323846;
 
 // ------------------------------------------------------------------ kernels
 
-// One pass of a small dense matrix A (n_out x n_in, row-major) along one axis
-// of every element's array viewed as [O][n_in][S]: out[o][r][s] =
-// sum_i A[r][i] in[o][i][s].  FAST (S == 1): a tile is 64 consecutive lines,
-// staged transposed so loads and stores stay coalesced; otherwise a tile is 64
-// consecutive (o, s) columns, s fastest.
+// One pass of a small dense matrix A (n_out x n_in, row-major; element e uses
+// A + e * a_stride) along one axis of every element's array viewed as
+// [O][n_in][S]: out[o][r][s] = sum_i A[r][i] in[o][i][s].  FAST (S == 1): a
+// tile is 64 consecutive lines, staged transposed so loads and stores stay
+// coalesced; otherwise a tile is 64 consecutive (o, s) columns, s fastest.
+// Each thread owns R output rows of one column (R >= n_out / AX_NR, a
+// compile-time count, so no FP64 instruction issues for rows that do not
+// exist beyond the last group of AX_NR).
 struct AxisJob {
   const double* const* in;
   double* const* out;
   const double* A;
+  long long a_stride;
   int n_in, n_out, S;
   long long O;
 };
 
-template <bool FAST>
+template <bool FAST, int R>
 __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
   extern __shared__ double sm[];
   const int nin = jb.n_in, nout = jb.n_out, S = jb.S;
@@ -68,8 +71,9 @@ __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
   double* Xs = sm + nout * nin;
   const double* __restrict__ in = jb.in[blockIdx.y];
   double* __restrict__ out = jb.out[blockIdx.y];
+  const double* __restrict__ A = jb.A + blockIdx.y * jb.a_stride;
   const int t = threadIdx.x;
-  for (int i = t; i < nout * nin; i += AX_THREADS) As[i] = jb.A[i];
+  for (int i = t; i < nout * nin; i += AX_THREADS) As[i] = A[i];
   const long long ncols_total = FAST ? jb.O : jb.O * (long long)S;
   const long long g0 = (long long)blockIdx.x * AX_TC;
   const int ncol = (int)min((long long)AX_TC, ncols_total - g0);
@@ -92,21 +96,23 @@ __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
   }
   __syncthreads();
   const int c = t % AX_TC, r = t / AX_TC;
-  double acc[AX_MAXR];
+  // rows r, r + AX_NR, ...: the last ones may not exist (row >= nout); their
+  // matrix row is clamped to a valid one and the result is not stored
+  int arow[R];
 #pragma unroll
-  for (int k = 0; k < AX_MAXR; ++k) acc[k] = 0.0;
+  for (int k = 0; k < R; ++k) arow[k] = min(r + k * AX_NR, nout - 1) * nin;
+  double acc[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) acc[k] = 0.0;
   for (int i = 0; i < nin; ++i) {
     const double x = Xs[i * AX_LD + c];
 #pragma unroll
-    for (int k = 0; k < AX_MAXR; ++k) {
-      const int row = r + k * AX_NR;
-      if (row < nout) acc[k] = fma(As[row * nin + i], x, acc[k]);
-    }
+    for (int k = 0; k < R; ++k) acc[k] = fma(As[arow[k] + i], x, acc[k]);
   }
   if (FAST) {
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < AX_MAXR; ++k) {
+    for (int k = 0; k < R; ++k) {
       const int row = r + k * AX_NR;
       if (row < nout) Xs[row * AX_LD + c] = acc[k];
     }
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
   } else if (c < ncol) {
     const long long g = g0 + c, o = g / S, s = g - o * S;
 #pragma unroll
-    for (int k = 0; k < AX_MAXR; ++k) {
+    for (int k = 0; k < R; ++k) {
       const int row = r + k * AX_NR;
       if (row < nout) out[(o * nout + row) * S + s] = acc[k];
     }
@@ -129,6 +135,9 @@ __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
 // Weighted Gram products C = X^T diag(w v) Y over n points (X, Y column-major
 // with leading dimensions ldx, ldy), split into chunks of GR_CH points whose
 // partial J1 x J2 sums are added in a fixed order by dg_gram_reduce_kernel.
+// Each thread owns a 2 x 2 output tile; tiles are numbered densely (row-major,
+// or the upper triangle ti <= tj when sym: X = Y, the lower half mirrored by
+// the reduction), 256 per CTA, grid.z over groups of 256 tiles.
 struct GramTask {
   const double* X;
   const double* Y;
@@ -136,72 +145,99 @@ struct GramTask {
   const double* v;  // optional second factor (NULL = 1)
   double* out;      // J1 x J2 row-major
   long long part;   // offset of this task's partials
-  int n, ldx, ldy, J1, J2, nchunk;
+  int n, ldx, ldy, J1, J2, nchunk, sym;
 };
 
-__global__ void __launch_bounds__(256) dg_gram_kernel(const GramTask* __restrict__ tasks, int tiles_b,
+__device__ __forceinline__ void gram_tile_of(int t, int nt, int sym, int* ti, int* tj) {
+  if (!sym) {
+    *ti = t / nt;
+    *tj = t - *ti * nt;
+    return;
+  }
+  // upper triangle, row by row: row i holds nt - i tiles
+  int i = 0, base = 0;
+  while (t >= base + (nt - i)) {
+    base += nt - i;
+    ++i;
+  }
+  *ti = i;
+  *tj = i + (t - base);
+}
+
+__global__ void __launch_bounds__(256) dg_gram_kernel(const GramTask* __restrict__ tasks,
                                                       double* __restrict__ partial) {
-  __shared__ double Xs[GR_R][GR_TILE + 2];
-  __shared__ double Ys[GR_R][GR_TILE + 2];
+  __shared__ double Xs[GR_R][MAX_J + 2];
+  __shared__ double Ys[GR_R][MAX_J + 2];
   const GramTask T = tasks[blockIdx.y];
   const int chunk = blockIdx.x;
   if (chunk >= T.nchunk) return;
-  const int ta = blockIdx.z / tiles_b, tb = blockIdx.z - ta * tiles_b;
-  const int a0 = ta * GR_TILE, b0 = tb * GR_TILE;
-  if (a0 >= T.J1 || b0 >= T.J2) return;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int nti = (T.J1 + 1) / 2, ntj = (T.J2 + 1) / 2;
+  const int ntiles = T.sym ? nti * (nti + 1) / 2 : nti * ntj;
+  const int tile0 = blockIdx.z * 256;
+  if (tile0 >= ntiles) return;
+  const int mytile = tile0 + threadIdx.x;
+  int ti = 0, tj = 0;
+  const bool active = mytile < ntiles;
+  if (active) gram_tile_of(mytile, T.sym ? nti : ntj, T.sym, &ti, &tj);
+  const int i0 = 2 * ti, j0 = 2 * tj;
   const int p0 = chunk * GR_CH, p1 = min(T.n, p0 + GR_CH);
-  double acc[4][4] = {};
+  double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
+  const int J1p = (T.J1 + 1) & ~1, J2p = (T.J2 + 1) & ~1;
   for (int p = p0; p < p1; p += GR_R) {
-    for (int q = threadIdx.x; q < GR_R * GR_TILE; q += 256) {
+    for (int q = threadIdx.x; q < GR_R * J1p; q += 256) {
       const int col = q / GR_R, rr = q - col * GR_R, pt = p + rr;
-      double xv = 0.0, yv = 0.0;
-      if (pt < p1) {
-        if (a0 + col < T.J1) {
-          double wt = T.w[pt];
-          if (T.v) wt *= T.v[pt];
-          xv = T.X[(size_t)(a0 + col) * T.ldx + pt] * wt;
-        }
-        if (b0 + col < T.J2) yv = T.Y[(size_t)(b0 + col) * T.ldy + pt];
+      double xv = 0.0;
+      if (pt < p1 && col < T.J1) {
+        double wt = T.w[pt];
+        if (T.v) wt *= T.v[pt];
+        xv = T.X[(size_t)col * T.ldx + pt] * wt;
       }
       Xs[rr][col] = xv;
-      Ys[rr][col] = yv;
+    }
+    for (int q = threadIdx.x; q < GR_R * J2p; q += 256) {
+      const int col = q / GR_R, rr = q - col * GR_R, pt = p + rr;
+      Ys[rr][col] = (pt < p1 && col < T.J2) ? T.Y[(size_t)col * T.ldy + pt] : 0.0;
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int rr = 0; rr < GR_R; ++rr) {
-      double a[4], b[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        a[k] = Xs[rr][ty * 4 + k];
-        b[k] = Ys[rr][tx * 4 + k];
+      for (int rr = 0; rr < GR_R; ++rr) {
+        const double a0 = Xs[rr][i0], a1 = Xs[rr][i0 + 1];
+        const double b0 = Ys[rr][j0], b1 = Ys[rr][j0 + 1];
+        acc00 = fma(a0, b0, acc00);
+        acc01 = fma(a0, b1, acc01);
+        acc10 = fma(a1, b0, acc10);
+        acc11 = fma(a1, b1, acc11);
       }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
+  if (!active) return;
   double* dst = partial + T.part + (size_t)chunk * T.J1 * T.J2;
+  const double v[2][2] = {{acc00, acc01}, {acc10, acc11}};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int ii = a0 + ty * 4 + i;
-    if (ii >= T.J1) continue;
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int jj = b0 + tx * 4 + j;
-      if (jj < T.J2) dst[(size_t)ii * T.J2 + jj] = acc[i][j];
+    for (int b = 0; b < 2; ++b) {
+      const int ii = i0 + a, jj = j0 + b;
+      if (ii < T.J1 && jj < T.J2) dst[(size_t)ii * T.J2 + jj] = v[a][b];
     }
-  }
 }
 
 __global__ void dg_gram_reduce_kernel(const GramTask* __restrict__ tasks, const double* __restrict__ partial) {
   const GramTask T = tasks[blockIdx.y];
   const int n = T.J1 * T.J2;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    int i = q / T.J2, j = q - (q / T.J2) * T.J2;
+    // symmetric tasks hold the tiles with i/2 <= j/2 only
+    if (T.sym && i / 2 > j / 2) {
+      const int t = i;
+      i = j;
+      j = t;
+    }
+    const int src = i * T.J2 + j;
     double s = 0.0;
-    for (int c = 0; c < T.nchunk; ++c) s += partial[T.part + (size_t)c * n + q];
+    for (int c = 0; c < T.nchunk; ++c) s += partial[T.part + (size_t)c * n + src];
     T.out[q] = s;
   }
 }
@@ -354,22 +390,6 @@ __global__ void dg_block_sum_kernel(BlockJob jb) {
     s = fma(K.gamma * jb.coef[(size_t)K.ra * J + i], jb.coef[(size_t)K.rb * J + j], s);
   }
   jb.out[(size_t)b * J * J + q] = s;
-}
-
-// phi = phi~ L^-T for every element of a batch (grid.y): phi[p, j] =
-// sum_{k <= j} phi~[p, k] L^-1[j][k].
-__global__ void dg_apply_linv_kernel(const double* __restrict__ phit, const double* __restrict__ linv,
-                                     double* __restrict__ phi, int J, int nL) {
-  const size_t off = (size_t)blockIdx.y * J * nL;
-  const double* L = linv + (size_t)blockIdx.y * J * J;
-  const long long total = (long long)nL * J;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(q / nL), p = (int)(q - (long long)j * nL);
-    double s = 0.0;
-    for (int k = 0; k <= j; ++k) s = fma(phit[off + (size_t)k * nL + p], L[j * J + k], s);
-    phi[off + q] = s;
-  }
 }
 
 // ------------------------------------------------------------------ host tables
@@ -551,16 +571,52 @@ size_t axis_smem(int nin, int nout) {
   return sizeof(double) * ((size_t)nout * nin + (size_t)std::max(nin, nout) * AX_LD);
 }
 
+template <bool FAST, int R>
+void launch_axis_r(dgdft_dg* dg, const AxisJob& jb, unsigned tiles, int nelem, size_t sm) {
+  dg_axis_kernel<FAST, R><<<dim3(tiles, nelem), AX_THREADS, sm, dg->st>>>(jb);
+}
+
+template <bool FAST>
+void launch_axis_fast(dgdft_dg* dg, const AxisJob& jb, unsigned tiles, int nelem, size_t sm) {
+  const int need = (jb.n_out + AX_NR - 1) / AX_NR;
+  if (need <= 4) launch_axis_r<FAST, 4>(dg, jb, tiles, nelem, sm);
+  else if (need <= 8) launch_axis_r<FAST, 8>(dg, jb, tiles, nelem, sm);
+  else if (need <= 12) launch_axis_r<FAST, 12>(dg, jb, tiles, nelem, sm);
+  else if (need <= 16) launch_axis_r<FAST, 16>(dg, jb, tiles, nelem, sm);
+  else if (need <= 20) launch_axis_r<FAST, 20>(dg, jb, tiles, nelem, sm);
+  else if (need <= 24) launch_axis_r<FAST, 24>(dg, jb, tiles, nelem, sm);
+  else launch_axis_r<FAST, 32>(dg, jb, tiles, nelem, sm);
+}
+
+template <bool FAST> bool set_axis_smem(int bytes) {
+  return cudaFuncSetAttribute(dg_axis_kernel<FAST, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(dg_axis_kernel<FAST, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(dg_axis_kernel<FAST, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(dg_axis_kernel<FAST, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(dg_axis_kernel<FAST, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(dg_axis_kernel<FAST, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(dg_axis_kernel<FAST, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess;
+}
+
+// A (n_out x n_in) along one axis of nelem arrays [O][n_in][S]; element e
+// uses A + e * a_stride.
 bool launch_axis(dgdft_dg* dg, const double* const* d_in, double* const* d_out, int nelem, const double* A,
-                 int nin, int nout, int S, long long O) {
-  AxisJob jb{d_in, d_out, A, nin, nout, S, O};
+                 int nin, int nout, int S, long long O, long long a_stride = 0) {
+  AxisJob jb{d_in, d_out, A, a_stride, nin, nout, S, O};
   const long long cols = (S == 1) ? O : O * S;
   const unsigned tiles = (unsigned)((cols + AX_TC - 1) / AX_TC);
   const size_t sm = axis_smem(nin, nout);
   if (S == 1)
-    dg_axis_kernel<true><<<dim3(tiles, nelem), AX_THREADS, sm, dg->st>>>(jb);
+    launch_axis_fast<true>(dg, jb, tiles, nelem, sm);
   else
-    dg_axis_kernel<false><<<dim3(tiles, nelem), AX_THREADS, sm, dg->st>>>(jb);
+    launch_axis_fast<false>(dg, jb, tiles, nelem, sm);
   ++dg->launches;
   return cuda_ok(dg, cudaGetLastError(), "axis kernel");
 }
@@ -595,9 +651,9 @@ bool run_grams(dgdft_dg* dg, std::vector<GramTask>& tasks) {
   }
   bool ok = cuda_ok(dg, cudaMemcpyAsync(d_t, h.data(), h.size() * sizeof(GramTask), cudaMemcpyHostToDevice, dg->st),
                     "Gram tasks");
-  const int ta = (maxJ1 + GR_TILE - 1) / GR_TILE, tb = (maxJ2 + GR_TILE - 1) / GR_TILE;
+  const int ntiles = ((maxJ1 + 1) / 2) * ((maxJ2 + 1) / 2);
   if (ok) {
-    dg_gram_kernel<<<dim3(maxc, (unsigned)h.size(), ta * tb), 256, 0, dg->st>>>(d_t, tb, dg->d_part);
+    dg_gram_kernel<<<dim3(maxc, (unsigned)h.size(), (ntiles + 255) / 256), 256, 0, dg->st>>>(d_t, dg->d_part);
     dg_gram_reduce_kernel<<<dim3(std::max(1, (maxJ1 * maxJ2 + 255) / 256), (unsigned)h.size()), 256, 0, dg->st>>>(
         d_t, dg->d_part);
     dg->launches += 2;
@@ -707,15 +763,35 @@ bool ortho_batch(dgdft_dg* dg, int nb, double* mass, long long mass_stride, doub
     t.out = mass + (size_t)e * mass_stride;
     t.n = t.ldx = t.ldy = dg->nL;
     t.J1 = t.J2 = J;
+    t.sym = 1;
     tasks.push_back(t);
   }
   if (!run_grams(dg, tasks)) return false;
   dg_chol_kernel<<<nb, 256, (size_t)J * J * sizeof(double), dg->st>>>(mass, mass_stride, linv, J, bad);
-  dg_apply_linv_kernel<<<dim3(256, nb), 256, 0, dg->st>>>(dg->d_phi, linv, dg->d_g[2], J, dg->nL);
-  dg->launches += 2;
+  ++dg->launches;
+  if (!cuda_ok(dg, cudaGetLastError(), "orthonormalisation")) return false;
+  // phi = phi~ L^-T: L^-1 along the J axis of [1][J][n_LGL]
+  std::vector<const double*> cin;
+  std::vector<double*> cout;
+  for (int e = 0; e < nb; ++e) cin.push_back(dg->d_phi + (size_t)e * J * dg->nL);
+  for (int e = 0; e < nb; ++e) cout.push_back(dg->d_g[2] + (size_t)e * J * dg->nL);
+  const double** d_in = nullptr;
+  double** d_out = nullptr;
+  if (!dmalloc(&d_in, cin.size()) || !dmalloc(&d_out, cout.size())) {
+    cudaFree(d_in);
+    dg->err = "pointer tables: out of memory";
+    return false;
+  }
+  bool ok = cuda_ok(dg, cudaMemcpyAsync(d_in, cin.data(), cin.size() * sizeof(void*), cudaMemcpyHostToDevice, dg->st),
+                    "pointer tables") &&
+            cuda_ok(dg, cudaMemcpyAsync(d_out, cout.data(), cout.size() * sizeof(void*), cudaMemcpyHostToDevice, dg->st),
+                    "pointer tables") &&
+            launch_axis(dg, d_in, d_out, nb, linv, J, J, dg->nL, 1, (long long)J * J) &&
+            cuda_ok(dg, cudaStreamSynchronize(dg->st), "orthonormalisation");
+  cudaFree(d_in);
+  cudaFree(d_out);
   std::swap(dg->d_phi, dg->d_g[2]);
-  return cuda_ok(dg, cudaGetLastError(), "orthonormalisation") &&
-         cuda_ok(dg, cudaStreamSynchronize(dg->st), "orthonormalisation");
+  return ok;
 }
 
 bool ensure_batch(dgdft_dg* dg, int nb) {
@@ -788,13 +864,10 @@ dgdft_status dgdft_dg_create(const dgdft_dg_config* cfg, dgdft_dg** out) {
   dg->t1_elem = (size_t)c.J * dg->nq[2] * dg->nq[1] * dg->nl[0];
   dg->t2_elem = (size_t)c.J * dg->nq[2] * dg->nl[1] * dg->nl[0];
   // shared memory of every axis pass
-  size_t smax = 0;
+  size_t smax = axis_smem(c.J, c.J);
   for (int d = 0; d < 3; ++d) smax = std::max({smax, axis_smem(dg->nq[d], dg->nl[d]), axis_smem(dg->nl[d], dg->nl[d])});
   if (smax > 220 * 1024) return dg->fail(DGDFT_EINVAL, "grids too large for the interpolation kernel");
-  if (cudaFuncSetAttribute(dg_axis_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(dg_axis_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) !=
-          cudaSuccess ||
+  if (!set_axis_smem<true>((int)smax) || !set_axis_smem<false>((int)smax) ||
       cudaFuncSetAttribute(dg_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(c.J * c.J * sizeof(double))) != cudaSuccess)
     return dg->fail(DGDFT_ECUDA, "kernel attributes");
@@ -1038,6 +1111,7 @@ dgdft_status dgdft_dg_assemble(dgdft_dg* dg, const double* const* z, int on_devi
         t.J1 = t.J2 = J;
         t.w = dg->d_w;
         t.X = t.Y = phi;
+        t.sym = 1;
         t.v = dg->d_v + (size_t)k * dg->nL;  // V_eff
         t.out = dg->d_pool + dg->vol_mat(k, 1);
         tasks.push_back(t);
@@ -1125,6 +1199,7 @@ dgdft_status dgdft_dg_assemble(dgdft_dg* dg, const double* const* z, int on_devi
         for (int q = 0; q < 3; ++q) {
           t.X = F[ff[q][0]];
           t.Y = F[ff[q][1]];
+          t.sym = ff[q][0] == ff[q][1];
           t.out = dg->d_pool + dg->face_mat(a, d, 4 + q);
           tasks.push_back(t);
         }
