@@ -31,6 +31,8 @@ Readings where the paper is silent (each listed in the design notes):
     periodic boundary.
   * Blocks are H_{K,K'} (rows: basis of K) for K' in the 3 x 3 x 3 periodic
     neighbourhood of K; coinciding neighbours are merged.
+  * Density (Eq. density) of the lowest n_occ eigenvectors of H^DG, one
+    electron per state as the equation is written (no spin factor).
 """
 
 from __future__ import annotations
@@ -281,3 +283,28 @@ def alb_on_lgl(dom, k: int, z: np.ndarray, orthonormalise: bool = True) -> np.nd
     g = ElementGrid(dom, k)
     phi = interpolate_to_lgl(dom, g, z)
     return orthonormalise_lgl(phi, g.w) if orthonormalise else phi
+
+
+# ---------------------------------------------------------------- density
+
+def dense_matrix(dom, rows: dict, J: int) -> np.ndarray:
+    """H^DG as one dense matrix (element-major: row K * J + j) from the
+    block rows {K: {K': H_{K,K'}}}."""
+    n = dom.n_elem * J
+    H = np.zeros((n, n))
+    for k, row in rows.items():
+        for kk, blk in row.items():
+            H[k * J:(k + 1) * J, kk * J:(kk + 1) * J] = blk
+    return H
+
+
+def density(dom, phis: dict, H: np.ndarray, n_occ: int, J: int):
+    """Eq. ELeq and Eq. density by dense diagonalisation (the DIAG route):
+    the lowest n_occ eigenpairs of the symmetric H^DG (orthonormal basis, so
+    a standard problem) and rho(x) = sum_i |psi_i(x)|^2 on every element's
+    LGL grid, psi_i = sum_{K,j} c_{i;K,j} phi_{K,j}.  Returns (eigenvalues,
+    {K: rho_K})."""
+    lam, c = np.linalg.eigh(0.5 * (H + H.T))
+    c = c[:, :n_occ]
+    rho = {k: np.sum((c[k * J:(k + 1) * J].T @ phis[k]) ** 2, axis=0) for k in range(dom.n_elem)}
+    return lam[:n_occ], rho

@@ -19,7 +19,10 @@ the oracle does not compute itself:
   * the KB term: with the constant function, sum_p gamma_p (int b_p)^2 over
     the elements the projector is cut into, against the integral over the
     ball (radial quadrature);
-  * symmetry H_{K,K'} = H_{K',K}^T with every term present.
+  * symmetry H_{K,K'} = H_{K',K}^T with every term present;
+  * the density (Eq. density): it integrates to the number of states with
+    every term present, and from the lowest plane waves of the cell it is
+    the uniform n / V (all 7 states) or 1 / V (the ground state alone).
 """
 
 import numpy as np
@@ -254,3 +257,42 @@ def test_blocks_symmetric_with_every_term():
         assert len(row) == 9  # 3 x 3 x 1 periodic neighbourhood
         for kk, blk in row.items():
             assert np.allclose(blk, rows[kk][k].T, atol=1e-10 * np.max(np.abs(blk)))
+
+
+def test_density_integrates_to_states():
+    dom = sdg.dg_small_layer()
+    gam = sdg.gamma_table(dom)
+    phis, v, projs = {}, {}, {}
+    for k in range(dom.n_elem):
+        g = dg.ElementGrid(dom, k)
+        phis[k] = dg.alb_on_lgl(dom, k, sdg.smooth_block(dom, k))
+        v[k] = sdg.potential_at(dom, *g.cell_pts)
+        projs[k] = sdg.projectors_at(dom, *g.cell_pts)
+    A = dg.Assembly(dom, phis, v, projs, gam, alpha=dom.alpha)
+    H = dg.dense_matrix(dom, {k: A.row(k) for k in range(dom.n_elem)}, dom.J)
+    for n_occ in (1, 10, dom.n_elem * dom.J):
+        lam, rho = dg.density(dom, phis, H, n_occ, dom.J)
+        total = sum(float(A.g(k).w @ rho[k]) for k in range(dom.n_elem))
+        assert abs(total - n_occ) < 1e-10 * n_occ
+        assert np.all(np.diff(lam) >= 0) and all(np.all(r >= 0) for r in rho.values())
+
+
+def test_density_of_planewaves_is_uniform():
+    dom = sdg.dg_small_cube(J=7)
+    waves = _planewaves(dom, dom.J)
+    phis = {}
+    for k in range(dom.n_elem):
+        qo = dom.corner(k) - dom.e_off
+        ax = [qo[d] + np.arange(dom.nq[d]) * dom.lq[d] / dom.nq[d] for d in range(3)]
+        z = np.stack([
+            (np.cos(G[2] * ax[2][:, None, None] + G[1] * ax[1][None, :, None]
+                    + G[0] * ax[0][None, None, :] + ph)).reshape(-1) for G, ph in waves])
+        phis[k] = dg.alb_on_lgl(dom, k, z)
+    v = {k: np.zeros(dom.n_lgl) for k in range(dom.n_elem)}
+    A = dg.Assembly(dom, phis, v, _empty(dom), np.zeros(0), alpha=dom.alpha)
+    H = dg.dense_matrix(dom, {k: A.row(k) for k in range(dom.n_elem)}, dom.J)
+    vol = float(np.prod(dom.cell))
+    for n_occ, level in ((1, 1.0), (dom.J, float(dom.J))):
+        lam, rho = dg.density(dom, phis, H, n_occ, dom.J)
+        for r in rho.values():
+            assert np.allclose(r, level / vol, rtol=1e-8, atol=0)
