@@ -228,13 +228,31 @@ def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0):
     ms = e0.elapsed_time(e1) / steps
     stage_ms, launches = d.dgdft_dg_last_timing()
     nblk = sum(len(d.dgdft_dg_neighbours(k)) for k in range(dom.n_elem))
+    # density by dense diagonalisation (Eq. density), half of the basis
+    # occupied (a synthetic occupation), once after the timed assemblies
+    n_occ = dom.n_elem * dom.J // 2
+    rho = torch.empty(dom.n_elem * dom.n_lgl, dtype=torch.float64, device="cuda")
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    d.dgdft_dg_density(blocks, n_occ, out=rho)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dens_stage, _ = d.dgdft_dg_last_timing()
+    density = {"n": dom.n_elem * dom.J, "n_occ": n_occ, "ms": round(d0.elapsed_time(d1), 2),
+               "eigensolve_ms": round(dens_stage["density_eigensolve"], 2),
+               "evaluation_ms": round(dens_stage["density_evaluation"], 2),
+               "eigensolver": "FP64 dense, one CTA (the Rayleigh-Ritz kernel)"}
+    del rho
     d.close()
+    stage_ms = {k: v for k, v in stage_ms.items() if not k.startswith("density")}
     flops = dg_flops_per_element(dom) * dom.n_elem
     achieved = flops / (ms / 1e3) / 1e12
     dominant = max(stage_ms, key=stage_ms.get)
     return {"ms_per_assembly": round(ms, 3), "elements": dom.n_elem, "J": dom.J,
             "lgl_points": list(dom.nl), "blocks": nblk,
             "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()}, "launches": launches,
+            "density": density,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                          "kernel": f"DG assembly (FP64 SIMT; dominant stage {dominant})",

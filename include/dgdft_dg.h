@@ -112,11 +112,27 @@ dgdft_status dgdft_dg_get_row(dgdft_dg* dg, int elem, double* blocks, int on_dev
 dgdft_status dgdft_dg_lgl_basis(dgdft_dg* dg, int elem, const double* z, int z_on_device, double* phi,
                                 int on_device);
 
+/* Density (Eq. density) by dense diagonalisation of the assembled H^DG (the
+ * DIAG route of Sec. II.B, for small systems): the lowest n_occ eigenpairs
+ * of H^DG c = lambda c (the basis is orthonormal, so a standard problem) by
+ * the library's FP64 dense eigensolver, then rho(x) = sum_{i < n_occ}
+ * |psi_i(x)|^2 with psi_i = sum_{K,j} c_{i;K,j} phi_{K,j}, one electron per
+ * state as Eq. density is written, on every element's LGL grid.  z: the same
+ * columns as the last assemble (z_on_device as there; the basis is rebuilt
+ * from them).  eig: n_occ eigenvalues, ascending (host).  rho: n_elem x n_LGL
+ * (element-major, x fastest; device when on_device, else host).
+ * DGDFT_ESTATE before a successful assemble; DGDFT_EINVAL for n_occ outside
+ * 1..n_elem J or n_elem J above 4096 (the dense eigensolver runs in one CTA:
+ * seconds at a few thousand).                                              */
+dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_device, int n_occ, double* eig,
+                              double* rho, int on_device);
+
 /* Kernel time of the last assembly per stage (CUDA events on the stream):
  * ms[0] interpolation, ms[1] orthonormalisation and gradients, ms[2] volume
  * integrals, ms[3] face traces and KB coefficients, ms[4] face integrals,
- * ms[5] block assembly; *launches = kernels launched.  n = entries of ms
- * (<= 6).                                                                 */
+ * ms[5] block assembly, and of the last density: ms[6] eigensolve, ms[7]
+ * density evaluation; *launches = kernels of the last assembly.  n = entries
+ * of ms (<= 8).                                                            */
 dgdft_status dgdft_dg_last_timing(dgdft_dg* dg, double* ms, int n, int* launches);
 
 const char* dgdft_dg_last_error(const dgdft_dg* dg);

@@ -99,6 +99,7 @@ _SIGS = {
     "dgdft_dg_neighbours": (C.c_int, [_P, C.c_int, _P, _P]),
     "dgdft_dg_get_row": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "dgdft_dg_lgl_basis": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int]),
+    "dgdft_dg_density": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dgdft_dg_last_timing": (C.c_int, [_P, _P, C.c_int, _P]),
     "dgdft_dg_last_error": (C.c_char_p, [_P]),
     "dgdft_dg_destroy": (None, [_P]),
@@ -445,7 +446,8 @@ STAGES = {"xy_fwd": 0, "z_mult": 1, "xy_inv": 2, "gram": 3, "update": 4, "raylei
           "residual": 6}
 
 
-DG_STAGES = ("interpolation", "orthonormalise_gradients", "volume", "traces_kb", "faces", "blocks")
+DG_STAGES = ("interpolation", "orthonormalise_gradients", "volume", "traces_kb", "faces", "blocks",
+             "density_eigensolve", "density_evaluation")
 
 
 class DG:
@@ -514,9 +516,7 @@ class DG:
         self._check(self.lib.dgdft_dg_set_projectors(self.h, elem, len(pid), _ptr(pid)[0], _ptr(rp)[0],
                                                      _ptr(idx)[0], _ptr(val)[0]), "set_projectors")
 
-    def dgdft_dg_assemble(self, blocks):
-        """blocks[K]: the J columns of element K on Q_K's grid, as (J, N_gQ)
-        rows (NumPy) or a contiguous N_gQ x J column-major device tensor."""
+    def _block_ptrs(self, blocks):
         ptrs = (C.c_void_p * self.n_elem)()
         keep = []
         dev = None
@@ -530,7 +530,24 @@ class DG:
             elif dev != d:
                 raise ValueError("blocks must all be on the host or all on the device")
             ptrs[k] = p
-        self._check(self.lib.dgdft_dg_assemble(self.h, ptrs, int(dev or 0)), "assemble")
+        return ptrs, int(dev or 0), keep
+
+    def dgdft_dg_assemble(self, blocks):
+        """blocks[K]: the J columns of element K on Q_K's grid, as (J, N_gQ)
+        rows (NumPy) or a contiguous N_gQ x J column-major device tensor."""
+        ptrs, dev, keep = self._block_ptrs(blocks)
+        self._check(self.lib.dgdft_dg_assemble(self.h, ptrs, dev), "assemble")
+
+    def dgdft_dg_density(self, blocks, n_occ, out=None):
+        """(eigenvalues, rho (n_elem, n_LGL)) of the lowest n_occ states of the
+        assembled H^DG; blocks as for assemble; out: an optional device tensor
+        of n_elem * n_LGL doubles for rho."""
+        ptrs, dev, keep = self._block_ptrs(blocks)
+        eig = np.zeros(int(n_occ))
+        rho = np.zeros((self.n_elem, self.n_lgl)) if out is None else out
+        p, rdev = _ptr(rho)
+        self._check(self.lib.dgdft_dg_density(self.h, ptrs, dev, int(n_occ), _ptr(eig)[0], p, rdev), "density")
+        return eig, rho
 
     def dgdft_dg_neighbours(self, elem):
         nb = np.zeros(27, np.int32)
@@ -553,7 +570,7 @@ class DG:
         return phi
 
     def dgdft_dg_last_timing(self):
-        ms = np.zeros(6)
+        ms = np.zeros(8)
         n = C.c_int()
-        self._check(self.lib.dgdft_dg_last_timing(self.h, _ptr(ms)[0], 6, C.byref(n)), "last_timing")
+        self._check(self.lib.dgdft_dg_last_timing(self.h, _ptr(ms)[0], 8, C.byref(n)), "last_timing")
         return dict(zip(DG_STAGES, ms.tolist())), n.value

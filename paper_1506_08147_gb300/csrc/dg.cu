@@ -19,6 +19,10 @@
 //   6. face integrals: weighted Gram products of the traces of both sides of
 //      every face;
 //   7. every block H_{K,K'} summed from its volume, KB and face terms.
+// Density (Eq. density, the DIAG route for small systems): H^DG scattered
+// into a dense matrix, its lowest eigenpairs by the library's FP64 dense
+// eigensolver (the one of the Rayleigh-Ritz step), the density matrix blocks
+// P_K = Y_K Y_K^T, and rho = sum_jj' phi_j P_K,jj' phi_j' on the LGL grids.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +32,7 @@
 #include <vector>
 
 #include "../../include/dgdft_dg.h"
+#include "internal.h"
 
 namespace {
 
@@ -392,6 +397,47 @@ __global__ void dg_block_sum_kernel(BlockJob jb) {
   jb.out[(size_t)b * J * J + q] = s;
 }
 
+// Dense H^DG (element-major, row K J + i) from the stored blocks.
+__global__ void dg_dense_kernel(const double* __restrict__ H, const int2* __restrict__ blk_kk, double* __restrict__ A,
+                                int J, long long n) {
+  const int b = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= J * J) return;
+  const int i = q / J, j = q - i * J;
+  const int2 kk = blk_kk[b];
+  A[((long long)kk.x * J + i) * n + (long long)kk.y * J + j] = H[(size_t)b * J * J + q];
+}
+
+__global__ void dg_identity_kernel(double* __restrict__ B, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * n;
+       q += (long long)gridDim.x * blockDim.x)
+    B[q] = (q / n == q % n) ? 1.0 : 0.0;
+}
+
+// P_K[j][j'] = sum_i Y[K J + j, i] Y[K J + j', i] (Y column-major n x m).
+__global__ void dg_dm_kernel(const double* __restrict__ Y, double* __restrict__ P, int J, long long n, int m) {
+  const int k = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= J * J) return;
+  const int j = q / J, jp = q - j * J;
+  const double* a = Y + (long long)k * J + j;
+  const double* b = Y + (long long)k * J + jp;
+  double s = 0.0;
+  for (int i = 0; i < m; ++i) s = fma(a[(long long)i * n], b[(long long)i * n], s);
+  P[(size_t)k * J * J + q] = s;
+}
+
+// rho[p] = sum_j phi[j][p] T[j][p] for every element of a batch (grid.y).
+__global__ void dg_rho_kernel(const double* __restrict__ phi, const double* __restrict__ T, double* __restrict__ rho,
+                              int J, int nL) {
+  const size_t off = (size_t)blockIdx.y * J * nL;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nL; p += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < J; ++j) s = fma(phi[off + (size_t)j * nL + p], T[off + (size_t)j * nL + p], s);
+    rho[(size_t)blockIdx.y * nL + p] = s;
+  }
+}
+
 // ------------------------------------------------------------------ host tables
 
 // P_N(x) and P_{N-1}(x) by the three-term recurrence.
@@ -520,6 +566,7 @@ struct dgdft_dg {
   int nblk = 0;
   bool assembled = false;
   double ms[6]{};
+  double density_ms[2]{};  // eigensolve, density evaluation
   int launches = 0;
   // batch scratch
   int batch = 0;
@@ -871,6 +918,7 @@ dgdft_status dgdft_dg_create(const dgdft_dg_config* cfg, dgdft_dg** out) {
       cudaFuncSetAttribute(dg_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(c.J * c.J * sizeof(double))) != cudaSuccess)
     return dg->fail(DGDFT_ECUDA, "kernel attributes");
+  dgdft::init_rr_kernels();
   // tables
   std::vector<double> hI[3], hD[3];
   for (int d = 0; d < 3; ++d) {
@@ -1343,9 +1391,146 @@ dgdft_status dgdft_dg_lgl_basis(dgdft_dg* dg, int elem, const double* z, int z_o
   return DGDFT_OK;
 }
 
+dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_device, int n_occ, double* eig,
+                              double* rho, int on_device) {
+  if (!dg) return DGDFT_EINVAL;
+  const int J = dg->J, nel = dg->nel;
+  const long long n = (long long)nel * J;
+  if (!z || !eig || !rho || n_occ < 1 || n_occ > n) return dg->fail(DGDFT_EINVAL, "density: bad arguments");
+  if (n > 4096) return dg->fail(DGDFT_EINVAL, "density: n_elem * J above 4096");
+  for (int k = 0; k < nel; ++k)
+    if (!z[k]) return dg->fail(DGDFT_EINVAL, "density: z[" + std::to_string(k) + "] is NULL");
+  if (!dg->assembled) return dg->fail(DGDFT_ESTATE, "density before a successful assemble");
+  const size_t JJ = (size_t)J * J;
+  double *dA = nullptr, *dB = nullptr, *dY = nullptr, *dth = nullptr, *work = nullptr, *dP = nullptr,
+         *drho = nullptr;
+  int2* dkk = nullptr;
+  dgdft::RRTask* dt = nullptr;
+  auto release = [&]() {
+    for (void* p : {(void*)dA, (void*)dB, (void*)dY, (void*)dth, (void*)work, (void*)dP, (void*)drho, (void*)dkk,
+                    (void*)dt})
+      cudaFree(p);
+  };
+  std::vector<int2> kk;
+  for (int k = 0; k < nel; ++k)
+    for (int k2 : dg->nb[k]) kk.push_back(make_int2(k, k2));
+  if (!dmalloc(&dA, (size_t)(n * n)) || !dmalloc(&dB, (size_t)(n * n)) || !dmalloc(&dY, (size_t)(n * n_occ)) ||
+      !dmalloc(&dth, (size_t)n_occ) || !dmalloc(&work, dgdft::rr_work_doubles((int)n, n_occ)) ||
+      !dmalloc(&dP, (size_t)nel * JJ) || !dmalloc(&dt, 1) || !upload(dg, &dkk, kk) ||
+      (!on_device && !dmalloc(&drho, (size_t)nel * dg->nL))) {
+    release();
+    return dg->fail(DGDFT_ENOMEM, "density storage");
+  }
+  double t_ms[2] = {0.0, 0.0};
+  bool ok = cuda_ok(dg, cudaMemsetAsync(dA, 0, sizeof(double) * n * n, dg->st), "density");
+  {
+    Timer tm(dg->st);
+    if (ok) {
+      const unsigned gx = (unsigned)((JJ + 255) / 256);
+      dg_dense_kernel<<<dim3(gx, dg->nblk), 256, 0, dg->st>>>(dg->d_H, dkk, dA, J, n);
+      dg_identity_kernel<<<1024, 256, 0, dg->st>>>(dB, n);
+      dgdft::RRTask t{};
+      t.A = dA;
+      t.B = dB;
+      t.ld = (int)n;
+      t.mode = dgdft::RR_FIXED;
+      t.n_fixed = (int)n;
+      t.m = n_occ;
+      t.Y = dY;
+      t.ldy = (int)n;
+      t.theta = dth;
+      t.work = work;
+      t.state = nullptr;
+      t.cond_max = 1e30;
+      ok = cuda_ok(dg, cudaMemcpyAsync(dt, &t, sizeof(t), cudaMemcpyHostToDevice, dg->st), "density task");
+      if (ok) {
+        dgdft::launch_rr(dt, 1, dg->st, (int)n, n_occ);
+        dg_dm_kernel<<<dim3(gx, nel), 256, 0, dg->st>>>(dY, dP, J, n, n_occ);
+      }
+      ok = ok && cuda_ok(dg, cudaGetLastError(), "density eigensolve") &&
+           cuda_ok(dg, cudaMemcpyAsync(eig, dth, sizeof(double) * n_occ, cudaMemcpyDeviceToHost, dg->st),
+                   "eigenvalues") &&
+           cuda_ok(dg, cudaStreamSynchronize(dg->st), "density eigensolve");
+    }
+    t_ms[0] = tm.stop();
+  }
+  if (ok && !std::isfinite(eig[0])) {
+    dg->err = "density: the eigensolver failed";
+    ok = false;
+  }
+  // density on each batch: phi from z again, then T = P_K phi and rho
+  size_t cap = dg->cfg.hbm_cap_bytes;
+  if (ok && !cap) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    cap = fr / 4;
+  }
+  const int nbat = (int)std::max<size_t>(1, std::min<size_t>(nel, cap / std::max<size_t>(1, batch_bytes(dg))));
+  if (ok && !ensure_batch(dg, nbat)) ok = false;
+  double* d_mass = nullptr;
+  int* d_bad = nullptr;
+  double* d_linv = nullptr;
+  if (ok && (!dmalloc(&d_mass, (size_t)nbat * JJ) || !dmalloc(&d_linv, (size_t)nbat * JJ) ||
+             !dmalloc(&d_bad, (size_t)nbat))) {
+    dg->err = "density scratch: out of memory";
+    ok = false;
+  }
+  Timer tm(dg->st);
+  for (int g0 = 0; ok && g0 < nel; g0 += nbat) {
+    const int nb = std::min(nbat, nel - g0);
+    std::vector<const double*> src(nb);
+    for (int e = 0; e < nb && ok; ++e) {
+      if (z_on_device) {
+        src[e] = z[g0 + e];
+      } else {
+        double* dst = dg->d_z + (size_t)e * J * dg->ngq;
+        ok = cuda_ok(dg, cudaMemcpyAsync(dst, z[g0 + e], sizeof(double) * J * dg->ngq, cudaMemcpyHostToDevice, dg->st),
+                     "copy of z");
+        src[e] = dst;
+      }
+    }
+    ok = ok && interp_batch(dg, nb, src.data()) && ortho_batch(dg, nb, d_mass, (long long)JJ, d_linv, d_bad);
+    if (!ok) break;
+    std::vector<const double*> cin;
+    std::vector<double*> cout;
+    for (int e = 0; e < nb; ++e) cin.push_back(dg->d_phi + (size_t)e * J * dg->nL);
+    for (int e = 0; e < nb; ++e) cout.push_back(dg->d_g[0] + (size_t)e * J * dg->nL);
+    const double** d_in = nullptr;
+    double** d_out = nullptr;
+    if (!dmalloc(&d_in, cin.size()) || !dmalloc(&d_out, cout.size())) {
+      cudaFree(d_in);
+      dg->err = "pointer tables: out of memory";
+      ok = false;
+      break;
+    }
+    ok = cuda_ok(dg, cudaMemcpyAsync(d_in, cin.data(), cin.size() * sizeof(void*), cudaMemcpyHostToDevice, dg->st),
+                 "pointer tables") &&
+         cuda_ok(dg, cudaMemcpyAsync(d_out, cout.data(), cout.size() * sizeof(void*), cudaMemcpyHostToDevice, dg->st),
+                 "pointer tables") &&
+         launch_axis(dg, d_in, d_out, nb, dP + (size_t)g0 * JJ, J, J, dg->nL, 1, (long long)JJ);
+    if (ok) {
+      double* out = (on_device ? rho : drho) + (size_t)g0 * dg->nL;
+      dg_rho_kernel<<<dim3(256, nb), 256, 0, dg->st>>>(dg->d_phi, dg->d_g[0], out, J, dg->nL);
+      ok = cuda_ok(dg, cudaGetLastError(), "density kernel") && cuda_ok(dg, cudaStreamSynchronize(dg->st), "density");
+    }
+    cudaFree(d_in);
+    cudaFree(d_out);
+  }
+  t_ms[1] = tm.stop();
+  cudaFree(d_mass);
+  cudaFree(d_linv);
+  cudaFree(d_bad);
+  if (ok && !on_device)
+    ok = cuda_ok(dg, cudaMemcpy(rho, drho, sizeof(double) * nel * dg->nL, cudaMemcpyDeviceToHost), "density copy");
+  dg->density_ms[0] = t_ms[0];
+  dg->density_ms[1] = t_ms[1];
+  release();
+  return ok ? DGDFT_OK : DGDFT_ECUDA;
+}
+
 dgdft_status dgdft_dg_last_timing(dgdft_dg* dg, double* ms, int n, int* launches) {
-  if (!dg || (n > 0 && !ms) || n > 6) return DGDFT_EINVAL;
-  for (int i = 0; i < n; ++i) ms[i] = dg->ms[i];
+  if (!dg || (n > 0 && !ms) || n > 8) return DGDFT_EINVAL;
+  for (int i = 0; i < n; ++i) ms[i] = i < 6 ? dg->ms[i] : dg->density_ms[i - 6];
   if (launches) *launches = dg->launches;
   return DGDFT_OK;
 }

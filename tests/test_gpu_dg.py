@@ -11,6 +11,11 @@ size (J = 40, 32 x 42 x 80 LGL points; sampled block rows), the blocks built
 from a real ALB solve, the plane-wave spectrum through the GPU path (a closed
 form), batching and host/device input invariance, and the error for a mass
 matrix that is not positive definite.
+
+Density (Eq. density, dense diagonalisation of H^DG): eigenvalues and rho
+against the oracle on the small layer at an occupation with a spectral gap
+(rho is unique there), rho integrating to the number of states, and the
+closed-form uniform density of the lowest plane waves.
 """
 
 import numpy as np
@@ -272,4 +277,68 @@ def test_assemble_from_alb_solve():
     print(f"max cond(mass matrix) {kappa:.2e} over {len(touched)} elements: rtol {rtol:.1e}")
     compare_rows(d, ora, [0, 7], "monolayer ALBs", rtol)
     compare_invariants(d, ora, [0, 7], "monolayer ALBs", rtol)
+    d.close()
+
+
+def _gap_occupation(lam, lo, hi):
+    """An occupation in [lo, hi) with the largest gap above it."""
+    gaps = lam[lo:hi] - lam[lo - 1:hi - 1]
+    n = lo + int(np.argmax(gaps))
+    return n, float(lam[n] - lam[n - 1])
+
+
+def test_density_small_layer_matches_oracle():
+    dom = sdg.dg_small_layer()
+    blocks = [sdg.smooth_block(dom, k) for k in range(dom.n_elem)]
+    d = make_dg(dom)
+    load_inputs(d, dom)
+    d.dgdft_dg_assemble(blocks)
+    ora = OracleDG(dom, blocks)
+    H = odg.dense_matrix(dom, {k: ora.row(k) for k in range(dom.n_elem)}, dom.J)
+    lam_all = np.linalg.eigvalsh(0.5 * (H + H.T))
+    n_occ, gap = _gap_occupation(lam_all, 10, 40)
+    eig, rho = d.dgdft_dg_density(blocks, n_occ)
+    lam, rho_o = odg.density(dom, ora.A.phis, H, n_occ, dom.J)
+    e_err = np.max(np.abs(eig - lam)) / np.max(np.abs(lam))
+    r_err = max(np.max(np.abs(rho[k] - rho_o[k])) for k in range(dom.n_elem)) / max(
+        np.max(rho_o[k]) for k in range(dom.n_elem))
+    total = sum(float(ora.A.g(k).w @ rho[k]) for k in range(dom.n_elem))
+    timing, _ = d.dgdft_dg_last_timing()
+    print(f"density n_occ {n_occ} (gap {gap:.2e} Ha): eigenvalue rel error {e_err:.2e}, rho rel error "
+          f"{r_err:.2e}, integral {total:.12f}; ms {timing['density_eigensolve']:.2f} + "
+          f"{timing['density_evaluation']:.2f}")
+    assert e_err < 1e-11
+    # rho is the projector onto the lowest n_occ states: its error scales
+    # with rounding / gap
+    assert r_err < 1e-10 * max(1.0, 1.0 / gap)
+    assert abs(total - n_occ) < 1e-9 * n_occ
+    d.close()
+
+
+def test_density_of_planewaves_on_gpu():
+    dom = sdg.dg_small_cube(J=7)
+    ms = sorted([(a, b, c) for a in range(-1, 2) for b in range(-1, 2) for c in range(-1, 2)],
+                key=lambda m: (sum(v * v for v in m), m))
+    waves = []
+    for m in ms:
+        G = 2 * np.pi * np.asarray(m) / np.asarray(dom.cell)
+        if m == (0, 0, 0):
+            waves.append((G, 0.0))
+        elif m > (0, 0, 0):
+            waves += [(G, 0.0), (G, -np.pi / 2)]
+    waves = waves[:dom.J]
+    blocks = []
+    for k in range(dom.n_elem):
+        qo = dom.corner(k) - dom.e_off
+        ax = [qo[d] + np.arange(dom.nq[d]) * dom.lq[d] / dom.nq[d] for d in range(3)]
+        blocks.append(np.stack([np.cos(G[2] * ax[2][:, None, None] + G[1] * ax[1][None, :, None]
+                                       + G[0] * ax[0][None, None, :] + ph).reshape(-1) for G, ph in waves]))
+    d = B.DG(dom.ne, dom.cell, dom.q_span, dom.nq, dom.nl, dom.J, dom.alpha, 0)
+    d.dgdft_dg_assemble(blocks)
+    vol = float(np.prod(dom.cell))
+    for n_occ, level in ((1, 1.0), (dom.J, float(dom.J))):
+        eig, rho = d.dgdft_dg_density(blocks, n_occ)
+        err = np.max(np.abs(rho * vol / level - 1.0))
+        print(f"plane waves, {n_occ} states: max |rho V / n - 1| = {err:.2e}")
+        assert err < 1e-9
     d.close()
