@@ -242,7 +242,7 @@ def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0):
     density = {"n": dom.n_elem * dom.J, "n_occ": n_occ, "ms": round(d0.elapsed_time(d1), 2),
                "eigensolve_ms": round(dens_stage["density_eigensolve"], 2),
                "evaluation_ms": round(dens_stage["density_evaluation"], 2),
-               "eigensolver": "FP64 dense, one CTA (the Rayleigh-Ritz kernel)"}
+               "eigensolver": "FP64 one-sided Jacobi, one cooperative kernel over all SMs"}
     del rho
     d.close()
     stage_ms = {k: v for k, v in stage_ms.items() if not k.startswith("density")}

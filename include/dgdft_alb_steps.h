@@ -103,9 +103,12 @@ dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int
                                                int J, const double* x, double* phi,
                                                int on_device);
 
-/* The converged Ritz block of element `elem` after a solve: x is N_g x m
- * (the m = n_compute Ritz vectors, Euclidean-orthonormal, ascending Ritz
- * values).  DGDFT_ESTATE before a solve. */
+/* The converged Ritz block of element `elem` after a solve or SCF step: x is
+ * N_g x m (the m = n_compute Ritz vectors, Euclidean-orthonormal, ascending
+ * Ritz values), host or device per on_device.  Read from the host copy that
+ * keep_block = 1 keeps, else from the resident wave of a workload that fits
+ * one memory-admission wave (valid until the next solve or step).
+ * DGDFT_ESTATE before a solve, or when neither holds the block. */
 dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device);
 
 /* Gram product C = U^T V in FP64 that allocates nothing.  The paper has no

@@ -115,15 +115,16 @@ dgdft_status dgdft_dg_lgl_basis(dgdft_dg* dg, int elem, const double* z, int z_o
 /* Density (Eq. density) by dense diagonalisation of the assembled H^DG (the
  * DIAG route of Sec. II.B, for small systems): the lowest n_occ eigenpairs
  * of H^DG c = lambda c (the basis is orthonormal, so a standard problem) by
- * the library's FP64 dense eigensolver, then rho(x) = sum_{i < n_occ}
+ * an FP64 one-sided Jacobi eigensolver over the whole GPU (sweeps until no
+ * pair of columns has a cosine above sqrt(n) 1e-15, at most 40; DGDFT_ENOTCONV
+ * beyond), then rho(x) = sum_{i < n_occ}
  * |psi_i(x)|^2 with psi_i = sum_{K,j} c_{i;K,j} phi_{K,j}, one electron per
  * state as Eq. density is written, on every element's LGL grid.  z: the same
  * columns as the last assemble (z_on_device as there; the basis is rebuilt
  * from them).  eig: n_occ eigenvalues, ascending (host).  rho: n_elem x n_LGL
  * (element-major, x fastest; device when on_device, else host).
  * DGDFT_ESTATE before a successful assemble; DGDFT_EINVAL for n_occ outside
- * 1..n_elem J or n_elem J above 4096 (the dense eigensolver runs in one CTA:
- * seconds at a few thousand).                                              */
+ * 1..n_elem J or n_elem J above 4096.                                      */
 dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_device, int n_occ, double* eig,
                               double* rho, int on_device);
 

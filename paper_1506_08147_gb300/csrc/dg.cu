@@ -20,19 +20,21 @@
 //      every face;
 //   7. every block H_{K,K'} summed from its volume, KB and face terms.
 // Density (Eq. density, the DIAG route for small systems): H^DG scattered
-// into a dense matrix, its lowest eigenpairs by the library's FP64 dense
-// eigensolver (the one of the Rayleigh-Ritz step), the density matrix blocks
-// P_K = Y_K Y_K^T, and rho = sum_jj' phi_j P_K,jj' phi_j' on the LGL grids.
+// into a dense matrix, its eigenpairs by a one-sided Jacobi eigensolver over
+// the whole GPU (one cooperative kernel), the density matrix blocks
+// P_K = Y_K Y_K^T of the lowest n_occ, and rho = sum_jj' phi_j P_K,jj' phi_j'
+// on the LGL grids.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/dgdft_dg.h"
-#include "internal.h"
 
 namespace {
 
@@ -408,12 +410,6 @@ __global__ void dg_dense_kernel(const double* __restrict__ H, const int2* __rest
   A[((long long)kk.x * J + i) * n + (long long)kk.y * J + j] = H[(size_t)b * J * J + q];
 }
 
-__global__ void dg_identity_kernel(double* __restrict__ B, long long n) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * n;
-       q += (long long)gridDim.x * blockDim.x)
-    B[q] = (q / n == q % n) ? 1.0 : 0.0;
-}
-
 // P_K[j][j'] = sum_i Y[K J + j, i] Y[K J + j', i] (Y column-major n x m).
 __global__ void dg_dm_kernel(const double* __restrict__ Y, double* __restrict__ P, int J, long long n, int m) {
   const int k = blockIdx.y;
@@ -435,6 +431,153 @@ __global__ void dg_rho_kernel(const double* __restrict__ phi, const double* __re
     double s = 0.0;
     for (int j = 0; j < J; ++j) s = fma(phi[off + (size_t)j * nL + p], T[off + (size_t)j * nL + p], s);
     rho[(size_t)blockIdx.y * nL + p] = s;
+  }
+}
+
+// One-sided (Hestenes) Jacobi eigensolver for a symmetric matrix, FP64, over
+// the whole GPU.  B = A + sigma I is positive definite (sigma from a
+// Gershgorin bound); rotations of column pairs make the columns of W = B V
+// mutually orthogonal, so that at convergence w_i = lambda_i(B) v_i:
+// eigenvalues |w_i| - sigma, eigenvectors the columns of V.  Each sweep visits
+// every pair once in n_pad - 1 rounds of disjoint pairs (the round-robin
+// tournament: index 0 fixed, the others rotating); a warp rotates one pair,
+// and the grid synchronises between rounds (a cooperative launch, so every
+// CTA is resident).  The sweeps stop when no pair's cosine |w_i . w_j| /
+// (|w_i| |w_j|) exceeds tol, or after max_sweeps.  W and V are column-major
+// n x n; off[s] (zeroed by the host) collects sweep s's largest cosine.
+__device__ __forceinline__ int jacobi_player(int i, int r, int n_pad) {
+  return i == 0 ? 0 : 1 + (i - 1 + r) % (n_pad - 1);
+}
+
+constexpr int JC_THREADS = 128;
+
+__global__ void __launch_bounds__(JC_THREADS) dg_jacobi_kernel(double* __restrict__ W, double* __restrict__ V, int n,
+                                                               int n_pad, int max_sweeps, double tol,
+                                                               unsigned long long* __restrict__ off,
+                                                               int* __restrict__ sweeps) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[JC_THREADS / 32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int npairs = n_pad / 2;
+  int s = 0;
+  for (; s < max_sweeps; ++s) {
+    double worst = 0.0;
+    for (int r = 0; r < n_pad - 1; ++r) {
+      for (int k = blockIdx.x; k < npairs; k += gridDim.x) {
+        // pair k of round r: (pos k, pos n_pad - 1 - k) on the circle
+        int p = jacobi_player(k, r, n_pad), q = jacobi_player(n_pad - 1 - k, r, n_pad);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        if (q >= n) continue;  // the padding column of an odd n
+        double* wp = W + (size_t)p * n;
+        double* wq = W + (size_t)q * n;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = threadIdx.x; i < n; i += JC_THREADS) {
+          const double x = wp[i], y = wq[i];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (lane == 0) {
+          red[warp][0] = a;
+          red[warp][1] = b;
+          red[warp][2] = g;
+        }
+        __syncthreads();
+        a = b = g = 0.0;
+#pragma unroll
+        for (int w = 0; w < JC_THREADS / 32; ++w) {
+          a += red[w][0];
+          b += red[w][1];
+          g += red[w][2];
+        }
+        __syncthreads();  // red is reused by the next pair
+        if (a <= 0.0 || b <= 0.0) continue;
+        const double cosv = fabs(g) / sqrt(a * b);
+        worst = fmax(worst, cosv);
+        if (cosv <= tol) continue;
+        // the rotation that makes the two columns orthogonal
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        double* vp = V + (size_t)p * n;
+        double* vq = V + (size_t)q * n;
+        for (int i = threadIdx.x; i < n; i += JC_THREADS) {
+          const double x = wp[i], y = wq[i];
+          wp[i] = c * x - sn * y;
+          wq[i] = sn * x + c * y;
+          const double u = vp[i], w = vq[i];
+          vp[i] = c * u - sn * w;
+          vq[i] = sn * u + c * w;
+        }
+      }
+      grid.sync();
+    }
+    // the sweep's largest cosine (non-negative doubles order as their bits)
+    if (threadIdx.x == 0 && worst > 0.0) atomicMax(off + s, (unsigned long long)__double_as_longlong(worst));
+    grid.sync();
+    const double sweep_worst = __longlong_as_double((long long)*(volatile unsigned long long*)(off + s));
+    if (sweep_worst <= tol) {
+      ++s;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps = s;
+}
+
+// Gershgorin lower bound per row: a_ii - sum_{j != i} |a_ij| (row-major A).
+__global__ void dg_gershgorin_kernel(const double* __restrict__ A, long long n, double* __restrict__ lo) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = A + (size_t)warp * n;
+  double s = 0.0;
+  for (long long j = lane; j < n; j += 32)
+    if (j != warp) s += fabs(row[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) lo[warp] = row[warp] - s;
+}
+
+// W = A + sigma I (column-major; A symmetric), V = I.
+__global__ void dg_jacobi_init_kernel(const double* __restrict__ A, double* __restrict__ W, double* __restrict__ V,
+                                      long long n, double sigma) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i = q % n, j = q / n;
+    W[q] = A[i * n + j] + (i == j ? sigma : 0.0);
+    V[q] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+// |w_i| per column (one warp each).
+__global__ void dg_colnorm_kernel(const double* __restrict__ W, long long n, double* __restrict__ nrm) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* col = W + (size_t)warp * n;
+  double s = 0.0;
+  for (long long i = lane; i < n; i += 32) s = fma(col[i], col[i], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) nrm[warp] = sqrt(s);
+}
+
+// Y[:, c] = V[:, order[c]] for the lowest m (column-major, n rows).
+__global__ void dg_gather_kernel(const double* __restrict__ V, const int* __restrict__ order, double* __restrict__ Y,
+                                 long long n, int m) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * m;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long c = q / n, i = q % n;
+    Y[q] = V[(size_t)order[c] * n + i];
   }
 }
 
@@ -567,6 +710,7 @@ struct dgdft_dg {
   bool assembled = false;
   double ms[6]{};
   double density_ms[2]{};  // eigensolve, density evaluation
+  int density_sweeps = 0;  // Jacobi sweeps of the last density
   int launches = 0;
   // batch scratch
   int batch = 0;
@@ -918,7 +1062,6 @@ dgdft_status dgdft_dg_create(const dgdft_dg_config* cfg, dgdft_dg** out) {
       cudaFuncSetAttribute(dg_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(c.J * c.J * sizeof(double))) != cudaSuccess)
     return dg->fail(DGDFT_ECUDA, "kernel attributes");
-  dgdft::init_rr_kernels();
   // tables
   std::vector<double> hI[3], hD[3];
   for (int d = 0; d < 3; ++d) {
@@ -1402,61 +1545,89 @@ dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_dev
     if (!z[k]) return dg->fail(DGDFT_EINVAL, "density: z[" + std::to_string(k) + "] is NULL");
   if (!dg->assembled) return dg->fail(DGDFT_ESTATE, "density before a successful assemble");
   const size_t JJ = (size_t)J * J;
-  double *dA = nullptr, *dB = nullptr, *dY = nullptr, *dth = nullptr, *work = nullptr, *dP = nullptr,
-         *drho = nullptr;
+  double *dA = nullptr, *dW = nullptr, *dV = nullptr, *dY = nullptr, *dlo = nullptr, *dnrm = nullptr,
+         *dP = nullptr, *drho = nullptr;
   int2* dkk = nullptr;
-  dgdft::RRTask* dt = nullptr;
+  int *dord = nullptr, *dsweeps = nullptr;
+  unsigned long long* doff = nullptr;
+  constexpr int MAX_SWEEPS = 40;
   auto release = [&]() {
-    for (void* p : {(void*)dA, (void*)dB, (void*)dY, (void*)dth, (void*)work, (void*)dP, (void*)drho, (void*)dkk,
-                    (void*)dt})
+    for (void* p : {(void*)dA, (void*)dW, (void*)dV, (void*)dY, (void*)dlo, (void*)dnrm, (void*)dP, (void*)drho,
+                    (void*)dkk, (void*)dord, (void*)dsweeps, (void*)doff})
       cudaFree(p);
   };
   std::vector<int2> kk;
   for (int k = 0; k < nel; ++k)
     for (int k2 : dg->nb[k]) kk.push_back(make_int2(k, k2));
-  if (!dmalloc(&dA, (size_t)(n * n)) || !dmalloc(&dB, (size_t)(n * n)) || !dmalloc(&dY, (size_t)(n * n_occ)) ||
-      !dmalloc(&dth, (size_t)n_occ) || !dmalloc(&work, dgdft::rr_work_doubles((int)n, n_occ)) ||
-      !dmalloc(&dP, (size_t)nel * JJ) || !dmalloc(&dt, 1) || !upload(dg, &dkk, kk) ||
+  if (!dmalloc(&dA, (size_t)(n * n)) || !dmalloc(&dW, (size_t)(n * n)) || !dmalloc(&dV, (size_t)(n * n)) ||
+      !dmalloc(&dY, (size_t)(n * n_occ)) || !dmalloc(&dlo, (size_t)n) || !dmalloc(&dnrm, (size_t)n) ||
+      !dmalloc(&dP, (size_t)nel * JJ) || !dmalloc(&dord, (size_t)n_occ) || !dmalloc(&dsweeps, 1) ||
+      !dmalloc(&doff, (size_t)MAX_SWEEPS) || !upload(dg, &dkk, kk) ||
       (!on_device && !dmalloc(&drho, (size_t)nel * dg->nL))) {
     release();
     return dg->fail(DGDFT_ENOMEM, "density storage");
   }
   double t_ms[2] = {0.0, 0.0};
-  bool ok = cuda_ok(dg, cudaMemsetAsync(dA, 0, sizeof(double) * n * n, dg->st), "density");
+  bool ok = cuda_ok(dg, cudaMemsetAsync(dA, 0, sizeof(double) * n * n, dg->st), "density") &&
+            cuda_ok(dg, cudaMemsetAsync(doff, 0, sizeof(unsigned long long) * MAX_SWEEPS, dg->st), "density");
   {
     Timer tm(dg->st);
+    const unsigned gx = (unsigned)((JJ + 255) / 256);
+    const unsigned gw = (unsigned)((n * 32 + 255) / 256);
+    std::vector<double> lo(n), lam(n);
     if (ok) {
-      const unsigned gx = (unsigned)((JJ + 255) / 256);
       dg_dense_kernel<<<dim3(gx, dg->nblk), 256, 0, dg->st>>>(dg->d_H, dkk, dA, J, n);
-      dg_identity_kernel<<<1024, 256, 0, dg->st>>>(dB, n);
-      dgdft::RRTask t{};
-      t.A = dA;
-      t.B = dB;
-      t.ld = (int)n;
-      t.mode = dgdft::RR_FIXED;
-      t.n_fixed = (int)n;
-      t.m = n_occ;
-      t.Y = dY;
-      t.ldy = (int)n;
-      t.theta = dth;
-      t.work = work;
-      t.state = nullptr;
-      t.cond_max = 1e30;
-      ok = cuda_ok(dg, cudaMemcpyAsync(dt, &t, sizeof(t), cudaMemcpyHostToDevice, dg->st), "density task");
-      if (ok) {
-        dgdft::launch_rr(dt, 1, dg->st, (int)n, n_occ);
-        dg_dm_kernel<<<dim3(gx, nel), 256, 0, dg->st>>>(dY, dP, J, n, n_occ);
-      }
-      ok = ok && cuda_ok(dg, cudaGetLastError(), "density eigensolve") &&
-           cuda_ok(dg, cudaMemcpyAsync(eig, dth, sizeof(double) * n_occ, cudaMemcpyDeviceToHost, dg->st),
+      dg_gershgorin_kernel<<<gw, 256, 0, dg->st>>>(dA, n, dlo);
+      ok = cuda_ok(dg, cudaGetLastError(), "density matrix") &&
+           cuda_ok(dg, cudaMemcpyAsync(lo.data(), dlo, sizeof(double) * n, cudaMemcpyDeviceToHost, dg->st),
+                   "Gershgorin bound") &&
+           cuda_ok(dg, cudaStreamSynchronize(dg->st), "Gershgorin bound");
+    }
+    int sweeps = 0;
+    if (ok) {
+      // B = A + sigma I with every eigenvalue >= 1
+      const double sigma = std::max(0.0, 1.0 - *std::min_element(lo.begin(), lo.end()));
+      dg_jacobi_init_kernel<<<1024, 256, 0, dg->st>>>(dA, dW, dV, n, sigma);
+      int occ = 0, nsm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dg_jacobi_kernel, JC_THREADS, 0);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dg->cfg.device);
+      const int n_pad = (int)(n + (n & 1));
+      const int grid = std::max(1, std::min(n_pad / 2, std::max(1, occ) * std::max(1, nsm)));
+      int nn = (int)n, maxs = MAX_SWEEPS;
+      // stop at a pair cosine of sqrt(n) 1e-15 (the columns' rounding level)
+      double tol = std::sqrt((double)n) * 1e-15;
+      void* args[] = {&dW, &dV, &nn, (void*)&n_pad, &maxs, &tol, &doff, &dsweeps};
+      ok = cuda_ok(dg, cudaLaunchCooperativeKernel((const void*)dg_jacobi_kernel, grid, JC_THREADS, args, 0, dg->st),
+                   "Jacobi eigensolver");
+      dg_colnorm_kernel<<<gw, 256, 0, dg->st>>>(dW, n, dnrm);
+      ok = ok && cuda_ok(dg, cudaGetLastError(), "Jacobi eigensolver") &&
+           cuda_ok(dg, cudaMemcpyAsync(lam.data(), dnrm, sizeof(double) * n, cudaMemcpyDeviceToHost, dg->st),
                    "eigenvalues") &&
-           cuda_ok(dg, cudaStreamSynchronize(dg->st), "density eigensolve");
+           cuda_ok(dg, cudaMemcpyAsync(&sweeps, dsweeps, sizeof(int), cudaMemcpyDeviceToHost, dg->st), "sweeps") &&
+           cuda_ok(dg, cudaStreamSynchronize(dg->st), "Jacobi eigensolver");
+      if (ok) {
+        for (double& v : lam) v -= sigma;
+        std::vector<int> order(n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lam[x] < lam[y]; });
+        order.resize(n_occ);
+        for (int i = 0; i < n_occ; ++i) eig[i] = lam[order[i]];
+        ok = cuda_ok(dg, cudaMemcpyAsync(dord, order.data(), sizeof(int) * n_occ, cudaMemcpyHostToDevice, dg->st),
+                     "order");
+        if (ok) {
+          dg_gather_kernel<<<1024, 256, 0, dg->st>>>(dV, dord, dY, n, n_occ);
+          dg_dm_kernel<<<dim3(gx, nel), 256, 0, dg->st>>>(dY, dP, J, n, n_occ);
+          ok = cuda_ok(dg, cudaGetLastError(), "density matrix blocks") &&
+               cuda_ok(dg, cudaStreamSynchronize(dg->st), "density matrix blocks");
+        }
+      }
+    }
+    dg->density_sweeps = sweeps;
+    if (ok && sweeps >= MAX_SWEEPS) {
+      release();
+      return dg->fail(DGDFT_ENOTCONV, "density: the Jacobi sweeps did not converge");
     }
     t_ms[0] = tm.stop();
-  }
-  if (ok && !std::isfinite(eig[0])) {
-    dg->err = "density: the eigensolver failed";
-    ok = false;
   }
   // density on each batch: phi from z again, then T = P_K phi and rho
   size_t cap = dg->cfg.hbm_cap_bytes;

@@ -295,8 +295,25 @@ template <class real> struct Wave {
   long long graph_kernels = 0;  // kernel nodes launched through graphs by run()
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // Instantiated iteration graphs kept across runs (solves and SCF steps):
+  // every pointer their nodes hold belongs to the wave, so they stay valid
+  // for its life.  Keyed by what changes the nodes: the residual kernel's
+  // iteration cap, the precise-H X' variant, the FP64 forward transform and
+  // the restart budget.
+  struct GraphSet {
+    int maxit = 0, precise = 0, fwd = 0, restart = 0;
+    cudaGraphExec_t exec = nullptr, exec2 = nullptr, pexec = nullptr, pexec2 = nullptr;
+    long long nodes1 = 0, nodes2 = 0;
+  };
+  std::vector<GraphSet> graphs;
 
   ~Wave() {
+    for (GraphSet& g : graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.exec2) cudaGraphExecDestroy(g.exec2);
+      if (g.pexec) cudaGraphExecDestroy(g.pexec);
+      if (g.pexec2) cudaGraphExecDestroy(g.pexec2);
+    }
     if (arena.base) cudaFree(arena.base);
     for (float* p : {nn_in, nn_out, nn_tmp0, nn_tmp1})
       if (p) cudaFree(p);
@@ -1036,6 +1053,15 @@ template <class real> struct Wave {
     cudaGraphExec_t exec = nullptr, exec2 = nullptr;
     long long nodes1 = 0, nodes2 = 0;
     cudaError_t ce = cudaSuccess;
+    // graphs of an earlier run with the same key are launched again (the
+    // learned preconditioner's buffers belong to the context: not cached)
+    const int want_precise = (precise_below > 0.0 && !fwd64()) ? 1 : 0;
+    const bool cacheable = !learned;
+    GraphSet* cached = nullptr;
+    if (cacheable)
+      for (GraphSet& g : graphs)
+        if (g.maxit == maxit && g.precise == want_precise && g.fwd == (int)fwd64() && g.restart == restart_max)
+          cached = &g;
     auto capture = [&](cudaStream_t cs, int which, int order, cudaGraphExec_t* out) -> cudaError_t {
       cudaGraph_t graph = nullptr;
       if (which >= 0) use(sub[which]);
@@ -1057,9 +1083,7 @@ template <class real> struct Wave {
       cudaGraphDestroy(graph);
       return e;
     };
-    if (!split) {
-      ce = capture(st, -1, 0, &exec);
-    } else {
+    if (split) {
       // the second half starts with its front part, then iterates
       // back + front: half an iteration behind the first half
       CK(cudaEventRecord(ev_fork, st));
@@ -1067,13 +1091,24 @@ template <class real> struct Wave {
       use(sub[1]);
       enqueue_front(st2, maxit);
       use(full);
+    }
+    cudaGraphExec_t pexec = nullptr, pexec2 = nullptr;
+    if (cached) {
+      exec = cached->exec;
+      exec2 = cached->exec2;
+      pexec = cached->pexec;
+      pexec2 = cached->pexec2;
+      nodes1 = cached->nodes1;
+      nodes2 = cached->nodes2;
+    } else if (!split) {
+      ce = capture(st, -1, 0, &exec);
+    } else {
       ce = capture(st, 0, 0, &exec);
       if (ce == cudaSuccess) ce = capture(st2, 1, 1, &exec2);
     }
     // the same iteration with the precise H X' (captured up front; the node
     // counts are equal)
-    cudaGraphExec_t pexec = nullptr, pexec2 = nullptr;
-    if (ce == cudaSuccess && precise_below > 0.0 && !fwd64()) {
+    if (!cached && ce == cudaSuccess && want_precise) {
       hx64 = true;
       const long long n1 = nodes1, n2 = nodes2;
       ce = split ? capture(st, 0, 0, &pexec) : capture(st, -1, 0, &pexec);
@@ -1098,6 +1133,21 @@ template <class real> struct Wave {
         cudaStreamWaitEvent(st, ev_join, 0);
       }
       return ctx->fail(DGDFT_ECUDA, "graph capture: " + cuda_err_string(ce));
+    }
+    if (!cached && cacheable) {
+      GraphSet g;
+      g.maxit = maxit;
+      g.precise = want_precise;
+      g.fwd = (int)fwd64();
+      g.restart = restart_max;
+      g.exec = exec;
+      g.exec2 = exec2;
+      g.pexec = pexec;
+      g.pexec2 = pexec2;
+      g.nodes1 = nodes1;
+      g.nodes2 = nodes2;
+      graphs.push_back(g);
+      cached = &graphs.back();
     }
     const int nel = (int)ids.size();
     const int every = std::max(1, ctx->cfg.check_every);
@@ -1204,10 +1254,12 @@ template <class real> struct Wave {
         if (active_res[active_res.size() / 2] < precise_below) precise = true;
       }
     }
-    cudaGraphExecDestroy(exec);
-    if (exec2) cudaGraphExecDestroy(exec2);
-    if (pexec) cudaGraphExecDestroy(pexec);
-    if (pexec2) cudaGraphExecDestroy(pexec2);
+    if (!cached) {
+      cudaGraphExecDestroy(exec);
+      if (exec2) cudaGraphExecDestroy(exec2);
+      if (pexec) cudaGraphExecDestroy(pexec);
+      if (pexec2) cudaGraphExecDestroy(pexec2);
+    }
     if (split) {
       // later work on the caller's stream sees the second half's results
       cudaEventRecord(ev_join, st2);
@@ -1963,13 +2015,29 @@ void dgdft_alb_destroy(dgdft_alb_ctx* ctx) {
 dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device) {
   if (!ctx || !x || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
   ElemHost& eh = ctx->el[elem];
-  if (!eh.solved || eh.block.empty()) return ctx->fail(DGDFT_ESTATE, "no Ritz block kept (solve with keep_block)");
-  if (on_device) {
-    CK(ctx_copy(ctx, x, eh.block.data(), sizeof(double) * eh.block.size(), cudaMemcpyHostToDevice));
-  } else {
-    std::memcpy(x, eh.block.data(), sizeof(double) * eh.block.size());
+  if (!eh.solved) return ctx->fail(DGDFT_ESTATE, "get_block before a solve");
+  if (!eh.block.empty()) {
+    if (on_device) {
+      CK(ctx_copy(ctx, x, eh.block.data(), sizeof(double) * eh.block.size(), cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(x, eh.block.data(), sizeof(double) * eh.block.size());
+    }
+    return DGDFT_OK;
   }
-  return DGDFT_OK;
+  // no host copy: the FP64 wave of a single-wave workload stays resident
+  // with the final block of the last solve or SCF step
+  if (ctx->cache) {
+    const WavePair* wp = static_cast<const WavePair*>(ctx->cache);
+    const Wave<double>& w = *wp->w64;
+    for (size_t i = 0; i < w.ids.size(); ++i) {
+      if (w.ids[i] != elem) continue;
+      const size_t n = (size_t)eh.ng() * eh.d.n_compute;
+      CK(ctx_copy(ctx, x, w.current_x((int)i), sizeof(double) * n,
+                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+      return DGDFT_OK;
+    }
+  }
+  return ctx->fail(DGDFT_ESTATE, "no Ritz block: solve with keep_block, or keep the workload in one wave");
 }
 
 }  // extern "C"

@@ -241,8 +241,8 @@ def test_assemble_from_alb_solve():
     torch = pytest.importorskip("torch")
     import synth
     els = synth.config2()
-    ctx = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_MIXED, tol=1e-6, maxit=600,
-                    keep_block=True)
+    # no keep_block: the blocks are read from the resident wave on the device
+    ctx = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_MIXED, tol=1e-6, maxit=600)
     for k, e in enumerate(els):
         B.load_element(ctx, k, e, synth.initial_block(e))
     st, rep = ctx.dgdft_alb_solve()
@@ -341,4 +341,28 @@ def test_density_of_planewaves_on_gpu():
         err = np.max(np.abs(rho * vol / level - 1.0))
         print(f"plane waves, {n_occ} states: max |rho V / n - 1| = {err:.2e}")
         assert err < 1e-9
+    d.close()
+
+
+def test_density_eigensolver_monolayer_scale():
+    """n = 36 x 40 = 1440: the GPU eigenvalues of the assembled H^DG against
+    numpy's dense eigvalsh of the same (GPU) blocks, and rho integrating to
+    n_occ under the quadrature."""
+    dom = sdg.dg_config2()
+    blocks = [sdg.smooth_block(dom, k) for k in range(dom.n_elem)]
+    d = make_dg(dom)
+    load_inputs(d, dom)
+    d.dgdft_dg_assemble(blocks)
+    rows = {k: d.dgdft_dg_get_row(k) for k in range(dom.n_elem)}
+    H = odg.dense_matrix(dom, rows, dom.J)
+    lam = np.linalg.eigvalsh(0.5 * (H + H.T))
+    n_occ = dom.n_elem * dom.J // 2
+    eig, rho = d.dgdft_dg_density(blocks, n_occ)
+    timing, _ = d.dgdft_dg_last_timing()
+    err = np.max(np.abs(eig - lam[:n_occ])) / np.max(np.abs(lam))
+    total = sum(float(odg.ElementGrid(dom, k).w @ rho[k]) for k in range(dom.n_elem))
+    print(f"n = {H.shape[0]}, n_occ = {n_occ}: eigenvalue error {err:.2e} of max |lambda| "
+          f"{np.max(np.abs(lam)):.1f}; integral {total:.10f}; eigensolve {timing['density_eigensolve']:.1f} ms")
+    assert err < 1e-12
+    assert abs(total - n_occ) < 1e-8 * n_occ
     d.close()

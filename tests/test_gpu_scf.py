@@ -172,6 +172,17 @@ def test_scf_step_monolayer_mixed():
         print(f"SCF step, element {[0, 32][k]}: max residual of the starting Ritz pairs {r0:.3e}, "
               f"after {np.max(got):.3e} (oracle {np.max(ref['res'][:e.J]):.3e})")
         assert np.max(got) <= max(1.5 * np.max(ref["res"][:e.J]), 5e-6)
+    # the same step again from the same block and potential: the iteration
+    # graphs captured by the first step are launched again and give bitwise
+    # the same ALBs, eigenvalues and residuals
+    first = [c.dgdft_alb_get_basis(k) for k in range(len(els0))]
+    for k in range(len(els0)):
+        c.dgdft_alb_set_initial(k, np.ascontiguousarray(blocks[k]))
+    st, reps2 = c.dgdft_alb_scf_step(N_ITER)
+    assert st == B.DGDFT_OK
+    for k in range(len(els0)):
+        for a, b in zip(first[k], c.dgdft_alb_get_basis(k)):
+            assert np.array_equal(a, b)
     c.close()
 
 
