@@ -66,9 +66,9 @@ enum {
                            or compensated SIMT (see bulk_kernels), the
                            Rayleigh-Ritz in double-float, ~2^-46), then the
                            FP64 check and FP64-accurate iterations to the
-                           tolerance (FP64 storage and Rayleigh-Ritz,
+                           tolerance (FP64 storage and residuals,
                            double-float FFT passes, Gram and update
-                           products, ~2^-46 relative)                      */
+                           products and Rayleigh-Ritz, ~2^-46 relative)    */
 };
 
 enum {

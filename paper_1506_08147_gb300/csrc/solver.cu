@@ -918,7 +918,11 @@ template <class real> struct Wave {
     g.out_id[1] = OUT_GRAM_B;
     for (int k = 0; k < 2; ++k) g.needs_p[k] = g.brow[k] = g.bcol[k] = 0;
     launch_gram<real>(batch, g, partial, partial_cap, st);
-    launch_rr(d_rr_init, batch.s.nel, st, batch.s.max_m, batch.s.max_m, std::is_same<real, float>::value);
+    // double-float reduction in the FP32 stage and in the mixed form's
+    // FP64-accurate stage (its pencils carry the double-float Gram's ~2^-44
+    // rounding; the reduction's ~2^-46 adds nothing), FP64 otherwise
+    launch_rr(d_rr_init, batch.s.nel, st, batch.s.max_m, batch.s.max_m,
+              std::is_same<real, float>::value || batch.s.dfloat);
     TsmmJob<real> t;
     t.nin = 1;
     t.in[0] = bref<real>(BX);
@@ -959,7 +963,8 @@ template <class real> struct Wave {
 
   // Rayleigh-Ritz and the block updates (operations 3, 4; H X for FP32).
   void enqueue_back(cudaStream_t st) {
-    launch_rr(d_rr_lob, batch.s.nel, st, 3 * batch.s.max_m, batch.s.max_m, std::is_same<real, float>::value);
+    launch_rr(d_rr_lob, batch.s.nel, st, 3 * batch.s.max_m, batch.s.max_m,
+              std::is_same<real, float>::value || batch.s.dfloat);
     {
       TsmmJob<real> t;
       t.nin = 3;
