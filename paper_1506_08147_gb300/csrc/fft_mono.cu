@@ -5,7 +5,9 @@
 // (the Teter preconditioner), the same three passes over HBM as the general
 // kernels, but with the short transforms held in registers instead of
 // shared-memory stages separated by barriers:
-//   fwd : 4 z-planes of one vector per CTA; each thread owns one x row
+//   fwd : one z-plane of one vector per CTA (64 threads, 14.4 KB of shared
+//         memory, 12 CTAs per SM, so that the load, transform and store
+//         phases of different CTAs overlap); each thread owns one x row
 //         (48 reals -> 24-point complex FFT in registers -> r2c split to 25
 //         complex), then the 64-point y lines as an 8 x 8 four-step transform
 //         inside a warp (8 lanes per line, __syncwarp only);
@@ -29,14 +31,15 @@ namespace dgdft {
 namespace {
 
 constexpr int MX = 48, MH = 24, MXH = 25, MY = 64;
-constexpr int MPL = 4;                  // z-planes per CTA (nz % 4 == 0)
+constexpr int MPL = 1;                  // z-planes per CTA (nz % MPL == 0)
 constexpr int MLINE = 72;               // padded y line: position y + y / 8
 constexpr int MROW = 52;                // padded real row (48 + 4): conflict-free float4 rows
 constexpr int MPLANE = MX * MY;         // 3072 reals per plane
 constexpr int MSPEC = MXH * MY;         // 1600 complex per plane of the half spectrum
-constexpr int MTHREADS = 256;           // one thread per row of the 4 planes
+constexpr int MTHREADS = 64 * MPL;      // one thread per row of the CTA's planes
+constexpr int MCTAS = 12 / MPL;         // CTAs per SM (shared memory, registers)
 constexpr int ZTHREADS = 160;           // z pass: 10 CTAs x 160 = 1600 columns
-constexpr size_t MSMEM = sizeof(float2) * MPL * MXH * MLINE;  // 57,600 B (the real planes alias it)
+constexpr size_t MSMEM = sizeof(float2) * MPL * MXH * MLINE;  // 14,400 B per plane (the real rows alias it)
 
 __constant__ float2 c_w48[48];
 __constant__ float2 c_w64[64];
@@ -141,7 +144,7 @@ __device__ __forceinline__ bool live(const ElemDev<float>& e, int filt) {
   return e.state[ST_ACTIVE] != 0 && (filt == 0 || e.state[ST_TETER] != 0);
 }
 
-// The 64-point y transforms of the 4 x 25 lines of a CTA's planes, in place
+// The 64-point y transforms of the MPL x 25 lines of a CTA's planes, in place
 // in the padded line layout.  Lane group g = lane / 8 of a warp takes one
 // line, lane q = lane % 8 its points q + 8 i (four-step: an 8-point DFT over
 // i, the twiddle w64^(q k1), an 8-point DFT over q).  Every thread calls it.
@@ -186,7 +189,7 @@ __device__ __forceinline__ void load_w64(float2* w64s) {
 }
 
 // Pass 1.  grid (nz / 4, columns, elements), 256 threads.
-__global__ void __launch_bounds__(MTHREADS, 3)
+__global__ void __launch_bounds__(MTHREADS, MCTAS)
     mono_fwd_kernel(const ElemDev<float>* __restrict__ elems, BRef<float> src, int ncols, int filt, int nz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float2 w64s[64];
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(ZTHREADS)
 
 // Pass 3.  grid (nz / 4, columns, elements), 256 threads.
 template <int MODE>
-__global__ void __launch_bounds__(MTHREADS, 3)
+__global__ void __launch_bounds__(MTHREADS, MCTAS)
     mono_inv_kernel(const ElemDev<float>* __restrict__ elems, BRef<float> dst, BRef<float> xsrc, int ncols,
                     int filt, int nz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -334,12 +337,12 @@ __global__ void __launch_bounds__(MTHREADS, 3)
   float4* out4 = reinterpret_cast<float4*>(resolve(e, dst) + off);
   if (MODE == XI_HAMILTONIAN) {
     if (e.n_sup > 0) {
-      // Kleinman-Bylander scatter: each support point of the 4 planes once.
+      // Kleinman-Bylander scatter: each support point of the CTA's planes once.
       // The coefficients of column j go to the shared-memory tail past the
       // rows (free once the spectrum is consumed); each thread takes SU
       // points at a time and their nonzeros four at a time, so the loads of
       // different points are in flight together.
-      constexpr int CTAIL = (int)(MSMEM / sizeof(float)) - MPL * MY * MROW;
+      constexpr int CTAIL = (int)(MSMEM / sizeof(float)) - MPL * MY * MROW;  // may be < 0: not staged
       constexpr int SU = 4;
       float* ctail = rows + MPL * MY * MROW;
       const float* cg = e.Ccoef + (size_t)j * e.n_proj;
@@ -347,8 +350,10 @@ __global__ void __launch_bounds__(MTHREADS, 3)
       if (staged)
         for (int q = threadIdx.x; q < e.n_proj; q += MTHREADS) ctail[q] = cg[q];
       const float* cj = staged ? ctail : cg;
-      const int sb = e.s_plane[z0], b1 = e.s_plane[z0 + 1], b2 = e.s_plane[z0 + 2], b3 = e.s_plane[z0 + 3];
-      const int se = e.s_plane[z0 + MPL];
+      const int sb = e.s_plane[z0], se = e.s_plane[z0 + MPL];
+      int bnd[MPL > 1 ? MPL - 1 : 1];  // first support point of planes 1 .. MPL - 1
+#pragma unroll
+      for (int i = 0; i < MPL - 1; ++i) bnd[i] = e.s_plane[z0 + 1 + i];
       __syncthreads();
       for (int s0 = sb + threadIdx.x; s0 < se; s0 += SU * MTHREADS) {
         int qb[SU], qe[SU], o[SU];
@@ -396,7 +401,9 @@ __global__ void __launch_bounds__(MTHREADS, 3)
         for (int u = 0; u < SU; ++u) {
           const int s = s0 + u * MTHREADS;
           if (s < se) {
-            const int pz = (s >= b1) + (s >= b2) + (s >= b3);
+            int pz = 0;
+#pragma unroll
+            for (int i = 0; i < MPL - 1; ++i) pz += s >= bnd[i];
             const int yy = o[u] / MX, xx = o[u] - yy * MX;
             rows[(pz * MY + yy) * MROW + xx] += acc[u];
           }
