@@ -240,6 +240,7 @@ def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0):
     torch.cuda.synchronize()
     dens_stage, _ = d.dgdft_dg_last_timing()
     density = {"n": dom.n_elem * dom.J, "n_occ": n_occ, "ms": round(d0.elapsed_time(d1), 2),
+               "sweeps": d.dgdft_dg_density_info(),
                "eigensolve_ms": round(dens_stage["density_eigensolve"], 2),
                "evaluation_ms": round(dens_stage["density_evaluation"], 2),
                "eigensolver": "FP64 one-sided Jacobi, one cooperative kernel over all SMs"}

@@ -128,6 +128,9 @@ dgdft_status dgdft_dg_lgl_basis(dgdft_dg* dg, int elem, const double* z, int z_o
 dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_device, int n_occ, double* eig,
                               double* rho, int on_device);
 
+/* Sweeps of the Jacobi eigensolver in the last dgdft_dg_density (host int). */
+dgdft_status dgdft_dg_density_info(dgdft_dg* dg, int* sweeps);
+
 /* Kernel time of the last assembly per stage (CUDA events on the stream):
  * ms[0] interpolation, ms[1] orthonormalisation and gradients, ms[2] volume
  * integrals, ms[3] face traces and KB coefficients, ms[4] face integrals,

@@ -100,6 +100,7 @@ _SIGS = {
     "dgdft_dg_get_row": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "dgdft_dg_lgl_basis": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int]),
     "dgdft_dg_density": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "dgdft_dg_density_info": (C.c_int, [_P, _P]),
     "dgdft_dg_last_timing": (C.c_int, [_P, _P, C.c_int, _P]),
     "dgdft_dg_last_error": (C.c_char_p, [_P]),
     "dgdft_dg_destroy": (None, [_P]),
@@ -568,6 +569,12 @@ class DG:
         phi = np.zeros((self.J, self.n_lgl))
         self._check(self.lib.dgdft_dg_lgl_basis(self.h, elem, _ptr(z)[0], 0, _ptr(phi)[0], 0), "lgl_basis")
         return phi
+
+    def dgdft_dg_density_info(self):
+        """Sweeps of the Jacobi eigensolver in the last density call."""
+        n = C.c_int()
+        self._check(self.lib.dgdft_dg_density_info(self.h, C.byref(n)), "density_info")
+        return n.value
 
     def dgdft_dg_last_timing(self):
         ms = np.zeros(8)

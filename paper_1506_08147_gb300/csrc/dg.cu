@@ -1699,6 +1699,12 @@ dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_dev
   return ok ? DGDFT_OK : DGDFT_ECUDA;
 }
 
+dgdft_status dgdft_dg_density_info(dgdft_dg* dg, int* sweeps) {
+  if (!dg || !sweeps) return DGDFT_EINVAL;
+  *sweeps = dg->density_sweeps;
+  return DGDFT_OK;
+}
+
 dgdft_status dgdft_dg_last_timing(dgdft_dg* dg, double* ms, int n, int* launches) {
   if (!dg || (n > 0 && !ms) || n > 8) return DGDFT_EINVAL;
   for (int i = 0; i < n; ++i) ms[i] = i < 6 ? dg->ms[i] : dg->density_ms[i - 6];

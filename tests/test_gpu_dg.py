@@ -361,8 +361,11 @@ def test_density_eigensolver_monolayer_scale():
     timing, _ = d.dgdft_dg_last_timing()
     err = np.max(np.abs(eig - lam[:n_occ])) / np.max(np.abs(lam))
     total = sum(float(odg.ElementGrid(dom, k).w @ rho[k]) for k in range(dom.n_elem))
+    sweeps = d.dgdft_dg_density_info()
     print(f"n = {H.shape[0]}, n_occ = {n_occ}: eigenvalue error {err:.2e} of max |lambda| "
-          f"{np.max(np.abs(lam)):.1f}; integral {total:.10f}; eigensolve {timing['density_eigensolve']:.1f} ms")
+          f"{np.max(np.abs(lam)):.1f}; integral {total:.10f}; eigensolve {timing['density_eigensolve']:.1f} ms, "
+          f"{sweeps} Jacobi sweeps")
+    assert 0 < sweeps < 40
     assert err < 1e-12
     assert abs(total - n_occ) < 1e-8 * n_occ
     d.close()
