@@ -438,20 +438,21 @@ __global__ void dg_rho_kernel(const double* __restrict__ phi, const double* __re
 // the whole GPU.  B = A + sigma I is positive definite (sigma from a
 // Gershgorin bound); rotations of column pairs make the columns of W = B V
 // mutually orthogonal, so that at convergence w_i = lambda_i(B) v_i:
-// eigenvalues |w_i| - sigma, eigenvectors the columns of V.  Each sweep visits
+// eigenvalues |w_i| - sigma, eigenvectors w_i / |w_i| (V itself is never
+// formed).  Each sweep visits
 // every pair once in n_pad - 1 rounds of disjoint pairs (the round-robin
-// tournament: index 0 fixed, the others rotating); a warp rotates one pair,
+// tournament: index 0 fixed, the others rotating); a CTA rotates one pair,
 // and the grid synchronises between rounds (a cooperative launch, so every
 // CTA is resident).  The sweeps stop when no pair's cosine |w_i . w_j| /
-// (|w_i| |w_j|) exceeds tol, or after max_sweeps.  W and V are column-major
-// n x n; off[s] (zeroed by the host) collects sweep s's largest cosine.
+// (|w_i| |w_j|) exceeds tol, or after max_sweeps.  W is column-major n x n;
+// off[s] (zeroed by the host) collects sweep s's largest cosine.
 __device__ __forceinline__ int jacobi_player(int i, int r, int n_pad) {
   return i == 0 ? 0 : 1 + (i - 1 + r) % (n_pad - 1);
 }
 
 constexpr int JC_THREADS = 128;
 
-__global__ void __launch_bounds__(JC_THREADS) dg_jacobi_kernel(double* __restrict__ W, double* __restrict__ V, int n,
+__global__ void __launch_bounds__(JC_THREADS) dg_jacobi_kernel(double* __restrict__ W, int n,
                                                                int n_pad, int max_sweeps, double tol,
                                                                unsigned long long* __restrict__ off,
                                                                int* __restrict__ sweeps) {
@@ -510,15 +511,10 @@ __global__ void __launch_bounds__(JC_THREADS) dg_jacobi_kernel(double* __restric
         const double zeta = (b - a) / (2.0 * g);
         const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-        double* vp = V + (size_t)p * n;
-        double* vq = V + (size_t)q * n;
         for (int i = threadIdx.x; i < n; i += JC_THREADS) {
           const double x = wp[i], y = wq[i];
           wp[i] = c * x - sn * y;
           wq[i] = sn * x + c * y;
-          const double u = vp[i], w = vq[i];
-          vp[i] = c * u - sn * w;
-          vq[i] = sn * u + c * w;
         }
       }
       grid.sync();
@@ -548,14 +544,13 @@ __global__ void dg_gershgorin_kernel(const double* __restrict__ A, long long n, 
   if (lane == 0) lo[warp] = row[warp] - s;
 }
 
-// W = A + sigma I (column-major; A symmetric), V = I.
-__global__ void dg_jacobi_init_kernel(const double* __restrict__ A, double* __restrict__ W, double* __restrict__ V,
-                                      long long n, double sigma) {
+// W = A + sigma I (column-major; A symmetric).
+__global__ void dg_jacobi_init_kernel(const double* __restrict__ A, double* __restrict__ W, long long n,
+                                      double sigma) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * n;
        q += (long long)gridDim.x * blockDim.x) {
     const long long i = q % n, j = q / n;
     W[q] = A[i * n + j] + (i == j ? sigma : 0.0);
-    V[q] = (i == j) ? 1.0 : 0.0;
   }
 }
 
@@ -571,13 +566,14 @@ __global__ void dg_colnorm_kernel(const double* __restrict__ W, long long n, dou
   if (lane == 0) nrm[warp] = sqrt(s);
 }
 
-// Y[:, c] = V[:, order[c]] for the lowest m (column-major, n rows).
-__global__ void dg_gather_kernel(const double* __restrict__ V, const int* __restrict__ order, double* __restrict__ Y,
-                                 long long n, int m) {
+// Y[:, c] = w_k / |w_k|, k = order[c], for the lowest m (column-major, n rows).
+__global__ void dg_gather_kernel(const double* __restrict__ W, const double* __restrict__ nrm,
+                                 const int* __restrict__ order, double* __restrict__ Y, long long n, int m) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * m;
        q += (long long)gridDim.x * blockDim.x) {
     const long long c = q / n, i = q % n;
-    Y[q] = V[(size_t)order[c] * n + i];
+    const int k = order[c];
+    Y[q] = W[(size_t)k * n + i] / nrm[k];
   }
 }
 
@@ -1545,22 +1541,21 @@ dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_dev
     if (!z[k]) return dg->fail(DGDFT_EINVAL, "density: z[" + std::to_string(k) + "] is NULL");
   if (!dg->assembled) return dg->fail(DGDFT_ESTATE, "density before a successful assemble");
   const size_t JJ = (size_t)J * J;
-  double *dA = nullptr, *dW = nullptr, *dV = nullptr, *dY = nullptr, *dlo = nullptr, *dnrm = nullptr,
-         *dP = nullptr, *drho = nullptr;
+  double *dA = nullptr, *dW = nullptr, *dY = nullptr, *dlo = nullptr, *dnrm = nullptr, *dP = nullptr,
+         *drho = nullptr;
   int2* dkk = nullptr;
   int *dord = nullptr, *dsweeps = nullptr;
   unsigned long long* doff = nullptr;
   constexpr int MAX_SWEEPS = 40;
   auto release = [&]() {
-    for (void* p : {(void*)dA, (void*)dW, (void*)dV, (void*)dY, (void*)dlo, (void*)dnrm, (void*)dP, (void*)drho,
-                    (void*)dkk, (void*)dord, (void*)dsweeps, (void*)doff})
+    for (void* p : {(void*)dA, (void*)dW, (void*)dY, (void*)dlo, (void*)dnrm, (void*)dP, (void*)drho, (void*)dkk,
+                    (void*)dord, (void*)dsweeps, (void*)doff})
       cudaFree(p);
   };
   std::vector<int2> kk;
   for (int k = 0; k < nel; ++k)
     for (int k2 : dg->nb[k]) kk.push_back(make_int2(k, k2));
-  if (!dmalloc(&dA, (size_t)(n * n)) || !dmalloc(&dW, (size_t)(n * n)) || !dmalloc(&dV, (size_t)(n * n)) ||
-      !dmalloc(&dY, (size_t)(n * n_occ)) || !dmalloc(&dlo, (size_t)n) || !dmalloc(&dnrm, (size_t)n) ||
+  if (!dmalloc(&dA, (size_t)(n * n)) || !dmalloc(&dW, (size_t)(n * n)) || !dmalloc(&dY, (size_t)(n * n_occ)) || !dmalloc(&dlo, (size_t)n) || !dmalloc(&dnrm, (size_t)n) ||
       !dmalloc(&dP, (size_t)nel * JJ) || !dmalloc(&dord, (size_t)n_occ) || !dmalloc(&dsweeps, 1) ||
       !dmalloc(&doff, (size_t)MAX_SWEEPS) || !upload(dg, &dkk, kk) ||
       (!on_device && !dmalloc(&drho, (size_t)nel * dg->nL))) {
@@ -1587,7 +1582,7 @@ dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_dev
     if (ok) {
       // B = A + sigma I with every eigenvalue >= 1
       const double sigma = std::max(0.0, 1.0 - *std::min_element(lo.begin(), lo.end()));
-      dg_jacobi_init_kernel<<<1024, 256, 0, dg->st>>>(dA, dW, dV, n, sigma);
+      dg_jacobi_init_kernel<<<1024, 256, 0, dg->st>>>(dA, dW, n, sigma);
       int occ = 0, nsm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dg_jacobi_kernel, JC_THREADS, 0);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dg->cfg.device);
@@ -1596,7 +1591,7 @@ dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_dev
       int nn = (int)n, maxs = MAX_SWEEPS;
       // stop at a pair cosine of sqrt(n) 1e-15 (the columns' rounding level)
       double tol = std::sqrt((double)n) * 1e-15;
-      void* args[] = {&dW, &dV, &nn, (void*)&n_pad, &maxs, &tol, &doff, &dsweeps};
+      void* args[] = {&dW, &nn, (void*)&n_pad, &maxs, &tol, &doff, &dsweeps};
       ok = cuda_ok(dg, cudaLaunchCooperativeKernel((const void*)dg_jacobi_kernel, grid, JC_THREADS, args, 0, dg->st),
                    "Jacobi eigensolver");
       dg_colnorm_kernel<<<gw, 256, 0, dg->st>>>(dW, n, dnrm);
@@ -1615,7 +1610,7 @@ dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_dev
         ok = cuda_ok(dg, cudaMemcpyAsync(dord, order.data(), sizeof(int) * n_occ, cudaMemcpyHostToDevice, dg->st),
                      "order");
         if (ok) {
-          dg_gather_kernel<<<1024, 256, 0, dg->st>>>(dV, dord, dY, n, n_occ);
+          dg_gather_kernel<<<1024, 256, 0, dg->st>>>(dW, dnrm, dord, dY, n, n_occ);
           dg_dm_kernel<<<dim3(gx, nel), 256, 0, dg->st>>>(dY, dP, J, n, n_occ);
           ok = cuda_ok(dg, cudaGetLastError(), "density matrix blocks") &&
                cuda_ok(dg, cudaStreamSynchronize(dg->st), "density matrix blocks");
