@@ -28,9 +28,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <numeric>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -1618,6 +1620,17 @@ dgdft_status dgdft_dg_density(dgdft_dg* dg, const double* const* z, int z_on_dev
       }
     }
     dg->density_sweeps = sweeps;
+    if (ok && std::getenv("DGDFT_TRACE")) {
+      std::vector<unsigned long long> h(MAX_SWEEPS);
+      cudaMemcpy(h.data(), doff, sizeof(unsigned long long) * MAX_SWEEPS, cudaMemcpyDeviceToHost);
+      std::fprintf(stderr, "[dgdft] Jacobi, largest pair cosine per sweep:");
+      for (int i = 0; i < sweeps; ++i) {
+        double v;
+        std::memcpy(&v, &h[i], sizeof(v));
+        std::fprintf(stderr, " %.1e", v);
+      }
+      std::fprintf(stderr, "\n");
+    }
     if (ok && sweeps >= MAX_SWEEPS) {
       release();
       return dg->fail(DGDFT_ENOTCONV, "density: the Jacobi sweeps did not converge");
