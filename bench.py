@@ -401,6 +401,14 @@ def run_ours(args):
         if dom == "update" and not args.tc_update:
             roof["kernel"] = "tsmm_rows (SIMT FP32 block update X' = [X W P] Y, FP32 stage)"
             roof["traffic"] = UPDATE_TRAFFIC_PER_ELEMENT * len(els)
+            # secondary: at 18 flop per byte the SIMT update is above the FP32
+            # ridge (~10 flop per byte here); useful flops of X' (with P' on
+            # the way): N_g m (3m) FMA per element
+            fp32_peak = 104 * 152 * 2.07e9 * 2 / 1e12
+            tf = sum(2.0 * e.ng * e.m * 3 * e.m for e in els) / (dom_ms / 1e3) / 1e12
+            roof["fp32_tflops"] = tf
+            roof["fp32_frac"] = tf / fp32_peak
+            roof["fp32_peak_source"] = "measured 104 FP32 FMA/clk/SM x 152 SMs x 2.07 GHz"
     # whole solve on the same basis: 20 N_g m s algorithmic bytes per
     # element-iteration (H W, Teter, Gram, updates, residual), over the
     # measured step time at the measured iteration counts
