@@ -196,6 +196,19 @@ def dg_config2(J: int = 40, alpha: float = 20.0) -> DGDomain:
                     atoms=atoms, gamma=gamma, coeffs=co, seed_key=(2, 9))
 
 
+def dg_config5(J: int = 120, alpha: float = 20.0) -> DGDomain:
+    """The 3,456-atom monolayer of the large workload (24 x 9 x 1 elements,
+    Q_K on 48 x 64 x 48 spanning 3 x 3 elements and the cell's z)."""
+    atoms, cell, gamma = _monolayer_system(5, 48, 18)
+    nq = (48, 64, 48)
+    le = cell / np.array([24, 9, 1])
+    h = le * np.array([3, 3, 1]) / np.asarray(nq)
+    ngrid = tuple(int(round(c / hh)) for c, hh in zip(cell, h))
+    co = _monolayer_coeffs(5, 48, 18, ngrid)
+    return DGDomain(cell=cell, ne=(24, 9, 1), q_span=(3, 3, 1), nq=nq, J=J, alpha=alpha,
+                    atoms=atoms, gamma=gamma, coeffs=co, seed_key=(5, 9))
+
+
 def dg_small_layer(J: int = 8, alpha: float = 20.0) -> DGDomain:
     """3 x 2 cells of the monolayer (24 atoms) cut into 3 x 3 x 1 elements;
     Q_K (3 x 3 elements) is the whole in-plane cell, on 24 x 24 x 30."""

@@ -369,3 +369,22 @@ def test_density_eigensolver_monolayer_scale():
     assert err < 1e-12
     assert abs(total - n_occ) < 1e-8 * n_occ
     d.close()
+
+
+def test_assemble_large_monolayer_row():
+    """The 3,456-atom monolayer: 216 elements, J = 120, 32 x 42 x 96 LGL
+    points (~800 MB of scratch per element, so the assembly runs in several
+    memory-capped batches).  Every element gets the same seeded columns (V_eff
+    and the projectors differ); block row 100 against the oracle."""
+    dom = sdg.dg_config5()
+    z = sdg.smooth_block(dom, 0)
+    blocks = [z] * dom.n_elem
+    d = make_dg(dom)
+    load_inputs(d, dom)
+    d.dgdft_dg_assemble(blocks)
+    timing, launches = d.dgdft_dg_last_timing()
+    print("large monolayer stage ms:", {k: round(v, 1) for k, v in timing.items() if not k.startswith("density")},
+          "launches", launches)
+    assert launches > 17  # more than one batch
+    compare_rows(d, OracleDG(dom, blocks), [100], "large monolayer")
+    d.close()
