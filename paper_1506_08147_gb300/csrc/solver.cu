@@ -138,6 +138,10 @@ struct dgdft_alb_ctx {
   // waves kept resident between solves when every element fits in one
   void* cache = nullptr;
   void (*cache_free)(void*) = nullptr;
+  // scratch of the restriction and orthonormalisation, kept between calls
+  // (grown when a call needs more)
+  void* ortho_buf = nullptr;
+  size_t ortho_cap = 0;
   std::vector<int> cache_proj_version;
   ConvNet* net = nullptr;  // learned preconditioner, created on first use
   int wait_polls = 0;      // bounded device waits: polls before giving up (0: default)
@@ -1343,11 +1347,15 @@ dgdft_status orthonormalise(dgdft_alb_ctx* ctx, Wave<double>& w, const std::vect
   const size_t npart = ortho_partial_doubles((int)nq, (int)nemax, Kmax);
   const size_t nbytes = sizeof(double) * (per * nq + nq + npart) + 2 * nq * sizeof(RRTask) +
                         4 * nq * sizeof(OrthoTask) + (10 * nq + 32) * ALIGN;
-  void* base = nullptr;
-  CK(cudaMalloc(&base, nbytes));
-  std::unique_ptr<void, decltype(&cudaFree)> guard(base, &cudaFree);
+  if (nbytes > ctx->ortho_cap) {
+    if (ctx->ortho_buf) cudaFree(ctx->ortho_buf);
+    ctx->ortho_buf = nullptr;
+    ctx->ortho_cap = 0;
+    CK(cudaMalloc(&ctx->ortho_buf, nbytes));
+    ctx->ortho_cap = nbytes;
+  }
   Arena a;
-  a.base = (char*)base;
+  a.base = (char*)ctx->ortho_buf;
   a.cap = nbytes;
   struct Slot {
     double *phit, *U, *G, *G2, *Y1, *Y2, *mats, *th, *work;
@@ -1478,17 +1486,23 @@ dgdft_status finish_wave(dgdft_alb_ctx* ctx, Wave<double>& w, int wave_idx, doub
     dgdft_status so = orthonormalise(ctx, w, idx, xs, Js, Ks, outs, rank_ok);
     if (so != DGDFT_OK) return so;
   }
+  // eigenvalues and residuals of every element to the host, one wait
+  for (size_t i = 0; i < nel; ++i) {
+    ElemHost& eh = ctx->el[w.ids[i]];
+    const ElemDev<double>& E = w.h[i];
+    eh.eig.resize(E.J);
+    eh.resid.resize(E.J);
+    CK(cudaMemcpyAsync(eh.eig.data(), E.theta, sizeof(double) * E.J, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(eh.resid.data(), E.res, sizeof(double) * E.J, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
   for (size_t i = 0; i < nel; ++i) {
     ElemHost& eh = ctx->el[w.ids[i]];
     const ElemDev<double>& E = w.h[i];
     const int* sw = &w.h_state[i * STATE_WORDS];
-    const int J = E.J, m = E.m;
+    const int m = E.m;
     const double* x = xs[i];
     const dgdft_status s = rank_ok[i] ? DGDFT_OK : DGDFT_ENOTCONV;
-    eh.eig.resize(J);
-    eh.resid.resize(J);
-    CK(ctx_copy(ctx, eh.eig.data(), E.theta, sizeof(double) * J, cudaMemcpyDeviceToHost));
-    CK(ctx_copy(ctx, eh.resid.data(), E.res, sizeof(double) * J, cudaMemcpyDeviceToHost));
     if (ctx->cfg.keep_block) {
       eh.block.resize((size_t)eh.ng() * m);
       CK(ctx_copy(ctx, eh.block.data(), x, sizeof(double) * eh.block.size(), cudaMemcpyDeviceToHost));
@@ -2009,6 +2023,7 @@ void dgdft_alb_destroy(dgdft_alb_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   ctx->drop_cache();
+  if (ctx->ortho_buf) cudaFree(ctx->ortho_buf);
   for (ElemHost& eh : ctx->el) eh.release();
   delete ctx->net;
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
