@@ -208,12 +208,15 @@ def dg_load_inputs(B, d, dom):
         d.dgdft_dg_set_projectors(k, pid, rp, idx, val)
 
 
-def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0):
+DFLOAT_PEAK_TFLOPS = 7.85 * 152 * 2.07e9 * 2 / 1e12  # measured double-float FMA/clk/SM
+
+
+def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0, dfloat=False, density=True):
     """Time the DG assembly (Eq. DGHamiltonian) of every element from the
     given device columns with CUDA events on the library's stream."""
     import torch
     d = B.DG(dom.ne, dom.cell, dom.q_span, dom.nq, dom.nl, dom.J, dom.alpha, 2 * len(dom.atoms),
-             stream=stream.cuda_stream, hbm_cap_bytes=cap_bytes)
+             stream=stream.cuda_stream, hbm_cap_bytes=cap_bytes, dfloat=dfloat)
     dg_load_inputs(B, d, dom)
     for _ in range(max(1, warmup)):
         d.dgdft_dg_assemble(blocks)
@@ -228,6 +231,25 @@ def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0):
     ms = e0.elapsed_time(e1) / steps
     stage_ms, launches = d.dgdft_dg_last_timing()
     nblk = sum(len(d.dgdft_dg_neighbours(k)) for k in range(dom.n_elem))
+    stage_ms = {k: v for k, v in stage_ms.items() if not k.startswith("density")}
+    flops = dg_flops_per_element(dom) * dom.n_elem
+    achieved = flops / (ms / 1e3) / 1e12
+    dominant = max(stage_ms, key=stage_ms.get)
+    if dfloat:
+        peak, src, kind = (DFLOAT_PEAK_TFLOPS, "double-float pairs: measured 7.85 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                           "double-float SIMT")
+    else:
+        peak, src, kind = (FP64_PEAK_TFLOPS, "FP64 pipe: measured 1.91 FMA/clk/SM x 152 SMs x 2.07 GHz", "FP64 SIMT")
+    out = {"ms_per_assembly": round(ms, 3), "elements": dom.n_elem, "J": dom.J,
+           "lgl_points": list(dom.nl), "blocks": nblk, "arith": "double-float" if dfloat else "fp64",
+           "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()}, "launches": launches,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": f"DG assembly ({kind}; dominant stage {dominant})",
+                        "peak_source": src, "algorithmic_flops": flops}}
+    if not density:
+        d.close()
+        return out
     # density by dense diagonalisation (Eq. density), half of the basis
     # occupied (a synthetic occupation), once after the timed assemblies
     n_occ = dom.n_elem * dom.J // 2
@@ -239,26 +261,15 @@ def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0):
     d1.record(stream)
     torch.cuda.synchronize()
     dens_stage, _ = d.dgdft_dg_last_timing()
-    density = {"n": dom.n_elem * dom.J, "n_occ": n_occ, "ms": round(d0.elapsed_time(d1), 2),
-               "sweeps": d.dgdft_dg_density_info(),
-               "eigensolve_ms": round(dens_stage["density_eigensolve"], 2),
-               "evaluation_ms": round(dens_stage["density_evaluation"], 2),
-               "eigensolver": "FP64 one-sided Jacobi, one cooperative kernel over all SMs"}
+    dens = {"n": dom.n_elem * dom.J, "n_occ": n_occ, "ms": round(d0.elapsed_time(d1), 2),
+            "sweeps": d.dgdft_dg_density_info(),
+            "eigensolve_ms": round(dens_stage["density_eigensolve"], 2),
+            "evaluation_ms": round(dens_stage["density_evaluation"], 2),
+            "eigensolver": "FP64 one-sided Jacobi, one cooperative kernel over all SMs"}
     del rho
     d.close()
-    stage_ms = {k: v for k, v in stage_ms.items() if not k.startswith("density")}
-    flops = dg_flops_per_element(dom) * dom.n_elem
-    achieved = flops / (ms / 1e3) / 1e12
-    dominant = max(stage_ms, key=stage_ms.get)
-    return {"ms_per_assembly": round(ms, 3), "elements": dom.n_elem, "J": dom.J,
-            "lgl_points": list(dom.nl), "blocks": nblk,
-            "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()}, "launches": launches,
-            "density": density,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": f"DG assembly (FP64 SIMT; dominant stage {dominant})",
-                         "peak_source": "FP64 pipe: measured 1.91 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                         "algorithmic_flops": flops}}
+    out["density"] = dens
+    return out
 
 
 def run_dg_only(args):
@@ -274,6 +285,8 @@ def run_dg_only(args):
     stream = torch.cuda.current_stream()
     out = dg_measure(B, dom, blocks, stream, args.steps, args.warmup, int(args.dg_cap_mb * 2 ** 20))
     out["workload"] = args.dg
+    out["dfloat_option"] = dg_measure(B, dom, blocks, stream, args.steps, args.warmup,
+                                      int(args.dg_cap_mb * 2 ** 20), dfloat=True, density=False)
     print(json.dumps({"dg_assembly": out}))
 
 
@@ -481,8 +494,10 @@ def run_ours(args):
     dg = None
     if ritz is not None:
         import synth.dg as sdg
-        dg = dg_measure(B, sdg.dg_config2(), ritz, stream, args.dg_steps, 1)
+        dom2 = sdg.dg_config2()
+        dg = dg_measure(B, dom2, ritz, stream, args.dg_steps, 1)
         dg["input"] = "the lowest J = 40 Ritz vectors of each element from the timed solve"
+        dg["dfloat_option"] = dg_measure(B, dom2, ritz, stream, args.dg_steps, 1, dfloat=True, density=False)
         del ritz
 
     # end to end through the public API from pinned host buffers

@@ -25,8 +25,9 @@
  *     (d_d u_a + d_d u_b) / 2; with one element along d the face joins the
  *     element to itself across the periodic boundary.
  *
- * Arithmetic: FP64.  All compute runs on the GPU on the stream of the
- * configuration; there is no CPU path.
+ * Arithmetic: FP64 by default, double-float pairs as an option (arith).
+ * All compute runs on the GPU on the stream of the configuration; there is
+ * no CPU path.
  */
 #ifndef DGDFT_DG_H
 #define DGDFT_DG_H
@@ -58,6 +59,14 @@ typedef struct {
   size_t hbm_cap_bytes; /* bound on the per-batch scratch (0 = a quarter of
                            the free device memory); elements are processed
                            in batches that fit it                          */
+  int arith;            /* contractions (interpolation, orthonormalisation,
+                           differentiation, Gram products): 0 = FP64;
+                           1 = double-float pairs on the FP32 pipes
+                           (~2^-48 relative per operation, ~3x faster).
+                           With nearly dependent columns (mass-matrix
+                           condition kappa) both forms lose about
+                           kappa^(1/2) of their unit in the basis's weak
+                           directions, double-float from its larger unit */
 } dgdft_dg_config;
 
 /* Validate the configuration, build the LGL, differentiation and

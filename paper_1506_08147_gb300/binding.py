@@ -50,7 +50,7 @@ class dgdft_dg_config(C.Structure):
     _fields_ = [("ne", C.c_int * 3), ("cell", C.c_double * 3), ("q_span", C.c_int * 3),
                 ("nq", C.c_int * 3), ("nl", C.c_int * 3), ("J", C.c_int), ("alpha", C.c_double),
                 ("n_proj", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
-                ("hbm_cap_bytes", C.c_size_t)]
+                ("hbm_cap_bytes", C.c_size_t), ("arith", C.c_int)]
 
 
 _P = C.c_void_p
@@ -456,7 +456,7 @@ class DG:
     entry points.  Arrays may be NumPy (host) or torch CUDA tensors."""
 
     def __init__(self, ne, cell, q_span, nq, nl, J, alpha, n_proj, stream=None, device=0,
-                 hbm_cap_bytes=0):
+                 hbm_cap_bytes=0, dfloat=False):
         self.lib = load()
         c = dgdft_dg_config()
         c.ne[:] = [int(v) for v in ne]
@@ -468,6 +468,7 @@ class DG:
         c.cuda_stream = stream
         c.device = int(device)
         c.hbm_cap_bytes = int(hbm_cap_bytes)
+        c.arith = 1 if dfloat else 0
         self.cfg = c
         self.J = int(J)
         self.nl = tuple(int(v) for v in nl)

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "../../include/dgdft_dg.h"
+#include "dfloat.cuh"
 
 namespace {
 
@@ -52,6 +53,17 @@ constexpr int GR_R = 16;                       // staged points per step
 constexpr int GR_CH = 2048;                    // points per split-K chunk
 
 constexpr double PI = 3.14159265358979323846;
+
+// Arithmetic of the contractions: FP64, or double-float pairs (FP32 h + l,
+// ~2^-48 relative per operation, on the FP32 pipes).
+using dgdft::dfl;
+__device__ __forceinline__ double to_t(double v, double*) { return v; }
+__device__ __forceinline__ dfl to_t(double v, dfl*) { return dgdft::dfl_of(v); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ dfl fma_t(dfl a, dfl b, dfl c) { return dgdft::dfl_fma(a, b, c); }
+__device__ __forceinline__ double val_t(double a) { return a; }
+__device__ __forceinline__ double val_t(dfl a) { return dgdft::dfl_val(a); }
+template <class T> __device__ __forceinline__ T zero_t() { return to_t(0.0, (T*)nullptr); }
 
 // ------------------------------------------------------------------ kernels
 
@@ -72,17 +84,17 @@ struct AxisJob {
   long long O;
 };
 
-template <bool FAST, int R>
+template <bool FAST, int R, class T>
 __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
   extern __shared__ double sm[];
   const int nin = jb.n_in, nout = jb.n_out, S = jb.S;
-  double* As = sm;
-  double* Xs = sm + nout * nin;
+  T* As = reinterpret_cast<T*>(sm);
+  T* Xs = As + nout * nin;
   const double* __restrict__ in = jb.in[blockIdx.y];
   double* __restrict__ out = jb.out[blockIdx.y];
   const double* __restrict__ A = jb.A + blockIdx.y * jb.a_stride;
   const int t = threadIdx.x;
-  for (int i = t; i < nout * nin; i += AX_THREADS) As[i] = A[i];
+  for (int i = t; i < nout * nin; i += AX_THREADS) As[i] = to_t(A[i], (T*)nullptr);
   const long long ncols_total = FAST ? jb.O : jb.O * (long long)S;
   const long long g0 = (long long)blockIdx.x * AX_TC;
   const int ncol = (int)min((long long)AX_TC, ncols_total - g0);
@@ -90,7 +102,7 @@ __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
     const double* src = in + g0 * nin;
     for (int q = t; q < ncol * nin; q += AX_THREADS) {
       const int c = q / nin, i = q - c * nin;
-      Xs[i * AX_LD + c] = src[q];
+      Xs[i * AX_LD + c] = to_t(src[q], (T*)nullptr);
     }
   } else {
     for (int q = t; q < nin * AX_TC; q += AX_THREADS) {
@@ -100,7 +112,7 @@ __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
         const long long g = g0 + c, o = g / S, s = g - o * S;
         v = in[(o * nin + i) * S + s];
       }
-      Xs[i * AX_LD + c] = v;
+      Xs[i * AX_LD + c] = to_t(v, (T*)nullptr);
     }
   }
   __syncthreads();
@@ -110,33 +122,34 @@ __global__ void __launch_bounds__(AX_THREADS) dg_axis_kernel(AxisJob jb) {
   int arow[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) arow[k] = min(r + k * AX_NR, nout - 1) * nin;
-  double acc[R];
+  T acc[R];
 #pragma unroll
-  for (int k = 0; k < R; ++k) acc[k] = 0.0;
+  for (int k = 0; k < R; ++k) acc[k] = zero_t<T>();
   for (int i = 0; i < nin; ++i) {
-    const double x = Xs[i * AX_LD + c];
+    const T x = Xs[i * AX_LD + c];
 #pragma unroll
-    for (int k = 0; k < R; ++k) acc[k] = fma(As[arow[k] + i], x, acc[k]);
+    for (int k = 0; k < R; ++k) acc[k] = fma_t(As[arow[k] + i], x, acc[k]);
   }
   if (FAST) {
     __syncthreads();
+    double* Xd = reinterpret_cast<double*>(Xs);  // the tile again, as doubles
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int row = r + k * AX_NR;
-      if (row < nout) Xs[row * AX_LD + c] = acc[k];
+      if (row < nout) Xd[row * AX_LD + c] = val_t(acc[k]);
     }
     __syncthreads();
     double* dst = out + g0 * nout;
     for (int q = t; q < ncol * nout; q += AX_THREADS) {
       const int cc = q / nout, i = q - cc * nout;
-      dst[q] = Xs[i * AX_LD + cc];
+      dst[q] = Xd[i * AX_LD + cc];
     }
   } else if (c < ncol) {
     const long long g = g0 + c, o = g / S, s = g - o * S;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int row = r + k * AX_NR;
-      if (row < nout) out[(o * nout + row) * S + s] = acc[k];
+      if (row < nout) out[(o * nout + row) * S + s] = val_t(acc[k]);
     }
   }
 }
@@ -173,63 +186,64 @@ __device__ __forceinline__ void gram_tile_of(int t, int nt, int sym, int* ti, in
   *tj = i + (t - base);
 }
 
+template <class T>
 __global__ void __launch_bounds__(256) dg_gram_kernel(const GramTask* __restrict__ tasks,
                                                       double* __restrict__ partial) {
-  __shared__ double Xs[GR_R][MAX_J + 2];
-  __shared__ double Ys[GR_R][MAX_J + 2];
-  const GramTask T = tasks[blockIdx.y];
+  __shared__ T Xs[GR_R][MAX_J + 2];
+  __shared__ T Ys[GR_R][MAX_J + 2];
+  const GramTask Tk = tasks[blockIdx.y];
   const int chunk = blockIdx.x;
-  if (chunk >= T.nchunk) return;
-  const int nti = (T.J1 + 1) / 2, ntj = (T.J2 + 1) / 2;
-  const int ntiles = T.sym ? nti * (nti + 1) / 2 : nti * ntj;
+  if (chunk >= Tk.nchunk) return;
+  const int nti = (Tk.J1 + 1) / 2, ntj = (Tk.J2 + 1) / 2;
+  const int ntiles = Tk.sym ? nti * (nti + 1) / 2 : nti * ntj;
   const int tile0 = blockIdx.z * 256;
   if (tile0 >= ntiles) return;
   const int mytile = tile0 + threadIdx.x;
   int ti = 0, tj = 0;
   const bool active = mytile < ntiles;
-  if (active) gram_tile_of(mytile, T.sym ? nti : ntj, T.sym, &ti, &tj);
+  if (active) gram_tile_of(mytile, Tk.sym ? nti : ntj, Tk.sym, &ti, &tj);
   const int i0 = 2 * ti, j0 = 2 * tj;
-  const int p0 = chunk * GR_CH, p1 = min(T.n, p0 + GR_CH);
-  double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
-  const int J1p = (T.J1 + 1) & ~1, J2p = (T.J2 + 1) & ~1;
+  const int p0 = chunk * GR_CH, p1 = min(Tk.n, p0 + GR_CH);
+  T acc00 = zero_t<T>(), acc01 = zero_t<T>(), acc10 = zero_t<T>(), acc11 = zero_t<T>();
+  const int J1p = (Tk.J1 + 1) & ~1, J2p = (Tk.J2 + 1) & ~1;
   for (int p = p0; p < p1; p += GR_R) {
     for (int q = threadIdx.x; q < GR_R * J1p; q += 256) {
       const int col = q / GR_R, rr = q - col * GR_R, pt = p + rr;
       double xv = 0.0;
-      if (pt < p1 && col < T.J1) {
-        double wt = T.w[pt];
-        if (T.v) wt *= T.v[pt];
-        xv = T.X[(size_t)col * T.ldx + pt] * wt;
+      if (pt < p1 && col < Tk.J1) {
+        double wt = Tk.w[pt];
+        if (Tk.v) wt *= Tk.v[pt];
+        xv = Tk.X[(size_t)col * Tk.ldx + pt] * wt;
       }
-      Xs[rr][col] = xv;
+      Xs[rr][col] = to_t(xv, (T*)nullptr);
     }
     for (int q = threadIdx.x; q < GR_R * J2p; q += 256) {
       const int col = q / GR_R, rr = q - col * GR_R, pt = p + rr;
-      Ys[rr][col] = (pt < p1 && col < T.J2) ? T.Y[(size_t)col * T.ldy + pt] : 0.0;
+      Ys[rr][col] = to_t((pt < p1 && col < Tk.J2) ? Tk.Y[(size_t)col * Tk.ldy + pt] : 0.0, (T*)nullptr);
     }
     __syncthreads();
     if (active) {
 #pragma unroll
       for (int rr = 0; rr < GR_R; ++rr) {
-        const double a0 = Xs[rr][i0], a1 = Xs[rr][i0 + 1];
-        const double b0 = Ys[rr][j0], b1 = Ys[rr][j0 + 1];
-        acc00 = fma(a0, b0, acc00);
-        acc01 = fma(a0, b1, acc01);
-        acc10 = fma(a1, b0, acc10);
-        acc11 = fma(a1, b1, acc11);
+        const T a0 = Xs[rr][i0], a1 = Xs[rr][i0 + 1];
+        const T b0 = Ys[rr][j0], b1 = Ys[rr][j0 + 1];
+        acc00 = fma_t(a0, b0, acc00);
+        acc01 = fma_t(a0, b1, acc01);
+        acc10 = fma_t(a1, b0, acc10);
+        acc11 = fma_t(a1, b1, acc11);
       }
     }
     __syncthreads();
   }
   if (!active) return;
-  double* dst = partial + T.part + (size_t)chunk * T.J1 * T.J2;
-  const double v[2][2] = {{acc00, acc01}, {acc10, acc11}};
+  double* dst = partial + Tk.part + (size_t)chunk * Tk.J1 * Tk.J2;
+  const double v[2][2] = {{val_t(acc00), val_t(acc01)}, {val_t(acc10), val_t(acc11)}};
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       const int ii = i0 + a, jj = j0 + b;
-      if (ii < T.J1 && jj < T.J2) dst[(size_t)ii * T.J2 + jj] = v[a][b];
+      if (ii < Tk.J1 && jj < Tk.J2) dst[(size_t)ii * Tk.J2 + jj] = v[a][b];
     }
 }
 
@@ -762,7 +776,10 @@ size_t axis_smem(int nin, int nout) {
 
 template <bool FAST, int R>
 void launch_axis_r(dgdft_dg* dg, const AxisJob& jb, unsigned tiles, int nelem, size_t sm) {
-  dg_axis_kernel<FAST, R><<<dim3(tiles, nelem), AX_THREADS, sm, dg->st>>>(jb);
+  if (dg->cfg.arith)
+    dg_axis_kernel<FAST, R, dfl><<<dim3(tiles, nelem), AX_THREADS, sm, dg->st>>>(jb);
+  else
+    dg_axis_kernel<FAST, R, double><<<dim3(tiles, nelem), AX_THREADS, sm, dg->st>>>(jb);
 }
 
 template <bool FAST>
@@ -777,21 +794,17 @@ void launch_axis_fast(dgdft_dg* dg, const AxisJob& jb, unsigned tiles, int nelem
   else launch_axis_r<FAST, 32>(dg, jb, tiles, nelem, sm);
 }
 
-template <bool FAST> bool set_axis_smem(int bytes) {
-  return cudaFuncSetAttribute(dg_axis_kernel<FAST, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(dg_axis_kernel<FAST, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(dg_axis_kernel<FAST, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(dg_axis_kernel<FAST, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(dg_axis_kernel<FAST, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(dg_axis_kernel<FAST, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(dg_axis_kernel<FAST, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+template <bool FAST, int R> bool set_smem_r(int bytes) {
+  return cudaFuncSetAttribute(dg_axis_kernel<FAST, R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(dg_axis_kernel<FAST, R, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
              cudaSuccess;
+}
+
+template <bool FAST> bool set_axis_smem(int bytes) {
+  return set_smem_r<FAST, 4>(bytes) && set_smem_r<FAST, 8>(bytes) && set_smem_r<FAST, 12>(bytes) &&
+         set_smem_r<FAST, 16>(bytes) && set_smem_r<FAST, 20>(bytes) && set_smem_r<FAST, 24>(bytes) &&
+         set_smem_r<FAST, 32>(bytes);
 }
 
 // A (n_out x n_in) along one axis of nelem arrays [O][n_in][S]; element e
@@ -842,7 +855,11 @@ bool run_grams(dgdft_dg* dg, std::vector<GramTask>& tasks) {
                     "Gram tasks");
   const int ntiles = ((maxJ1 + 1) / 2) * ((maxJ2 + 1) / 2);
   if (ok) {
-    dg_gram_kernel<<<dim3(maxc, (unsigned)h.size(), (ntiles + 255) / 256), 256, 0, dg->st>>>(d_t, dg->d_part);
+    const dim3 grid(maxc, (unsigned)h.size(), (ntiles + 255) / 256);
+    if (dg->cfg.arith)
+      dg_gram_kernel<dfl><<<grid, 256, 0, dg->st>>>(d_t, dg->d_part);
+    else
+      dg_gram_kernel<double><<<grid, 256, 0, dg->st>>>(d_t, dg->d_part);
     dg_gram_reduce_kernel<<<dim3(std::max(1, (maxJ1 * maxJ2 + 255) / 256), (unsigned)h.size()), 256, 0, dg->st>>>(
         d_t, dg->d_part);
     dg->launches += 2;
@@ -1029,6 +1046,7 @@ dgdft_status dgdft_dg_create(const dgdft_dg_config* cfg, dgdft_dg** out) {
   if (c.J < 1 || c.J > MAX_J) return dg->fail(DGDFT_EINVAL, "J out of range (1..128)");
   if (!(c.alpha >= 0.0) || !std::isfinite(c.alpha)) return dg->fail(DGDFT_EINVAL, "alpha must be >= 0");
   if (c.n_proj < 0) return dg->fail(DGDFT_EINVAL, "n_proj must be >= 0");
+  if (c.arith != 0 && c.arith != 1) return dg->fail(DGDFT_EINVAL, "arith must be 0 (FP64) or 1 (double-float)");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return dg->fail(DGDFT_ECUDA, "no CUDA device");
   if (c.device < 0 || c.device >= ndev || cudaSetDevice(c.device) != cudaSuccess)

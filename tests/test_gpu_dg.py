@@ -27,11 +27,14 @@ from paper_1506_08147_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
 
-# FP64 throughout on both sides; differences come from summation order and
-# from the two sides' own tables (LGL nodes, differentiation and
-# interpolation matrices agree to ~1e-14 relative), amplified by the mass
-# matrix's conditioning in the orthonormalisation.
+# FP64 on the oracle's side, FP64 or double-float pairs (dfloat) on the
+# GPU's; differences come from summation order, from the two sides' own
+# tables (LGL nodes, differentiation and interpolation matrices agree to
+# ~1e-14 relative) and from the pair arithmetic's ~2^-48 per operation,
+# amplified by the mass matrix's conditioning in the orthonormalisation.
 H_RTOL = 1e-9
+UNIT = {False: np.finfo(float).eps, True: 2.0 ** -44}  # rounding unit of the GPU's contractions
+ARITH = [pytest.param(False, id="fp64"), pytest.param(True, id="dfloat")]
 
 
 def make_dg(dom, **kw):
@@ -130,14 +133,15 @@ def test_lgl_basis_matches_oracle(make):
     d.close()
 
 
+@pytest.mark.parametrize("dfloat", ARITH)
 @pytest.mark.parametrize("make", [sdg.dg_small_layer, sdg.dg_small_cube])
-def test_assemble_small_domains_every_block(make):
+def test_assemble_small_domains_every_block(make, dfloat):
     dom = make()
     blocks = [sdg.smooth_block(dom, k) for k in range(dom.n_elem)]
-    d = make_dg(dom)
+    d = make_dg(dom, dfloat=dfloat)
     load_inputs(d, dom)
     d.dgdft_dg_assemble(blocks)
-    compare_rows(d, OracleDG(dom, blocks), range(dom.n_elem), f"{dom.ne}")
+    compare_rows(d, OracleDG(dom, blocks), range(dom.n_elem), f"{dom.ne} dfloat={dfloat}")
     # the assembled matrix is symmetric across block rows
     rows = {k: d.dgdft_dg_get_row(k) for k in range(dom.n_elem)}
     for k, row in rows.items():
@@ -169,7 +173,8 @@ def test_batches_and_host_device_inputs_agree():
     d2.close()
 
 
-def test_planewave_spectrum_on_gpu():
+@pytest.mark.parametrize("dfloat", ARITH)
+def test_planewave_spectrum_on_gpu(dfloat):
     """Q_K = the cell, V = 0, no projectors: the DG matrix from the lowest
     plane waves has eigenvalues 1/2 |G|^2 (complete shells)."""
     dom = sdg.dg_small_cube(J=7)
@@ -189,7 +194,7 @@ def test_planewave_spectrum_on_gpu():
         ax = [qo[d] + np.arange(dom.nq[d]) * dom.lq[d] / dom.nq[d] for d in range(3)]
         blocks.append(np.stack([np.cos(G[2] * ax[2][:, None, None] + G[1] * ax[1][None, :, None]
                                        + G[0] * ax[0][None, None, :] + ph).reshape(-1) for G, ph in waves]))
-    d = B.DG(dom.ne, dom.cell, dom.q_span, dom.nq, dom.nl, dom.J, dom.alpha, 0)
+    d = B.DG(dom.ne, dom.cell, dom.q_span, dom.nq, dom.nl, dom.J, dom.alpha, 0, dfloat=dfloat)
     d.dgdft_dg_assemble(blocks)
     n = dom.n_elem * dom.J
     H = np.zeros((n, n))
@@ -199,7 +204,7 @@ def test_planewave_spectrum_on_gpu():
     ev = np.linalg.eigvalsh(0.5 * (H + H.T))
     exact = np.sort([0.5 * float(G @ G) for G, _ in waves])
     err = np.max(np.abs(ev[:dom.J] - exact))
-    print(f"plane-wave spectrum: max error {err:.2e} Ha")
+    print(f"plane-wave spectrum (dfloat={dfloat}): max error {err:.2e} Ha")
     assert err < 1e-9
     d.close()
 
@@ -219,22 +224,24 @@ def test_zero_column_reports_enotconv():
     d.close()
 
 
-def test_assemble_monolayer_full_size_sampled_rows():
+@pytest.mark.parametrize("dfloat", ARITH)
+def test_assemble_monolayer_full_size_sampled_rows(dfloat):
     """The 576-atom monolayer: 36 elements, J = 40, 32 x 42 x 80 LGL points,
     smooth seeded columns on the 48 x 64 x 40 grids; rows 0 and 7 against the
     oracle."""
     dom = sdg.dg_config2()
     blocks = [sdg.smooth_block(dom, k) for k in range(dom.n_elem)]
-    d = make_dg(dom)
+    d = make_dg(dom, dfloat=dfloat)
     load_inputs(d, dom)
     d.dgdft_dg_assemble(blocks)
     timing, launches = d.dgdft_dg_last_timing()
     print("stage ms:", {k: round(v, 3) for k, v in timing.items()}, "launches", launches)
-    compare_rows(d, OracleDG(dom, blocks), [0, 7], "monolayer")
+    compare_rows(d, OracleDG(dom, blocks), [0, 7], f"monolayer dfloat={dfloat}")
     d.close()
 
 
-def test_assemble_from_alb_solve():
+@pytest.mark.parametrize("dfloat", ARITH)
+def test_assemble_from_alb_solve(dfloat):
     """Blocks from a real ALB solve of the 36-element workload (the lowest J
     Ritz vectors of each element) handed over on the device; rows 0 and 7
     against the oracle from the same columns."""
@@ -255,7 +262,7 @@ def test_assemble_from_alb_solve():
         ctx.dgdft_alb_get_block(k, out=x)
         dev.append(x[:dom.J * ng])
     ctx.close()
-    d = make_dg(dom)
+    d = make_dg(dom, dfloat=dfloat)
     load_inputs(d, dom)
     d.dgdft_dg_assemble(dev)
     host = [t.view(dom.J, ng).cpu().numpy() for t in dev]
@@ -264,8 +271,8 @@ def test_assemble_from_alb_solve():
     # bases (and spans) are fixed only to rounding amplified by kappa^(1/2)
     # in their weak directions, times the length of the sums (interpolation
     # over 40-64 terms per pass, quadrature over 1e5 points): the tolerance
-    # is 1e3 eps kappa_max^(1/2) relative, kappa_max over every element the
-    # two block rows touch.
+    # is 1e3 u kappa_max^(1/2) relative (u the unit of the GPU's arithmetic),
+    # kappa_max over every element the two block rows touch.
     ora = OracleDG(dom, host)
     touched = sorted({kk for k in (0, 7) for kk in odg.neighbours(dom, k)})
     kappa = 0.0
@@ -273,9 +280,9 @@ def test_assemble_from_alb_solve():
         g = ora.A.g(k)
         pt = odg.interpolate_to_lgl(dom, g, host[k])
         kappa = max(kappa, np.linalg.cond((pt * g.w) @ pt.T))
-    rtol = 1e3 * np.finfo(float).eps * np.sqrt(kappa)
+    rtol = 1e3 * UNIT[dfloat] * np.sqrt(kappa)
     print(f"max cond(mass matrix) {kappa:.2e} over {len(touched)} elements: rtol {rtol:.1e}")
-    compare_rows(d, ora, [0, 7], "monolayer ALBs", rtol)
+    compare_rows(d, ora, [0, 7], f"monolayer ALBs dfloat={dfloat}", rtol)
     compare_invariants(d, ora, [0, 7], "monolayer ALBs", rtol)
     d.close()
 
