@@ -19,6 +19,9 @@ What it computes, per extended element Q_K (Sec. II.A, Eq. localproblem):
   * the DG Hamiltonian assembled from the ALBs (Eq. DGHamiltonian): LGL
     quadrature and differentiation, trigonometric interpolation from Q_K's
     grid, the volume, KB and interior-penalty face blocks (``dg``).
+  * the sphere-cutoff planewave set (|G|^2/2 <= ecut, Eq. Ngecut's
+    cutoff): its projector and the Galerkin eigenpairs of H on its span by
+    dense diagonalisation (``cutoff``).
 
 Pins (tests/test_oracle_*.py) tie every function to closed forms, brute-force
 diagonalisation and invariants rather than to itself.  Functions whose

@@ -19,6 +19,7 @@ from .workloads import (  # noqa: F401
     config3,
     config4,
     config5,
+    cutoff_boxes,
     element_box,
     initial_block,
     random_element,

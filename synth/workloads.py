@@ -16,6 +16,9 @@ Workloads (sizes in bohr, grids x by y by z):
      J = 16 + round(80 (n_at - 4) / 36), m = 8 ceil(1.2 J / 8).
   5  monolayer 48 x 18 cells (3,456 atoms) cut into 24 x 9 elements; extended
      element on 48 x 64 x 48; 144 computed, 120 kept.
+Small boxes for the sphere-cutoff planewave set (config id 8): two standalone
+periodic boxes at spacing 0.78 on 12 x 12 x 16 and 16 x 12 x 12 points, with
+4 and 5 random atoms and their projectors, residual 1e-8 Ha.
 """
 
 from __future__ import annotations
@@ -201,3 +204,13 @@ def config3(elems=None):
         specs.append((n, n_at, J, m))
     ids = range(128) if elems is None else elems
     return [random_element(3, k, *specs[k]) for k in ids]
+
+
+CUTOFF_BOXES = (((12, 12, 16), 4, 8, 12), ((16, 12, 12), 5, 10, 16))
+
+
+def cutoff_boxes(elems=None):
+    """Two small standalone boxes (grid, atoms, J, m as in CUTOFF_BOXES)
+    whose dense Hamiltonians the sphere-cutoff oracle diagonalises."""
+    ids = range(len(CUTOFF_BOXES)) if elems is None else elems
+    return [random_element(8, k, *CUTOFF_BOXES[k], tol=1e-8) for k in ids]
