@@ -140,6 +140,22 @@ typedef struct {
                              restricted and the J left singular vectors of
                              the largest singular values kept.  Other
                              values give DGDFT_EINVAL.                      */
+  double ecut;            /* planewave set of the local problem.  0 (default):
+                             every G of the FFT grid.  > 0 (Ha): the sphere
+                             |G|^2/2 <= ecut (the kinetic-energy cutoff
+                             that Eq. Ngecut turns into the grid; with
+                             Eq. Ngecut's value (pi n_d / L_d)^2 / 2 the
+                             sphere inscribed in the grid's frequencies),
+                             solved as the Galerkin problem on the span of
+                             those planewaves: the starting block is
+                             projected onto it, residuals are measured as
+                             |P (H x - theta x)| with P that projection,
+                             and the returned vectors lie in it.  One more
+                             FFT pair per iteration.  Needs
+                             DGDFT_PREC_FP64, the Teter preconditioner and
+                             at least 3 n_compute planewaves in the set of
+                             every element; otherwise, or when negative or
+                             not finite, DGDFT_EINVAL.                     */
 } dgdft_alb_config;
 
 /* Per-element outcome of dgdft_alb_solve. */

@@ -111,6 +111,15 @@ dgdft_status dgdft_alb_restrict_orthonormalise(dgdft_alb_ctx* ctx, int elem, int
  * DGDFT_ESTATE before a solve, or when neither holds the block. */
 dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on_device);
 
+/* Projection onto the sphere-cutoff planewave set of the context
+ * (dgdft_alb_config.ecut > 0): px_i = F^-1 [ mask F x_i ], mask(G) = 1
+ * where |G|^2/2 <= ecut, else 0 (the orthogonal projector P of the solve's
+ * Galerkin problem), FP64.  x, px: N_g x k column-major, 1 <= k <=
+ * n_compute.  DGDFT_EINVAL when the context has ecut = 0, DGDFT_ESTATE
+ * before the element's potential is set. */
+dgdft_status dgdft_alb_project_cutoff(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* px,
+                                      int on_device);
+
 /* Gram product C = U^T V in FP64 that allocates nothing.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory while
  * they run (code inside a custom memory pool that must not fragment, or

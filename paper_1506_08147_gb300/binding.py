@@ -36,7 +36,7 @@ class dgdft_alb_config(C.Structure):
                 ("cuda_stream", C.c_void_p), ("device", C.c_int), ("keep_block", C.c_int),
                 ("bulk_kernels", C.c_int), ("h_fp64_forward", C.c_int),
                 ("autotune_cache", C.c_char_p), ("precond_weights", C.c_char_p),
-                ("device_wait_polls", C.c_int), ("restrict_all", C.c_int)]
+                ("device_wait_polls", C.c_int), ("restrict_all", C.c_int), ("ecut", C.c_double)]
 
 
 class dgdft_solve_report(C.Structure):
@@ -68,6 +68,7 @@ _SIGS = {
     "dgdft_alb_destroy": (None, [_P]),
     "dgdft_alb_apply_h": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dgdft_alb_apply_teter": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
+    "dgdft_alb_project_cutoff": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dgdft_alb_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "dgdft_alb_rayleigh_ritz": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P]),
     "dgdft_alb_lobpcg_gram": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, C.c_int]),
@@ -160,7 +161,7 @@ class Context:
     def __init__(self, elems, precision=DGDFT_PREC_FP64, tol=1e-6, maxit=400, check_every=4,
                  stream=None, keep_block=False, hbm_cap_bytes=0, precond=DGDFT_PRECOND_TETER,
                  precond_weights=None, simt_gram=False, h_fp64_forward=False, device_wait_polls=0,
-                 tc_update=False, restrict_all=False, autotune_cache=None):
+                 tc_update=False, restrict_all=False, autotune_cache=None, ecut=0.0):
         self.lib = load()
         cfg = dgdft_alb_config()
         self.lib.dgdft_alb_config_init(C.byref(cfg))
@@ -173,6 +174,7 @@ class Context:
         cfg.bulk_kernels = 1 if simt_gram else (2 if tc_update else 0)
         cfg.device_wait_polls = int(device_wait_polls)
         cfg.restrict_all = int(bool(restrict_all))
+        cfg.ecut = float(ecut)
         cfg.h_fp64_forward = int(h_fp64_forward)
         cfg.hbm_cap_bytes = int(hbm_cap_bytes)
         cfg.cuda_stream = stream
@@ -367,6 +369,14 @@ class Context:
         out = np.zeros_like(r)
         self._check(self.lib.dgdft_alb_apply_teter(self.h, elem, r.shape[0], _ptr(r)[0], _ptr(t)[0],
                                                    _ptr(out)[0], 0), "apply_teter")
+        return out
+
+    def dgdft_alb_project_cutoff(self, elem, x):
+        """x: (k, N_g) rows; returns P x (the context's sphere-cutoff set)."""
+        x = np.ascontiguousarray(x, np.float64)
+        out = np.zeros_like(x)
+        self._check(self.lib.dgdft_alb_project_cutoff(self.h, elem, x.shape[0], _ptr(x)[0], _ptr(out)[0], 0),
+                    "project_cutoff")
         return out
 
     def dgdft_alb_gram(self, u, v):

@@ -72,6 +72,7 @@ template <class real> struct ElemDev {
   int m, J;                 // block size, kept vectors
   double scale;             // 2 / N_g: normalisation of r2c forward + c2r inverse
   double tol;
+  double ecut;              // planewave set |G|^2/2 <= ecut (Ha); 0: every G of the grid
   FftPlan px, py, pz;       // x plan is for the half length nh
   // twiddle tables e^{-2 pi i t / n} per axis: [TW_H] n = nx/2 (t < nh),
   // [TW_X] n = nx (t <= nh, r2c post-processing), [TW_Y] n = ny, [TW_Z] n = nz;

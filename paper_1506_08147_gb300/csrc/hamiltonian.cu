@@ -157,6 +157,8 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
           const float sv = g * inv_tkf;
           const float num = 27.0f + sv * (18.0f + sv * (12.0f + sv * 8.0f));
           f = num / (num + 16.0f * sv * sv * sv * sv);
+        } else if (MODE == ZM_MASK) {
+          f = (g <= (float)e.ecut) ? 1.0f : 0.0f;
         }
         s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (TZ)(f * scalef));
       }
@@ -167,7 +169,9 @@ __global__ void z_mult_kernel(const ElemDev<real>* __restrict__ elems, int ncols
         if (c >= nplane) continue;
         const int y = udiv_small(c, mag_nxh), kx = c - y * e.nxh;
         const double g = e.gx2[kx] + e.gy2[y] + e.gz2[gz];
-        double f = (MODE == ZM_KINETIC) ? g : teter_factor(g / fmax(tk, 1e-8));
+        double f = (MODE == ZM_KINETIC) ? g
+                   : (MODE == ZM_TETER) ? teter_factor(g / fmax(tk, 1e-8))
+                                        : ((g <= e.ecut) ? 1.0 : 0.0);
         f *= e.scale;
         s[gz * ZROW + cc] = cscale(s[gz * ZROW + cc], (TZ)f);
       }
@@ -385,6 +389,15 @@ void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const do
   launch_xy_inv<real, real, real, XI_PLAIN>(b, dst, src, ncols, f, st);
 }
 
+// Sphere-cutoff projection: the grid passes of the Teter preconditioner
+// with the mask |G|^2/2 <= ecut as the multiplier (FP64 throughout; the
+// mask is decided on the same FP64 symbols as the kinetic term).
+void launch_project(const Batch<double>& b, BRef<double> src, BRef<double> dst, int ncols, cudaStream_t st) {
+  launch_xy_fwd<double, double, double>(b, src, ncols, 0, st);
+  launch_z_mult<double, double, ZM_MASK>(b, ncols, nullptr, 0, st);
+  launch_xy_inv<double, double, double, XI_PLAIN>(b, dst, src, ncols, 0, st);
+}
+
 // Allow the plane and column kernels the full opt-in shared memory once.
 template <class real> static void opt_in_smem_t() {
   opt_in_dynamic_smem((const void*)xy_fwd_kernel<real, double, double, 24, 64>);
@@ -437,6 +450,9 @@ static void opt_in_smem_dfloat() {
 
 void init_hamiltonian_kernels() {
   init_mono_kernels();
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, double, ZM_MASK, 40>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, double, ZM_MASK, 48>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, double, ZM_MASK>);
   opt_in_smem_t<double>();
   opt_in_smem_t<float>();
   opt_in_smem_dfloat();

@@ -106,6 +106,18 @@ std::vector<double> kinetic_axis(int n, double L, bool half) {
   return g;
 }
 
+// Grid frequencies of the element with |G|^2/2 <= ecut (the whole grid,
+// both halves of every axis).
+long long cutoff_set_size(const dgdft_element_desc& d, double ecut) {
+  std::vector<double> gx = kinetic_axis(d.nx, d.Lx, false);
+  const std::vector<double> gy = kinetic_axis(d.ny, d.Ly, false), gz = kinetic_axis(d.nz, d.Lz, false);
+  std::sort(gx.begin(), gx.end());
+  long long cnt = 0;
+  for (double z : gz)
+    for (double y : gy) cnt += std::upper_bound(gx.begin(), gx.end(), ecut - y - z) - gx.begin();
+  return cnt;
+}
+
 // Device arena: one allocation carved into aligned pieces.
 struct Arena {
   char* base = nullptr;
@@ -605,6 +617,7 @@ template <class real> struct Wave {
     E.J = d.n_keep;
     E.scale = 2.0 / (double)E.ng;
     E.tol = ctx->cfg.tol;
+    E.ecut = ctx->cfg.ecut;
     plan_length(E.nh, E.px);
     plan_length(d.ny, E.py);
     plan_length(d.nz, E.pz);
@@ -910,7 +923,30 @@ template <class real> struct Wave {
     if (!tc_gram(0, st)) launch_gram<real>(batch, gram12(), partial, partial_cap, st);
   }
 
+  // Sphere-cutoff planewave set (FP64 waves of a context with ecut > 0):
+  // the blocks stay in the span of the set, so the Gram products of the
+  // unprojected H equal those of the Galerkin problem.  The starting block
+  // is projected; W = T(P R) keeps the set because the Teter multiplier is
+  // diagonal in G.  X' = [X W P] Y and P' = [W P] Y_wp are projected again
+  // before their H applies: each FFT round trip leaves ~1e-16 of a column
+  // outside the set, which coefficients Y of an ill-conditioned pencil would
+  // multiply (measured: 3e-10 after 45 iterations without it) and which
+  // would reach the Ritz values through the Gram products.
+  bool cutoff() const { return std::is_same<real, double>::value && ctx->cfg.ecut > 0.0; }
+  void project_block(int sel, cudaStream_t st, int next = 0) {
+    if constexpr (std::is_same<real, double>::value)
+      launch_project(batch, bref<real>(sel, next), bref<real>(sel, next), 0, st);
+  }
+  // R (in W) -> P R, and its norm |P R| in place of |R| in the residual sums
+  void project_residual(cudaStream_t st) {
+    if constexpr (std::is_same<real, double>::value) {
+      launch_project(batch, bref<real>(BW), bref<real>(BW), 0, st);
+      launch_rnorm(batch, rnchunk, st);
+    }
+  }
+
   void enqueue_initial(cudaStream_t st) {
+    if (cutoff()) project_block(BX, st);
     launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st, fwd64());
     GramJob<real> g;
     g.npairs = 2;
@@ -947,6 +983,7 @@ template <class real> struct Wave {
   void enqueue_front(cudaStream_t st, int maxit) {
     if (batch.s.max_nproj > 0) launch_proj_coef<real>(batch, bref<real>(BX), 0, st);
     launch_residual<real>(batch, rnchunk, st);
+    if (cutoff()) project_residual(st);
     launch_post_residual<real>(batch, rnchunk, maxit, st);
     if (std::is_same<real, float>::value) launch_shift<real>(batch, st);
     precondition(st);
@@ -991,6 +1028,7 @@ template <class real> struct Wave {
       if (std::is_same<real, double>::value) {
         // FP64: H X' by the FFT (three FP64 passes cost less than the FP64
         // block update [HX HW HP] Y on the FP64 pipe)
+        if (cutoff()) project_block(BX, st, 1);
         launch_apply_h<real>(batch, bref<real>(BX, 1), bref<real>(BHX, 1), 0, st, false);
       } else {
         // FP32: HX is recomputed as H X rather than updated as [HX HW HP] Y,
@@ -1011,6 +1049,7 @@ template <class real> struct Wave {
       if (!f32) {
         launch_tsmm<real>(batch, u, st);
         // H P' by the FFT, as H X'
+        if (cutoff()) project_block(BP, st, 1);
         launch_apply_h<real>(batch, bref<real>(BP, 1), bref<real>(BHP, 1), 0, st, false);
       } else {
         u.in[0] = bref<real>(BHW);
@@ -1036,6 +1075,7 @@ template <class real> struct Wave {
     launch_theta<real>(batch, rnchunk, 1, st);
     if (batch.s.max_nproj > 0) launch_proj_coef<real>(batch, bref<real>(BX), 0, st);
     launch_residual<real>(batch, rnchunk, st);
+    if (cutoff()) project_residual(st);
     launch_post_residual<real>(batch, rnchunk, 1 << 30, st);
     CK(cudaGetLastError());
     return read_states();
@@ -1804,6 +1844,9 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   if (!(cfg->tol > 0.0) || cfg->maxit <= 0) return DGDFT_EINVAL;
   if (cfg->bulk_kernels < 0 || cfg->bulk_kernels > 2) return DGDFT_EINVAL;
   if (cfg->restrict_all != 0 && cfg->restrict_all != 1) return DGDFT_EINVAL;
+  if (!(cfg->ecut >= 0.0) || !std::isfinite(cfg->ecut)) return DGDFT_EINVAL;
+  if (cfg->ecut > 0.0 && (cfg->precision != DGDFT_PREC_FP64 || cfg->precond != DGDFT_PRECOND_TETER))
+    return DGDFT_EINVAL;
   for (int i = 0; i < n_elem; ++i) {
     const dgdft_element_desc& d = elems[i];
     FftPlan p;
@@ -1823,6 +1866,8 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
       ne *= d.e_hi[a] - d.e_lo[a];
     }
     if (ne < d.n_keep) return DGDFT_EINVAL;
+    // the LOBPCG basis [X W P] needs 3m independent planewaves in the set
+    if (cfg->ecut > 0.0 && cutoff_set_size(d, cfg->ecut) < 3ll * d.n_compute) return DGDFT_EINVAL;
   }
   std::unique_ptr<dgdft_alb_ctx> ctx(new dgdft_alb_ctx());
   ctx->cfg = *cfg;
@@ -2133,6 +2178,19 @@ dgdft_status teter_t(dgdft_alb_ctx* ctx, int elem, int k, const double* r, const
   return step_out<real>(ctx, wout, ys, n, on_device);
 }
 
+dgdft_status project_t(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* px, int on_device) {
+  Wave<double> w;
+  dgdft_status s = with_step_wave<double>(ctx, elem, w);
+  if (s != DGDFT_OK) return s;
+  const size_t n = (size_t)w.h[0].ng * k;
+  double* xs = w.h[0].blk[BW][0];
+  double* ys = w.h[0].blk[BHW][0];
+  if ((s = step_in<double>(ctx, xs, x, n, on_device)) != DGDFT_OK) return s;
+  launch_project(w.batch, bptr<double>(xs), bptr<double>(ys), k, ctx->stream);
+  CK(cudaGetLastError());
+  return step_out<double>(ctx, px, ys, n, on_device);
+}
+
 template <class real>
 dgdft_status gram_t(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, const double* v, double* c,
                     int on_device) {
@@ -2392,6 +2450,14 @@ dgdft_status dgdft_alb_apply_teter(dgdft_alb_ctx* ctx, int elem, int k, const do
     if (!(t_kin[i] > 0.0)) return DGDFT_EINVAL;
   return ctx->cfg.precision == DGDFT_PREC_FP64 ? teter_t<double>(ctx, elem, k, r, t_kin, w, on_device)
                                                 : teter_t<float>(ctx, elem, k, r, t_kin, w, on_device);
+}
+
+dgdft_status dgdft_alb_project_cutoff(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* px,
+                                      int on_device) {
+  if (!ctx || !x || !px || elem < 0 || elem >= (int)ctx->el.size()) return DGDFT_EINVAL;
+  if (k < 1 || k > ctx->el[elem].d.n_compute) return DGDFT_EINVAL;
+  if (!(ctx->cfg.ecut > 0.0)) return ctx->fail(DGDFT_EINVAL, "project_cutoff: no planewave cutoff (ecut = 0)");
+  return project_t(ctx, elem, k, x, px, on_device);
 }
 
 dgdft_status dgdft_alb_gram(dgdft_alb_ctx* ctx, int ng, int p, int q, const double* u, const double* v, double* c,

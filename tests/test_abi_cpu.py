@@ -78,6 +78,38 @@ def test_invalid_descriptors_rejected(lib, kw):
     assert lib.dgdft_alb_create(C.byref(cfg), 1, arr, C.byref(h)) == B.DGDFT_EINVAL
 
 
+@pytest.mark.parametrize("kw", [
+    dict(ecut=-1.0),                                  # negative cutoff
+    dict(ecut=float("nan")),                          # not finite
+    dict(ecut=1.0, precision=B.DGDFT_PREC_MIXED),     # the cutoff runs in FP64 only
+    dict(ecut=1.0, precond=B.DGDFT_PRECOND_LEARNED),  # and with the Teter preconditioner
+    dict(ecut=0.5),                                   # 19 planewaves < 3 m = 48
+])
+def test_invalid_cutoff_rejected(lib, kw):
+    cfg = B.dgdft_alb_config()
+    lib.dgdft_alb_config_init(C.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    arr = (B.dgdft_element_desc * 1)(_desc())
+    h = C.c_void_p()
+    assert lib.dgdft_alb_create(C.byref(cfg), 1, arr, C.byref(h)) == B.DGDFT_EINVAL
+
+
+def test_valid_cutoff_passes_validation(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    # 16^3 on a 10 bohr box: |G|^2/2 <= 1 Ha holds 57 planewaves >= 3 m = 48,
+    # so create() gets as far as the device check
+    cfg = B.dgdft_alb_config()
+    lib.dgdft_alb_config_init(C.byref(cfg))
+    cfg.ecut = 1.0
+    arr = (B.dgdft_element_desc * 1)(_desc())
+    h = C.c_void_p()
+    assert lib.dgdft_alb_create(C.byref(cfg), 1, arr, C.byref(h)) == B.DGDFT_ECUDA
+    assert lib.dgdft_alb_project_cutoff(None, 0, 1, None, None, 0) == B.DGDFT_EINVAL
+
+
 def test_no_cpu_fallback_without_device(lib):
     import torch
     if torch.cuda.is_available():
