@@ -116,3 +116,27 @@ def test_monolayer_element_cutoff():
     # Courant-Fischer: the Galerkin eigenvalues lie above the grid's (both
     # sides' Ritz values are within res^2 / gap of their eigenvalues)
     assert np.all(eig >= eig_g - 1e-8)
+
+
+def test_scf_step_stays_in_the_set(boxes):
+    """SCF-mode steps of the cutoff solve: box 0 restarts from a block with
+    out-of-set noise (the step projects it), box 1 from its resident block."""
+    ec = _ecut(boxes, 0.9)
+    ctx = _ctx(boxes, ec, 1e-8)
+    st, _ = ctx.dgdft_alb_solve()
+    assert st == B.DGDFT_OK
+    el0 = boxes[0]
+    x0 = ctx.dgdft_alb_get_block(0)
+    noise = np.random.default_rng(9).standard_normal(x0.shape)
+    ctx.dgdft_alb_set_initial(0, np.ascontiguousarray(x0 + 1e-4 * noise))
+    st, rep = ctx.dgdft_alb_scf_step(3)
+    assert st in (B.DGDFT_OK, B.DGDFT_ENOTCONV)
+    for i, el in enumerate(boxes):
+        _, eig, _ = ctx.dgdft_alb_get_basis(i)
+        x = ctx.dgdft_alb_get_block(i)[:el.J]
+        mu, _ = oc.galerkin_eigenpairs(el, ec, el.J)
+        assert np.max(np.abs(oc.project(x, el.n, el.L, ec) - x)) <= 1e-12 * np.max(np.abs(x))
+        # Ritz values of a subspace of range(P) lie above the Galerkin eigenvalues
+        assert np.all(eig >= mu - 1e-11)
+        assert np.max(eig - mu) <= (1e-4 if i == 0 else 1e-11)
+    ctx.close()
