@@ -272,6 +272,38 @@ def dg_measure(B, dom, blocks, stream, steps, warmup, cap_bytes=0, dfloat=False,
     return out
 
 
+def cutoff_measure(B, el, stream):
+    """One element solved in FP64 on the sphere |G|^2/2 <= ecut (0.91 of
+    Eq. Ngecut's value, no grid frequency on the sphere) and on the whole
+    grid, from the same start; ms per iteration from CUDA events."""
+    import torch
+
+    import synth
+    ec = 0.91 * min(0.5 * (np.pi * nd / ld) ** 2 for nd, ld in zip(el.n, el.L))
+    out = {"element": "monolayer element 0 (48x64x40, m=48, J=40), plain FP64, tol 1e-6 Ha",
+           "ecut_ha": ec}
+    for key, e in (("cutoff", ec), ("grid", 0.0)):
+        c = B.Context([B.element_dict(el)], precision=B.DGDFT_PREC_FP64, tol=el.tol, maxit=400,
+                      stream=stream.cuda_stream, ecut=e)
+        B.load_element(c, 0, el)
+        c.dgdft_alb_set_initial(0, synth.initial_block(el))
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        st, rep = c.dgdft_alb_solve()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        _, eig, res = c.dgdft_alb_get_basis(0)
+        c.close()
+        ms = t0.elapsed_time(t1)
+        out[key] = {"status": int(st), "iterations": int(rep[0]["iterations"]), "ms": round(ms, 2),
+                    "ms_per_iteration": round(ms / max(1, rep[0]["iterations"]), 3),
+                    "max_resid": float(np.max(res)), "theta_0": float(eig[0])}
+    out["per_iteration_ratio"] = out["cutoff"]["ms_per_iteration"] / out["grid"]["ms_per_iteration"]
+    return out
+
+
 def run_dg_only(args):
     """Profiling mode: the DG assembly alone on seeded smooth columns."""
     import torch
@@ -562,6 +594,16 @@ def run_ours(args):
                                                "one-iteration warm-up step"}
         c64.close()
 
+    # sphere-cutoff planewave set (FP64 option): one monolayer element solved
+    # with ecut = 0.91 of Eq. Ngecut's value and on the whole grid, each timed
+    # with CUDA events on the library's stream
+    cutoff = None
+    if args.cutoff and rank == 0 and world == 1 and args.config == 2:
+        try:
+            cutoff = cutoff_measure(B, els[0], stream)
+        except Exception as exc:  # reported in the line, never fatal to it
+            cutoff = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         cpu = cpu_baseline(els[0], args.cpu_seconds)
@@ -590,6 +632,7 @@ def run_ours(args):
         "iterations_max": int(max(iters)) if iters else None,
         "roofline": roof, "step_roofline": step_roof, "stages": stage_report, "scf_step": scf,
         "dg_assembly": dg,
+        "cutoff_variant": cutoff,
         "plain_fp64": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
         "cpu_baseline": cpu,
@@ -750,6 +793,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--scf-steps", type=int, default=4, help="timed SCF-mode steps (0: skip)")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--no-cutoff", dest="cutoff", action="store_false",
+                    help="skip the sphere-cutoff variant's timing")
     ap.add_argument("--only-stage", default=None,
                     choices=["xy_fwd", "z_mult", "xy_inv", "gram", "update", "rayleigh_ritz", "residual"],
                     help="profiling mode: after the warm-up solves, launch one stage --stage-reps times and exit")
