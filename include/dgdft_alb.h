@@ -150,12 +150,18 @@ typedef struct {
                              those planewaves: the starting block is
                              projected onto it, residuals are measured as
                              |P (H x - theta x)| with P that projection,
-                             and the returned vectors lie in it.  One more
-                             FFT pair per iteration.  Needs
-                             DGDFT_PREC_FP64, the Teter preconditioner and
-                             at least 3 n_compute planewaves in the set of
-                             every element; otherwise, or when negative or
-                             not finite, DGDFT_EINVAL.                     */
+                             and the returned vectors lie in it.  Three
+                             more FFT round trips per iteration (R, X', P'
+                             projected).  In DGDFT_PREC_MIXED the FP32
+                             stage decides the mask in FP32 (a frequency
+                             within FP32 rounding of the sphere may be
+                             decided differently there) and the FP64 check
+                             and iterations project with the FP64 decision,
+                             which fixes the result.  Needs the Teter
+                             preconditioner and at least 3 n_compute
+                             planewaves in the set of every element;
+                             otherwise, or when negative or not finite,
+                             DGDFT_EINVAL.                                 */
 } dgdft_alb_config;
 
 /* Per-element outcome of dgdft_alb_solve. */

@@ -114,7 +114,8 @@ dgdft_status dgdft_alb_get_block(dgdft_alb_ctx* ctx, int elem, double* x, int on
 /* Projection onto the sphere-cutoff planewave set of the context
  * (dgdft_alb_config.ecut > 0): px_i = F^-1 [ mask F x_i ], mask(G) = 1
  * where |G|^2/2 <= ecut, else 0 (the orthogonal projector P of the solve's
- * Galerkin problem), FP64.  x, px: N_g x k column-major, 1 <= k <=
+ * Galerkin problem), with the FP64 stage's passes (FP64; double-float,
+ * ~2^-44 relative, in DGDFT_PREC_MIXED).  x, px: N_g x k column-major, 1 <= k <=
  * n_compute.  DGDFT_EINVAL when the context has ecut = 0, DGDFT_ESTATE
  * before the element's potential is set. */
 dgdft_status dgdft_alb_project_cutoff(dgdft_alb_ctx* ctx, int elem, int k, const double* x, double* px,

@@ -906,26 +906,28 @@ __global__ void __launch_bounds__(256) residual_kernel(const ElemDev<real>* __re
 
 // r.r of the W block per chunk of the residual kernel (same chunks, same
 // grid), overwriting that kernel's first partial sum: the residual norm of
-// the sphere-cutoff set is |P R|, taken after W = R was projected.
-__global__ void __launch_bounds__(256) rnorm_kernel(const ElemDev<double>* __restrict__ elems, int nchunk) {
-  const ElemDev<double>& e = elems[blockIdx.z];
+// the sphere-cutoff set is |P R|, taken after W = R was projected.  Sums in
+// the working precision within a CTA (as the residual kernel), FP64 across.
+template <class real>
+__global__ void __launch_bounds__(256) rnorm_kernel(const ElemDev<real>* __restrict__ elems, int nchunk) {
+  const ElemDev<real>& e = elems[blockIdx.z];
   if (!e.state[ST_ACTIVE]) return;
   const int j = blockIdx.y;
   if (j >= e.m) return;
   const int kc = (((e.ng + nchunk - 1) / nchunk) + 3) & ~3;
   const int beg = blockIdx.x * kc, end = min(e.ng, beg + kc);
-  const double* R = e.blk[BW][0] + (size_t)j * e.ng;
-  double s = 0.0;
+  const real* R = e.blk[BW][0] + (size_t)j * e.ng;
+  real s = 0;
   for (int i = beg + threadIdx.x; i < end; i += blockDim.x) s += R[i] * R[i];
-  __shared__ double red[8];
+  __shared__ real red[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   s = warp_sum(s);
   if (lane == 0) red[warp] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double v = 0.0;
+    real v = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
-    e.rpart[((size_t)j * nchunk + blockIdx.x) * 4] = v;
+    e.rpart[((size_t)j * nchunk + blockIdx.x) * 4] = (double)v;
   }
 }
 
@@ -1159,7 +1161,10 @@ void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStrea
 }
 
 void launch_rnorm(const Batch<double>& b, int nchunk, cudaStream_t st) {
-  rnorm_kernel<<<dim3(nchunk, b.s.max_m, b.s.nel), 256, 0, st>>>(b.d_elems, nchunk);
+  rnorm_kernel<double><<<dim3(nchunk, b.s.max_m, b.s.nel), 256, 0, st>>>(b.d_elems, nchunk);
+}
+void launch_rnorm(const Batch<float>& b, int nchunk, cudaStream_t st) {
+  rnorm_kernel<float><<<dim3(nchunk, b.s.max_m, b.s.nel), 256, 0, st>>>(b.d_elems, nchunk);
 }
 
 template <class real>

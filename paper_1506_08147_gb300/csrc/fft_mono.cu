@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(ZTHREADS)
   rfft<NZ, false>(v);
   const float gxy = e.gx2f[kx] + e.gy2f[y];
   const float scalef = (float)e.scale;
+  const float ecutf = (float)e.ecut;  // mask of the sphere-cutoff set (FP32 decision)
   float inv_tk = 1.f;
   if (MODE == ZM_TETER) {
     // FP32 reciprocal: one FP64 division per thread costs ~16 FP64-pipe
@@ -277,6 +278,8 @@ __global__ void __launch_bounds__(ZTHREADS)
       const float sv = g * inv_tk;
       const float num = 27.0f + sv * (18.0f + sv * (12.0f + sv * 8.0f));
       f = num / (num + 16.0f * sv * sv * sv * sv);
+    } else if (MODE == ZM_MASK) {
+      f = (g <= ecutf) ? 1.0f : 0.0f;
     }
     v[z] = cscale(v[z], f * scalef);
   }
@@ -450,11 +453,15 @@ void mono_z(const Batch<float>& b, int mode, int ncols, const double* tkin_overr
   if (s.uni_nz == 40) {
     if (mode == ZM_TETER)
       mono_z_kernel<40, ZM_TETER><<<g, ZTHREADS, 0, st>>>(b.d_elems, ncols, tkin_override, filt);
+    else if (mode == ZM_MASK)
+      mono_z_kernel<40, ZM_MASK><<<g, ZTHREADS, 0, st>>>(b.d_elems, ncols, tkin_override, filt);
     else
       mono_z_kernel<40, ZM_KINETIC><<<g, ZTHREADS, 0, st>>>(b.d_elems, ncols, tkin_override, filt);
   } else {
     if (mode == ZM_TETER)
       mono_z_kernel<48, ZM_TETER><<<g, ZTHREADS, 0, st>>>(b.d_elems, ncols, tkin_override, filt);
+    else if (mode == ZM_MASK)
+      mono_z_kernel<48, ZM_MASK><<<g, ZTHREADS, 0, st>>>(b.d_elems, ncols, tkin_override, filt);
     else
       mono_z_kernel<48, ZM_KINETIC><<<g, ZTHREADS, 0, st>>>(b.d_elems, ncols, tkin_override, filt);
   }

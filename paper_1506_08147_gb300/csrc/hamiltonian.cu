@@ -390,12 +390,28 @@ void launch_teter(const Batch<real>& b, BRef<real> src, BRef<real> dst, const do
 }
 
 // Sphere-cutoff projection: the grid passes of the Teter preconditioner
-// with the mask |G|^2/2 <= ecut as the multiplier (FP64 throughout; the
-// mask is decided on the same FP64 symbols as the kinetic term).
+// with the mask |G|^2/2 <= ecut as the multiplier.  FP64 vectors: FP64
+// passes, or double-float passes in the mixed form's FP64 waves; the mask is
+// decided on the FP64 symbols of the kinetic term, in the same order.
 void launch_project(const Batch<double>& b, BRef<double> src, BRef<double> dst, int ncols, cudaStream_t st) {
+  if (b.s.dfloat) {
+    launch_xy_fwd<double, dff, dff>(b, src, ncols, 0, st);
+    launch_z_mult<double, dff, ZM_MASK>(b, ncols, nullptr, 0, st);
+    launch_xy_inv<double, dff, dff, XI_PLAIN>(b, dst, src, ncols, 0, st);
+    return;
+  }
   launch_xy_fwd<double, double, double>(b, src, ncols, 0, st);
   launch_z_mult<double, double, ZM_MASK>(b, ncols, nullptr, 0, st);
   launch_xy_inv<double, double, double, XI_PLAIN>(b, dst, src, ncols, 0, st);
+}
+// FP32 vectors (the mixed form's FP32 stage): FP32 passes (the register-
+// resident ones on the monolayer grids), the mask decided on the FP32
+// symbols; a frequency within FP32 rounding of the sphere may be decided
+// differently from the FP64 stage, whose projections decide the result.
+void launch_project(const Batch<float>& b, BRef<float> src, BRef<float> dst, int ncols, cudaStream_t st) {
+  launch_xy_fwd<float, float, float>(b, src, ncols, 0, st);
+  launch_z_mult<float, float, ZM_MASK>(b, ncols, nullptr, 0, st);
+  launch_xy_inv<float, float, float, XI_PLAIN>(b, dst, src, ncols, 0, st);
 }
 
 // Allow the plane and column kernels the full opt-in shared memory once.
@@ -453,6 +469,12 @@ void init_hamiltonian_kernels() {
   opt_in_dynamic_smem((const void*)z_mult_kernel<double, double, ZM_MASK, 40>);
   opt_in_dynamic_smem((const void*)z_mult_kernel<double, double, ZM_MASK, 48>);
   opt_in_dynamic_smem((const void*)z_mult_kernel<double, double, ZM_MASK>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_MASK, 40>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_MASK, 48>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<double, dff, ZM_MASK>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<float, float, ZM_MASK, 40>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<float, float, ZM_MASK, 48>);
+  opt_in_dynamic_smem((const void*)z_mult_kernel<float, float, ZM_MASK>);
   opt_in_smem_t<double>();
   opt_in_smem_t<float>();
   opt_in_smem_dfloat();

@@ -54,8 +54,9 @@ enum { XI_HAMILTONIAN = 0, XI_PLAIN = 1 };
 
 // hamiltonian.cu
 // Orthogonal projection onto the span of the planewaves with |G|^2/2 <=
-// ecut (each element's own ecut), FP64 vectors: dst = F^-1 mask F src.
+// ecut (each element's own ecut): dst = F^-1 mask F src.
 void launch_project(const Batch<double>& b, BRef<double> src, BRef<double> dst, int ncols, cudaStream_t st);
+void launch_project(const Batch<float>& b, BRef<float> src, BRef<float> dst, int ncols, cudaStream_t st);
 template <class real>
 void launch_apply_h(const Batch<real>& b, BRef<real> src, BRef<real> dst, int ncols, cudaStream_t st,
                     bool fwd64 = false);
@@ -133,9 +134,10 @@ void launch_residual(const Batch<real>& b, int nchunk, cudaStream_t st);
 // convergence and iteration bookkeeping.
 template <class real>
 void launch_post_residual(const Batch<real>& b, int nchunk, int maxit, cudaStream_t st);
-// r.r partial sums of the W block (FP64 vectors) in the residual kernel's
-// chunks, replacing that kernel's first sum: after W = P R was projected.
+// r.r partial sums of the W block in the residual kernel's chunks,
+// replacing that kernel's first sum: after W = P R was projected.
 void launch_rnorm(const Batch<double>& b, int nchunk, cudaStream_t st);
+void launch_rnorm(const Batch<float>& b, int nchunk, cudaStream_t st);
 // End of an iteration: flip the X/P/HX/HP buffers, mark P valid.
 template <class real>
 void launch_restart(const Batch<real>& b, cudaStream_t st);

@@ -923,26 +923,26 @@ template <class real> struct Wave {
     if (!tc_gram(0, st)) launch_gram<real>(batch, gram12(), partial, partial_cap, st);
   }
 
-  // Sphere-cutoff planewave set (FP64 waves of a context with ecut > 0):
-  // the blocks stay in the span of the set, so the Gram products of the
-  // unprojected H equal those of the Galerkin problem.  The starting block
-  // is projected; W = T(P R) keeps the set because the Teter multiplier is
-  // diagonal in G.  X' = [X W P] Y and P' = [W P] Y_wp are projected again
-  // before their H applies: each FFT round trip leaves ~1e-16 of a column
-  // outside the set, which coefficients Y of an ill-conditioned pencil would
-  // multiply (measured: 3e-10 after 45 iterations without it) and which
-  // would reach the Ritz values through the Gram products.
-  bool cutoff() const { return std::is_same<real, double>::value && ctx->cfg.ecut > 0.0; }
+  // Sphere-cutoff planewave set (a context with ecut > 0): the blocks stay
+  // in the span of the set, so the Gram products of the unprojected H equal
+  // those of the Galerkin problem.  The starting block is projected; W =
+  // T(P R) keeps the set because the Teter multiplier is diagonal in G.
+  // X' = [X W P] Y and P' = [W P] Y_wp are projected again before their H
+  // applies: each FFT round trip leaves a rounding's worth of a column
+  // outside the set (~1e-16 in FP64), which coefficients Y of an
+  // ill-conditioned pencil would multiply (measured: 3e-10 after 45 FP64
+  // iterations without it) and which would reach the Ritz values through the
+  // Gram products.  In the FP32 stage HP' stays the update [HW HP] Y_wp, so
+  // it differs from H of the projected P' by H of the removed part, the size
+  // of that update's own FP32 rounding.
+  bool cutoff() const { return ctx->cfg.ecut > 0.0; }
   void project_block(int sel, cudaStream_t st, int next = 0) {
-    if constexpr (std::is_same<real, double>::value)
-      launch_project(batch, bref<real>(sel, next), bref<real>(sel, next), 0, st);
+    launch_project(batch, bref<real>(sel, next), bref<real>(sel, next), 0, st);
   }
   // R (in W) -> P R, and its norm |P R| in place of |R| in the residual sums
   void project_residual(cudaStream_t st) {
-    if constexpr (std::is_same<real, double>::value) {
-      launch_project(batch, bref<real>(BW), bref<real>(BW), 0, st);
-      launch_rnorm(batch, rnchunk, st);
-    }
+    launch_project(batch, bref<real>(BW), bref<real>(BW), 0, st);
+    launch_rnorm(batch, rnchunk, st);
   }
 
   void enqueue_initial(cudaStream_t st) {
@@ -1036,6 +1036,10 @@ template <class real> struct Wave {
         // and would leave HX inconsistent with X (the residual then stalls or
         // diverges near 1e-4 Ha)
         if (restart_max > 0) launch_restart<real>(batch, st);
+        if (cutoff()) {
+          project_block(BX, st, 1);
+          project_block(BP, st, 1);
+        }
         launch_apply_h<real>(batch, bref<real>(BX, 1), bref<real>(BHX, 1), 0, st, fwd64() || hx64);
       }
       TsmmJob<real> u;
@@ -1069,6 +1073,8 @@ template <class real> struct Wave {
     cudaStream_t st = ctx->stream;
     dgdft_status s = reset_states(tol);
     if (s != DGDFT_OK) return s;
+    // the FP32 stage's block, projected by the FP64 stage's mask
+    if (cutoff()) project_block(BX, st);
     launch_apply_h<real>(batch, bref<real>(BX), bref<real>(BHX), 0, st, fwd64());
     launch_theta<real>(batch, rnchunk, 0, st);
     launch_residual<real>(batch, rnchunk, st);
@@ -1845,8 +1851,7 @@ dgdft_status dgdft_alb_create(const dgdft_alb_config* cfg, int n_elem, const dgd
   if (cfg->bulk_kernels < 0 || cfg->bulk_kernels > 2) return DGDFT_EINVAL;
   if (cfg->restrict_all != 0 && cfg->restrict_all != 1) return DGDFT_EINVAL;
   if (!(cfg->ecut >= 0.0) || !std::isfinite(cfg->ecut)) return DGDFT_EINVAL;
-  if (cfg->ecut > 0.0 && (cfg->precision != DGDFT_PREC_FP64 || cfg->precond != DGDFT_PRECOND_TETER))
-    return DGDFT_EINVAL;
+  if (cfg->ecut > 0.0 && cfg->precond != DGDFT_PRECOND_TETER) return DGDFT_EINVAL;
   for (int i = 0; i < n_elem; ++i) {
     const dgdft_element_desc& d = elems[i];
     FftPlan p;

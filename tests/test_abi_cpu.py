@@ -81,8 +81,7 @@ def test_invalid_descriptors_rejected(lib, kw):
 @pytest.mark.parametrize("kw", [
     dict(ecut=-1.0),                                  # negative cutoff
     dict(ecut=float("nan")),                          # not finite
-    dict(ecut=1.0, precision=B.DGDFT_PREC_MIXED),     # the cutoff runs in FP64 only
-    dict(ecut=1.0, precond=B.DGDFT_PRECOND_LEARNED),  # and with the Teter preconditioner
+    dict(ecut=1.0, precond=B.DGDFT_PRECOND_LEARNED),  # the cutoff needs the Teter preconditioner
     dict(ecut=0.5),                                   # 19 planewaves < 3 m = 48
 ])
 def test_invalid_cutoff_rejected(lib, kw):

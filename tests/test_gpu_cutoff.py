@@ -8,7 +8,9 @@ oracle's eigenvectors within the Davis-Kahan bound.  On one monolayer element
 (48 x 64 x 40, the transforms specialised for that grid): the projection
 step against the oracle, and a solve whose vectors lie in the set, whose
 projected residuals meet the tolerance and whose Ritz values lie above the
-grid problem's (Courant-Fischer).  Sizes of the set are chosen with no
+grid problem's (Courant-Fischer).  The chosen mixed form (FP32 stage with its
+FP32 mask, FP64 check and iterations) on both: against the oracle, and on
+the monolayer element against the FP64 cutoff solve.  Sizes of the set are chosen with no
 frequency on the sphere, so membership is never a rounding decision.
 """
 
@@ -31,8 +33,8 @@ def _ecut(els, frac):
     return ec
 
 
-def _ctx(els, ec, tol, **kw):
-    ctx = B.Context([B.element_dict(e) for e in els], precision=B.DGDFT_PREC_FP64, tol=tol, maxit=800,
+def _ctx(els, ec, tol, precision=B.DGDFT_PREC_FP64, **kw):
+    ctx = B.Context([B.element_dict(e) for e in els], precision=precision, tol=tol, maxit=800,
                     keep_block=True, ecut=ec, **kw)
     for i, e in enumerate(els):
         B.load_element(ctx, i, e, synth.initial_block(e))
@@ -140,3 +142,48 @@ def test_scf_step_stays_in_the_set(boxes):
         assert np.all(eig >= mu - 1e-11)
         assert np.max(eig - mu) <= (1e-4 if i == 0 else 1e-11)
     ctx.close()
+
+
+def test_mixed_form_small_boxes(boxes):
+    ec = _ecut(boxes, 0.9)
+    ctx = _ctx(boxes, ec, 1e-6, precision=B.DGDFT_PREC_MIXED)
+    st, rep = ctx.dgdft_alb_solve()
+    assert st == B.DGDFT_OK, rep
+    for i, el in enumerate(boxes):
+        J = el.J
+        phi, eig, res = ctx.dgdft_alb_get_basis(i)
+        x = ctx.dgdft_alb_get_block(i)[:J]
+        mu, _ = oc.galerkin_eigenpairs(el, ec, J)
+        print(f"mixed, box {i}: iterations {rep[i]['iterations']} (FP32 {rep[i]['iterations_bulk']}), "
+              f"max |theta - oracle| {np.max(np.abs(eig - mu)):.2e}")
+        assert np.max(res) <= 1e-6
+        assert np.max(np.abs(eig - mu)) <= 1e-9
+        assert np.max(np.abs(oc.project(x, el.n, el.L, ec) - x)) <= 1e-12 * np.max(np.abs(x))
+        r = oc.project(H.apply_h(x, el) - eig[:, None] * x, el.n, el.L, ec)
+        assert np.max(np.linalg.norm(r, axis=1) / np.linalg.norm(x, axis=1)) <= 1.05e-6
+        assert OA.sin_max_angle(phi, OA.restrict(x, el, J)) <= 1e-10
+    ctx.close()
+
+
+def test_mixed_form_monolayer_element():
+    el = synth.config2(elems=[0])[0]
+    ec = _ecut([el], 0.91)
+    out = {}
+    for name, prec in (("fp64", B.DGDFT_PREC_FP64), ("mixed", B.DGDFT_PREC_MIXED)):
+        ctx = _ctx([el], ec, el.tol, precision=prec)
+        st, rep = ctx.dgdft_alb_solve()
+        assert st == B.DGDFT_OK, rep
+        _, eig, res = ctx.dgdft_alb_get_basis(0)
+        out[name] = (eig, res, ctx.dgdft_alb_get_block(0)[:el.J], rep[0])
+        ctx.close()
+    eig, res, x, rep = out["mixed"]
+    print(f"mixed, monolayer element with the cutoff: {rep['iterations']} iterations "
+          f"(FP32 {rep['iterations_bulk']}) in {rep['seconds']:.3f} s; FP64: {out['fp64'][3]['iterations']} "
+          f"in {out['fp64'][3]['seconds']:.3f} s; max |theta_mixed - theta_fp64| "
+          f"{np.max(np.abs(eig - out['fp64'][0])):.2e}")
+    assert np.max(res) <= el.tol
+    assert np.max(np.abs(eig - out["fp64"][0])) <= 1e-8
+    assert np.max(np.abs(oc.project(x, el.n, el.L, ec) - x)) <= 1e-12 * np.max(np.abs(x))
+    r = oc.project(H.apply_h(x, el) - eig[:, None] * x, el.n, el.L, ec)
+    assert np.max(np.linalg.norm(r, axis=1) / np.linalg.norm(x, axis=1)) <= 1.05 * el.tol
+
