@@ -109,6 +109,25 @@ def test_valid_cutoff_passes_validation(lib):
     assert lib.dgdft_alb_project_cutoff(None, 0, 1, None, None, 0) == B.DGDFT_EINVAL
 
 
+@pytest.mark.parametrize("ecut", [0.7, 1.0, 1.9])
+def test_cutoff_set_size_matches_oracle(lib, ecut):
+    """The library's count of planewaves in the sphere, seen through create()'s
+    3 m check, equals the oracle mask's count: m = count / 3 passes
+    validation, one more column is rejected."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from oracle import cutoff as oc
+    count = int(oc.cutoff_mask((16, 16, 16), (10.0, 10.0, 10.0), ecut).sum())
+    for m, want in ((count // 3, B.DGDFT_ECUDA), (count // 3 + 1, B.DGDFT_EINVAL)):
+        cfg = B.dgdft_alb_config()
+        lib.dgdft_alb_config_init(C.byref(cfg))
+        cfg.ecut = ecut
+        arr = (B.dgdft_element_desc * 1)(_desc(mj=(m, 1)))
+        h = C.c_void_p()
+        assert lib.dgdft_alb_create(C.byref(cfg), 1, arr, C.byref(h)) == want, (ecut, count, m)
+
+
 def test_no_cpu_fallback_without_device(lib):
     import torch
     if torch.cuda.is_available():
