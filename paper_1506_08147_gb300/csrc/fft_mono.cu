@@ -12,7 +12,8 @@
 //         complex), then the 64-point y lines as an 8 x 8 four-step transform
 //         inside a warp (8 lanes per line, __syncwarp only);
 //   z   : one thread per (kx, y) column: 40- or 48-point FFT in registers,
-//         the kinetic symbol (or the Teter factor), inverse FFT;
+//         the kinetic symbol (or the Teter factor, or the sphere-cutoff
+//         mask), inverse FFT;
 //   inv : the inverse y lines, then per row the c2r recombination and the
 //         24-point inverse in registers, then the epilogue (Kleinman-Bylander
 //         scatter, (V - sigma) psi) on the plane in shared memory.

@@ -9,7 +9,9 @@
 //   xy_fwd : per (plane z, vector j): real plane -> r2c along x (as a complex
 //            FFT of length nx/2 plus an even/odd split) -> FFT along y;
 //   z_mult : per (tile of (y, kx) columns, vector j): FFT along z, multiply by
-//            the kinetic symbol |G|^2/2 (or the Teter factor), inverse FFT;
+//            the kinetic symbol |G|^2/2 (or the Teter factor, or the mask of
+//            the sphere |G|^2/2 <= ecut for the cutoff's projection), inverse
+//            FFT;
 //   xy_inv : inverse y, c2r along x, fused epilogue adding V_eff psi and the
 //            projector scatter for the points of plane z.
 #include <type_traits>
