@@ -133,3 +133,20 @@ def test_interlacing_and_monotone_in_ecut():
     # the sphere changes the problem: inside Eq. Ngecut's sphere the
     # eigenvalues lie measurably above the grid's
     assert gaps[0.9] > 1e-6
+
+
+def test_teter_keeps_the_set():
+    """The Galerkin iteration relies on the Teter multiplier being diagonal in
+    G: T(P r) lies in the set, so W = T(P R) needs no projection of its own."""
+    from oracle import teter
+    el = _box0()
+    ec = _ecut(el)
+    gen = np.random.default_rng(11)
+    r = gen.standard_normal((4, el.ng))
+    x = gen.standard_normal((4, el.ng))
+    w = teter.precondition(oc.project(r, el.n, el.L, ec), x, el.n, el.L)
+    assert np.max(np.abs(oc.project(w, el.n, el.L, ec) - w)) < 1e-12 * np.max(np.abs(w))
+    # and T commutes with P
+    tp = teter.precondition(oc.project(r, el.n, el.L, ec), x, el.n, el.L)
+    pt = oc.project(teter.precondition(r, x, el.n, el.L), el.n, el.L, ec)
+    assert np.max(np.abs(tp - pt)) < 1e-12 * np.max(np.abs(pt))
