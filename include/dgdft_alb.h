@@ -8,8 +8,9 @@
  *
  *     (-1/2 Lap + V_eff^{Q_K} + V_nl^{Q_K}) phi~_{K,j} = lambda_{K,j} phi~_{K,j},
  *
- * discretised by planewaves on a uniform periodic grid (grid rule Eq. Ngecut),
- * by LOBPCG (Sec. II.B, operations 1-5) for the lowest n_compute (m)
+ * discretised by planewaves on a uniform periodic grid (grid rule Eq. Ngecut;
+ * every G of the grid, or the sphere |G|^2/2 <= ecut, see
+ * dgdft_alb_config.ecut), by LOBPCG (Sec. II.B, operations 1-5) for the lowest n_compute (m)
  * eigenpairs; restrict the lowest n_keep (J) eigenvectors to E_K,
  * orthonormalise them (so that the ALB overlap matrix is the identity,
  * Eq. orthonormal) and return them on E_K's grid points (zero elsewhere).
